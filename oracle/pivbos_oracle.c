@@ -1,0 +1,646 @@
+/*
+ * pivbos oracle -- TEST INFRASTRUCTURE, not the product.
+ *
+ * A plain, slow, serial-per-ray FP64 restatement of the image generator of
+ * Rajendran, Bane & Vlachos, "PIV/BOS Synthetic Image Generation in Variable
+ * Density Environments" (arXiv 1812.05902).  It exists only so that the CUDA
+ * library can be checked against something written independently from the
+ * paper.  Only tests/, __graft_entry__.smoke() and the cpu_baseline leg of
+ * bench.py may load it.  It shares no source with the CUDA path (its own
+ * Philox, its own field preparation, its own optics).
+ *
+ * Stage map (paper Section 3, Fig. 2):
+ *   om_philox4x64 / om_lens_point ....... Sec. 3.1 (light field generation)
+ *   om_medium_build / om_sample ......... Sec. 3.2, Eq. 1 (Gladstone-Dale),
+ *                                         Eq. 6 (gradient of n on the grid)
+ *   om_trace (integration part) ......... Sec. 3.2, Eqs. 2-6 (Sharma RK4) and
+ *                                         the first-order scheme of Sec. 3.2
+ *   om_trace (optics part) .............. Sec. 3.3, Eq. 7 (Snell), apertures
+ *   om_trace (sensor) / om_deposit ...... Sec. 3.4, Eq. 8 (diffraction spot)
+ *
+ * Readings where the paper is silent (box faces, final step, windows,
+ * quantisation, ideal lens) are documented at each function.
+ *
+ * Parity status: every function here is pinned by tests/test_oracle_*.py
+ * against closed forms, library routines or brute force, except where a
+ * comment says "parity unpinned".
+ *
+ * Build: gcc -O2 -std=c11 -fopenmp -ffp-contract=off -shared -fPIC
+ * (-ffp-contract=off so that x86 and Arm give the same FP64 results.)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OM_MAX_SURF 16
+
+/* ray status codes (same numbering as the public header, written out here
+ * independently) */
+enum {
+    OM_REACHED = 0,
+    OM_KILLED_STOP = 1,      /* blocked by an aperture (Sec. 3.3, item 3) */
+    OM_KILLED_MISS = 2,      /* missed a surface or its clear aperture */
+    OM_KILLED_TIR = 3,       /* total internal reflection (Sec. 3.3, item 2) */
+    OM_KILLED_OFF_SENSOR = 4,/* hit the sensor plane outside the pixel array */
+    OM_KILLED_MAXSTEP = 5    /* integration step budget exhausted */
+};
+
+enum { OM_SURF_SPHERE = 0, OM_SURF_PLANE = 1, OM_SURF_IDEAL_THIN = 2, OM_SURF_STOP = 3 };
+enum { OM_EULER = 0, OM_RK4 = 1 };
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11).  Sec. 3.1 draws one lens point per ray; the    */
+/* counter-based generator makes every ray's draw independent of order.    */
+/* ------------------------------------------------------------------------ */
+static void om_mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void om_philox4x64(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4])
+{
+    /* multipliers and Weyl key increments of Philox4x64 from the SC'11 paper */
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t hi0, lo0, hi1, lo1;
+        om_mulhilo64(M0, c0, &hi0, &lo0);
+        om_mulhilo64(M1, c2, &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n1 = lo1;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        uint64_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 64-bit word -> double uniform in the open interval (0,1): top 53 bits plus
+ * one half, times 2^-53. */
+double om_u01(uint64_t w)
+{
+    return ((double)(w >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+/* Sec. 3.1: a ray is the vector from its source to a point on the lens.
+ * The lens point is drawn uniformly over the aiming disk (radius a, centred on
+ * the optical axis at z = aim_z): r = a sqrt(u1), phi = 2 pi u2.  Counter =
+ * (ray, source, frame, purpose 0); key = (seed, 0). */
+void om_lens_point(uint64_t seed, uint32_t source_id, uint32_t ray_id, uint32_t frame,
+                   double aim_r, double aim_z, double p[3])
+{
+    uint64_t ctr[4] = { ray_id, source_id, frame, 0 };
+    uint64_t key[2] = { seed, 0 };
+    uint64_t w[4];
+    om_philox4x64(ctr, key, w);
+    double u1 = om_u01(w[0]);
+    double u2 = om_u01(w[1]);
+    double r = aim_r * sqrt(u1);
+    double phi = 2.0 * M_PI * u2;
+    p[0] = r * cos(phi);
+    p[1] = r * sin(phi);
+    p[2] = aim_z;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Medium: Eq. 1 (n = K rho + 1) at grid nodes, gradient of n at the nodes   */
+/* by second-order finite differences (the grid gradient Eq. 6 needs).      */
+/* Nodes sit at origin + i * spacing, x fastest: index (k*ny + j)*nx + i.   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int n[3];
+    double origin[3], spacing[3];
+    double K;
+    double *dn;     /* n - 1 = K rho at nodes */
+    double *g[3];   /* dn/dx, dn/dy, dn/dz at nodes */
+} om_medium;
+
+static size_t om_idx(const om_medium *m, int i, int j, int k)
+{
+    return ((size_t)k * (size_t)m->n[1] + (size_t)j) * (size_t)m->n[0] + (size_t)i;
+}
+
+/* derivative of the node values f along one axis at node position q (0..N-1),
+ * reading neighbours through get(q') -- central difference inside,
+ * second-order one-sided at the two end nodes, two-point difference when the
+ * axis has only two nodes. */
+static double om_diff(const om_medium *m, int axis, int i, int j, int k)
+{
+    int N = m->n[axis];
+    int q = axis == 0 ? i : (axis == 1 ? j : k);
+    double h = m->spacing[axis];
+#define OM_AT(qq) m->dn[axis == 0 ? om_idx(m, (qq), j, k) : (axis == 1 ? om_idx(m, i, (qq), k) : om_idx(m, i, j, (qq)))]
+    double d;
+    if (N == 2) {
+        d = (OM_AT(1) - OM_AT(0)) / h;
+    } else if (q == 0) {
+        d = (-3.0 * OM_AT(0) + 4.0 * OM_AT(1) - OM_AT(2)) / (2.0 * h);
+    } else if (q == N - 1) {
+        d = (3.0 * OM_AT(N - 1) - 4.0 * OM_AT(N - 2) + OM_AT(N - 3)) / (2.0 * h);
+    } else {
+        d = (OM_AT(q + 1) - OM_AT(q - 1)) / (2.0 * h);
+    }
+#undef OM_AT
+    return d;
+}
+
+om_medium *om_medium_build(const float *rho, int nx, int ny, int nz,
+                           const double origin[3], const double spacing[3], double K)
+{
+    if (nx < 2 || ny < 2 || nz < 2) return NULL;
+    om_medium *m = (om_medium *)calloc(1, sizeof(om_medium));
+    m->n[0] = nx; m->n[1] = ny; m->n[2] = nz;
+    for (int a = 0; a < 3; ++a) { m->origin[a] = origin[a]; m->spacing[a] = spacing[a]; }
+    m->K = K;
+    size_t N = (size_t)nx * ny * nz;
+    m->dn = (double *)malloc(N * sizeof(double));
+    for (int a = 0; a < 3; ++a) m->g[a] = (double *)malloc(N * sizeof(double));
+    /* Eq. 1 */
+    for (size_t p = 0; p < N; ++p) m->dn[p] = K * (double)rho[p];
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                for (int a = 0; a < 3; ++a)
+                    m->g[a][om_idx(m, i, j, k)] = om_diff(m, a, i, j, k);
+    return m;
+}
+
+void om_medium_free(om_medium *m)
+{
+    if (!m) return;
+    free(m->dn);
+    for (int a = 0; a < 3; ++a) free(m->g[a]);
+    free(m);
+}
+
+/* copy out the node arrays (for tests) */
+void om_medium_nodes(const om_medium *m, double *dn, double *gx, double *gy, double *gz)
+{
+    size_t N = (size_t)m->n[0] * m->n[1] * m->n[2];
+    memcpy(dn, m->dn, N * sizeof(double));
+    memcpy(gx, m->g[0], N * sizeof(double));
+    memcpy(gy, m->g[1], N * sizeof(double));
+    memcpy(gz, m->g[2], N * sizeof(double));
+}
+
+/* Trilinear interpolation of n-1 and of each gradient component at point x,
+ * with the point clamped into the box.  Sec. 3.2 evaluates n and its
+ * gradient at the ray position from the grid ("the grid point corresponding
+ * to the given location of the ray"); trilinear sampling is how a position
+ * between nodes is given a value. */
+void om_sample(const om_medium *m, const double x[3], double *dn, double g[3])
+{
+    int i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = (x[a] - m->origin[a]) / m->spacing[a];
+        if (u < 0.0) u = 0.0;
+        if (u > (double)(m->n[a] - 1)) u = (double)(m->n[a] - 1);
+        int i = (int)floor(u);
+        if (i > m->n[a] - 2) i = m->n[a] - 2;
+        i0[a] = i;
+        f[a] = u - (double)i;
+    }
+    double acc_dn = 0.0, acc_g[3] = { 0.0, 0.0, 0.0 };
+    for (int c = 0; c < 8; ++c) {
+        int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+        double w = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) * (dk ? f[2] : 1.0 - f[2]);
+        size_t p = om_idx(m, i0[0] + di, i0[1] + dj, i0[2] + dk);
+        acc_dn += w * m->dn[p];
+        for (int a = 0; a < 3; ++a) acc_g[a] += w * m->g[a][p];
+    }
+    *dn = acc_dn;
+    for (int a = 0; a < 3; ++a) g[a] = acc_g[a];
+}
+
+/* Eq. 6: D = n grad(n), using the first form (n times the sampled gradient). */
+static void om_D(const om_medium *m, const double R[3], double D[3])
+{
+    double dn, g[3];
+    om_sample(m, R, &dn, g);
+    double n = 1.0 + dn;
+    for (int a = 0; a < 3; ++a) D[a] = n * g[a];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Optics (Sec. 3.3) and sensor (Sec. 3.4)                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int type;
+    double z;        /* vertex (or plane) position on the axis */
+    double R;        /* signed radius of curvature, centre at z + R (spheres) */
+    double f;        /* focal length (ideal thin lens) */
+    double n_after;  /* refractive index after the surface */
+    double clear_r;  /* clear (or stop) radius */
+} om_surface;
+
+typedef struct {
+    int ns;
+    om_surface s[OM_MAX_SURF];
+    double n_object;        /* index of the space the rays start in */
+    double aim_z, aim_r;    /* disk the lens points are drawn on (Sec. 3.1) */
+    double sensor_z, pitch;
+    int W, H;
+    double sigma;           /* Gaussian sigma of the spot, metres (d_tau/4) */
+} om_optics;
+
+typedef struct {
+    double vol_pos[3], vol_dir[3];
+    double sensor_xy[2];
+    double sensor_dir[3];
+    int32_t status, steps;
+} om_ray_state;
+
+/* Eq. 8 as printed (rule 0: 2.44 pi f# (M+1) lambda) or the textbook Airy
+ * diameter (rule 1: 2.44 f# (M+1) lambda).  The spot is a Gaussian whose
+ * e^-2 diameter is d_tau, so sigma = d_tau / 4. */
+double om_sigma_from_eq8(double f_number, double M, double lambda, int rule)
+{
+    double dtau = 2.44 * (rule == 0 ? M_PI : 1.0) * f_number * (M + 1.0) * lambda;
+    return dtau / 4.0;
+}
+
+om_optics *om_optics_build(const double *surf /* [ns][6]: type z R f n_after clear_r */, int ns,
+                           double n_object, double aim_z, double aim_r,
+                           double sensor_z, double pitch, int W, int H, double sigma)
+{
+    if (ns < 0 || ns > OM_MAX_SURF) return NULL;
+    om_optics *o = (om_optics *)calloc(1, sizeof(om_optics));
+    o->ns = ns;
+    for (int i = 0; i < ns; ++i) {
+        o->s[i].type = (int)surf[6 * i + 0];
+        o->s[i].z = surf[6 * i + 1];
+        o->s[i].R = surf[6 * i + 2];
+        o->s[i].f = surf[6 * i + 3];
+        o->s[i].n_after = surf[6 * i + 4];
+        o->s[i].clear_r = surf[6 * i + 5];
+    }
+    o->n_object = n_object;
+    o->aim_z = aim_z; o->aim_r = aim_r;
+    o->sensor_z = sensor_z; o->pitch = pitch; o->W = W; o->H = H;
+    o->sigma = sigma;
+    return o;
+}
+
+void om_optics_free(om_optics *o) { free(o); }
+
+/* Eq. 7 in vector form.  N is the unit surface normal facing the incoming
+ * ray (N.d < 0).  Returns 0 on total internal reflection (the ray is then
+ * killed -- the paper only says TIR must be considered). */
+int om_refract(const double d[3], const double N[3], double n_i, double n_f, double out[3])
+{
+    double eta = n_i / n_f;
+    double ci = -(N[0] * d[0] + N[1] * d[1] + N[2] * d[2]);
+    double k = 1.0 - eta * eta * (1.0 - ci * ci);
+    if (k < 0.0) return 0;
+    double a = eta * ci - sqrt(k);
+    for (int q = 0; q < 3; ++q) out[q] = eta * d[q] + a * N[q];
+    return 1;
+}
+
+/* move the point P along d to the plane z = zp; 0 if the plane is behind */
+static int om_to_plane(double P[3], const double d[3], double zp)
+{
+    if (!(d[2] > 0.0)) return 0;
+    double t = (zp - P[2]) / d[2];
+    if (t < 0.0) return 0;
+    P[0] += t * d[0];
+    P[1] += t * d[1];
+    P[2] = zp;
+    return 1;
+}
+
+/* Sec. 3.3: intersect with a spherical surface given by its vertex on the
+ * axis and signed radius.  The ray is first moved to the vertex plane; with
+ * Q the point there relative to the vertex (Q_z = 0) the hit parameter solves
+ * t^2 + 2 b t + c = 0, b = d.Q - R d_z, c = |Q|^2, and the root on the
+ * vertex-side cap is the one of smaller magnitude, c / (-b - sign(b) sqrt(b^2 - c)).
+ * Returns 0 on a miss. */
+int om_sphere_hit(double P[3], const double d[3], double zv, double R, double N[3])
+{
+    double t0;
+    if (!(d[2] > 0.0)) return 0;
+    t0 = (zv - P[2]) / d[2];
+    double Q[3] = { P[0] + t0 * d[0], P[1] + t0 * d[1], 0.0 };
+    double b = d[0] * Q[0] + d[1] * Q[1] - R * d[2];
+    double c = Q[0] * Q[0] + Q[1] * Q[1];
+    double disc = b * b - c;
+    if (disc < 0.0) return 0;
+    double sq = sqrt(disc);
+    double denom = -b - (b >= 0.0 ? sq : -sq);
+    double t1 = denom != 0.0 ? c / denom : 0.0;
+    if (t0 + t1 < 0.0) return 0;
+    double H[3] = { Q[0] + t1 * d[0], Q[1] + t1 * d[1], t1 * d[2] };
+    /* must lie on the hemisphere that contains the vertex */
+    if (!((H[2] - R) * R < 0.0)) return 0;
+    /* unit normal (H - C)/R, C = (0,0,R); orient it against the ray */
+    double Nn[3] = { H[0] / R, H[1] / R, (H[2] - R) / R };
+    double s = Nn[0] * d[0] + Nn[1] * d[1] + Nn[2] * d[2];
+    if (s > 0.0) { Nn[0] = -Nn[0]; Nn[1] = -Nn[1]; Nn[2] = -Nn[2]; }
+    P[0] = H[0]; P[1] = H[1]; P[2] = zv + H[2];
+    N[0] = Nn[0]; N[1] = Nn[1]; N[2] = Nn[2];
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One ray, all four stages (Sec. 3, Fig. 2).                               */
+/* ------------------------------------------------------------------------ */
+int om_max_steps(const om_medium *m, double step)
+{
+    double diag2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double L = (double)(m->n[a] - 1) * m->spacing[a];
+        diag2 += L * L;
+    }
+    return (int)ceil(2.0 * sqrt(diag2) / step) + 4;
+}
+
+int om_trace(const om_medium *m, const om_optics *o, const double src[3],
+             uint64_t seed, uint32_t source_id, uint32_t ray_id, uint32_t frame,
+             int integrator, double step, om_ray_state *out)
+{
+    double R[3], d[3], p[3];
+    int status = OM_REACHED, steps = 0;
+
+    /* Sec. 3.1: origin = source, direction = unit vector to the lens point */
+    om_lens_point(seed, source_id, ray_id, frame, o->aim_r, o->aim_z, p);
+    double L2 = 0.0;
+    for (int a = 0; a < 3; ++a) { R[a] = src[a]; d[a] = p[a] - src[a]; L2 += d[a] * d[a]; }
+    double L = sqrt(L2);
+    for (int a = 0; a < 3; ++a) d[a] /= L;
+
+    /* Sec. 3.2: straight outside the grid (no gradient there), Eqs. 3-6 inside.
+     * Reading: no refraction at the box faces; T = n(R) d at the entry. */
+    if (m) {
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = m->origin[a];
+            hi[a] = m->origin[a] + (double)(m->n[a] - 1) * m->spacing[a];
+        }
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) if (R[a] < lo[a] || R[a] > hi[a]) inside = 0;
+        int enters = inside;
+        if (!inside) {
+            double tn = -INFINITY, tf = INFINITY;
+            int ok = 1;
+            for (int a = 0; a < 3; ++a) {
+                if (d[a] == 0.0) {
+                    if (R[a] < lo[a] || R[a] > hi[a]) ok = 0;
+                } else {
+                    double t1 = (lo[a] - R[a]) / d[a];
+                    double t2 = (hi[a] - R[a]) / d[a];
+                    double tmin = t1 < t2 ? t1 : t2, tmax = t1 < t2 ? t2 : t1;
+                    if (tmin > tn) tn = tmin;
+                    if (tmax < tf) tf = tmax;
+                }
+            }
+            if (ok && tn <= tf && tn >= 0.0) {
+                enters = 1;
+                for (int a = 0; a < 3; ++a) R[a] += tn * d[a];
+            }
+        }
+        if (enters) {
+            double dn, g[3];
+            om_sample(m, R, &dn, g);
+            double T[3];
+            for (int a = 0; a < 3; ++a) T[a] = (1.0 + dn) * d[a];
+            int maxs = om_max_steps(m, step);
+            int done = 0;
+            for (int k = 0; k < maxs && !done; ++k) {
+                /* reading: before each step, the parameter distance to the box
+                 * boundary along the current tangent; if a full step would reach
+                 * it, take one shortened final step that ends on the face. */
+                double dexit = INFINITY;
+                for (int a = 0; a < 3; ++a) {
+                    if (T[a] > 0.0) { double q = (hi[a] - R[a]) / T[a]; if (q < dexit) dexit = q; }
+                    else if (T[a] < 0.0) { double q = (lo[a] - R[a]) / T[a]; if (q < dexit) dexit = q; }
+                }
+                double h = step;
+                if (step >= dexit) { h = dexit > 0.0 ? dexit : 0.0; done = 1; }
+                if (integrator == OM_RK4) {
+                    /* Eqs. 3 and 5 (Sharma et al.'s Runge-Kutta-Nystrom step) */
+                    double A[3], B[3], C[3], X[3];
+                    om_D(m, R, A);
+                    for (int a = 0; a < 3; ++a) A[a] *= h;
+                    for (int a = 0; a < 3; ++a) X[a] = R[a] + (0.5 * T[a] + A[a] / 8.0) * h;
+                    om_D(m, X, B);
+                    for (int a = 0; a < 3; ++a) B[a] *= h;
+                    for (int a = 0; a < 3; ++a) X[a] = R[a] + (T[a] + 0.5 * B[a]) * h;
+                    om_D(m, X, C);
+                    for (int a = 0; a < 3; ++a) C[a] *= h;
+                    for (int a = 0; a < 3; ++a) {
+                        R[a] = R[a] + (T[a] + (A[a] + 2.0 * B[a]) / 6.0) * h;
+                        T[a] = T[a] + (A[a] + 4.0 * B[a] + C[a]) / 6.0;
+                    }
+                } else {
+                    /* first-order (piecewise-linear) scheme: both updates from
+                     * the state at the start of the step */
+                    double Dv[3];
+                    om_D(m, R, Dv);
+                    for (int a = 0; a < 3; ++a) {
+                        R[a] = R[a] + T[a] * h;
+                        T[a] = T[a] + Dv[a] * h;
+                    }
+                }
+                ++steps;
+            }
+            if (!done) status = OM_KILLED_MAXSTEP;
+            double Tn = sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+            for (int a = 0; a < 3; ++a) d[a] = T[a] / Tn;
+        }
+    }
+    if (out) {
+        for (int a = 0; a < 3; ++a) { out->vol_pos[a] = R[a]; out->vol_dir[a] = d[a]; }
+        out->steps = steps;
+    }
+
+    /* Sec. 3.3: the optical elements in sequence */
+    double n_cur = o->n_object;
+    for (int s = 0; s < o->ns && status == OM_REACHED; ++s) {
+        const om_surface *S = &o->s[s];
+        if (S->type == OM_SURF_SPHERE && S->R != 0.0) {
+            double N[3], dn2[3];
+            if (!om_sphere_hit(R, d, S->z, S->R, N)) { status = OM_KILLED_MISS; break; }
+            if (R[0] * R[0] + R[1] * R[1] > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
+            if (!om_refract(d, N, n_cur, S->n_after, dn2)) { status = OM_KILLED_TIR; break; }
+            for (int a = 0; a < 3; ++a) d[a] = dn2[a];
+            n_cur = S->n_after;
+        } else {
+            if (!om_to_plane(R, d, S->z)) { status = OM_KILLED_MISS; break; }
+            double r2 = R[0] * R[0] + R[1] * R[1];
+            if (S->type == OM_SURF_STOP) {
+                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_STOP; break; }
+            } else if (S->type == OM_SURF_IDEAL_THIN) {
+                /* reading: an ideal (perfectly stigmatic) thin lens acting on
+                 * the slopes, u' = u - x / f */
+                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
+                double sx = d[0] / d[2] - R[0] / S->f;
+                double sy = d[1] / d[2] - R[1] / S->f;
+                double nn = sqrt(sx * sx + sy * sy + 1.0);
+                d[0] = sx / nn; d[1] = sy / nn; d[2] = 1.0 / nn;
+            } else { /* flat refracting surface (sphere with R = 0 too) */
+                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
+                double N[3] = { 0.0, 0.0, -1.0 }, dn2[3];
+                if (!om_refract(d, N, n_cur, S->n_after, dn2)) { status = OM_KILLED_TIR; break; }
+                for (int a = 0; a < 3; ++a) d[a] = dn2[a];
+                n_cur = S->n_after;
+            }
+        }
+    }
+
+    /* Sec. 3.4: line-plane intersection with the sensor; pixel (i, j) covers
+     * [i, i+1) x [j, j+1) with the optical axis at the array centre */
+    double px = 0.0, py = 0.0;
+    if (status == OM_REACHED) {
+        if (!om_to_plane(R, d, o->sensor_z)) status = OM_KILLED_MISS;
+        else {
+            px = R[0] / o->pitch + 0.5 * (double)o->W;
+            py = R[1] / o->pitch + 0.5 * (double)o->H;
+            if (!(px >= 0.0 && px < (double)o->W && py >= 0.0 && py < (double)o->H))
+                status = OM_KILLED_OFF_SENSOR;
+        }
+    }
+    if (out) {
+        out->sensor_xy[0] = px; out->sensor_xy[1] = py;
+        for (int a = 0; a < 3; ++a) out->sensor_dir[a] = d[a];
+        out->status = status;
+    }
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.4 deposit: Gaussian spot of standard deviation sigma centred on the */
+/* hit, integrated over each pixel with erf, over the pixels within 3 sigma  */
+/* (clipped to the sensor), renormalised over that window and quantised to   */
+/* 32.32 fixed point; the rounding remainder goes to the largest weight      */
+/* (first in row-major order) so every ray adds exactly 2^32.               */
+/* ------------------------------------------------------------------------ */
+static void om_axis_weights(double p, double sp, int N, int *lo, int *hi, double *w /* size >= hi-lo+1 */)
+{
+    int a = (int)floor(p - 3.0 * sp);
+    int b = (int)floor(p + 3.0 * sp);
+    if (a < 0) a = 0;
+    if (b > N - 1) b = N - 1;
+    double s = 0.0;
+    for (int i = a; i <= b; ++i) {
+        double e1 = erf(((double)(i + 1) - p) / (M_SQRT2 * sp));
+        double e0 = erf(((double)i - p) / (M_SQRT2 * sp));
+        w[i - a] = 0.5 * (e1 - e0);
+        s += w[i - a];
+    }
+    for (int i = a; i <= b; ++i) w[i - a] /= s;
+    *lo = a; *hi = b;
+}
+
+/* returns the number of pixels touched; adds into image (row-major, y = row) */
+int om_deposit(const om_optics *o, double px, double py, int64_t *image, int atomic)
+{
+    double sp = o->sigma / o->pitch;
+    int xlo, xhi, ylo, yhi;
+    double wx[4096], wy[4096];
+    om_axis_weights(px, sp, o->W, &xlo, &xhi, wx);
+    om_axis_weights(py, sp, o->H, &ylo, &yhi, wy);
+    const double two32 = 4294967296.0;
+    int64_t sum = 0, qmax = -1;
+    int imax = 0, jmax = 0;
+    for (int j = ylo; j <= yhi; ++j)
+        for (int i = xlo; i <= xhi; ++i) {
+            int64_t q = (int64_t)llrint(wx[i - xlo] * wy[j - ylo] * two32);
+            sum += q;
+            if (q > qmax) { qmax = q; imax = i; jmax = j; }
+        }
+    int64_t rem = (int64_t)4294967296LL - sum;
+    for (int j = ylo; j <= yhi; ++j)
+        for (int i = xlo; i <= xhi; ++i) {
+            int64_t q = (int64_t)llrint(wx[i - xlo] * wy[j - ylo] * two32);
+            if (i == imax && j == jmax) q += rem;
+            if (q == 0) continue;
+            int64_t *dst = &image[(size_t)j * (size_t)o->W + (size_t)i];
+            if (atomic) {
+#pragma omp atomic
+                *dst += q;
+            } else {
+                *dst += q;
+            }
+        }
+    return (xhi - xlo + 1) * (yhi - ylo + 1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Whole render: every ray of every source, image accumulated.  stats[6]    */
+/* counts rays by final status.  Rays are independent (Sec. 3.5), so the    */
+/* loop is spread over host threads; the integer image makes the order      */
+/* irrelevant.                                                              */
+/* ------------------------------------------------------------------------ */
+void om_render(const om_medium *m, const om_optics *o, const double *sources, int64_t n_sources,
+               int32_t rays_per_source, int64_t first_ray, int64_t ray_count,
+               uint64_t seed, uint32_t frame, int integrator, double step,
+               int64_t *image, int64_t *stats, int nthreads)
+{
+    int64_t total = n_sources * (int64_t)rays_per_source;
+    int64_t end = first_ray + ray_count;
+    if (end > total) end = total;
+    int64_t cnt[6] = { 0, 0, 0, 0, 0, 0 };
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+    {
+        int64_t lc[6] = { 0, 0, 0, 0, 0, 0 };
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t r = first_ray; r < end; ++r) {
+            int64_t s = r / rays_per_source;
+            uint32_t k = (uint32_t)(r % rays_per_source);
+            om_ray_state st;
+            int status = om_trace(m, o, &sources[3 * s], seed, (uint32_t)s, k, frame, integrator, step, &st);
+            if (status == OM_REACHED) om_deposit(o, st.sensor_xy[0], st.sensor_xy[1], image, 1);
+            lc[status] += 1;
+        }
+#pragma omp critical
+        for (int q = 0; q < 6; ++q) cnt[q] += lc[q];
+    }
+    if (stats) for (int q = 0; q < 6; ++q) stats[q] += cnt[q];
+}
+
+/* Per-ray states for a list of ray ids (id = source * rays_per_source + ray). */
+void om_trace_many(const om_medium *m, const om_optics *o, const double *sources,
+                   int32_t rays_per_source, const int64_t *ray_ids, int64_t n,
+                   uint64_t seed, uint32_t frame, int integrator, double step,
+                   om_ray_state *out, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t r = ray_ids[q];
+        int64_t s = r / rays_per_source;
+        uint32_t k = (uint32_t)(r % rays_per_source);
+        om_trace(m, o, &sources[3 * s], seed, (uint32_t)s, k, frame, integrator, step, &out[q]);
+    }
+}
+
+/* helpers exposed for tests */
+void om_sample_many(const om_medium *m, const double *x, int64_t n, double *dn, double *g)
+{
+    for (int64_t q = 0; q < n; ++q) om_sample(m, &x[3 * q], &dn[q], &g[3 * q]);
+}
+
+int om_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
