@@ -1,0 +1,349 @@
+"""Benchmark: rays/s traced to the sensor on one GB300 (and N by torchrun).
+
+Default workload (config C1): PIV uniform medium n = 1.000277, 10,000
+particles uniform in a 50x50x1 mm sheet, 10,000 rays each, thick biconvex
+lens (R = +-0.1 m, 10 mm, n = 1.5) at f/4 and M = 0.2, the sheet 2 mm before
+and 2 mm behind focus (two images per step), 1024x1024 sensor, 17 um pitch.
+
+A step is one pass of the whole path over both images: medium build from
+the density grid (Eq. 1 and the node gradients), Morton ordering of the
+sources, the fused trace/optics/deposit kernel and the fixed-point -> float
+finalisation.  Inputs are resident on the GPU when the timed region starts;
+L2 is flushed between timed steps.  The e2e figure runs the same step through
+the C ABI with host buffers (host density and sources in, host image out).
+
+--impl reference times the CPU oracle (the paper's method written plainly in
+FP64 C) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1812_05902_gb300 import scenes  # noqa: E402
+
+WORKLOAD_NAMES = {
+    "c0": "BOS linear-gradient slab, 32^3 grid, 64x64 dots x 100 rays, Euler 0.1 mm, ideal lens f/8 M=0.1, 256^2",
+    "c1": "PIV uniform medium n=1.000277, 1e4 particles x 1e4 rays in a 50x50x1 mm sheet, thick biconvex lens "
+          "R=+-0.1 m d=10 mm n=1.5 f/4 M=0.2, sheet -2 mm and +2 mm from focus (2 images), 1024^2 17 um",
+    "c2": "BOS k^-5/3 turbulence 256^3 over 0.1 m, 1e5 dots x 1e3 rays, RK4 0.2 mm, thick lens f/8 M=0.1, 1024^2",
+    "c4": "Tomo-PIV 1e5 particles x 1e4 rays in a 100x100x30 mm 256^3 turbulence field, RK4 0.2 mm, thick lens "
+          "f/4 M=0.2, 2048^2",
+}
+METRIC = "rays/s traced to sensor at 1 GB300 (plain vs surrogate at ≤0.01 px RMS error)"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _frames(workload):
+    if workload == "c1":
+        return scenes.c1()
+    if workload == "c0":
+        return scenes.c0()
+    if workload == "c2":
+        return scenes.c2()
+    if workload == "c4":
+        return scenes.c4()
+    raise SystemExit("unknown workload %s" % workload)
+
+
+# ----------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# ----------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# roofline of the dominant kernel
+# ----------------------------------------------------------------------------
+# Algorithmic FP64 operations per ray of the render kernel on a thick-lens
+# scene (lens point direction 12, volume entry/exit 21, stop 9, two spheres
+# 2 x 68, sensor 10, spot window 4): the FP64 pipe bounds this kernel.
+FP64_OPS_PER_RAY_THICK_LENS = 192.0
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal FP64 rate
+
+
+def roofline(workload, frames, render_ms, render_launches, peaks, peak_kind):
+    if render_launches == 0:
+        return None
+    rays_per_launch = sum(f.n_rays for f in frames) / len(frames)
+    t = render_ms / render_launches * 1e-3
+    ops = FP64_OPS_PER_RAY_THICK_LENS * rays_per_launch
+    achieved = ops / t / 1e12
+    peak = FP64_NOMINAL_TFLOPS
+    return {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "render_kernel<RK4>", "peak_source": "nominal FP64 of the profiling recipe",
+            "launch_ms": round(t * 1e3, 4), "rays_per_launch": int(rays_per_launch)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------
+def oracle_sample(frames, seconds_target=12.0, max_rays=None):
+    import oracle
+    fr = frames[0]
+    med = oracle.Medium.from_scene(fr.medium) if fr.medium is not None else None
+    opt = oracle.Optics.from_scene(fr.optics)
+    threads = oracle.threads()
+    chunk = 200000
+    done, t_total = 0, 0.0
+    img = np.zeros((fr.optics.height, fr.optics.width), dtype=np.int64)
+    while t_total < seconds_target and (max_rays is None or done < max_rays):
+        t0 = time.perf_counter()
+        oracle.render(med, opt, fr.sources, fr.rays_per_source, fr.seed, fr.frame_index, fr.integrator,
+                      fr.step, image=img, first_ray=done, ray_count=chunk)
+        t_total += time.perf_counter() - t0
+        done += chunk
+        if done >= fr.n_rays:
+            break
+    return done / t_total, threads, done, t_total
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    frames = _frames(args.workload)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(frames, seconds_target=1.0)
+    sample_s = max(2.0, min(20.0, 150.0 / max(args.steps, 1)))
+    for _ in range(args.steps):
+        v, threads, done, t = oracle_sample(frames, seconds_target=sample_s)
+        vals.append(v)
+    value = statistics.median(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(f.n_rays for f in frames) / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "name": args.workload},
+        "cpu_baseline": {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle",
+                         "sample": "first %d rays (source order) of image 1 per step, ~%.0f s each" % (done, sample_s)},
+        "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1812_05902_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1812_05902_gb300 import pivbos as P
+
+    frames = _frames(args.workload)
+    # weak scaling: every rank renders its own images (seed offset by rank)
+    for fr in frames:
+        fr.seed = fr.seed + 1000003 * rank
+    opt = P.Optics(frames[0].optics)
+    W, H = frames[0].optics.width, frames[0].optics.height
+    rho_d = [torch.tensor(fr.medium.rho, device=dev) for fr in frames]
+    src_d = [torch.tensor(fr.sources, dtype=torch.float64, device=dev) for fr in frames]
+    meds = [P.Medium(fr.medium, rho=rho_d[i]) for i, fr in enumerate(frames)]
+    img = torch.zeros((H, W), dtype=torch.int64, device=dev)
+    fimg = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in frames]
+    stats = torch.zeros(P.RAY_NSTATUS, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for i, fr in enumerate(frames):
+            P.pivbos_medium_refill(meds[i].h, rho_d[i])
+            img.zero_()
+            P.pivbos_render(meds[i].h, opt.h, src_d[i], len(fr.sources), fr.rays_per_source, fr.seed,
+                            fr.frame_index, fr.integrator, fr.step, img, stats)
+            P.pivbos_image_finalize(img, H * W, fimg[i])
+
+    for _ in range(args.warmup):
+        step()
+    P.pivbos_sync()
+    # exact-total check of the last warm-up image (outside the timed region)
+    stats.zero_()
+    step()
+    P.pivbos_sync()
+    st = stats.cpu().numpy()
+    assert int(st.sum()) == sum(fr.n_rays for fr in frames)
+
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    P.pivbos_timing_reset()
+    P.pivbos_timing_enable(True)
+    launches0 = P.pivbos_kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = P.pivbos_kernel_launches() - launches0
+    P.pivbos_timing_enable(False)
+    render_ms, render_n = P.pivbos_timing_read("render")
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in times)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rays_step = sum(fr.n_rays for fr in frames)
+    value = rays_step * args.steps * world / (ms * 1e-3)
+
+    # e2e: same step through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        rho_h = [torch.tensor(fr.medium.rho).pin_memory() for fr in frames]
+        src_h = [torch.tensor(fr.sources, dtype=torch.float64).pin_memory() for fr in frames]
+        img_h = torch.zeros((H, W), dtype=torch.int64).pin_memory()
+
+        def step_host():
+            for i, fr in enumerate(frames):
+                P.pivbos_medium_refill(meds[i].h, rho_h[i])
+                img_h.zero_()
+                P.pivbos_render(meds[i].h, opt.h, src_h[i], len(fr.sources), fr.rays_per_source, fr.seed,
+                                fr.frame_index, fr.integrator, fr.step, img_h, None)
+
+        step_host()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            step_host()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = sum(r.numel() * 4 + s.numel() * 8 + H * W * 8 for r, s in zip(rho_h, src_h))
+        e2e = {"value": rays_step * max(1, args.steps) * world / dt, "unit": "rays/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(H * W * 8 * len(frames))}
+
+    peaks, peak_kind = _peaks()
+    rf = roofline(args.workload, frames, render_ms, render_n, peaks, peak_kind)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, threads, done, t = oracle_sample(frames, seconds_target=12.0)
+        cpu = {"value": v, "unit": "rays/s", "cores": threads, "kind": "oracle",
+               "sample": "first %d rays (source order) of image 1, %.1f s of CPU work" % (done, t)}
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES[args.workload], "name": args.workload,
+                       "rays_per_step": rays_step, "images_per_step": len(frames), "l2": "flushed between steps",
+                       "parallelism": "replicas (weak)" if world > 1 else "single GPU"},
+            "gpu_launches": int(launches), "clocks": clk, "roofline": rf, "e2e": e2e, "cpu_baseline": cpu,
+            "impl": "pivbos",
+        }
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pivbos", choices=["pivbos", "reference"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOAD_NAMES))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

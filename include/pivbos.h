@@ -1,0 +1,216 @@
+/*
+ * pivbos -- ray-traced PIV/BOS image generation on one GB300 (sm_103a).
+ *
+ * C ABI of the CUDA library libpivbos.so.  The calls follow the problem
+ * statement of Rajendran, Bane & Vlachos, "PIV/BOS Synthetic Image Generation
+ * in Variable Density Environments" (arXiv 1812.05902), Sec. 3: rays leave
+ * sources (particles or BOS dots) toward the lens (Sec. 3.1), bend in a
+ * refractive-index field built from density by the Gladstone-Dale relation
+ * (Sec. 3.2, Eqs. 1-6), pass the optical elements (Sec. 3.3, Eq. 7) and
+ * deposit a diffraction spot on the sensor (Sec. 3.4, Eq. 8).
+ *
+ * Conventions shared by every call:
+ *  - SI units.  z is the optical axis, from the sources toward the sensor.
+ *  - Every call returns a pivbos_status and never aborts the process; a
+ *    message for the last failure on the calling thread is available from
+ *    pivbos_last_error().
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that take a stream are asynchronous on it unless stated
+ *    otherwise; device errors detected inside kernels are latched in a
+ *    per-device status word that pivbos_sync() returns and clears.
+ *  - Handles own their device memory, are immutable after creation except
+ *    through pivbos_medium_refill(), and may be shared by renders on
+ *    different streams of the device they were created on.
+ *  - Device pointers must belong to the current device; host pointers may
+ *    be pageable or pinned.
+ */
+#ifndef PIVBOS_H
+#define PIVBOS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIVBOS_OK = 0,
+    PIVBOS_ERR_INVALID_ARG = 1,     /* NULL pointer, bad size, bad enum, wrong device */
+    PIVBOS_ERR_OOM = 2,             /* device or host allocation failed */
+    PIVBOS_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+    PIVBOS_ERR_DEVICE_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    PIVBOS_ERR_OVERFLOW = 5,        /* more than 2^31 rays in one render */
+    PIVBOS_ERR_UNSUPPORTED = 6      /* valid but outside what the kernels handle */
+} pivbos_status;
+
+/* Final state of a ray (pivbos_ray_state.status); also the index into the
+ * per-render counters of pivbos_render(). */
+enum {
+    PIVBOS_RAY_REACHED = 0,     /* deposited on the sensor */
+    PIVBOS_RAY_STOP = 1,        /* blocked by an aperture (Sec. 3.3, item 3) */
+    PIVBOS_RAY_MISS = 2,        /* missed a surface or left its clear radius */
+    PIVBOS_RAY_TIR = 3,         /* total internal reflection (Sec. 3.3, item 2) */
+    PIVBOS_RAY_OFF_SENSOR = 4,  /* crossed the sensor plane outside the pixels */
+    PIVBOS_RAY_MAXSTEP = 5,     /* integration step budget exhausted */
+    PIVBOS_RAY_NSTATUS = 6
+};
+
+/* Optical element kinds (Sec. 3.3). */
+enum {
+    PIVBOS_SURF_SPHERE = 0,     /* refracting sphere: vertex z, signed radius (centre at z + R) */
+    PIVBOS_SURF_PLANE = 1,      /* flat refracting surface at z */
+    PIVBOS_SURF_IDEAL_THIN = 2, /* ideal thin lens of focal length f at z (slopes u' = u - x/f) */
+    PIVBOS_SURF_STOP = 3        /* aperture: rays outside clear_radius at z are blocked */
+};
+
+/* Integrators of the ray equation (Sec. 3.2). */
+enum {
+    PIVBOS_EULER = 0,           /* first-order piecewise-linear scheme */
+    PIVBOS_RK4 = 1              /* Runge-Kutta scheme of Sharma et al., Eqs. 3-6 */
+};
+
+#define PIVBOS_MAX_SURFACES 16
+/* The spot window is at most this many pixels per axis: sigma/pitch must not
+ * exceed (PIVBOS_MAX_WINDOW - 2) / 6. */
+#define PIVBOS_MAX_WINDOW 12
+
+typedef struct {
+    int32_t type;          /* PIVBOS_SURF_* */
+    int32_t reserved;      /* must be 0 */
+    double z_vertex;       /* m, position of the vertex (or plane) on the axis */
+    double radius;         /* m, signed radius of curvature (spheres only) */
+    double focal;          /* m, focal length (ideal thin lens only) */
+    double n_after;        /* refractive index after the surface */
+    double clear_radius;   /* m, clear (or stop) radius */
+} pivbos_surface;
+
+/* Per-ray result of pivbos_trace_exit_states (96 bytes, naturally aligned). */
+typedef struct {
+    double vol_pos[3];     /* where the ray left the density box (its source if it never entered) */
+    double vol_dir[3];     /* unit direction there */
+    double sensor_xy[2];   /* pixel coordinates on the sensor (valid if status is REACHED or OFF_SENSOR) */
+    double sensor_dir[3];  /* unit direction at the sensor plane */
+    int32_t status;        /* PIVBOS_RAY_* */
+    int32_t steps;         /* integration steps taken inside the box */
+} pivbos_ray_state;
+
+typedef struct pivbos_medium pivbos_medium;
+typedef struct pivbos_optics pivbos_optics;
+
+/* ---------------------------------------------------------------------------
+ * Medium (Sec. 3.2).  rho is a density grid [nz][ny][nx] (x fastest, float32,
+ * kg/m^3) with nodes at origin + (i, j, k) * spacing.  The library stores
+ * n - 1 = K_GD * rho (Eq. 1) and grad n at every node (second-order central
+ * differences, second-order one-sided at the faces, two-point differences on
+ * an axis with two nodes) as one float4 per node; rays are straight outside
+ * the box [origin, origin + (n-1) * spacing] and inside it follow the ray
+ * equation with n and grad n sampled trilinearly (clamped to the box).
+ *
+ * rho_on_device: 1 if rho is a device pointer on the current device, 0 for
+ * host memory (copied).  The call does not keep rho.  nx, ny, nz >= 2;
+ * spacing > 0; K_GD finite.  The grid build runs on `stream`; the handle is
+ * usable by work later on that stream (or after pivbos_sync).
+ * Errors: INVALID_ARG, OOM, CUDA.
+ * ------------------------------------------------------------------------- */
+pivbos_status pivbos_medium_create(const float* rho, int rho_on_device, int nx, int ny, int nz,
+                                   const double origin[3], const double spacing[3], double K_GD,
+                                   void* stream, pivbos_medium** out);
+
+/* Rebuild the node field of an existing medium from a new density grid of
+ * the same dimensions (time series, or one frame per step), on `stream`.
+ * Renders enqueued earlier on other streams must be complete. */
+pivbos_status pivbos_medium_refill(pivbos_medium* m, const float* rho, int rho_on_device, void* stream);
+
+void pivbos_medium_destroy(pivbos_medium* m);
+
+/* ---------------------------------------------------------------------------
+ * Optics and sensor (Sec. 3.3-3.4).  `surfaces` are applied in order
+ * (n_surfaces <= PIVBOS_MAX_SURFACES, may be 0); n_object is the refractive
+ * index the rays travel in before the first surface.  Rays are aimed at points
+ * drawn uniformly over the disk of radius aim_radius centred on the axis at
+ * z = aim_z (Sec. 3.1: a ray joins its source to a point on the lens).  The
+ * sensor is the plane z = sensor_z with width x height square pixels of
+ * pixel_pitch; pixel (i, j) covers x/pitch + width/2 in [i, i+1) and
+ * y/pitch + height/2 in [j, j+1).  The spot is a Gaussian of sigma = d_tau/4
+ * with d_tau from Eq. 8: dtau_rule 0 uses the printed 2.44 pi f# (M+1) lambda,
+ * dtau_rule 1 the textbook 2.44 f# (M+1) lambda.  The host arrays are copied.
+ * Errors: INVALID_ARG; UNSUPPORTED if sigma/pitch exceeds
+ * (PIVBOS_MAX_WINDOW - 2) / 6.
+ * ------------------------------------------------------------------------- */
+pivbos_status pivbos_optics_create(const pivbos_surface* surfaces, int n_surfaces, double n_object,
+                                   double aim_z, double aim_radius,
+                                   double f_number, double magnification, double wavelength,
+                                   int dtau_rule, double sensor_z, double pixel_pitch,
+                                   int width, int height, pivbos_optics** out);
+
+void pivbos_optics_destroy(pivbos_optics* o);
+
+/* ---------------------------------------------------------------------------
+ * Render (Sec. 3, all four steps; Sec. 3.5: one GPU thread per ray).
+ * Traces rays_per_source rays from each of n_sources sources ([n][3] float64,
+ * metres) and adds their spots into `image` ([height][width] int64, 32.32
+ * fixed point: every ray that reaches the sensor adds exactly 2^32, so the
+ * image is bit-identical from run to run and sums of partial renders equal
+ * the whole render).  Ray k of source s draws its lens point from
+ * Philox4x64-10 with counter (k, s, frame, 0) and key (seed, 0).  m may be
+ * NULL (uniform medium everywhere).  integrator: PIVBOS_EULER or PIVBOS_RK4;
+ * step: parameter step (t with dt = ds/n, so the arc length per step is about
+ * n * step), > 0.
+ *
+ * sources_on_device / image_on_device: 1 for device pointers, 0 for host
+ * memory.  With a host image the call copies it to the device, renders,
+ * copies it back and synchronises `stream` before returning.  stats, if not
+ * NULL, is a device array of PIVBOS_RAY_NSTATUS int64 counters that the call
+ * adds the final status of every ray into.
+ * Errors: INVALID_ARG; OVERFLOW if n_sources * rays_per_source > 2^31;
+ * OOM; CUDA.
+ * ------------------------------------------------------------------------- */
+pivbos_status pivbos_render(const pivbos_medium* m, const pivbos_optics* o,
+                            const double* sources, int64_t n_sources, int sources_on_device,
+                            int32_t rays_per_source, uint64_t seed, uint32_t frame,
+                            int integrator, double step,
+                            int64_t* image, int image_on_device, int64_t* stats, void* stream);
+
+/* Per-ray exit states for the parity checks: the same tracing as
+ * pivbos_render, without the deposit.  ray_ids (device, int64, may be NULL
+ * for "all rays in order") lists flattened ids source * rays_per_source + k;
+ * out (device) receives n_rays pivbos_ray_state.  Errors as pivbos_render. */
+pivbos_status pivbos_trace_exit_states(const pivbos_medium* m, const pivbos_optics* o,
+                                       const double* sources, int64_t n_sources, int sources_on_device,
+                                       int32_t rays_per_source, uint64_t seed, uint32_t frame,
+                                       int integrator, double step,
+                                       const int64_t* ray_ids, int64_t n_rays,
+                                       pivbos_ray_state* out, void* stream);
+
+/* int64 32.32 image -> float32 intensity in rays (value * 2^-32).  Device
+ * pointers, n_pixels >= 0. */
+pivbos_status pivbos_image_finalize(const int64_t* image, int64_t n_pixels, float* out, void* stream);
+
+/* Wait for `stream`, then return (and clear) the device status word of the
+ * current device: PIVBOS_OK or the first device-side error latched since the
+ * last call. */
+pivbos_status pivbos_sync(void* stream);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* pivbos_last_error(void);
+
+/* Kernel timing for measurement: when enabled, every kernel the library
+ * launches is bracketed by CUDA events on its stream.  pivbos_timing_read
+ * waits for the recorded events and returns the summed milliseconds and the
+ * launch count of kernels whose name starts with `prefix` since the last
+ * reset. */
+pivbos_status pivbos_timing_enable(int on);
+pivbos_status pivbos_timing_reset(void);
+pivbos_status pivbos_timing_read(const char* prefix, double* ms_total, int64_t* launches);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t pivbos_kernel_launches(void);
+
+/* Library version string. */
+const char* pivbos_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIVBOS_H */

@@ -1,0 +1,216 @@
+// Render kernels: the fused per-ray path (Sec. 3.1-3.4) with the deposit into
+// a shared-memory tile, the per-ray exit-state kernel used for parity, and
+// the fixed-point -> float finalisation.
+#include "trace.cuh"
+
+namespace pivbos {
+
+constexpr int kRenderThreads = 256;
+constexpr int kTileW = 32;
+constexpr int kTileH = 32;
+
+__device__ __forceinline__ void add_q(unsigned long long* tile, int ax, int ay, int64_t* image, int W,
+                                      int gx, int gy, unsigned long long q)
+{
+    const int tx = gx - ax, ty = gy - ay;
+    if ((unsigned)tx < (unsigned)kTileW && (unsigned)ty < (unsigned)kTileH) {
+        atomicAdd(&tile[ty * kTileW + tx], q);
+    } else {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * W + gx]), q);
+    }
+}
+
+// Quantise the spot of one ray and add it (tile if inside, image otherwise).
+__device__ __forceinline__ void deposit_ray(const DevOptics& o, double px, double py,
+                                            unsigned long long* tile, int ax, int ay, int64_t* image)
+{
+    SpotWindow sw;
+    spot_window(o, px, py, sw);
+    long long sum = 0, qmax = -1;
+    int imax = 0, jmax = 0;
+    for (int j = 0; j < sw.ny; ++j) {
+        const float wyj = sw.wy[j] * sw.scale;
+#pragma unroll
+        for (int i = 0; i < PIVBOS_MAX_WINDOW; ++i) {
+            if (i < sw.nx) {
+                const long long q = __float2ll_rn(sw.wx[i] * wyj);
+                sum += q;
+                if (q > qmax) { qmax = q; imax = i; jmax = j; }
+            }
+        }
+    }
+    const long long rem = 4294967296LL - sum;
+    for (int j = 0; j < sw.ny; ++j) {
+        const float wyj = sw.wy[j] * sw.scale;
+#pragma unroll
+        for (int i = 0; i < PIVBOS_MAX_WINDOW; ++i) {
+            if (i < sw.nx) {
+                long long q = __float2ll_rn(sw.wx[i] * wyj);
+                if (i == imax && j == jmax) q += rem;
+                if (q != 0)
+                    add_q(tile, ax, ay, image, o.W, sw.x0 + i, sw.y0 + j, (unsigned long long)q);
+            }
+        }
+    }
+}
+
+// Work: the flattened (Morton slot, ray) index space is cut into chunks of
+// rays_per_cta consecutive rays; a CTA takes one chunk, so its rays come
+// from one source or a few neighbouring ones and their spots fall in one
+// 32x32 shared tile anchored at the first hit.
+template <int INTEG>
+__global__ void __launch_bounds__(kRenderThreads)
+render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restrict__ stats,
+              uint32_t rays_per_cta, uint64_t total_rays)
+{
+    __shared__ unsigned long long tile[kTileW * kTileH];
+    __shared__ int s_anchor_tid;
+    __shared__ int s_ax, s_ay;
+    __shared__ unsigned long long s_cnt[PIVBOS_RAY_NSTATUS];
+
+    for (int q = threadIdx.x; q < kTileW * kTileH; q += blockDim.x) tile[q] = 0ull;
+    if (threadIdx.x == 0) {
+        s_anchor_tid = 0x7fffffff;
+        s_ax = -(1 << 28);
+        s_ay = -(1 << 28);
+    }
+    if (threadIdx.x < PIVBOS_RAY_NSTATUS) s_cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+
+    const uint64_t first = (uint64_t)blockIdx.x * rays_per_cta;
+    const uint64_t last = min(first + rays_per_cta, total_rays);
+    const uint32_t rps = P.rays_per_source;
+    unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
+
+    uint64_t idx = first + threadIdx.x;
+    RayOut r;
+    r.status = -1;
+    // first ray of every thread: its hit anchors the tile
+    if (idx < last) {
+        const uint32_t flat = (uint32_t)idx;
+        const uint32_t slot = flat / rps, k = flat - slot * rps;
+        const uint32_t sid = P.perm ? __ldg(P.perm + slot) : slot;
+        const double* s = P.sources + 3 * (size_t)sid;
+        trace_ray<INTEG>(P, __ldg(s), __ldg(s + 1), __ldg(s + 2), sid, k, r, nullptr);
+        if (r.status == PIVBOS_RAY_REACHED) atomicMin(&s_anchor_tid, (int)threadIdx.x);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x == s_anchor_tid) {
+        s_ax = (int)floor(r.px) - kTileW / 2;
+        s_ay = (int)floor(r.py) - kTileH / 2;
+    }
+    __syncthreads();
+    const int ax = s_ax, ay = s_ay;
+    if (idx < last) {
+        cnt[r.status]++;
+        if (r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, tile, ax, ay, image);
+    }
+    for (idx += blockDim.x; idx < last; idx += blockDim.x) {
+        const uint32_t flat = (uint32_t)idx;
+        const uint32_t slot = flat / rps, k = flat - slot * rps;
+        const uint32_t sid = P.perm ? __ldg(P.perm + slot) : slot;
+        const double* s = P.sources + 3 * (size_t)sid;
+        trace_ray<INTEG>(P, __ldg(s), __ldg(s + 1), __ldg(s + 2), sid, k, r, nullptr);
+        cnt[r.status]++;
+        if (r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, tile, ax, ay, image);
+    }
+    if (stats) {
+#pragma unroll
+        for (int q = 0; q < PIVBOS_RAY_NSTATUS; ++q) {
+            unsigned v = cnt[q];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[q], (unsigned long long)v);
+        }
+    }
+    __syncthreads();
+    // flush the tile: one global atomic per touched pixel
+    for (int q = threadIdx.x; q < kTileW * kTileH; q += blockDim.x) {
+        const unsigned long long v = tile[q];
+        if (v) {
+            const int gx = ax + (q % kTileW), gy = ay + (q / kTileW);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * P.o.W + gx]), v);
+        }
+    }
+    if (stats && threadIdx.x < PIVBOS_RAY_NSTATUS && s_cnt[threadIdx.x])
+        atomicAdd(reinterpret_cast<unsigned long long*>(&stats[threadIdx.x]), s_cnt[threadIdx.x]);
+}
+
+template <int INTEG>
+__global__ void __launch_bounds__(128)
+trace_states_kernel(const TraceParams P, const int64_t* __restrict__ ray_ids, int64_t n,
+                    pivbos_ray_state* __restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int64_t id = ray_ids ? ray_ids[q] : q;
+    const uint32_t rps = P.rays_per_source;
+    pivbos_ray_state st;
+    RayOut r;
+    if (id < 0 || id >= (int64_t)P.n_sources * rps) {
+        // an id outside the render: reported as a miss with no geometry
+        for (int a = 0; a < 3; ++a) { st.vol_pos[a] = 0.0; st.vol_dir[a] = 0.0; st.sensor_dir[a] = 0.0; }
+        st.sensor_xy[0] = st.sensor_xy[1] = 0.0;
+        st.status = PIVBOS_RAY_MISS;
+        st.steps = 0;
+        atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_INVALID_ARG);
+    } else {
+        const uint32_t sid = (uint32_t)(id / rps), k = (uint32_t)(id - (int64_t)sid * rps);
+        const double* s = P.sources + 3 * (size_t)sid;
+        trace_ray<INTEG>(P, s[0], s[1], s[2], sid, k, r, &st);
+    }
+    out[q] = st;
+}
+
+__global__ void finalize_kernel(const int64_t* __restrict__ img, int64_t n, float* __restrict__ out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride)
+        out[q] = (float)((double)img[q] * 0x1p-32);
+}
+
+cudaError_t launch_render(const TraceParams& p, int integrator, int64_t* image, int64_t* stats,
+                          uint32_t rays_per_cta, cudaStream_t s)
+{
+    const uint64_t total = (uint64_t)p.n_sources * p.rays_per_source;
+    if (total == 0) return cudaSuccess;
+    const uint64_t blocks = (total + rays_per_cta - 1) / rays_per_cta;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+    timing_begin("render", s);
+    if (integrator == PIVBOS_RK4)
+        render_kernel<PIVBOS_RK4><<<(unsigned)blocks, kRenderThreads, 0, s>>>(p, image, stats, rays_per_cta, total);
+    else
+        render_kernel<PIVBOS_EULER><<<(unsigned)blocks, kRenderThreads, 0, s>>>(p, image, stats, rays_per_cta, total);
+    timing_end("render", s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_states(const TraceParams& p, int integrator, const int64_t* ray_ids,
+                                int64_t n_rays, pivbos_ray_state* out, cudaStream_t s)
+{
+    if (n_rays == 0) return cudaSuccess;
+    const int64_t blocks = (n_rays + 127) / 128;
+    if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+    timing_begin("trace_states", s);
+    if (integrator == PIVBOS_RK4)
+        trace_states_kernel<PIVBOS_RK4><<<(unsigned)blocks, 128, 0, s>>>(p, ray_ids, n_rays, out);
+    else
+        trace_states_kernel<PIVBOS_EULER><<<(unsigned)blocks, 128, 0, s>>>(p, ray_ids, n_rays, out);
+    timing_end("trace_states", s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const int64_t* image, int64_t n, float* out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    timing_begin("finalize", s);
+    finalize_kernel<<<(unsigned)blocks, 256, 0, s>>>(image, n, out);
+    timing_end("finalize", s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace pivbos

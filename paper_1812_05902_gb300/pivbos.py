@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libpivbos.so (include/pivbos.h).
+
+Argument marshalling only: every step of the ray-tracing path runs in the
+CUDA kernels of the library.  PyTorch is used for device memory and streams:
+functions that take device buffers accept CUDA tensors (their ``data_ptr()``
+is passed) and run on ``torch.cuda.current_stream()`` unless a stream is
+given.  If the library is missing, importing the binding raises; there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpivbos.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_OVERFLOW, ERR_UNSUPPORTED = range(7)
+RAY_REACHED, RAY_STOP, RAY_MISS, RAY_TIR, RAY_OFF_SENSOR, RAY_MAXSTEP = range(6)
+RAY_NSTATUS = 6
+SURF_SPHERE, SURF_PLANE, SURF_IDEAL_THIN, SURF_STOP = range(4)
+EULER, RK4 = 0, 1
+MAX_SURFACES = 16
+MAX_WINDOW = 12
+
+RAY_STATE = np.dtype([
+    ("vol_pos", "<f8", (3,)), ("vol_dir", "<f8", (3,)),
+    ("sensor_xy", "<f8", (2,)), ("sensor_dir", "<f8", (3,)),
+    ("status", "<i4"), ("steps", "<i4"),
+])
+assert RAY_STATE.itemsize == 96
+
+
+class pivbos_surface(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("reserved", ctypes.c_int32), ("z_vertex", ctypes.c_double),
+                ("radius", ctypes.c_double), ("focal", ctypes.c_double), ("n_after", ctypes.c_double),
+                ("clear_radius", ctypes.c_double)]
+
+
+class PivbosError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("pivbos status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpivbos.so is not built (run __graft_entry__.build() or "
+                          "python paper_1812_05902_gb300/build.py)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    I32, I64, U32, U64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+    sig = {
+        "pivbos_medium_create": ([P, I, I, I, I, P, P, D, P, P], I),
+        "pivbos_medium_refill": ([P, P, I, P], I),
+        "pivbos_medium_destroy": ([P], None),
+        "pivbos_optics_create": ([P, I, D, D, D, D, D, D, I, D, D, I, I, P], I),
+        "pivbos_optics_destroy": ([P], None),
+        "pivbos_render": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
+        "pivbos_trace_exit_states": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I64, P, P], I),
+        "pivbos_image_finalize": ([P, I64, P, P], I),
+        "pivbos_sync": ([P], I),
+        "pivbos_last_error": ([], ctypes.c_char_p),
+        "pivbos_timing_enable": ([I], I),
+        "pivbos_timing_reset": ([], I),
+        "pivbos_timing_read": ([ctypes.c_char_p, ctypes.POINTER(D), ctypes.POINTER(I64)], I),
+        "pivbos_version": ([], ctypes.c_char_p),
+        "pivbos_kernel_launches": ([], I64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+_lib = _load()
+EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destroy", "pivbos_optics_create",
+            "pivbos_optics_destroy", "pivbos_render", "pivbos_trace_exit_states", "pivbos_image_finalize",
+            "pivbos_sync", "pivbos_last_error", "pivbos_timing_enable", "pivbos_timing_reset",
+            "pivbos_timing_read", "pivbos_version", "pivbos_kernel_launches")
+
+
+def lib():
+    return _lib
+
+
+def _check(st):
+    if st != OK:
+        raise PivbosError(st, _lib.pivbos_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _addr(buf):
+    """(address, on_device) of a CUDA tensor or a C-contiguous numpy array."""
+    if buf is None:
+        return None, 0
+    if hasattr(buf, "data_ptr"):
+        if buf.is_cuda:
+            if not buf.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return ctypes.c_void_p(buf.data_ptr()), 1
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(buf.data_ptr()), 0
+    if not buf.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(buf.ctypes.data), 0
+
+
+# ---------------------------------------------------------------------------
+# C-named entry points (same names and argument order as include/pivbos.h)
+# ---------------------------------------------------------------------------
+def pivbos_medium_create(rho, nx, ny, nz, origin, spacing, K_GD, stream=None):
+    p, on_dev = _addr(rho)
+    o = (ctypes.c_double * 3)(*origin)
+    h = (ctypes.c_double * 3)(*spacing)
+    out = ctypes.c_void_p()
+    _check(_lib.pivbos_medium_create(p, on_dev, nx, ny, nz, o, h, K_GD, _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def pivbos_medium_refill(m, rho, stream=None):
+    p, on_dev = _addr(rho)
+    _check(_lib.pivbos_medium_refill(m, p, on_dev, _stream(stream)))
+
+
+def pivbos_medium_destroy(m):
+    _lib.pivbos_medium_destroy(m)
+
+
+def pivbos_optics_create(surfaces, n_object, aim_z, aim_radius, f_number, magnification, wavelength,
+                         dtau_rule, sensor_z, pixel_pitch, width, height):
+    n = len(surfaces)
+    arr = (pivbos_surface * max(n, 1))()
+    for i, s in enumerate(surfaces):
+        arr[i] = pivbos_surface(int(s[0]), 0, *[float(v) for v in s[1:6]])
+    out = ctypes.c_void_p()
+    _check(_lib.pivbos_optics_create(arr if n else None, n, n_object, aim_z, aim_radius, f_number, magnification,
+                                     wavelength, dtau_rule, sensor_z, pixel_pitch, width, height,
+                                     ctypes.byref(out)))
+    return out
+
+
+def pivbos_optics_destroy(o):
+    _lib.pivbos_optics_destroy(o)
+
+
+def pivbos_render(m, o, sources, n_sources, rays_per_source, seed, frame, integrator, step, image,
+                  stats=None, stream=None):
+    sp, s_dev = _addr(sources)
+    ip, i_dev = _addr(image)
+    st_p, _ = _addr(stats)
+    _check(_lib.pivbos_render(m, o, sp, n_sources, s_dev, rays_per_source, seed, frame, integrator, step,
+                              ip, i_dev, st_p, _stream(stream)))
+
+
+def pivbos_trace_exit_states(m, o, sources, n_sources, rays_per_source, seed, frame, integrator, step,
+                             ray_ids, n_rays, out, stream=None):
+    sp, s_dev = _addr(sources)
+    rp, _ = _addr(ray_ids)
+    op, _ = _addr(out)
+    _check(_lib.pivbos_trace_exit_states(m, o, sp, n_sources, s_dev, rays_per_source, seed, frame,
+                                         integrator, step, rp, n_rays, op, _stream(stream)))
+
+
+def pivbos_image_finalize(image, n_pixels, out, stream=None):
+    ip, _ = _addr(image)
+    op, _ = _addr(out)
+    _check(_lib.pivbos_image_finalize(ip, n_pixels, op, _stream(stream)))
+
+
+def pivbos_sync(stream=None):
+    _check(_lib.pivbos_sync(_stream(stream)))
+
+
+def pivbos_last_error():
+    return _lib.pivbos_last_error().decode()
+
+
+def pivbos_timing_enable(on=True):
+    _check(_lib.pivbos_timing_enable(1 if on else 0))
+
+
+def pivbos_timing_reset():
+    _check(_lib.pivbos_timing_reset())
+
+
+def pivbos_timing_read(prefix):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(_lib.pivbos_timing_read(prefix.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def pivbos_kernel_launches():
+    return int(_lib.pivbos_kernel_launches())
+
+
+def pivbos_version():
+    return _lib.pivbos_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# RAII helpers over scenes.Frame descriptions
+# ---------------------------------------------------------------------------
+class Medium:
+    def __init__(self, scene_medium, rho=None, stream=None):
+        r = scene_medium.rho if rho is None else rho
+        if not hasattr(r, "data_ptr"):
+            r = np.ascontiguousarray(r, dtype=np.float32)
+        nx, ny, nz = scene_medium.dims
+        self.h = pivbos_medium_create(r, nx, ny, nz, scene_medium.origin, scene_medium.spacing,
+                                      scene_medium.K, stream)
+
+    def refill(self, rho, stream=None):
+        pivbos_medium_refill(self.h, rho, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pivbos_medium_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+class Optics:
+    def __init__(self, so):
+        self.W, self.H = so.width, so.height
+        self.h = pivbos_optics_create([s.as_row() for s in so.surfaces], so.n_object, so.aim_z, so.aim_r,
+                                      so.f_number, so.magnification, so.wavelength, so.dtau_rule,
+                                      so.sensor_z, so.pitch, so.width, so.height)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pivbos_optics_destroy(self.h)
+            self.h = None
+
+    __del__ = close
