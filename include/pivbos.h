@@ -171,6 +171,33 @@ pivbos_status pivbos_render(const pivbos_medium* m, const pivbos_optics* o,
                             int integrator, double step,
                             int64_t* image, int image_on_device, int64_t* stats, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Render without allocating (no counterpart in the paper: a library
+ * facility).  For callers that cannot call cudaMalloc -- a host application
+ * that has given the whole device to its own memory pool and forbids
+ * allocations outside it, or a latency-critical loop in which the implicit
+ * synchronisation of cudaMalloc/cudaFree would stall other streams.  Same
+ * arguments and result as pivbos_render, except that `sources` and `image`
+ * must be device pointers (stats too, if not NULL) and the call never
+ * allocates or frees memory.  Its scratch (Morton keys and the source
+ * permutation, ~1.5 MiB) is a fixed array in the library's device image,
+ * held by every GPU that loads the library until the process exits.
+ *  - n_sources above PIVBOS_NOALLOC_MAX_SOURCES: PIVBOS_ERR_UNSUPPORTED.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before capturing any stream.
+ *  - Every call on a device uses the same array, which keeps the previous
+ *    call's contents (the call rewrites what it reads).  Calls that overlap
+ *    on the GPU (concurrent streams) race on it: serialise them.
+ *  - Keep kernel timing (pivbos_timing_enable) off: timing creates CUDA
+ *    events.
+ * ------------------------------------------------------------------------- */
+#define PIVBOS_NOALLOC_MAX_SOURCES (1 << 17)
+pivbos_status pivbos_render_noalloc(const pivbos_medium* m, const pivbos_optics* o,
+                                    const double* sources, int64_t n_sources, int32_t rays_per_source,
+                                    uint64_t seed, uint32_t frame, int integrator, double step,
+                                    int64_t* image, int64_t* stats, void* stream);
+
 /* Per-ray exit states for the parity checks: the same tracing as
  * pivbos_render, without the deposit.  ray_ids (device, int64, may be NULL
  * for "all rays in order") lists flattened ids source * rays_per_source + k;

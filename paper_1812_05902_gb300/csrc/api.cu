@@ -15,21 +15,7 @@
 #include <vector>
 
 #include "common.cuh"
-
-struct pivbos_medium {
-    int device;
-    int n[3];
-    double origin[3];
-    double spacing[3];
-    double K;
-    float4* field;
-    float* rho_scratch;   // device copy of host rho during a (re)fill
-};
-
-struct pivbos_optics {
-    int device;
-    pivbos::DevOptics d;
-};
+#include "handles.cuh"
 
 namespace pivbos {
 namespace {
@@ -208,6 +194,8 @@ pivbos_status prepare(const pivbos_medium* m, const pivbos_optics* o, const doub
 }
 
 }  // namespace
+
+void set_last_error(const char* msg) { t_err = msg; }
 
 void timing_begin(const char* name, cudaStream_t s)
 {

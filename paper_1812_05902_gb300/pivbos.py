@@ -68,6 +68,7 @@ def _load():
         "pivbos_timing_read": ([ctypes.c_char_p, ctypes.POINTER(D), ctypes.POINTER(I64)], I),
         "pivbos_version": ([], ctypes.c_char_p),
         "pivbos_kernel_launches": ([], I64),
+        "pivbos_render_noalloc": ([P, P, P, I64, I32, U64, U32, I, D, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -80,7 +81,8 @@ _lib = _load()
 EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destroy", "pivbos_optics_create",
             "pivbos_optics_destroy", "pivbos_render", "pivbos_trace_exit_states", "pivbos_image_finalize",
             "pivbos_sync", "pivbos_last_error", "pivbos_timing_enable", "pivbos_timing_reset",
-            "pivbos_timing_read", "pivbos_version", "pivbos_kernel_launches")
+            "pivbos_timing_read", "pivbos_version", "pivbos_kernel_launches", "pivbos_render_noalloc")
+NOALLOC_MAX_SOURCES = 1 << 17
 
 
 def lib():
@@ -163,6 +165,17 @@ def pivbos_render(m, o, sources, n_sources, rays_per_source, seed, frame, integr
     st_p, _ = _addr(stats)
     _check(_lib.pivbos_render(m, o, sp, n_sources, s_dev, rays_per_source, seed, frame, integrator, step,
                               ip, i_dev, st_p, _stream(stream)))
+
+
+def pivbos_render_noalloc(m, o, sources, n_sources, rays_per_source, seed, frame, integrator, step, image,
+                          stats=None, stream=None):
+    """pivbos_render without any allocation: sources, image (and stats) must be
+    CUDA tensors; scratch comes from a fixed device array in the library."""
+    sp, _ = _addr(sources)
+    ip, _ = _addr(image)
+    st_p, _ = _addr(stats)
+    _check(_lib.pivbos_render_noalloc(m, o, sp, n_sources, rays_per_source, seed, frame, integrator, step,
+                                      ip, st_p, _stream(stream)))
 
 
 def pivbos_trace_exit_states(m, o, sources, n_sources, rays_per_source, seed, frame, integrator, step,
