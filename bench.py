@@ -52,15 +52,17 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _frames(workload):
+def _frames(workload, scale=1.0):
+    """The workload's frames; scale < 1 shrinks source and ray counts (used
+    only for profiling captures, never for a reported number)."""
     if workload == "c1":
-        return scenes.c1()
+        return scenes.c1(scale=scale)
     if workload == "c0":
-        return scenes.c0()
+        return scenes.c0(scale=scale)
     if workload == "c2":
-        return scenes.c2()
+        return scenes.c2(scale=scale)
     if workload == "c4":
-        return scenes.c4()
+        return scenes.c4(scale=scale)
     raise SystemExit("unknown workload %s" % workload)
 
 
@@ -203,7 +205,7 @@ def run_gpu(args, rank, world):
     libbuild.build()
     from paper_1812_05902_gb300 import pivbos as P
 
-    frames = _frames(args.workload)
+    frames = _frames(args.workload, args.scale)
     # weak scaling: every rank renders its own images (seed offset by rank)
     for fr in frames:
         fr.seed = fr.seed + 1000003 * rank
@@ -310,7 +312,9 @@ def run_gpu(args, rank, world):
             "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAMES[args.workload], "name": args.workload,
+            "config": {"workload": WORKLOAD_NAMES[args.workload] + ("" if args.scale == 1.0 else
+                                                                     " (scaled by %g)" % args.scale),
+                       "name": args.workload,
                        "rays_per_step": rays_step, "images_per_step": len(frames), "l2": "flushed between steps",
                        "parallelism": "replicas (weak)" if world > 1 else "single GPU"},
             "gpu_launches": int(launches), "clocks": clk, "roofline": rf, "e2e": e2e, "cpu_baseline": cpu,
@@ -328,6 +332,8 @@ def main():
     ap.add_argument("--workload", default="c1", choices=sorted(WORKLOAD_NAMES))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload (profiling captures only; the JSON line says so)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

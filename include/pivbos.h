@@ -179,8 +179,8 @@ pivbos_status pivbos_render(const pivbos_medium* m, const pivbos_optics* o,
  * synchronisation of cudaMalloc/cudaFree would stall other streams.  Same
  * arguments and result as pivbos_render, except that `sources` and `image`
  * must be device pointers (stats too, if not NULL) and the call never
- * allocates or frees memory.  Its scratch (Morton keys and the source
- * permutation, ~1.5 MiB) is a fixed array in the library's device image,
+ * allocates or frees memory.  Its scratch (Morton keys, the source
+ * permutation and a sorted copy of the sources, ~4.5 MiB) is a fixed array in the library's device image,
  * held by every GPU that loads the library until the process exits.
  *  - n_sources above PIVBOS_NOALLOC_MAX_SOURCES: PIVBOS_ERR_UNSUPPORTED.
  *  - The first call on a device looks up the array's device address

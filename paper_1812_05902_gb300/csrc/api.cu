@@ -105,6 +105,12 @@ pivbos_status check_device_ptr(const void* p, int dev, const char* what)
 
 bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
+dfc to_dfc(double v)
+{
+    const float hi = (float)v;
+    return dfc{hi, (float)(v - (double)hi)};
+}
+
 uint32_t next_pow2(uint32_t v)
 {
     uint32_t p = 1;
@@ -165,10 +171,10 @@ pivbos_status prepare(const pivbos_medium* m, const pivbos_optics* o, const doub
             p.m.n[a] = m->n[a];
             p.m.h[a] = (float)m->spacing[a];
             p.m.inv_h[a] = (float)(1.0 / m->spacing[a]);
-            p.m.inv_hd[a] = 1.0 / m->spacing[a];
-            p.m.origin[a] = m->origin[a];
-            p.m.lo[a] = m->origin[a];
-            p.m.hi[a] = m->origin[a] + (double)(m->n[a] - 1) * m->spacing[a];
+            p.m.inv_hd[a] = to_dfc(1.0 / m->spacing[a]);
+            p.m.origin[a] = to_dfc(m->origin[a]);
+            p.m.lo[a] = to_dfc(m->origin[a]);
+            p.m.hi[a] = to_dfc(m->origin[a] + (double)(m->n[a] - 1) * m->spacing[a]);
             const double L = (double)(m->n[a] - 1) * m->spacing[a];
             diag2 += L * L;
         }
@@ -186,6 +192,7 @@ pivbos_status prepare(const pivbos_medium* m, const pivbos_optics* o, const doub
     p.frame = frame;
     p.step = (float)step;
     p.step_d = step;
+    p.step_df = to_dfc(step);
     st = status_word(dev, &p.status_word);
     if (st) return st;
     out->dev = dev;
@@ -365,30 +372,39 @@ pivbos_status pivbos_optics_create(const pivbos_surface* surfaces, int n_surface
     DevOptics& d = o->d;
     memset(&d, 0, sizeof d);
     d.ns = n_surfaces;
+    double n_cur = n_object;
     for (int i = 0; i < n_surfaces; ++i) {
         const pivbos_surface& s = surfaces[i];
-        d.s[i].type = s.type;
-        d.s[i].z = s.z_vertex;
-        d.s[i].R = s.radius;
-        d.s[i].f = s.focal;
-        d.s[i].n_after = s.n_after;
-        d.s[i].clear_r2 = s.clear_radius * s.clear_radius;
+        DevSurface& D = d.s[i];
+        // a sphere of zero radius is a flat refracting surface
+        D.type = (s.type == PIVBOS_SURF_SPHERE && s.radius == 0.0) ? PIVBOS_SURF_PLANE : s.type;
+        D.R_f = (float)s.radius;
+        D.clear_r2 = (float)(s.clear_radius * s.clear_radius);
+        D.z = to_dfc(s.z_vertex);
+        D.R = to_dfc(s.radius);
+        D.invR = to_dfc(s.radius != 0.0 ? 1.0 / s.radius : 0.0);
+        D.inv_f = to_dfc(s.type == PIVBOS_SURF_IDEAL_THIN ? 1.0 / s.focal : 0.0);
+        if (D.type == PIVBOS_SURF_SPHERE || D.type == PIVBOS_SURF_PLANE) {
+            const double eta = n_cur / s.n_after;
+            D.eta = to_dfc(eta);
+            D.eta2 = to_dfc(eta * eta);
+            n_cur = s.n_after;
+        }
     }
     d.W = width;
     d.H = height;
-    d.n_object = n_object;
-    d.aim_z = aim_z;
-    d.aim_r = aim_radius;
+    d.aim_z = to_dfc(aim_z);
+    d.aim_r = to_dfc(aim_radius);
     const double dtau = 2.44 * (dtau_rule == 0 ? M_PI : 1.0) * f_number * (magnification + 1.0) * wavelength;
     const double sigma = dtau / 4.0;
     const double sp = sigma / pixel_pitch;
     d.sigma_px = (float)sp;
-    d.win3 = 3.0 * sp;
+    d.win3 = (float)(3.0 * sp);
     d.inv_sqrt2_sigma = (float)(1.0 / (M_SQRT2 * sp));
-    d.sensor_z = sensor_z;
-    d.inv_pitch = 1.0 / pixel_pitch;
-    d.half_w = 0.5 * width;
-    d.half_h = 0.5 * height;
+    d.sensor_z = to_dfc(sensor_z);
+    d.inv_pitch = to_dfc(1.0 / pixel_pitch);
+    d.half_w = 0.5f * (float)width;
+    d.half_h = 0.5f * (float)height;
     *out = o;
     return PIVBOS_OK;
 }
@@ -422,15 +438,17 @@ pivbos_status pivbos_render(const pivbos_medium* m, const pivbos_optics* o, cons
     const uint32_t n = (uint32_t)n_sources;
     const uint32_t n_pow2 = next_pow2(n < 2 ? 2 : n);
     const size_t img_bytes = (size_t)o->d.W * o->d.H * sizeof(int64_t);
-    // scratch: keys | perm | sources copy | image copy
+    // scratch: keys | perm | double-float sources | sources copy | image copy
     const size_t off_perm = (size_t)n_pow2 * 8;
-    const size_t off_src = off_perm + (((size_t)n * 4 + 255) & ~(size_t)255);
+    const size_t off_sdf = off_perm + (((size_t)n * 4 + 255) & ~(size_t)255);
+    const size_t off_src = off_sdf + (((size_t)n * 24 + 255) & ~(size_t)255);
     const size_t off_img = off_src + (sources_on_device ? 0 : (((size_t)n * 24 + 255) & ~(size_t)255));
     const size_t bytes = off_img + (image_on_device ? 0 : img_bytes);
     char* scratch = nullptr;
     PV_CUDA(cudaMallocAsync((void**)&scratch, bytes, s), "render scratch allocation");
     uint64_t* keys = (uint64_t*)scratch;
     uint32_t* perm = (uint32_t*)(scratch + off_perm);
+    float2* sdf = (float2*)(scratch + off_sdf);
     const double* dsrc = sources;
     int64_t* dimg = image;
     cudaError_t e = cudaSuccess;
@@ -442,10 +460,11 @@ pivbos_status pivbos_render(const pivbos_medium* m, const pivbos_optics* o, cons
         dimg = (int64_t*)(scratch + off_img);
         e = cudaMemcpyAsync(dimg, image, img_bytes, cudaMemcpyHostToDevice, s);
     }
-    if (e == cudaSuccess) e = launch_morton_sort(dsrc, n, keys, n_pow2, perm, s);
+    if (e == cudaSuccess) e = launch_morton_sort(dsrc, n, keys, n_pow2, perm, sdf, s);
     if (e == cudaSuccess) {
         pr.p.sources = dsrc;
         pr.p.perm = perm;
+        pr.p.src_df = sdf;
         e = launch_render(pr.p, integrator, dimg, stats, rays_per_cta_setting(), s);
     }
     if (e == cudaSuccess && !image_on_device)

@@ -8,6 +8,11 @@
 
 namespace pivbos {
 
+// Double-float constant (hi + lo), prepared on the host.
+struct dfc {
+    float hi, lo;
+};
+
 // Device view of a medium: one float4 {n-1, dn/dx, dn/dy, dn/dz} per node,
 // x fastest.  Grid coordinates g = (x - origin) / spacing.
 struct DevMedium {
@@ -15,41 +20,41 @@ struct DevMedium {
     int n[3];
     float h[3];          // spacing (float)
     float inv_h[3];      // 1 / spacing (float)
-    double origin[3];
-    double inv_hd[3];    // 1 / spacing (double)
-    double lo[3], hi[3]; // box corners
+    dfc origin[3];       // node (0,0,0)
+    dfc inv_hd[3];       // 1 / spacing (double-float)
+    dfc lo[3], hi[3];    // box corners
     int max_steps;       // step budget for a parameter step of 1 m (scaled per render)
     int present;         // 0 = no medium: rays are straight everywhere
 };
 
 struct DevSurface {
     int type;
-    int pad;
-    double z, R, f, n_after, clear_r2;
+    float R_f;         // signed radius (FP32, for sign tests)
+    float clear_r2;    // clear radius squared (FP32, for the aperture tests)
+    float pad;
+    dfc z, R, invR;    // vertex position, radius, 1/R
+    dfc eta, eta2;     // n_before / n_after and its square (refracting surfaces)
+    dfc inv_f;         // 1 / focal length (ideal thin lens)
 };
 
 struct DevOptics {
     int ns;
     int W, H;
-    int pad;
+    float win3;            // 3 sigma in pixels
     DevSurface s[PIVBOS_MAX_SURFACES];
-    double n_object;
-    double aim_z;
-    double aim_r;
-    float sigma_px;
-    float pad2;        // spot sigma in pixels
-    double sensor_z;
-    double inv_pitch;
-    double half_w, half_h; // W/2, H/2
-    double win3;           // 3 sigma in pixels (double, for the window bounds)
+    dfc aim_z, aim_r;
+    dfc sensor_z, inv_pitch;
+    float half_w, half_h;  // W/2, H/2
     float inv_sqrt2_sigma; // 1 / (sqrt(2) sigma_px)
+    float sigma_px;
 };
 
 struct TraceParams {
     DevMedium m;
     DevOptics o;
-    const double* sources;    // [S][3] device
+    const double* sources;    // [S][3] device (FP64 as given)
     const uint32_t* perm;     // Morton order of sources (nullptr = identity)
+    const float2* src_df;     // [slot][3] sources in Morton order as double-float (render only)
     uint32_t n_sources;
     uint32_t rays_per_source;
     uint64_t seed;
@@ -57,14 +62,17 @@ struct TraceParams {
     int max_steps;
     float step;               // parameter step
     double step_d;
+    dfc step_df;
     int* status_word;         // device status word (first error latched)
 };
 
 // Internal launchers (each defined in the translation unit holding the kernel).
 cudaError_t launch_medium_prep(const float* rho, float4* field, int nx, int ny, int nz,
                                const double spacing[3], double K, cudaStream_t s);
+// Sort the sources along a Morton curve: perm[slot] = source index, and
+// src_df[3 * slot + a] = coordinate a of that source as double-float.
 cudaError_t launch_morton_sort(const double* sources, uint32_t n, uint64_t* keys_scratch,
-                               uint32_t n_pow2, uint32_t* perm, cudaStream_t s);
+                               uint32_t n_pow2, uint32_t* perm, float2* src_df, cudaStream_t s);
 cudaError_t launch_render(const TraceParams& p, int integrator, int64_t* image, int64_t* stats,
                           uint32_t rays_per_cta, cudaStream_t s);
 cudaError_t launch_trace_states(const TraceParams& p, int integrator, const int64_t* ray_ids,

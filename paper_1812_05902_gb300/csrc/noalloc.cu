@@ -4,7 +4,8 @@
 // forbids allocations outside it, or a latency-critical loop in which the
 // implicit device-wide synchronisation of cudaMalloc/cudaFree would stall
 // other streams.  This entry point takes its only scratch (the Morton keys
-// and the source permutation) from a file-scope device array of fixed size,
+// and the source permutation and sorted copy) from a file-scope device array
+// of fixed size,
 // which every GPU that loads the library holds until the process exits.
 #include <math.h>
 #include <stdarg.h>
@@ -21,11 +22,13 @@ namespace {
 constexpr size_t kStatusBytes = 256;
 constexpr size_t kKeysBytes = (size_t)PIVBOS_NOALLOC_MAX_SOURCES * sizeof(uint64_t);
 constexpr size_t kPermBytes = (size_t)PIVBOS_NOALLOC_MAX_SOURCES * sizeof(uint32_t);
-constexpr size_t kScratchBytes = kStatusBytes + kKeysBytes + kPermBytes;
+constexpr size_t kSrcBytes = (size_t)PIVBOS_NOALLOC_MAX_SOURCES * 3 * sizeof(float2);
+constexpr size_t kScratchBytes = kStatusBytes + kKeysBytes + kPermBytes + kSrcBytes;
 
 }  // namespace
 
-// [status word | sort keys (next power of two of n) | permutation (n)]
+// [status word | sort keys (next power of two of n) | permutation (n) |
+//  sources in Morton order as double-float (n x 3)]
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
@@ -60,6 +63,12 @@ pivbos_status scratch_address(int dev, unsigned char** out)
     }
     *out = g_scratch_addr[dev];
     return PIVBOS_OK;
+}
+
+pivbos::dfc split(double v)
+{
+    const float hi = (float)v;
+    return pivbos::dfc{hi, (float)(v - (double)hi)};
 }
 
 pivbos_status device_buffer(const void* p, int dev, const char* what)
@@ -128,10 +137,10 @@ extern "C" pivbos_status pivbos_render_noalloc(const pivbos_medium* m, const piv
             p.m.n[a] = m->n[a];
             p.m.h[a] = (float)m->spacing[a];
             p.m.inv_h[a] = (float)(1.0 / m->spacing[a]);
-            p.m.inv_hd[a] = 1.0 / m->spacing[a];
-            p.m.origin[a] = m->origin[a];
-            p.m.lo[a] = m->origin[a];
-            p.m.hi[a] = m->origin[a] + (double)(m->n[a] - 1) * m->spacing[a];
+            p.m.inv_hd[a] = split(1.0 / m->spacing[a]);
+            p.m.origin[a] = split(m->origin[a]);
+            p.m.lo[a] = split(m->origin[a]);
+            p.m.hi[a] = split(m->origin[a] + (double)(m->n[a] - 1) * m->spacing[a]);
             const double L = (double)(m->n[a] - 1) * m->spacing[a];
             diag2 += L * L;
         }
@@ -147,6 +156,7 @@ extern "C" pivbos_status pivbos_render_noalloc(const pivbos_medium* m, const piv
     p.frame = frame;
     p.step = (float)step;
     p.step_d = step;
+    p.step_df = split(step);
 
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = (uint32_t)n_sources;
@@ -155,14 +165,16 @@ extern "C" pivbos_status pivbos_render_noalloc(const pivbos_medium* m, const piv
     int* status = (int*)scratch;
     uint64_t* keys = (uint64_t*)(scratch + kStatusBytes);
     uint32_t* perm = (uint32_t*)(scratch + kStatusBytes + kKeysBytes);
+    float2* src_df = (float2*)(scratch + kStatusBytes + kKeysBytes + kPermBytes);
     // the array keeps the previous call's contents: the keys and the
     // permutation are fully rewritten below; the status word is cleared
     e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e != cudaSuccess) return err(PIVBOS_ERR_CUDA, "status clear: %s", cudaGetErrorString(e));
     p.status_word = status;
-    e = pivbos::launch_morton_sort(sources, n, keys, n_pow2, perm, s);
+    e = pivbos::launch_morton_sort(sources, n, keys, n_pow2, perm, src_df, s);
     if (e != cudaSuccess) return err(PIVBOS_ERR_CUDA, "sort: %s", cudaGetErrorString(e));
     p.perm = perm;
+    p.src_df = src_df;
     e = pivbos::launch_render(p, integrator, image, stats, 2048u, s);
     if (e != cudaSuccess) return err(PIVBOS_ERR_CUDA, "render: %s", cudaGetErrorString(e));
     return PIVBOS_OK;

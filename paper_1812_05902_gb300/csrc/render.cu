@@ -21,7 +21,7 @@ __device__ __forceinline__ void add_q(unsigned long long* tile, int ax, int ay, 
 }
 
 // Quantise the spot of one ray and add it (tile if inside, image otherwise).
-__device__ __forceinline__ void deposit_ray(const DevOptics& o, double px, double py,
+__device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
                                             unsigned long long* tile, int ax, int ay, int64_t* image)
 {
     SpotWindow sw;
@@ -54,7 +54,8 @@ __device__ __forceinline__ void deposit_ray(const DevOptics& o, double px, doubl
     }
 }
 
-// Work: the flattened (Morton slot, ray) index space is cut into chunks of
+// Work: the flattened (Morton slot, ray) index space (sources in Morton order,
+// read as double-float from P.src_df) is cut into chunks of
 // rays_per_cta consecutive rays; a CTA takes one chunk, so its rays come
 // from one source or a few neighbouring ones and their spots fall in one
 // 32x32 shared tile anchored at the first hit.
@@ -82,37 +83,37 @@ render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restr
     const uint32_t rps = P.rays_per_source;
     unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
 
-    uint64_t idx = first + threadIdx.x;
-    RayOut r;
-    r.status = -1;
-    // first ray of every thread: its hit anchors the tile
-    if (idx < last) {
-        const uint32_t flat = (uint32_t)idx;
-        const uint32_t slot = flat / rps, k = flat - slot * rps;
-        const uint32_t sid = P.perm ? __ldg(P.perm + slot) : slot;
-        const double* s = P.sources + 3 * (size_t)sid;
-        trace_ray<INTEG>(P, __ldg(s), __ldg(s + 1), __ldg(s + 2), sid, k, r, nullptr);
-        if (r.status == PIVBOS_RAY_REACHED) atomicMin(&s_anchor_tid, (int)threadIdx.x);
-    }
-    __syncthreads();
-    if ((int)threadIdx.x == s_anchor_tid) {
-        s_ax = (int)floor(r.px) - kTileW / 2;
-        s_ay = (int)floor(r.py) - kTileH / 2;
-    }
-    __syncthreads();
-    const int ax = s_ax, ay = s_ay;
-    if (idx < last) {
-        cnt[r.status]++;
-        if (r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, tile, ax, ay, image);
-    }
-    for (idx += blockDim.x; idx < last; idx += blockDim.x) {
-        const uint32_t flat = (uint32_t)idx;
-        const uint32_t slot = flat / rps, k = flat - slot * rps;
-        const uint32_t sid = P.perm ? __ldg(P.perm + slot) : slot;
-        const double* s = P.sources + 3 * (size_t)sid;
-        trace_ray<INTEG>(P, __ldg(s), __ldg(s + 1), __ldg(s + 2), sid, k, r, nullptr);
-        cnt[r.status]++;
-        if (r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, tile, ax, ay, image);
+    // one uniform loop over the CTA's rays; after the first round every
+    // thread's first hit is known and the lowest-thread hit anchors the tile
+    const int rounds = (int)((last - first + blockDim.x - 1) / blockDim.x);
+    int ax = -(1 << 28), ay = -(1 << 28);
+    for (int round = 0; round < rounds; ++round) {
+        const uint64_t idx = first + (uint64_t)round * blockDim.x + threadIdx.x;
+        const bool active = idx < last;
+        RayOut r;
+        r.status = PIVBOS_RAY_MISS;
+        if (active) {
+            const uint32_t flat = (uint32_t)idx;
+            const uint32_t slot = flat / rps, k = flat - slot * rps;
+            const uint32_t sid = __ldg(P.perm + slot);
+            const float2* s = P.src_df + 3 * (size_t)slot;
+            const float2 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2);
+            trace_ray<INTEG>(P, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, sid, k, r, nullptr);
+            cnt[r.status]++;
+        }
+        if (round == 0) {
+            if (active && r.status == PIVBOS_RAY_REACHED) atomicMin(&s_anchor_tid, (int)threadIdx.x);
+            __syncthreads();
+            if ((int)threadIdx.x == s_anchor_tid) {
+                float f;
+                s_ax = df_floor(r.px, f) - kTileW / 2;
+                s_ay = df_floor(r.py, f) - kTileH / 2;
+            }
+            __syncthreads();
+            ax = s_ax;
+            ay = s_ay;
+        }
+        if (active && r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, tile, ax, ay, image);
     }
     if (stats) {
 #pragma unroll
@@ -156,7 +157,7 @@ trace_states_kernel(const TraceParams P, const int64_t* __restrict__ ray_ids, in
     } else {
         const uint32_t sid = (uint32_t)(id / rps), k = (uint32_t)(id - (int64_t)sid * rps);
         const double* s = P.sources + 3 * (size_t)sid;
-        trace_ray<INTEG>(P, s[0], s[1], s[2], sid, k, r, &st);
+        trace_ray<INTEG>(P, df_from_double(s[0]), df_from_double(s[1]), df_from_double(s[2]), sid, k, r, &st);
     }
     out[q] = st;
 }

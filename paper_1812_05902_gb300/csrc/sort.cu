@@ -5,6 +5,8 @@
 //
 // Keys: 16 bits per axis over [-1 m, 1 m) (clamped), interleaved, in the
 // high 32 bits; the source index in the low 32 bits (so keys are unique).
+// The last pass writes the permutation and the sorted source positions as
+// double-float pairs, the form the tracer reads.
 // Sort: bitonic network over the next power of two, with all strides below
 // kSortBlock elements done in shared memory.
 #include "common.cuh"
@@ -91,14 +93,23 @@ __global__ void bitonic_global_kernel(uint64_t* __restrict__ keys, uint32_t n_po
     keys[l] = b;
 }
 
-__global__ void keys_to_perm_kernel(const uint64_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ perm)
+__global__ void keys_to_perm_kernel(const uint64_t* __restrict__ keys, const double* __restrict__ src, uint32_t n,
+                                    uint32_t* __restrict__ perm, float2* __restrict__ src_df)
 {
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n) perm[q] = (uint32_t)keys[q];
+    if (q >= n) return;
+    const uint32_t sid = (uint32_t)keys[q];
+    perm[q] = sid;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double v = src[3 * (size_t)sid + a];
+        const float hi = __double2float_rn(v);
+        src_df[3 * (size_t)q + a] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
 }
 
 cudaError_t launch_morton_sort(const double* sources, uint32_t n, uint64_t* keys, uint32_t n_pow2,
-                               uint32_t* perm, cudaStream_t s)
+                               uint32_t* perm, float2* src_df, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     timing_begin("sort", s);
@@ -115,7 +126,7 @@ cudaError_t launch_morton_sort(const double* sources, uint32_t n, uint64_t* keys
         bitonic_shared_kernel<<<blocks, kSortThreads, 0, s>>>(keys, n_pow2, k);
         ++launched;
     }
-    keys_to_perm_kernel<<<(n + 255) / 256, 256, 0, s>>>(keys, n, perm);
+    keys_to_perm_kernel<<<(n + 255) / 256, 256, 0, s>>>(keys, sources, n, perm, src_df);
     timing_end("sort", s);
     count_launches(launched);
     return cudaGetLastError();

@@ -1,26 +1,37 @@
 // Device functions of the ray tracer: one GPU thread follows one ray through
 // all four steps of the method (arXiv 1812.05902, Sec. 3 and Sec. 3.5).
 //
-// Precision plan (GB300 runs FP64 at a small fraction of FP32):
-//  * lens point: FP64 from 53-bit uniforms (as the method draws it);
-//  * straight runs, lens surfaces, sensor plane: FP64;
+// Precision plan.  GB300 issues FP64 at 1/64 of its FP32 rate, so the
+// tracer uses no FP64 arithmetic on its hot path:
+//  * positions and directions outside the density box, the lens surfaces
+//    and the sensor plane are double-float (df64.cuh, ~48 bits): the sensor
+//    position must be right to 1e-5 pixel (1.7e-10 m at 17 um pitch) on
+//    coordinates up to ~1e-2 m, beyond FP32's 24 bits;
+//  * decisions (apertures, clear radii, hemisphere, total internal
+//    reflection) compare the FP32 leading parts;
+//  * the lens point is drawn from 53-bit uniforms: the radius a sqrt(u1) and
+//    the angle 2 pi u2 (df_sincospi) in double-float;
 //  * integration: the ray is carried as a straight reference line
-//    R0 + T0 t (FP64) plus an FP32 perturbation (rho, tau) that the
+//    R0 + T0 t (double-float) plus an FP32 perturbation (rho, tau) that the
 //    Runge-Kutta update acts on.  The update of Eq. 3 is linear in (R, T), so
 //    R_i = R0 + T0 t_i + rho_i, T_i = T0 + tau_i gives exactly
 //        rho_{i+1} = rho_i + [tau_i + (A + 2B)/6] dt,
 //        tau_{i+1} = tau_i + (A + 4B + C)/6,
-//    and the FP32 rounding applies to deflections (~1e-5 rad, ~1e-5 m) rather
-//    than to absolute positions (~1 m) and directions (~1).
-//  * sample positions for the field are FP32 grid coordinates (error
-//    ~1e-5 of a cell), which only perturbs where n is evaluated.
+//    and FP32 rounding applies to the deflection (~1e-5 rad, ~1e-5 m), not
+//    to absolute positions (~1 m) and directions (~1);
+//  * the reference line is stepped in double-float grid coordinates and a
+//    sample's cell fraction is taken as (hi - cell) + (lo + offset), so the
+//    field is evaluated where the oracle evaluates it to ~1e-7 of a cell.
 #pragma once
 
 #include <math.h>
 
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace pivbos {
+
+__device__ __forceinline__ df dfk(dfc c) { return df{c.hi, c.lo}; }
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11).  Only the first two
@@ -43,6 +54,16 @@ __device__ __forceinline__ void philox_lens_words(uint64_t c0, uint64_t c1, uint
     }
     w0 = c0;
     w1 = c1;
+}
+
+// 53-bit uniform ((w >> 11) + 1/2) 2^-53 as a double-float: the top 24 bits
+// exactly in hi, the remaining 29 bits (and the half) in lo.
+__device__ __forceinline__ df u01_df(uint64_t w)
+{
+    const uint64_t m = w >> 11;
+    const float hi = (float)(uint32_t)(m >> 29) * 0x1p-24f;
+    const float lo = ((float)(uint32_t)(m & 0x1fffffffull) + 0.5f) * 0x1p-53f;
+    return fast_two_sum(hi, lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -84,95 +105,157 @@ __device__ __forceinline__ float3 eval_D(const DevMedium& m, float gx, float gy,
     return make_float3(n * v.y, n * v.z, n * v.w);
 }
 
+// Cell index and fraction of the grid coordinate gh + gl along one axis of
+// N nodes, clamped to [0, N-1].  gh is the leading part of a double-float
+// coordinate (up to N-1 cells) and gl the small rest (its low part plus the
+// FP32 offset of the sample point), so the fraction keeps ~1e-7 of a cell
+// wherever the point is in the grid.
+__device__ __forceinline__ void cell_split(float gh, float gl, int N, int& i, float& f)
+{
+    const float s = gh + gl;
+    if (!(s > 0.0f)) {           // also catches NaN
+        i = 0;
+        f = 0.0f;
+    } else if (s >= (float)(N - 1)) {
+        i = N - 2;
+        f = 1.0f;
+    } else {
+        i = min((int)s, N - 2);
+        f = fminf(fmaxf(__fadd_rn(__fsub_rn(gh, (float)i), gl), 0.0f), 1.0f);
+    }
+}
+
+__device__ __forceinline__ float3 eval_D_split(const DevMedium& m, float hx, float lx, float hy, float ly, float hz,
+                                               float lz)
+{
+    int i, j, k;
+    float fx, fy, fz;
+    cell_split(hx, lx, m.n[0], i, fx);
+    cell_split(hy, ly, m.n[1], j, fy);
+    cell_split(hz, lz, m.n[2], k, fz);
+    const int sy = m.n[0];
+    const int sz = m.n[0] * m.n[1];
+    const float4* p = m.field + ((k * m.n[1] + j) * m.n[0] + i);
+    const float4 c000 = __ldg(p), c100 = __ldg(p + 1);
+    const float4 c010 = __ldg(p + sy), c110 = __ldg(p + sy + 1);
+    const float4 c001 = __ldg(p + sz), c101 = __ldg(p + sz + 1);
+    const float4 c011 = __ldg(p + sz + sy), c111 = __ldg(p + sz + sy + 1);
+    const float4 x00 = lerp4(c000, c100, fx), x10 = lerp4(c010, c110, fx);
+    const float4 x01 = lerp4(c001, c101, fx), x11 = lerp4(c011, c111, fx);
+    const float4 y0 = lerp4(x00, x10, fy), y1 = lerp4(x01, x11, fy);
+    const float4 v = lerp4(y0, y1, fz);
+    const float n = 1.0f + v.x;
+    return make_float3(n * v.y, n * v.z, n * v.w);
+}
+
 struct RayOut {
-    double px, py;     // sensor pixel coordinates
+    df px, py;     // sensor pixel coordinates
     int status;
     int steps;
 };
+
+__device__ __forceinline__ void put3(double* dst, df x, df y, df z)
+{
+    dst[0] = df_to_double(x);
+    dst[1] = df_to_double(y);
+    dst[2] = df_to_double(z);
+}
 
 // ---------------------------------------------------------------------------
 // One ray through all stages.  INTEG: PIVBOS_EULER or PIVBOS_RK4.  If st is
 // not null the full exit state is written (parity path).
 // ---------------------------------------------------------------------------
 template <int INTEG>
-__device__ __forceinline__ void trace_ray(const TraceParams& P, double sx, double sy, double sz,
-                                          uint32_t sid, uint32_t rid, RayOut& out,
-                                          pivbos_ray_state* st)
+__device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df sz, uint32_t sid, uint32_t rid,
+                                          RayOut& out, pivbos_ray_state* st)
 {
     const DevMedium& m = P.m;
     const DevOptics& o = P.o;
 
     // ---- Sec. 3.1: source -> point on the lens ----------------------------
-    // 53-bit uniforms in (0,1); r = a sqrt(u1), phi = 2 pi u2 (FP64)
     uint64_t w0, w1;
     philox_lens_words(rid, sid, P.frame, 0ull, P.seed, 0ull, w0, w1);
-    const double u1 = ((double)(w0 >> 11) + 0.5) * 0x1p-53;
-    const double u2 = ((double)(w1 >> 11) + 0.5) * 0x1p-53;
-    double sq_u1;
+    const df rr = df_mul(dfk(o.aim_r), df_sqrt(u01_df(w0)));
+    const df u2 = u01_df(w1);
+    df sn, cs;
+    df_sincospi(df{2.0f * u2.hi, 2.0f * u2.lo}, sn, cs);
+    df Rx = sx, Ry = sy, Rz = sz;
+    df dx = df_sub(df_mul(rr, cs), sx);
+    df dy = df_sub(df_mul(rr, sn), sy);
+    df dz = df_sub(dfk(o.aim_z), sz);
     {
-        double y = (double)rsqrtf((float)u1);
-        y = y * (1.5 - 0.5 * u1 * y * y);
-        y = y * (1.5 - 0.5 * u1 * y * y);
-        sq_u1 = u1 * y;
-    }
-    const double rr = o.aim_r * sq_u1;
-    double sn, cs;
-    sincospi(2.0 * u2, &sn, &cs);
-    double Rx = sx, Ry = sy, Rz = sz;
-    double dx = rr * cs - sx;
-    double dy = rr * sn - sy;
-    double dz = o.aim_z - sz;
-    {
-        const double l2 = dx * dx + dy * dy + dz * dz;
-        double y = (double)rsqrtf((float)l2);
-        y = y * (1.5 - 0.5 * l2 * y * y);   // two Newton steps in FP64
-        y = y * (1.5 - 0.5 * l2 * y * y);
-        dx *= y; dy *= y; dz *= y;
+        const df inv = df_rsqrt(df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz)));
+        dx = df_mul(dx, inv);
+        dy = df_mul(dy, inv);
+        dz = df_mul(dz, inv);
     }
     int status = PIVBOS_RAY_REACHED;
     int steps = 0;
 
     // ---- Sec. 3.2: through the density box ------------------------------
     if (m.present) {
-        const bool inside = Rx >= m.lo[0] && Rx <= m.hi[0] && Ry >= m.lo[1] && Ry <= m.hi[1] &&
-                            Rz >= m.lo[2] && Rz <= m.hi[2];
+        const df lo0 = dfk(m.lo[0]), lo1 = dfk(m.lo[1]), lo2 = dfk(m.lo[2]);
+        const df hi0 = dfk(m.hi[0]), hi1 = dfk(m.hi[1]), hi2 = dfk(m.hi[2]);
+        const bool inside = !df_lt(Rx, lo0) && !df_gt(Rx, hi0) && !df_lt(Ry, lo1) && !df_gt(Ry, hi1) &&
+                            !df_lt(Rz, lo2) && !df_gt(Rz, hi2);
         bool enters = inside;
-        double tn = 0.0;
+        df tn = dfv(0.0f);
         if (!inside) {
-            // slab test on the straight line (FP64; the entry parameter only
-            // moves the start point along the line)
-            double t_near = -INFINITY, t_far = INFINITY;
+            // slab test on the straight line in FP32 decides whether and
+            // through which face the ray enters; the entry parameter of that
+            // face is then solved in double-float, so the integration starts
+            // on the face (a start shifted along the ray would shift every
+            // sample point of the field)
+            float t_near = -INFINITY, t_far = INFINITY;
+            int a_near = -1;
             bool ok = true;
-            const double dd[3] = {dx, dy, dz};
-            const double RR[3] = {Rx, Ry, Rz};
+            const float dd[3] = {dx.hi, dy.hi, dz.hi};
+            const float RR[3] = {Rx.hi, Ry.hi, Rz.hi};
+            const float LO[3] = {m.lo[0].hi, m.lo[1].hi, m.lo[2].hi};
+            const float HI[3] = {m.hi[0].hi, m.hi[1].hi, m.hi[2].hi};
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                if (dd[a] == 0.0) {
-                    if (RR[a] < m.lo[a] || RR[a] > m.hi[a]) ok = false;
+                if (dd[a] == 0.0f) {
+                    if (RR[a] < LO[a] || RR[a] > HI[a]) ok = false;
                 } else {
-                    const double inv = 1.0 / dd[a];
-                    const double t1 = (m.lo[a] - RR[a]) * inv;
-                    const double t2 = (m.hi[a] - RR[a]) * inv;
-                    t_near = fmax(t_near, fmin(t1, t2));
-                    t_far = fmin(t_far, fmax(t1, t2));
+                    const float inv = 1.0f / dd[a];
+                    const float t1 = (LO[a] - RR[a]) * inv;
+                    const float t2 = (HI[a] - RR[a]) * inv;
+                    const float tmin = fminf(t1, t2);
+                    if (tmin > t_near) {
+                        t_near = tmin;
+                        a_near = a;
+                    }
+                    t_far = fminf(t_far, fmaxf(t1, t2));
                 }
             }
-            if (ok && t_near <= t_far && t_near >= 0.0) {
+            if (ok && t_near <= t_far && t_near >= 0.0f && a_near >= 0) {
                 enters = true;
-                tn = t_near;
+                const df Ra = a_near == 0 ? Rx : (a_near == 1 ? Ry : Rz);
+                const df da = a_near == 0 ? dx : (a_near == 1 ? dy : dz);
+                const dfc face = da.hi > 0.0f ? m.lo[a_near] : m.hi[a_near];
+                tn = df_div(df_sub(dfk(face), Ra), da);
+                if (tn.hi < 0.0f) tn = dfv(0.0f);
             }
         }
         if (enters) {
-            const double R0x = Rx + tn * dx, R0y = Ry + tn * dy, R0z = Rz + tn * dz;
-            // grid coordinates of the entry point and of the reference line
-            const float g0x = (float)((R0x - m.origin[0]) * m.inv_hd[0]);
-            const float g0y = (float)((R0y - m.origin[1]) * m.inv_hd[1]);
-            const float g0z = (float)((R0z - m.origin[2]) * m.inv_hd[2]);
-            const float n0 = 1.0f + sample_field(m, g0x, g0y, g0z).x;
+            const df R0x = df_fma(dx, tn, Rx);
+            const df R0y = df_fma(dy, tn, Ry);
+            const df R0z = df_fma(dz, tn, Rz);
+            // reference line R0 + T0 t in grid units (double-float): g0 at
+            // the entry, dG per full step
+            const df ihx = dfk(m.inv_hd[0]), ihy = dfk(m.inv_hd[1]), ihz = dfk(m.inv_hd[2]);
+            df grx = df_mul(df_sub(R0x, dfk(m.origin[0])), ihx);
+            df gry = df_mul(df_sub(R0y, dfk(m.origin[1])), ihy);
+            df grz = df_mul(df_sub(R0z, dfk(m.origin[2])), ihz);
+            const float n0 = 1.0f + sample_field(m, grx.hi + grx.lo, gry.hi + gry.lo, grz.hi + grz.lo).x;
             // reading: no refraction at the faces; T = n d at the entry
-            const double T0x = (double)n0 * dx, T0y = (double)n0 * dy, T0z = (double)n0 * dz;
-            const float T0fx = (float)T0x, T0fy = (float)T0y, T0fz = (float)T0z;
-            const float G0x = T0fx * m.inv_h[0], G0y = T0fy * m.inv_h[1], G0z = T0fz * m.inv_h[2];
+            const df T0x = df_mul_f(dx, n0), T0y = df_mul_f(dy, n0), T0z = df_mul_f(dz, n0);
+            const df dGx = df_mul(df_mul(T0x, ihx), dfk(P.step_df));
+            const df dGy = df_mul(df_mul(T0y, ihy), dfk(P.step_df));
+            const df dGz = df_mul(df_mul(T0z, ihz), dfk(P.step_df));
+            const float T0fx = T0x.hi, T0fy = T0y.hi, T0fz = T0z.hi;
+            const float ix = m.inv_h[0], iy = m.inv_h[1], iz = m.inv_h[2];
             float rhx = 0.f, rhy = 0.f, rhz = 0.f;   // position perturbation (m)
             float tax = 0.f, tay = 0.f, taz = 0.f;   // tangent perturbation
             const float hstep = P.step;
@@ -181,167 +264,175 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, double sx, doubl
             int k = 0;
             bool done = false;
             for (; k < P.max_steps; ++k) {
-                const float t = (float)k * hstep;
-                const float gx = fmaf(G0x, t, g0x) + rhx * m.inv_h[0];
-                const float gy = fmaf(G0y, t, g0y) + rhy * m.inv_h[1];
-                const float gz = fmaf(G0z, t, g0z) + rhz * m.inv_h[2];
+                // current point = reference (grx, gry, grz) + perturbation (cells)
+                const float ox = fmaf(rhx, ix, grx.lo), oy = fmaf(rhy, iy, gry.lo), oz = fmaf(rhz, iz, grz.lo);
                 const float Tx = T0fx + tax, Ty = T0fy + tay, Tz = T0fz + taz;
                 // parameter distance to the box boundary along the tangent
                 float dexit = INFINITY;
-                if (Tx > 0.f) dexit = fminf(dexit, (ex - gx) * m.h[0] / Tx);
-                else if (Tx < 0.f) dexit = fminf(dexit, -gx * m.h[0] / Tx);
-                if (Ty > 0.f) dexit = fminf(dexit, (ey - gy) * m.h[1] / Ty);
-                else if (Ty < 0.f) dexit = fminf(dexit, -gy * m.h[1] / Ty);
-                if (Tz > 0.f) dexit = fminf(dexit, (ez - gz) * m.h[2] / Tz);
-                else if (Tz < 0.f) dexit = fminf(dexit, -gz * m.h[2] / Tz);
+                if (Tx > 0.f) dexit = fminf(dexit, ((ex - grx.hi) - ox) * m.h[0] / Tx);
+                else if (Tx < 0.f) dexit = fminf(dexit, (-grx.hi - ox) * m.h[0] / Tx);
+                if (Ty > 0.f) dexit = fminf(dexit, ((ey - gry.hi) - oy) * m.h[1] / Ty);
+                else if (Ty < 0.f) dexit = fminf(dexit, (-gry.hi - oy) * m.h[1] / Ty);
+                if (Tz > 0.f) dexit = fminf(dexit, ((ez - grz.hi) - oz) * m.h[2] / Tz);
+                else if (Tz < 0.f) dexit = fminf(dexit, (-grz.hi - oz) * m.h[2] / Tz);
                 float h = hstep;
                 if (hstep >= dexit) {
                     h = fmaxf(dexit, 0.f);
                     done = true;
                 }
-                if (INTEG == PIVBOS_RK4) {
-                    // Eqs. 3 and 5
-                    const float3 Dv = eval_D(m, gx, gy, gz);
-                    const float Ax = Dv.x * h, Ay = Dv.y * h, Az = Dv.z * h;
-                    const float bxp = (0.5f * Tx + 0.125f * Ax) * h;
-                    const float byp = (0.5f * Ty + 0.125f * Ay) * h;
-                    const float bzp = (0.5f * Tz + 0.125f * Az) * h;
-                    const float3 Db = eval_D(m, fmaf(bxp, m.inv_h[0], gx), fmaf(byp, m.inv_h[1], gy),
-                                             fmaf(bzp, m.inv_h[2], gz));
-                    const float Bx = Db.x * h, By = Db.y * h, Bz = Db.z * h;
-                    const float cxp = (Tx + 0.5f * Bx) * h;
-                    const float cyp = (Ty + 0.5f * By) * h;
-                    const float czp = (Tz + 0.5f * Bz) * h;
-                    const float3 Dc = eval_D(m, fmaf(cxp, m.inv_h[0], gx), fmaf(cyp, m.inv_h[1], gy),
-                                             fmaf(czp, m.inv_h[2], gz));
-                    const float Cx = Dc.x * h, Cy = Dc.y * h, Cz = Dc.z * h;
-                    const float s6 = 1.0f / 6.0f;
-                    rhx = fmaf(tax + (Ax + 2.f * Bx) * s6, h, rhx);
-                    rhy = fmaf(tay + (Ay + 2.f * By) * s6, h, rhy);
-                    rhz = fmaf(taz + (Az + 2.f * Bz) * s6, h, rhz);
-                    tax += (Ax + 4.f * Bx + Cx) * s6;
-                    tay += (Ay + 4.f * By + Cy) * s6;
-                    taz += (Az + 4.f * Bz + Cz) * s6;
-                } else {
-                    // first-order scheme: both updates from the old state
-                    const float3 Dv = eval_D(m, gx, gy, gz);
-                    rhx = fmaf(tax, h, rhx);
-                    rhy = fmaf(tay, h, rhy);
-                    rhz = fmaf(taz, h, rhz);
-                    tax = fmaf(Dv.x, h, tax);
-                    tay = fmaf(Dv.y, h, tay);
-                    taz = fmaf(Dv.z, h, taz);
+                // Stages of the step.  RK4 (Eqs. 3 and 5): K1 = A at the
+                // start, K2 = B at (T/2 + A/8) h, K3 = C at (T + B/2) h;
+                // rho += (tau + (A + 2B)/6) h, tau += (A + 4B + C)/6.
+                // First-order scheme: one stage, rho += tau h, tau += A.
+                float sRx = 0.f, sRy = 0.f, sRz = 0.f;   // sum of wR * K
+                float sTx = 0.f, sTy = 0.f, sTz = 0.f;   // sum of wT * K
+                float kx = 0.f, ky = 0.f, kz = 0.f;      // K of the previous stage
+                constexpr int kStages = INTEG == PIVBOS_RK4 ? 3 : 1;
+#pragma unroll 1
+                for (int sg = 0; sg < kStages; ++sg) {
+                    const float cT = sg == 0 ? 0.f : (sg == 1 ? 0.5f : 1.f);
+                    const float cK = sg == 0 ? 0.f : (sg == 1 ? 0.125f : 0.5f);
+                    const float px = (cT * Tx + cK * kx) * h;
+                    const float py = (cT * Ty + cK * ky) * h;
+                    const float pz = (cT * Tz + cK * kz) * h;
+                    const float3 Dv = eval_D_split(m, grx.hi, fmaf(px, ix, ox), gry.hi, fmaf(py, iy, oy), grz.hi,
+                                                   fmaf(pz, iz, oz));
+                    kx = Dv.x * h;
+                    ky = Dv.y * h;
+                    kz = Dv.z * h;
+                    const float wR = INTEG == PIVBOS_RK4 ? (sg == 0 ? 1.f / 6.f : (sg == 1 ? 2.f / 6.f : 0.f)) : 0.f;
+                    const float wT = INTEG == PIVBOS_RK4 ? (sg == 1 ? 4.f / 6.f : 1.f / 6.f) : 1.f;
+                    sRx = fmaf(wR, kx, sRx); sRy = fmaf(wR, ky, sRy); sRz = fmaf(wR, kz, sRz);
+                    sTx = fmaf(wT, kx, sTx); sTy = fmaf(wT, ky, sTy); sTz = fmaf(wT, kz, sTz);
                 }
+                rhx = fmaf(tax + sRx, h, rhx);
+                rhy = fmaf(tay + sRy, h, rhy);
+                rhz = fmaf(taz + sRz, h, rhz);
+                tax += sTx;
+                tay += sTy;
+                taz += sTz;
                 if (done) {
                     h_last = h;
                     break;
                 }
+                grx = df_add(grx, dGx);
+                gry = df_add(gry, dGy);
+                grz = df_add(grz, dGz);
             }
             steps = done ? k + 1 : k;
             if (!done) status = PIVBOS_RAY_MAXSTEP;
-            const double t_exit = (double)k * P.step_d + (double)h_last;
-            Rx = R0x + T0x * t_exit + (double)rhx;
-            Ry = R0y + T0y * t_exit + (double)rhy;
-            Rz = R0z + T0z * t_exit + (double)rhz;
-            const double Tx = T0x + (double)tax, Ty = T0y + (double)tay, Tz = T0z + (double)taz;
-            const double l2 = Tx * Tx + Ty * Ty + Tz * Tz;
-            double y = (double)rsqrtf((float)l2);
-            y = y * (1.5 - 0.5 * l2 * y * y);
-            y = y * (1.5 - 0.5 * l2 * y * y);
-            dx = Tx * y; dy = Ty * y; dz = Tz * y;
+            const df t_exit = df_add_f(df_mul_f(dfk(P.step_df), (float)k), h_last);
+            Rx = df_add_f(df_add(R0x, df_mul(T0x, t_exit)), rhx);
+            Ry = df_add_f(df_add(R0y, df_mul(T0y, t_exit)), rhy);
+            Rz = df_add_f(df_add(R0z, df_mul(T0z, t_exit)), rhz);
+            const df Tx = df_add_f(T0x, tax), Ty = df_add_f(T0y, tay), Tz = df_add_f(T0z, taz);
+            const df inv = df_rsqrt(df_add(df_add(df_sqr(Tx), df_sqr(Ty)), df_sqr(Tz)));
+            dx = df_mul(Tx, inv);
+            dy = df_mul(Ty, inv);
+            dz = df_mul(Tz, inv);
         }
     }
     if (st) {
-        st->vol_pos[0] = Rx; st->vol_pos[1] = Ry; st->vol_pos[2] = Rz;
-        st->vol_dir[0] = dx; st->vol_dir[1] = dy; st->vol_dir[2] = dz;
+        put3(st->vol_pos, Rx, Ry, Rz);
+        put3(st->vol_dir, dx, dy, dz);
         st->steps = steps;
     }
 
-    // ---- Sec. 3.3: optical elements in sequence (FP64) --------------------
-    double n_cur = o.n_object;
+    // ---- Sec. 3.3: optical elements in sequence ---------------------------
     for (int s = 0; s < o.ns && status == PIVBOS_RAY_REACHED; ++s) {
-        const DevSurface S = o.s[s];
-        if (!(dz > 0.0)) { status = PIVBOS_RAY_MISS; break; }
-        const double t0 = (S.z - Rz) / dz;
-        if (S.type == PIVBOS_SURF_SPHERE && S.R != 0.0) {
+        const DevSurface& S = o.s[s];
+        if (!(dz.hi > 0.0f)) { status = PIVBOS_RAY_MISS; break; }
+        const df inv_dz = df_rcp(dz);
+        const df t0 = df_mul(df_sub(dfk(S.z), Rz), inv_dz);
+        if (S.type == PIVBOS_SURF_SPHERE && S.R_f != 0.0f) {
             // vertex-relative quadratic t^2 + 2 b t + c = 0 from the point Q
             // on the vertex plane; the vertex-side root has the smaller
             // magnitude: t = c / (-b - sign(b) sqrt(b^2 - c))
-            const double Qx = Rx + t0 * dx, Qy = Ry + t0 * dy;
-            const double b = dx * Qx + dy * Qy - S.R * dz;
-            const double c = Qx * Qx + Qy * Qy;
-            const double disc = b * b - c;
-            if (disc < 0.0) { status = PIVBOS_RAY_MISS; break; }
-            const double sq = sqrt(disc);
-            const double den = -b - (b >= 0.0 ? sq : -sq);
-            const double t1 = den != 0.0 ? c / den : 0.0;
-            if (t0 + t1 < 0.0) { status = PIVBOS_RAY_MISS; break; }
-            const double Hx = Qx + t1 * dx, Hy = Qy + t1 * dy, Hz = t1 * dz;
-            if (!((Hz - S.R) * S.R < 0.0)) { status = PIVBOS_RAY_MISS; break; }
-            if (Hx * Hx + Hy * Hy > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
-            const double invR = 1.0 / S.R;
-            double Nx = Hx * invR, Ny = Hy * invR, Nz = (Hz - S.R) * invR;
-            if (Nx * dx + Ny * dy + Nz * dz > 0.0) { Nx = -Nx; Ny = -Ny; Nz = -Nz; }
+            const df Qx = df_fma(t0, dx, Rx), Qy = df_fma(t0, dy, Ry);
+            const df R = dfk(S.R);
+            const df b = df_sub(df_add(df_mul(dx, Qx), df_mul(dy, Qy)), df_mul(R, dz));
+            const df c = df_add(df_sqr(Qx), df_sqr(Qy));
+            const df disc = df_sub(df_sqr(b), c);
+            if (disc.hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
+            const df sq = df_sqrt(disc);
+            const df den = b.hi >= 0.0f ? df_sub(df_neg(b), sq) : df_add(df_neg(b), sq);
+            const df t1 = den.hi != 0.0f ? df_div(c, den) : dfv(0.0f);
+            if (df_add(t0, t1).hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
+            const df Hx = df_fma(t1, dx, Qx), Hy = df_fma(t1, dy, Qy), Hz = df_mul(t1, dz);
+            const df HzR = df_sub(Hz, R);
+            if (!(HzR.hi * S.R_f < 0.0f)) { status = PIVBOS_RAY_MISS; break; }
+            if (Hx.hi * Hx.hi + Hy.hi * Hy.hi > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
+            const df invR = dfk(S.invR);
+            df Nx = df_mul(Hx, invR), Ny = df_mul(Hy, invR), Nz = df_mul(HzR, invR);
+            if (Nx.hi * dx.hi + Ny.hi * dy.hi + Nz.hi * dz.hi > 0.0f) {
+                Nx = df_neg(Nx); Ny = df_neg(Ny); Nz = df_neg(Nz);
+            }
             // Eq. 7, vector form
-            const double eta = n_cur / S.n_after;
-            const double ci = -(Nx * dx + Ny * dy + Nz * dz);
-            const double kk = 1.0 - eta * eta * (1.0 - ci * ci);
-            if (kk < 0.0) { status = PIVBOS_RAY_TIR; break; }
-            const double a = eta * ci - sqrt(kk);
-            dx = eta * dx + a * Nx;
-            dy = eta * dy + a * Ny;
-            dz = eta * dz + a * Nz;
-            Rx = Hx; Ry = Hy; Rz = S.z + Hz;
-            n_cur = S.n_after;
+            const df eta = dfk(S.eta);
+            const df ci = df_neg(df_add(df_add(df_mul(Nx, dx), df_mul(Ny, dy)), df_mul(Nz, dz)));
+            const df kk = df_sub(dfv(1.0f), df_mul(dfk(S.eta2), df_sub(dfv(1.0f), df_sqr(ci))));
+            if (kk.hi < 0.0f) { status = PIVBOS_RAY_TIR; break; }
+            const df a = df_sub(df_mul(eta, ci), df_sqrt(kk));
+            dx = df_fma(eta, dx, df_mul(a, Nx));
+            dy = df_fma(eta, dy, df_mul(a, Ny));
+            dz = df_fma(eta, dz, df_mul(a, Nz));
+            Rx = Hx;
+            Ry = Hy;
+            Rz = df_add(dfk(S.z), Hz);
         } else {
-            if (t0 < 0.0) { status = PIVBOS_RAY_MISS; break; }
-            Rx += t0 * dx; Ry += t0 * dy; Rz = S.z;
-            const double r2 = Rx * Rx + Ry * Ry;
+            if (t0.hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
+            Rx = df_fma(t0, dx, Rx);
+            Ry = df_fma(t0, dy, Ry);
+            Rz = dfk(S.z);
+            const float r2 = Rx.hi * Rx.hi + Ry.hi * Ry.hi;
             if (S.type == PIVBOS_SURF_STOP) {
                 if (r2 > S.clear_r2) { status = PIVBOS_RAY_STOP; break; }
             } else if (S.type == PIVBOS_SURF_IDEAL_THIN) {
                 if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
-                const double invdz = 1.0 / dz;
-                const double ux = dx * invdz - Rx / S.f;
-                const double uy = dy * invdz - Ry / S.f;
-                const double inn = 1.0 / sqrt(ux * ux + uy * uy + 1.0);
-                dx = ux * inn; dy = uy * inn; dz = inn;
+                const df invf = dfk(S.inv_f);
+                const df ux = df_sub(df_mul(dx, inv_dz), df_mul(Rx, invf));
+                const df uy = df_sub(df_mul(dy, inv_dz), df_mul(Ry, invf));
+                const df inn = df_rsqrt(df_add_f(df_add(df_sqr(ux), df_sqr(uy)), 1.0f));
+                dx = df_mul(ux, inn);
+                dy = df_mul(uy, inn);
+                dz = inn;
             } else {
                 if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
                 // flat surface, normal (0, 0, -1)
-                const double eta = n_cur / S.n_after;
-                const double ci = dz;
-                const double kk = 1.0 - eta * eta * (1.0 - ci * ci);
-                if (kk < 0.0) { status = PIVBOS_RAY_TIR; break; }
-                const double a = eta * ci - sqrt(kk);
-                dx = eta * dx;
-                dy = eta * dy;
-                dz = eta * dz - a;
-                n_cur = S.n_after;
+                const df eta = dfk(S.eta);
+                const df kk = df_sub(dfv(1.0f), df_mul(dfk(S.eta2), df_sub(dfv(1.0f), df_sqr(dz))));
+                if (kk.hi < 0.0f) { status = PIVBOS_RAY_TIR; break; }
+                const df a = df_sub(df_mul(eta, dz), df_sqrt(kk));
+                dx = df_mul(eta, dx);
+                dy = df_mul(eta, dy);
+                dz = df_sub(df_mul(eta, dz), a);
             }
         }
     }
 
     // ---- Sec. 3.4: sensor plane -------------------------------------------
-    double px = 0.0, py = 0.0;
+    df px = dfv(0.0f), py = dfv(0.0f);
     if (status == PIVBOS_RAY_REACHED) {
-        if (!(dz > 0.0)) {
+        if (!(dz.hi > 0.0f)) {
             status = PIVBOS_RAY_MISS;
         } else {
-            const double t = (o.sensor_z - Rz) / dz;
-            if (t < 0.0) {
+            const df t = df_mul(df_sub(dfk(o.sensor_z), Rz), df_rcp(dz));
+            if (t.hi < 0.0f) {
                 status = PIVBOS_RAY_MISS;
             } else {
-                px = (Rx + t * dx) * o.inv_pitch + o.half_w;
-                py = (Ry + t * dy) * o.inv_pitch + o.half_h;
-                if (!(px >= 0.0 && px < (double)o.W && py >= 0.0 && py < (double)o.H))
-                    status = PIVBOS_RAY_OFF_SENSOR;
+                const df ipitch = dfk(o.inv_pitch);
+                px = df_add_f(df_mul(df_fma(t, dx, Rx), ipitch), o.half_w);
+                py = df_add_f(df_mul(df_fma(t, dy, Ry), ipitch), o.half_h);
+                const bool inx = !df_lt(px, dfv(0.0f)) && df_lt(px, dfv((float)o.W));
+                const bool iny = !df_lt(py, dfv(0.0f)) && df_lt(py, dfv((float)o.H));
+                if (!(inx && iny)) status = PIVBOS_RAY_OFF_SENSOR;
             }
         }
     }
     if (st) {
-        st->sensor_xy[0] = px; st->sensor_xy[1] = py;
-        st->sensor_dir[0] = dx; st->sensor_dir[1] = dy; st->sensor_dir[2] = dz;
+        st->sensor_xy[0] = df_to_double(px);
+        st->sensor_xy[1] = df_to_double(py);
+        put3(st->sensor_dir, dx, dy, dz);
         st->status = status;
     }
     out.px = px;
@@ -363,16 +454,18 @@ struct SpotWindow {
     float scale;   // 2^32 / (sum wx * sum wy)
 };
 
-__device__ __forceinline__ void axis_weights(double p, double win3, int N, float inv_s2, int& lo,
-                                             int& cnt, float* w, float& sum)
+__device__ __forceinline__ void axis_weights(df p, float win3, int N, float inv_s2, int& lo, int& cnt, float* w,
+                                             float& sum)
 {
-    int a = (int)floor(p - win3);
-    int b = (int)floor(p + win3);
+    float fa, fb;
+    int a = df_floor(df_add_f(p, -win3), fa);
+    int b = df_floor(df_add_f(p, win3), fb);
     a = max(a, 0);
     b = min(b, N - 1);
     lo = a;
     cnt = b - a + 1;
-    const float f = (float)(p - (double)a);   // hit position inside the window
+    // hit position relative to the window start (exact difference, then FP32)
+    const float f = __fadd_rn(__fsub_rn(p.hi, (float)a), p.lo);
     float e_prev = erff((0.0f - f) * inv_s2);
     sum = 0.f;
 #pragma unroll
@@ -388,7 +481,7 @@ __device__ __forceinline__ void axis_weights(double p, double win3, int N, float
     }
 }
 
-__device__ __forceinline__ void spot_window(const DevOptics& o, double px, double py, SpotWindow& sw)
+__device__ __forceinline__ void spot_window(const DevOptics& o, df px, df py, SpotWindow& sw)
 {
     float sx, sy;
     axis_weights(px, o.win3, o.W, o.inv_sqrt2_sigma, sw.x0, sw.nx, sw.wx, sx);
