@@ -125,25 +125,78 @@ class Clocks:
 # ----------------------------------------------------------------------------
 # roofline of the dominant kernel
 # ----------------------------------------------------------------------------
-# Algorithmic FP64 operations per ray of the render kernel on a thick-lens
-# scene (lens point direction 12, volume entry/exit 21, stop 9, two spheres
-# 2 x 68, sensor 10, spot window 4): the FP64 pipe bounds this kernel.
-FP64_OPS_PER_RAY_THICK_LENS = 192.0
-FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal FP64 rate
+# The render kernel is bound by instruction issue on the FP32/INT32 pipes
+# (no FP64 left on the path, no tensor-core work, DRAM and L2 lightly used),
+# so its roofline is the SM issue rate: 152 SMs x 128 lanes x clock.  The
+# algorithmic work of one ray is a static count of FP32/INT32 lane operations
+# of the double-float and FP32 formulation, per stage:
+#   ray generation (Philox4x64-10, lens point, direction)  710
+#   volume entry + exit to the optics                       470
+#   each integration step: RK4 430, first-order 160
+#   per surface: sphere 530, stop/plane/ideal lens 80
+#   sensor plane 125, spot deposit 450, bookkeeping 40
+OPS_RAY_BASE = 710 + 470 + 125 + 450 + 40
+OPS_STEP = {scenes.RK4: 430.0, scenes.EULER: 160.0}
+OPS_SURF = {scenes.SPHERE: 530.0, scenes.PLANE: 80.0, scenes.IDEAL_THIN: 80.0, scenes.STOP: 80.0}
+ISSUE_LANES_PER_SM = 128
+N_SM = 152
 
 
-def roofline(workload, frames, render_ms, render_launches, peaks, peak_kind):
+def kernel_source_hash():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for path in sorted(glob.glob(os.path.join(ROOT, "paper_1812_05902_gb300", "csrc", "*"))):
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per render launch from the committed ncu record, or None
+    when the record is for another workload or the kernels changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "render_%s_traffic.json" % workload)) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return int(rec["dram_bytes_read"] + rec["dram_bytes_write"])
+
+
+def ops_per_ray(frame, mean_steps):
+    surf = sum(OPS_SURF[s.type] for s in frame.optics.surfaces)
+    return OPS_RAY_BASE + surf + OPS_STEP[frame.integrator] * mean_steps
+
+
+def roofline(frames, mean_steps, render_ms, render_launches, sm_max_mhz, traffic=None):
     if render_launches == 0:
         return None
-    rays_per_launch = sum(f.n_rays for f in frames) / len(frames)
     t = render_ms / render_launches * 1e-3
-    ops = FP64_OPS_PER_RAY_THICK_LENS * rays_per_launch
+    rays = sum(f.n_rays for f in frames) / len(frames)
+    ops = sum(ops_per_ray(f, ms) * f.n_rays for f, ms in zip(frames, mean_steps)) / len(frames)
     achieved = ops / t / 1e12
-    peak = FP64_NOMINAL_TFLOPS
-    return {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
-            "kernel": "render_kernel<RK4>", "peak_source": "nominal FP64 of the profiling recipe",
-            "launch_ms": round(t * 1e3, 4), "rays_per_launch": int(rays_per_launch)}
+    peak = N_SM * ISSUE_LANES_PER_SM * (sm_max_mhz or 2070.0) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "kernel": "render_kernel", "op": "FP32/INT32 lane operation (1 per lane instruction)",
+            "peak_source": "issue rate derived from 152 SMs x 128 lanes x max SM clock",
+            "ops_per_ray": round(ops / rays, 1), "launch_ms": round(t * 1e3, 4), "rays_per_launch": int(rays)}
+
+
+def mean_steps(P, frame, opt, med, src_d, n=65536):
+    """Mean integration steps per ray on a seeded sample of the frame's rays
+    (outside the timed region), for the algorithmic operation count."""
+    import torch
+    rng = np.random.default_rng(12345)
+    ids = torch.tensor(np.unique(rng.integers(0, frame.n_rays, n)), dtype=torch.int64, device="cuda")
+    out = torch.empty(len(ids) * P.RAY_STATE.itemsize, dtype=torch.uint8, device="cuda")
+    P.pivbos_trace_exit_states(med.h if med else None, opt.h, src_d, len(frame.sources), frame.rays_per_source,
+                               frame.seed, frame.frame_index, frame.integrator, frame.step, ids, len(ids), out)
+    P.pivbos_sync()
+    st = np.frombuffer(out.cpu().numpy().tobytes(), dtype=P.RAY_STATE)
+    return float(st["steps"].mean())
 
 
 # ----------------------------------------------------------------------------
@@ -300,8 +353,9 @@ def run_gpu(args, rank, world):
         e2e = {"value": rays_step * max(1, args.steps) * world / dt, "unit": "rays/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(H * W * 8 * len(frames))}
 
-    peaks, peak_kind = _peaks()
-    rf = roofline(args.workload, frames, render_ms, render_n, peaks, peak_kind)
+    msteps = [mean_steps(P, fr, opt, meds[i], src_d[i]) for i, fr in enumerate(frames)]
+    rf = roofline(frames, msteps, render_ms, render_n, clk.get("sm_max_mhz"),
+                  recorded_traffic(args.workload) if args.scale == 1.0 else None)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, threads, done, t = oracle_sample(frames, seconds_target=12.0)
@@ -311,7 +365,8 @@ def run_gpu(args, rank, world):
         out = {
             "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32 (double-float f32 pairs for positions/directions)",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD_NAMES[args.workload] + ("" if args.scale == 1.0 else
                                                                      " (scaled by %g)" % args.scale),
                        "name": args.workload,

@@ -182,6 +182,12 @@ pivbos_status prepare(const pivbos_medium* m, const pivbos_optics* o, const doub
         const double ms = ceil(2.0 * sqrt(diag2) / step) + 4.0;
         if (ms > 2.0e9) return fail(PIVBOS_ERR_UNSUPPORTED, "step too small for the box (%g steps)", ms);
         p.max_steps = (int)ms;
+        p.m.z_key = (float)(m->origin[2] + 0.5 * (double)(m->n[2] - 1) * m->spacing[2]);
+        // reorder rays for gather locality when a ray makes many field
+        // evaluations (the box depth in steps times the stages per step)
+        const double evals = (double)(m->n[2] - 1) * m->spacing[2] / step * (integrator == PIVBOS_RK4 ? 3.0 : 1.0);
+        p.reorder = evals >= 64.0 ? 1 : 0;
+        p.cell_cache = pivbos::tuning_cell_cache(p.reorder);
     }
     p.o = o->d;
     p.sources = sources;
@@ -203,6 +209,16 @@ pivbos_status prepare(const pivbos_medium* m, const pivbos_optics* o, const doub
 }  // namespace
 
 void set_last_error(const char* msg) { t_err = msg; }
+
+int tuning_cell_cache(int dense)
+{
+    static int v = -2;
+    if (v == -2) {
+        const char* s = getenv("PIVBOS_CELL_CACHE");
+        v = s ? (atoi(s) != 0 ? 1 : 0) : -1;
+    }
+    return v >= 0 ? v : dense;
+}
 
 void timing_begin(const char* name, cudaStream_t s)
 {

@@ -25,6 +25,7 @@ struct DevMedium {
     dfc lo[3], hi[3];    // box corners
     int max_steps;       // step budget for a parameter step of 1 m (scaled per render)
     int present;         // 0 = no medium: rays are straight everywhere
+    float z_key;         // mid-plane of the box (ordering key plane)
 };
 
 struct DevSurface {
@@ -63,6 +64,8 @@ struct TraceParams {
     float step;               // parameter step
     double step_d;
     dfc step_df;
+    int reorder;              // trace each CTA's rays in mid-plane Morton order
+    int cell_cache;           // keep the last cell's corners in registers
     int* status_word;         // device status word (first error latched)
 };
 
@@ -78,6 +81,10 @@ cudaError_t launch_render(const TraceParams& p, int integrator, int64_t* image, 
 cudaError_t launch_trace_states(const TraceParams& p, int integrator, const int64_t* ray_ids,
                                 int64_t n_rays, pivbos_ray_state* out, cudaStream_t s);
 cudaError_t launch_finalize(const int64_t* image, int64_t n, float* out, cudaStream_t s);
+
+// Tuning knob (api.cu): keep cell corners in registers during integration;
+// PIVBOS_CELL_CACHE=0/1 overrides the default (on for dense media).
+int tuning_cell_cache(int dense);
 
 // Kernel timing hooks (api.cu): bracket a launch with events when enabled.
 // Every launcher also counts its kernels (count_launches).

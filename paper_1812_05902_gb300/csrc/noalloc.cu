@@ -147,6 +147,12 @@ extern "C" pivbos_status pivbos_render_noalloc(const pivbos_medium* m, const piv
         const double ms = ceil(2.0 * sqrt(diag2) / step) + 4.0;
         if (ms > 2.0e9) return err(PIVBOS_ERR_UNSUPPORTED, "step too small for the box (%g steps)", ms);
         p.max_steps = (int)ms;
+        p.m.z_key = (float)(m->origin[2] + 0.5 * (double)(m->n[2] - 1) * m->spacing[2]);
+        // reorder rays for gather locality when a ray makes many field
+        // evaluations (the box depth in steps times the stages per step)
+        const double evals = (double)(m->n[2] - 1) * m->spacing[2] / step * (integrator == PIVBOS_RK4 ? 3.0 : 1.0);
+        p.reorder = evals >= 64.0 ? 1 : 0;
+        p.cell_cache = pivbos::tuning_cell_cache(p.reorder);
     }
     p.o = o->d;
     p.sources = sources;

@@ -6,8 +6,47 @@
 namespace pivbos {
 
 constexpr int kRenderThreads = 256;
+constexpr int kRenderMinBlocks = 3;   // CTAs per SM the register budget must allow
 constexpr int kTileW = 32;
 constexpr int kTileH = 32;
+constexpr int kMaxOrderRays = 2048;   // a CTA reorders at most this many rays
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Ordering key of a ray: Morton code of the grid cell where its straight
+// line from the source to its lens point crosses the mid-plane of the box
+// (FP32 throughout -- only the order of tracing depends on it), above the
+// ray's index within the CTA.
+__device__ __forceinline__ uint32_t ray_order_key(const TraceParams& P, uint32_t flat, uint32_t local)
+{
+    const uint32_t rps = P.rays_per_source;
+    const uint32_t slot = flat / rps, k = flat - slot * rps;
+    const uint32_t sid = __ldg(P.perm + slot);
+    const float2* sp = P.src_df + 3 * (size_t)slot;
+    const float sx = __ldg(sp).x, sy = __ldg(sp + 1).x, sz = __ldg(sp + 2).x;
+    uint64_t w0, w1;
+    philox_lens_words(k, sid, P.frame, 0ull, P.seed, 0ull, w0, w1);
+    const float u1 = ((float)(uint32_t)(w0 >> 40) + 0.5f) * 0x1p-24f;
+    const float u2 = ((float)(uint32_t)(w1 >> 40) + 0.5f) * 0x1p-24f;
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    const float r = P.o.aim_r.hi * sqrtf(u1);
+    const float dz = P.o.aim_z.hi - sz;
+    const float t = dz != 0.0f ? fminf(fmaxf((P.m.z_key - sz) / dz, 0.0f), 1.0f) : 0.0f;
+    const float x = fmaf(r * cs - sx, t, sx), y = fmaf(r * sn - sy, t, sy);
+    const float gx = fminf(fmaxf((x - P.m.origin[0].hi) * P.m.inv_h[0], 0.0f), 1023.0f);
+    const float gy = fminf(fmaxf((y - P.m.origin[1].hi) * P.m.inv_h[1], 0.0f), 1023.0f);
+    const uint32_t code = spread10((uint32_t)gx) | (spread10((uint32_t)gy) << 1);
+    return (code << 11) | local;
+}
 
 __device__ __forceinline__ void add_q(unsigned long long* tile, int ax, int ay, int64_t* image, int W,
                                       int gx, int gy, unsigned long long q)
@@ -59,12 +98,13 @@ __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
 // rays_per_cta consecutive rays; a CTA takes one chunk, so its rays come
 // from one source or a few neighbouring ones and their spots fall in one
 // 32x32 shared tile anchored at the first hit.
-template <int INTEG>
-__global__ void __launch_bounds__(kRenderThreads)
+template <int INTEG, bool CACHE>
+__global__ void __launch_bounds__(kRenderThreads, CACHE ? 2 : kRenderMinBlocks)
 render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restrict__ stats,
               uint32_t rays_per_cta, uint64_t total_rays)
 {
     __shared__ unsigned long long tile[kTileW * kTileH];
+    __shared__ uint32_t s_order[kMaxOrderRays];
     __shared__ int s_anchor_tid;
     __shared__ int s_ax, s_ay;
     __shared__ unsigned long long s_cnt[PIVBOS_RAY_NSTATUS];
@@ -83,13 +123,41 @@ render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restr
     const uint32_t rps = P.rays_per_source;
     unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
 
+    // In a dense medium, trace the CTA's rays in the order of where they
+    // cross the box: a warp then gathers from a few neighbouring cells
+    // instead of the whole cone of a source.
+    const uint32_t n_here = (uint32_t)(last - first);
+    const bool reorder = P.reorder && n_here <= (uint32_t)kMaxOrderRays;
+    if (reorder) {
+        uint32_t n_pow2 = 1;
+        while (n_pow2 < n_here) n_pow2 <<= 1;
+        for (uint32_t q = threadIdx.x; q < n_pow2; q += blockDim.x)
+            s_order[q] = q < n_here ? ray_order_key(P, (uint32_t)first + q, q) : 0xffffffffu;
+        __syncthreads();
+        for (uint32_t kk = 2; kk <= n_pow2; kk <<= 1) {
+            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+                for (uint32_t t = threadIdx.x; t < n_pow2 / 2; t += blockDim.x) {
+                    const uint32_t i = 2 * t - (t & (j - 1));
+                    const uint32_t l = i + j;
+                    const bool up = (i & kk) == 0;
+                    const uint32_t a = s_order[i], b = s_order[l];
+                    if ((a > b) == up) {
+                        s_order[i] = b;
+                        s_order[l] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
     // one uniform loop over the CTA's rays; after the first round every
     // thread's first hit is known and the lowest-thread hit anchors the tile
     const int rounds = (int)((last - first + blockDim.x - 1) / blockDim.x);
     int ax = -(1 << 28), ay = -(1 << 28);
     for (int round = 0; round < rounds; ++round) {
-        const uint64_t idx = first + (uint64_t)round * blockDim.x + threadIdx.x;
-        const bool active = idx < last;
+        const uint32_t e = (uint32_t)round * blockDim.x + threadIdx.x;
+        const bool active = e < n_here;
+        const uint64_t idx = first + (reorder && active ? (s_order[e] & 0x7ffu) : e);
         RayOut r;
         r.status = PIVBOS_RAY_MISS;
         if (active) {
@@ -98,7 +166,7 @@ render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restr
             const uint32_t sid = __ldg(P.perm + slot);
             const float2* s = P.src_df + 3 * (size_t)slot;
             const float2 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2);
-            trace_ray<INTEG>(P, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, sid, k, r, nullptr);
+            trace_ray<INTEG, CACHE>(P, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, sid, k, r, nullptr);
             cnt[r.status]++;
         }
         if (round == 0) {
@@ -157,7 +225,7 @@ trace_states_kernel(const TraceParams P, const int64_t* __restrict__ ray_ids, in
     } else {
         const uint32_t sid = (uint32_t)(id / rps), k = (uint32_t)(id - (int64_t)sid * rps);
         const double* s = P.sources + 3 * (size_t)sid;
-        trace_ray<INTEG>(P, df_from_double(s[0]), df_from_double(s[1]), df_from_double(s[2]), sid, k, r, &st);
+        trace_ray<INTEG, false>(P, df_from_double(s[0]), df_from_double(s[1]), df_from_double(s[2]), sid, k, r, &st);
     }
     out[q] = st;
 }
@@ -177,10 +245,18 @@ cudaError_t launch_render(const TraceParams& p, int integrator, int64_t* image, 
     const uint64_t blocks = (total + rays_per_cta - 1) / rays_per_cta;
     if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     timing_begin("render", s);
-    if (integrator == PIVBOS_RK4)
-        render_kernel<PIVBOS_RK4><<<(unsigned)blocks, kRenderThreads, 0, s>>>(p, image, stats, rays_per_cta, total);
-    else
-        render_kernel<PIVBOS_EULER><<<(unsigned)blocks, kRenderThreads, 0, s>>>(p, image, stats, rays_per_cta, total);
+    const bool cache = p.cell_cache != 0;
+    if (integrator == PIVBOS_RK4) {
+        if (cache)
+            render_kernel<PIVBOS_RK4, true><<<(unsigned)blocks, kRenderThreads, 0, s>>>(p, image, stats, rays_per_cta, total);
+        else
+            render_kernel<PIVBOS_RK4, false><<<(unsigned)blocks, kRenderThreads, 0, s>>>(p, image, stats, rays_per_cta, total);
+    } else {
+        if (cache)
+            render_kernel<PIVBOS_EULER, true><<<(unsigned)blocks, kRenderThreads, 0, s>>>(p, image, stats, rays_per_cta, total);
+        else
+            render_kernel<PIVBOS_EULER, false><<<(unsigned)blocks, kRenderThreads, 0, s>>>(p, image, stats, rays_per_cta, total);
+    }
     timing_end("render", s);
     count_launches(1);
     return cudaGetLastError();

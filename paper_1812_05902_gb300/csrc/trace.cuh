@@ -125,25 +125,68 @@ __device__ __forceinline__ void cell_split(float gh, float gl, int N, int& i, fl
     }
 }
 
-__device__ __forceinline__ float3 eval_D_split(const DevMedium& m, float hx, float lx, float hy, float ly, float hz,
-                                               float lz)
+// Corners of the last cell a ray sampled.  Consecutive Runge-Kutta stages
+// and steps mostly fall in the same cell (the first stage of a step lies
+// within ~1e-11 m of the last stage of the previous one), so keeping the
+// eight float4 corners in registers saves most of the gathers.
+template <bool CACHE>
+struct CellCache {
+    __device__ __forceinline__ void reset() {}
+};
+template <>
+struct CellCache<true> {
+    int cell;
+    float4 c[8];
+    __device__ __forceinline__ void reset() { cell = -1; }
+};
+
+// D = n grad n (Eq. 6) from the trilinear samples of n - 1 and grad n at the
+// grid point gh + gl (see cell_split), written as the weighted sum of the
+// eight corner values, w = (1-fx or fx)(1-fy or fy)(1-fz or fz).
+template <bool CACHE>
+__device__ __forceinline__ float3 eval_D_split(const DevMedium& m, CellCache<CACHE>& cc, float hx, float lx, float hy,
+                                               float ly, float hz, float lz)
 {
     int i, j, k;
     float fx, fy, fz;
     cell_split(hx, lx, m.n[0], i, fx);
     cell_split(hy, ly, m.n[1], j, fy);
     cell_split(hz, lz, m.n[2], k, fz);
-    const int sy = m.n[0];
-    const int sz = m.n[0] * m.n[1];
-    const float4* p = m.field + ((k * m.n[1] + j) * m.n[0] + i);
-    const float4 c000 = __ldg(p), c100 = __ldg(p + 1);
-    const float4 c010 = __ldg(p + sy), c110 = __ldg(p + sy + 1);
-    const float4 c001 = __ldg(p + sz), c101 = __ldg(p + sz + 1);
-    const float4 c011 = __ldg(p + sz + sy), c111 = __ldg(p + sz + sy + 1);
-    const float4 x00 = lerp4(c000, c100, fx), x10 = lerp4(c010, c110, fx);
-    const float4 x01 = lerp4(c001, c101, fx), x11 = lerp4(c011, c111, fx);
-    const float4 y0 = lerp4(x00, x10, fy), y1 = lerp4(x01, x11, fy);
-    const float4 v = lerp4(y0, y1, fz);
+    const int cell = (k * m.n[1] + j) * m.n[0] + i;
+    float4 c[8];
+    if constexpr (CACHE) {
+        if (cell != cc.cell) {
+            const int sy = m.n[0];
+            const int sz = m.n[0] * m.n[1];
+            const float4* p = m.field + cell;
+            cc.c[0] = __ldg(p);           cc.c[1] = __ldg(p + 1);
+            cc.c[2] = __ldg(p + sy);      cc.c[3] = __ldg(p + sy + 1);
+            cc.c[4] = __ldg(p + sz);      cc.c[5] = __ldg(p + sz + 1);
+            cc.c[6] = __ldg(p + sz + sy); cc.c[7] = __ldg(p + sz + sy + 1);
+            cc.cell = cell;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) c[q] = cc.c[q];
+    } else {
+        const int sy = m.n[0];
+        const int sz = m.n[0] * m.n[1];
+        const float4* p = m.field + cell;
+        c[0] = __ldg(p);           c[1] = __ldg(p + 1);
+        c[2] = __ldg(p + sy);      c[3] = __ldg(p + sy + 1);
+        c[4] = __ldg(p + sz);      c[5] = __ldg(p + sz + 1);
+        c[6] = __ldg(p + sz + sy); c[7] = __ldg(p + sz + sy + 1);
+    }
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    const float w00 = gy * gz, w10 = fy * gz, w01 = gy * fz, w11 = fy * fz;
+    const float w[8] = {gx * w00, fx * w00, gx * w10, fx * w10, gx * w01, fx * w01, gx * w11, fx * w11};
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        v.x = fmaf(w[q], c[q].x, v.x);
+        v.y = fmaf(w[q], c[q].y, v.y);
+        v.z = fmaf(w[q], c[q].z, v.z);
+        v.w = fmaf(w[q], c[q].w, v.w);
+    }
     const float n = 1.0f + v.x;
     return make_float3(n * v.y, n * v.z, n * v.w);
 }
@@ -165,7 +208,7 @@ __device__ __forceinline__ void put3(double* dst, df x, df y, df z)
 // One ray through all stages.  INTEG: PIVBOS_EULER or PIVBOS_RK4.  If st is
 // not null the full exit state is written (parity path).
 // ---------------------------------------------------------------------------
-template <int INTEG>
+template <int INTEG, bool CACHE>
 __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df sz, uint32_t sid, uint32_t rid,
                                           RayOut& out, pivbos_ray_state* st)
 {
@@ -263,18 +306,17 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
             float h_last = 0.f;
             int k = 0;
             bool done = false;
+            CellCache<CACHE> cache;
+            cache.reset();
             for (; k < P.max_steps; ++k) {
                 // current point = reference (grx, gry, grz) + perturbation (cells)
                 const float ox = fmaf(rhx, ix, grx.lo), oy = fmaf(rhy, iy, gry.lo), oz = fmaf(rhz, iz, grz.lo);
                 const float Tx = T0fx + tax, Ty = T0fy + tay, Tz = T0fz + taz;
                 // parameter distance to the box boundary along the tangent
                 float dexit = INFINITY;
-                if (Tx > 0.f) dexit = fminf(dexit, ((ex - grx.hi) - ox) * m.h[0] / Tx);
-                else if (Tx < 0.f) dexit = fminf(dexit, (-grx.hi - ox) * m.h[0] / Tx);
-                if (Ty > 0.f) dexit = fminf(dexit, ((ey - gry.hi) - oy) * m.h[1] / Ty);
-                else if (Ty < 0.f) dexit = fminf(dexit, (-gry.hi - oy) * m.h[1] / Ty);
-                if (Tz > 0.f) dexit = fminf(dexit, ((ez - grz.hi) - oz) * m.h[2] / Tz);
-                else if (Tz < 0.f) dexit = fminf(dexit, (-grz.hi - oz) * m.h[2] / Tz);
+                if (Tx != 0.f) dexit = fminf(dexit, (Tx > 0.f ? (ex - grx.hi) - ox : -grx.hi - ox) * __fdividef(m.h[0], Tx));
+                if (Ty != 0.f) dexit = fminf(dexit, (Ty > 0.f ? (ey - gry.hi) - oy : -gry.hi - oy) * __fdividef(m.h[1], Ty));
+                if (Tz != 0.f) dexit = fminf(dexit, (Tz > 0.f ? (ez - grz.hi) - oz : -grz.hi - oz) * __fdividef(m.h[2], Tz));
                 float h = hstep;
                 if (hstep >= dexit) {
                     h = fmaxf(dexit, 0.f);
@@ -295,8 +337,8 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
                     const float px = (cT * Tx + cK * kx) * h;
                     const float py = (cT * Ty + cK * ky) * h;
                     const float pz = (cT * Tz + cK * kz) * h;
-                    const float3 Dv = eval_D_split(m, grx.hi, fmaf(px, ix, ox), gry.hi, fmaf(py, iy, oy), grz.hi,
-                                                   fmaf(pz, iz, oz));
+                    const float3 Dv = eval_D_split<CACHE>(m, cache, grx.hi, fmaf(px, ix, ox), gry.hi,
+                                                          fmaf(py, iy, oy), grz.hi, fmaf(pz, iz, oz));
                     kx = Dv.x * h;
                     ky = Dv.y * h;
                     kz = Dv.z * h;
