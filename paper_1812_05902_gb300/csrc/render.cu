@@ -59,6 +59,17 @@ __device__ __forceinline__ void add_q(unsigned long long* tile, int ax, int ay, 
     }
 }
 
+// Round-to-nearest-even of a non-negative float below 2^33 to an integer
+// with FP32/INT32 instructions only (the 64-bit float-to-integer conversion
+// runs on GB300's narrow FP64 pipe).  Below 2^23 adding 2^23 rounds to an
+// integer in the mantissa; from 2^23 up the float is already an integer.
+__device__ __forceinline__ long long round_pos_to_ll(float x)
+{
+    if (x < 8388608.0f) return (long long)(__float_as_uint(x + 8388608.0f) - 0x4B000000u);
+    const uint32_t b = __float_as_uint(x);
+    return (long long)((b & 0x7FFFFFu) | 0x800000u) << ((int)(b >> 23) - 150);
+}
+
 // Quantise the spot of one ray and add it (tile if inside, image otherwise).
 __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
                                             unsigned long long* tile, int ax, int ay, int64_t* image)
@@ -67,28 +78,25 @@ __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
     spot_window(o, px, py, sw);
     long long sum = 0, qmax = -1;
     int imax = 0, jmax = 0;
+#pragma unroll 1
     for (int j = 0; j < sw.ny; ++j) {
         const float wyj = sw.wy[j] * sw.scale;
-#pragma unroll
-        for (int i = 0; i < PIVBOS_MAX_WINDOW; ++i) {
-            if (i < sw.nx) {
-                const long long q = __float2ll_rn(sw.wx[i] * wyj);
-                sum += q;
-                if (q > qmax) { qmax = q; imax = i; jmax = j; }
-            }
+#pragma unroll 1
+        for (int i = 0; i < sw.nx; ++i) {
+            const long long q = round_pos_to_ll(sw.wx[i] * wyj);
+            sum += q;
+            if (q > qmax) { qmax = q; imax = i; jmax = j; }
         }
     }
     const long long rem = 4294967296LL - sum;
+#pragma unroll 1
     for (int j = 0; j < sw.ny; ++j) {
         const float wyj = sw.wy[j] * sw.scale;
-#pragma unroll
-        for (int i = 0; i < PIVBOS_MAX_WINDOW; ++i) {
-            if (i < sw.nx) {
-                long long q = __float2ll_rn(sw.wx[i] * wyj);
-                if (i == imax && j == jmax) q += rem;
-                if (q != 0)
-                    add_q(tile, ax, ay, image, o.W, sw.x0 + i, sw.y0 + j, (unsigned long long)q);
-            }
+#pragma unroll 1
+        for (int i = 0; i < sw.nx; ++i) {
+            long long q = round_pos_to_ll(sw.wx[i] * wyj);
+            if (i == imax && j == jmax) q += rem;
+            if (q != 0) add_q(tile, ax, ay, image, o.W, sw.x0 + i, sw.y0 + j, (unsigned long long)q);
         }
     }
 }

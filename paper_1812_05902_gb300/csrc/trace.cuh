@@ -509,17 +509,15 @@ __device__ __forceinline__ void axis_weights(df p, float win3, int N, float inv_
     // hit position relative to the window start (exact difference, then FP32)
     const float f = __fadd_rn(__fsub_rn(p.hi, (float)a), p.lo);
     float e_prev = erff((0.0f - f) * inv_s2);
+    float fi = 1.0f;   // pixel edge index, exact in FP32
     sum = 0.f;
-#pragma unroll
-    for (int i = 0; i < PIVBOS_MAX_WINDOW; ++i) {
-        if (i < cnt) {
-            const float e_next = erff(((float)(i + 1) - f) * inv_s2);
-            w[i] = 0.5f * (e_next - e_prev);
-            sum += w[i];
-            e_prev = e_next;
-        } else {
-            w[i] = 0.f;
-        }
+#pragma unroll 1
+    for (int i = 0; i < cnt; ++i) {
+        const float e_next = erff((fi - f) * inv_s2);
+        w[i] = 0.5f * (e_next - e_prev);
+        sum += w[i];
+        e_prev = e_next;
+        fi += 1.0f;
     }
 }
 
