@@ -40,6 +40,8 @@ WORKLOAD_NAMES = {
     "c2": "BOS k^-5/3 turbulence 256^3 over 0.1 m, 1e5 dots x 1e3 rays, RK4 0.2 mm, thick lens f/8 M=0.1, 1024^2",
     "c4": "Tomo-PIV 1e5 particles x 1e4 rays in a 100x100x30 mm 256^3 turbulence field, RK4 0.2 mm, thick lens "
           "f/4 M=0.2, 2048^2",
+    "c3": "64 frames in one persistent graph-replayed launch: 10^U(3,5) sources, grids 64^3-256^3, shock / "
+          "gradient / turbulence in rotation, 10^U(3,4) rays/source, RK4 0.2 mm, thick lens f/8 M=0.1, 1024^2",
 }
 METRIC = "rays/s traced to sensor at 1 GB300 (plain vs surrogate at ≤0.01 px RMS error)"
 
@@ -63,6 +65,8 @@ def _frames(workload, scale=1.0):
         return scenes.c2(scale=scale)
     if workload == "c4":
         return scenes.c4(scale=scale)
+    if workload == "c3":
+        return scenes.c3(scale=scale)
     raise SystemExit("unknown workload %s" % workload)
 
 
@@ -378,6 +382,64 @@ def run_gpu(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
+def run_batch(args, rank, world):
+    """C3: all frames in one persistent launch (CUDA graph replay per step)."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1812_05902_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1812_05902_gb300 import pivbos as P
+    frames = _frames("c3", args.scale)
+    for fr in frames:
+        fr.seed = fr.seed + 1000003 * rank
+    opt = P.Optics(frames[0].optics)
+    meds, srcs, imgs, descs = [], [], [], []
+    for fr in frames:
+        meds.append(P.Medium(fr.medium, rho=torch.tensor(fr.medium.rho, device=dev)))
+        srcs.append(torch.tensor(fr.sources, dtype=torch.float64, device=dev))
+        imgs.append(torch.zeros((fr.optics.height, fr.optics.width), dtype=torch.int64, device=dev))
+        descs.append(P.frame_desc(meds[-1].h, opt.h, srcs[-1], len(fr.sources), fr.rays_per_source,
+                                  fr.frame_index, fr.seed, fr.step, imgs[-1]))
+    batch = P.pivbos_batch_create(descs, scenes.RK4, None)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        P.pivbos_batch_render(batch)
+    P.pivbos_sync()
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = P.pivbos_kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.pivbos_batch_render(batch)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    launches = P.pivbos_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in times)
+    rays = sum(fr.n_rays for fr in frames)
+    P.pivbos_batch_destroy(batch)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": rays * args.steps * world / (ms * 1e-3), "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (double-float f32 pairs for positions/directions)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES["c3"] + ("" if args.scale == 1.0 else " (scaled by %g)" % args.scale),
+                       "name": "c3", "frames": len(frames), "rays_per_step": rays, "l2": "flushed between steps"},
+            "gpu_launches": int(launches), "clocks": clk, "roofline": None, "e2e": None, "cpu_baseline": None,
+            "impl": "pivbos"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,7 +461,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        run_gpu(args, rank, world)
+        if args.workload == "c3":
+            run_batch(args, rank, world)
+        else:
+            run_gpu(args, rank, world)
     finally:
         if world > 1:
             import torch.distributed as dist

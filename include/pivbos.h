@@ -209,6 +209,69 @@ pivbos_status pivbos_trace_exit_states(const pivbos_medium* m, const pivbos_opti
                                        const int64_t* ray_ids, int64_t n_rays,
                                        pivbos_ray_state* out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched rendering (many frames of uneven size in one persistent launch).
+ * A frame is one pivbos_render call's worth of arguments with device
+ * buffers.  pivbos_batch_create validates the frames, allocates the
+ * per-frame sort scratch and a device work queue, and orders the frames by
+ * estimated work (largest first).  pivbos_batch_render enqueues, on
+ * `stream`, the Morton ordering of every frame's sources and one persistent
+ * kernel whose CTAs pop (frame, chunk of rays) items until all frames are
+ * done; images and stats are accumulated into exactly as pivbos_render
+ * would.  With tuning.use_graph the first call captures this sequence into
+ * a CUDA graph (on a private stream) and every call launches that graph on
+ * `stream` (the frames' buffers must stay at the same addresses; their
+ * contents may change).
+ * All frames of a batch share one integrator.  The batch does not own the
+ * media, optics or buffers, which must outlive it.
+ * Errors: as pivbos_render; INVALID_ARG for a frame with host buffers.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    const pivbos_medium* medium;   /* NULL = uniform medium */
+    const pivbos_optics* optics;
+    const double* sources;         /* device [n_sources][3] */
+    int64_t n_sources;
+    int32_t rays_per_source;
+    uint32_t frame;                /* Philox counter word of the frame */
+    uint64_t seed;
+    double step;                   /* integration parameter step, > 0 */
+    int64_t* image;                /* device int64 [H][W] of the optics, accumulated into */
+    int64_t* stats;                /* device int64 [PIVBOS_RAY_NSTATUS] or NULL */
+} pivbos_frame_desc;
+
+typedef struct {
+    int32_t rays_per_cta;          /* rays per work item: 256..2048, multiple of 256 */
+    int32_t cell_cache;            /* 1: keep the last cell's corners in registers */
+    int32_t ctas_per_sm;           /* persistent CTAs per SM: 1..3 (1..2 with cell_cache) */
+    int32_t use_graph;             /* 1: capture once per stream, then replay a CUDA graph */
+} pivbos_tuning;
+
+typedef struct pivbos_batch pivbos_batch;
+
+/* Defaults: 2048 rays per item, no cell cache, 3 CTAs per SM, graphs on. */
+pivbos_status pivbos_default_tuning(pivbos_tuning* out);
+
+pivbos_status pivbos_batch_create(const pivbos_frame_desc* frames, int n_frames, int integrator,
+                                  const pivbos_tuning* tuning /* NULL = defaults */, pivbos_batch** out);
+pivbos_status pivbos_batch_render(pivbos_batch* b, void* stream);
+void pivbos_batch_destroy(pivbos_batch* b);
+
+/* Autotuner for one frame (synchronous on `stream`; allocates its own
+ * scratch, never writes the frame's image or stats).
+ *  - step: starting from frame->step, the largest step (doubling, at most
+ *    64x; halving, at most 64x, if the start is too coarse) whose estimated
+ *    sensor error on n_sample_rays seeded rays stays within tol_px pixels;
+ *    the error of step h is estimated from the traces with h and h/2
+ *    (Richardson: x 16/15 for RK4, x 2 for the first-order scheme).  With
+ *    no medium the step is returned unchanged.
+ *  - tuning: the fastest of rays_per_cta in {512, 1024, 2048} with and
+ *    without the cell cache, timed on a sub-frame of about 4e6 rays.
+ * Results are only suggestions: the caller decides which step to render
+ * with (the step changes the integration, hence the image). */
+pivbos_status pivbos_autotune(const pivbos_frame_desc* frame, int integrator, double tol_px,
+                              int32_t n_sample_rays, double* step_out, pivbos_tuning* tuning_out,
+                              void* stream);
+
 /* int64 32.32 image -> float32 intensity in rays (value * 2^-32).  Device
  * pointers, n_pixels >= 0. */
 pivbos_status pivbos_image_finalize(const int64_t* image, int64_t n_pixels, float* out, void* stream);

@@ -210,6 +210,23 @@ pivbos_status prepare(const pivbos_medium* m, const pivbos_optics* o, const doub
 
 void set_last_error(const char* msg) { t_err = msg; }
 
+pivbos_status prepare_trace(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
+                            int64_t n_sources, int sources_on_device, int32_t rays_per_source, uint64_t seed,
+                            uint32_t frame, int integrator, double step, TraceParams* p, int* dev, uint64_t* total)
+{
+    Prepared pr;
+    const pivbos_status st = prepare(m, o, sources, n_sources, sources_on_device, rays_per_source, seed, frame,
+                                     integrator, step, &pr);
+    if (st) return st;
+    *p = pr.p;
+    *dev = pr.dev;
+    *total = pr.total;
+    return PIVBOS_OK;
+}
+
+bool g_timing_suppressed = false;
+void timing_suppress(bool on) { g_timing_suppressed = on; }
+
 int tuning_cell_cache(int dense)
 {
     static int v = -2;
@@ -223,7 +240,7 @@ int tuning_cell_cache(int dense)
 void timing_begin(const char* name, cudaStream_t s)
 {
     std::lock_guard<std::mutex> lk(g_tmu);
-    if (!g_timing) return;
+    if (!g_timing || g_timing_suppressed) return;
     TimingRec r;
     r.name = name;
     if (cudaEventCreate(&r.a) != cudaSuccess) return;
@@ -237,7 +254,7 @@ void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relax
 void timing_end(const char* name, cudaStream_t s)
 {
     std::lock_guard<std::mutex> lk(g_tmu);
-    if (!g_timing || t_open < 0 || t_open >= (long)g_pending.size()) return;
+    if (!g_timing || g_timing_suppressed || t_open < 0 || t_open >= (long)g_pending.size()) return;
     TimingRec& r = g_pending[t_open];
     if (r.name != name || r.b) return;
     if (cudaEventCreate(&r.b) != cudaSuccess) return;

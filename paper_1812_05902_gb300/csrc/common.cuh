@@ -69,6 +69,16 @@ struct TraceParams {
     int* status_word;         // device status word (first error latched)
 };
 
+// One frame of a batch render (device copy).
+struct BatchFrame {
+    TraceParams p;
+    int64_t* image;
+    int64_t* stats;
+    uint32_t rays_per_cta;
+    uint32_t pad;
+    uint64_t total_rays;
+};
+
 // Internal launchers (each defined in the translation unit holding the kernel).
 cudaError_t launch_medium_prep(const float* rho, float4* field, int nx, int ny, int nz,
                                const double spacing[3], double K, cudaStream_t s);
@@ -80,6 +90,8 @@ cudaError_t launch_render(const TraceParams& p, int integrator, int64_t* image, 
                           uint32_t rays_per_cta, cudaStream_t s);
 cudaError_t launch_trace_states(const TraceParams& p, int integrator, const int64_t* ray_ids,
                                 int64_t n_rays, pivbos_ray_state* out, cudaStream_t s);
+cudaError_t launch_batch(const BatchFrame* frames, const uint64_t* item_start, int n_frames, uint64_t total_items,
+                         unsigned long long* counter, int integrator, bool cache, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_finalize(const int64_t* image, int64_t n, float* out, cudaStream_t s);
 
 // Tuning knob (api.cu): keep cell corners in registers during integration;

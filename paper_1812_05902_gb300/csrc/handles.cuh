@@ -21,4 +21,10 @@ struct pivbos_optics {
 namespace pivbos {
 // Message returned by pivbos_last_error() on this thread.
 void set_last_error(const char* msg);
+// Validation and parameter assembly shared by every render entry point.
+pivbos_status prepare_trace(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
+                            int64_t n_sources, int sources_on_device, int32_t rays_per_source, uint64_t seed,
+                            uint32_t frame, int integrator, double step, TraceParams* p, int* dev, uint64_t* total);
+// Keep kernel timing out of captured streams.
+void timing_suppress(bool on);
 }  // namespace pivbos

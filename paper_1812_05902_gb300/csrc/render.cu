@@ -106,28 +106,31 @@ __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
 // rays_per_cta consecutive rays; a CTA takes one chunk, so its rays come
 // from one source or a few neighbouring ones and their spots fall in one
 // 32x32 shared tile anchored at the first hit.
-template <int INTEG, bool CACHE>
-__global__ void __launch_bounds__(kRenderThreads, CACHE ? 2 : kRenderMinBlocks)
-render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restrict__ stats,
-              uint32_t rays_per_cta, uint64_t total_rays)
-{
-    __shared__ unsigned long long tile[kTileW * kTileH];
-    __shared__ uint32_t s_order[kMaxOrderRays];
-    __shared__ int s_anchor_tid;
-    __shared__ int s_ax, s_ay;
-    __shared__ unsigned long long s_cnt[PIVBOS_RAY_NSTATUS];
+// Shared memory of one CTA working on one chunk of rays.
+struct ChunkShared {
+    unsigned long long tile[kTileW * kTileH];
+    uint32_t order[kMaxOrderRays];
+    unsigned long long cnt[PIVBOS_RAY_NSTATUS];
+    int anchor_tid, ax, ay;
+};
 
-    for (int q = threadIdx.x; q < kTileW * kTileH; q += blockDim.x) tile[q] = 0ull;
+// Rays [first, last) of the flattened (Morton slot, ray) space of one render:
+// trace (in mid-plane Morton order in dense media), deposit into the shared
+// tile anchored at the first hit, flush the tile, add the status counts.
+// Every thread of the CTA must call it; it leaves `sh` free for reuse.
+template <int INTEG, bool CACHE>
+__device__ __forceinline__ void render_chunk(const TraceParams& P, ChunkShared& sh, uint64_t first, uint64_t last,
+                                             int64_t* __restrict__ image, int64_t* __restrict__ stats)
+{
+    for (int q = threadIdx.x; q < kTileW * kTileH; q += blockDim.x) sh.tile[q] = 0ull;
     if (threadIdx.x == 0) {
-        s_anchor_tid = 0x7fffffff;
-        s_ax = -(1 << 28);
-        s_ay = -(1 << 28);
+        sh.anchor_tid = 0x7fffffff;
+        sh.ax = -(1 << 28);
+        sh.ay = -(1 << 28);
     }
-    if (threadIdx.x < PIVBOS_RAY_NSTATUS) s_cnt[threadIdx.x] = 0ull;
+    if (threadIdx.x < PIVBOS_RAY_NSTATUS) sh.cnt[threadIdx.x] = 0ull;
     __syncthreads();
 
-    const uint64_t first = (uint64_t)blockIdx.x * rays_per_cta;
-    const uint64_t last = min(first + rays_per_cta, total_rays);
     const uint32_t rps = P.rays_per_source;
     unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
 
@@ -140,7 +143,7 @@ render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restr
         uint32_t n_pow2 = 1;
         while (n_pow2 < n_here) n_pow2 <<= 1;
         for (uint32_t q = threadIdx.x; q < n_pow2; q += blockDim.x)
-            s_order[q] = q < n_here ? ray_order_key(P, (uint32_t)first + q, q) : 0xffffffffu;
+            sh.order[q] = q < n_here ? ray_order_key(P, (uint32_t)first + q, q) : 0xffffffffu;
         __syncthreads();
         for (uint32_t kk = 2; kk <= n_pow2; kk <<= 1) {
             for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
@@ -148,24 +151,24 @@ render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restr
                     const uint32_t i = 2 * t - (t & (j - 1));
                     const uint32_t l = i + j;
                     const bool up = (i & kk) == 0;
-                    const uint32_t a = s_order[i], b = s_order[l];
+                    const uint32_t a = sh.order[i], b = sh.order[l];
                     if ((a > b) == up) {
-                        s_order[i] = b;
-                        s_order[l] = a;
+                        sh.order[i] = b;
+                        sh.order[l] = a;
                     }
                 }
                 __syncthreads();
             }
         }
     }
-    // one uniform loop over the CTA's rays; after the first round every
+    // one uniform loop over the chunk's rays; after the first round every
     // thread's first hit is known and the lowest-thread hit anchors the tile
-    const int rounds = (int)((last - first + blockDim.x - 1) / blockDim.x);
+    const int rounds = (int)((n_here + blockDim.x - 1) / blockDim.x);
     int ax = -(1 << 28), ay = -(1 << 28);
     for (int round = 0; round < rounds; ++round) {
         const uint32_t e = (uint32_t)round * blockDim.x + threadIdx.x;
         const bool active = e < n_here;
-        const uint64_t idx = first + (reorder && active ? (s_order[e] & 0x7ffu) : e);
+        const uint64_t idx = first + (reorder && active ? (sh.order[e] & 0x7ffu) : e);
         RayOut r;
         r.status = PIVBOS_RAY_MISS;
         if (active) {
@@ -178,38 +181,93 @@ render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restr
             cnt[r.status]++;
         }
         if (round == 0) {
-            if (active && r.status == PIVBOS_RAY_REACHED) atomicMin(&s_anchor_tid, (int)threadIdx.x);
+            if (active && r.status == PIVBOS_RAY_REACHED) atomicMin(&sh.anchor_tid, (int)threadIdx.x);
             __syncthreads();
-            if ((int)threadIdx.x == s_anchor_tid) {
+            if ((int)threadIdx.x == sh.anchor_tid) {
                 float f;
-                s_ax = df_floor(r.px, f) - kTileW / 2;
-                s_ay = df_floor(r.py, f) - kTileH / 2;
+                sh.ax = df_floor(r.px, f) - kTileW / 2;
+                sh.ay = df_floor(r.py, f) - kTileH / 2;
             }
             __syncthreads();
-            ax = s_ax;
-            ay = s_ay;
+            ax = sh.ax;
+            ay = sh.ay;
         }
-        if (active && r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, tile, ax, ay, image);
+        if (active && r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, sh.tile, ax, ay, image);
     }
     if (stats) {
 #pragma unroll
         for (int q = 0; q < PIVBOS_RAY_NSTATUS; ++q) {
             unsigned v = cnt[q];
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[q], (unsigned long long)v);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sh.cnt[q], (unsigned long long)v);
         }
     }
     __syncthreads();
     // flush the tile: one global atomic per touched pixel
     for (int q = threadIdx.x; q < kTileW * kTileH; q += blockDim.x) {
-        const unsigned long long v = tile[q];
+        const unsigned long long v = sh.tile[q];
         if (v) {
             const int gx = ax + (q % kTileW), gy = ay + (q / kTileW);
             atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * P.o.W + gx]), v);
         }
     }
-    if (stats && threadIdx.x < PIVBOS_RAY_NSTATUS && s_cnt[threadIdx.x])
-        atomicAdd(reinterpret_cast<unsigned long long*>(&stats[threadIdx.x]), s_cnt[threadIdx.x]);
+    if (stats && threadIdx.x < PIVBOS_RAY_NSTATUS && sh.cnt[threadIdx.x])
+        atomicAdd(reinterpret_cast<unsigned long long*>(&stats[threadIdx.x]), sh.cnt[threadIdx.x]);
+    __syncthreads();
+}
+
+template <int INTEG, bool CACHE>
+__global__ void __launch_bounds__(kRenderThreads, CACHE ? 2 : kRenderMinBlocks)
+render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restrict__ stats,
+              uint32_t rays_per_cta, uint64_t total_rays)
+{
+    __shared__ ChunkShared sh;
+    const uint64_t first = (uint64_t)blockIdx.x * rays_per_cta;
+    const uint64_t last = min(first + rays_per_cta, total_rays);
+    render_chunk<INTEG, CACHE>(P, sh, first, last, image, stats);
+}
+
+// Persistent batch kernel: CTAs pop work items (a frame and a chunk of its
+// rays) from a device counter until the queue is empty.  Items are numbered
+// frame by frame in the order the host chose (largest work first); the
+// frame's parameters are copied to shared memory once per item.
+template <int INTEG, bool CACHE>
+__global__ void __launch_bounds__(kRenderThreads, CACHE ? 2 : kRenderMinBlocks)
+batch_kernel(const BatchFrame* __restrict__ frames, const uint64_t* __restrict__ item_start, int n_frames,
+             uint64_t total_items, unsigned long long* __restrict__ counter)
+{
+    __shared__ ChunkShared sh;
+    __shared__ TraceParams sP;
+    __shared__ unsigned long long s_item;
+    __shared__ int s_frame;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long it = atomicAdd(counter, 1ull);
+            s_item = it;
+            int lo = 0, hi = n_frames - 1;
+            if (it < total_items) {
+                while (lo < hi) {   // last frame whose first item <= it
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (item_start[mid] <= it) lo = mid; else hi = mid - 1;
+                }
+            }
+            s_frame = lo;
+        }
+        __syncthreads();
+        const unsigned long long it = s_item;
+        if (it >= total_items) break;
+        const int f = s_frame;
+        {
+            const int* src = reinterpret_cast<const int*>(&frames[f].p);
+            int* dst = reinterpret_cast<int*>(&sP);
+            for (int q = threadIdx.x; q < (int)(sizeof(TraceParams) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+        }
+        __syncthreads();
+        const BatchFrame& F = frames[f];
+        const uint64_t first = (it - item_start[f]) * (uint64_t)F.rays_per_cta;
+        const uint64_t last = min(first + F.rays_per_cta, F.total_rays);
+        render_chunk<INTEG, CACHE>(sP, sh, first, last, F.image, F.stats);
+    }
 }
 
 template <int INTEG>
@@ -266,6 +324,28 @@ cudaError_t launch_render(const TraceParams& p, int integrator, int64_t* image, 
             render_kernel<PIVBOS_EULER, false><<<(unsigned)blocks, kRenderThreads, 0, s>>>(p, image, stats, rays_per_cta, total);
     }
     timing_end("render", s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchFrame* frames, const uint64_t* item_start, int n_frames, uint64_t total_items,
+                         unsigned long long* counter, int integrator, bool cache, int ctas_per_sm, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)(sms * ctas_per_sm);
+    if (integrator == PIVBOS_RK4) {
+        if (cache)
+            batch_kernel<PIVBOS_RK4, true><<<grid, kRenderThreads, 0, s>>>(frames, item_start, n_frames, total_items, counter);
+        else
+            batch_kernel<PIVBOS_RK4, false><<<grid, kRenderThreads, 0, s>>>(frames, item_start, n_frames, total_items, counter);
+    } else {
+        if (cache)
+            batch_kernel<PIVBOS_EULER, true><<<grid, kRenderThreads, 0, s>>>(frames, item_start, n_frames, total_items, counter);
+        else
+            batch_kernel<PIVBOS_EULER, false><<<grid, kRenderThreads, 0, s>>>(frames, item_start, n_frames, total_items, counter);
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -39,6 +39,18 @@ class pivbos_surface(ctypes.Structure):
                 ("clear_radius", ctypes.c_double)]
 
 
+class pivbos_frame_desc(ctypes.Structure):
+    _fields_ = [("medium", ctypes.c_void_p), ("optics", ctypes.c_void_p), ("sources", ctypes.c_void_p),
+                ("n_sources", ctypes.c_int64), ("rays_per_source", ctypes.c_int32), ("frame", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("step", ctypes.c_double), ("image", ctypes.c_void_p),
+                ("stats", ctypes.c_void_p)]
+
+
+class pivbos_tuning(ctypes.Structure):
+    _fields_ = [("rays_per_cta", ctypes.c_int32), ("cell_cache", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
 class PivbosError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("pivbos status %d: %s" % (status, msg))
@@ -69,6 +81,11 @@ def _load():
         "pivbos_version": ([], ctypes.c_char_p),
         "pivbos_kernel_launches": ([], I64),
         "pivbos_render_noalloc": ([P, P, P, I64, I32, U64, U32, I, D, P, P, P], I),
+        "pivbos_default_tuning": ([P], I),
+        "pivbos_batch_create": ([P, I, I, P, P], I),
+        "pivbos_batch_render": ([P, P], I),
+        "pivbos_batch_destroy": ([P], None),
+        "pivbos_autotune": ([P, I, D, I32, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -81,7 +98,9 @@ _lib = _load()
 EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destroy", "pivbos_optics_create",
             "pivbos_optics_destroy", "pivbos_render", "pivbos_trace_exit_states", "pivbos_image_finalize",
             "pivbos_sync", "pivbos_last_error", "pivbos_timing_enable", "pivbos_timing_reset",
-            "pivbos_timing_read", "pivbos_version", "pivbos_kernel_launches", "pivbos_render_noalloc")
+            "pivbos_timing_read", "pivbos_version", "pivbos_kernel_launches", "pivbos_render_noalloc",
+            "pivbos_default_tuning", "pivbos_batch_create", "pivbos_batch_render", "pivbos_batch_destroy",
+            "pivbos_autotune")
 NOALLOC_MAX_SOURCES = 1 << 17
 
 
@@ -176,6 +195,42 @@ def pivbos_render_noalloc(m, o, sources, n_sources, rays_per_source, seed, frame
     st_p, _ = _addr(stats)
     _check(_lib.pivbos_render_noalloc(m, o, sp, n_sources, rays_per_source, seed, frame, integrator, step,
                                       ip, st_p, _stream(stream)))
+
+
+def frame_desc(medium, optics, sources, n_sources, rays_per_source, frame, seed, step, image, stats=None):
+    return pivbos_frame_desc(medium, optics, ctypes.c_void_p(sources.data_ptr()), n_sources, rays_per_source,
+                             frame, seed, step, ctypes.c_void_p(image.data_ptr()),
+                             ctypes.c_void_p(stats.data_ptr()) if stats is not None else None)
+
+
+def pivbos_default_tuning():
+    t = pivbos_tuning()
+    _check(_lib.pivbos_default_tuning(ctypes.byref(t)))
+    return t
+
+
+def pivbos_batch_create(descs, integrator, tuning=None):
+    arr = (pivbos_frame_desc * len(descs))(*descs)
+    out = ctypes.c_void_p()
+    _check(_lib.pivbos_batch_create(arr, len(descs), integrator, ctypes.byref(tuning) if tuning else None,
+                                    ctypes.byref(out)))
+    return out
+
+
+def pivbos_batch_render(batch, stream=None):
+    _check(_lib.pivbos_batch_render(batch, _stream(stream)))
+
+
+def pivbos_batch_destroy(batch):
+    _lib.pivbos_batch_destroy(batch)
+
+
+def pivbos_autotune(desc, integrator, tol_px, n_sample_rays, stream=None):
+    step = ctypes.c_double()
+    t = pivbos_tuning()
+    _check(_lib.pivbos_autotune(ctypes.byref(desc), integrator, tol_px, n_sample_rays, ctypes.byref(step),
+                                ctypes.byref(t), _stream(stream)))
+    return step.value, t
 
 
 def pivbos_trace_exit_states(m, o, sources, n_sources, rays_per_source, seed, frame, integrator, step,

@@ -45,8 +45,9 @@ def test_struct_layouts_match_header(P):
 #include <stddef.h>
 #include "pivbos.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\n", sizeof(pivbos_surface), offsetof(pivbos_surface, clear_radius),
-         sizeof(pivbos_ray_state), offsetof(pivbos_ray_state, status));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(pivbos_surface), offsetof(pivbos_surface, clear_radius),
+         sizeof(pivbos_ray_state), offsetof(pivbos_ray_state, status), sizeof(pivbos_frame_desc),
+         offsetof(pivbos_frame_desc, stats), sizeof(pivbos_tuning));
   return 0;
 }
 """
@@ -60,6 +61,9 @@ int main(void) {
     assert vals[1] == P.pivbos_surface.clear_radius.offset
     assert vals[2] == P.RAY_STATE.itemsize
     assert vals[3] == P.RAY_STATE.fields["status"][1]
+    assert vals[4] == ctypes.sizeof(P.pivbos_frame_desc)
+    assert vals[5] == P.pivbos_frame_desc.stats.offset
+    assert vals[6] == ctypes.sizeof(P.pivbos_tuning)
 
 
 def test_argument_errors_without_a_device(P):
