@@ -198,6 +198,17 @@ pivbos_status pivbos_render_noalloc(const pivbos_medium* m, const pivbos_optics*
                                     uint64_t seed, uint32_t frame, int integrator, double step,
                                     int64_t* image, int64_t* stats, void* stream);
 
+/* The render of sources [first_source, first_source + n_sources) of a larger
+ * source set: `sources` points at that sub-range and ray k of local source s
+ * draws its lens point with counter (k, first_source + s, frame, 0).  Renders
+ * of disjoint ranges (on one GPU or on several) add up, bit for bit, to the
+ * render of the whole set.  first_source + n_sources <= 2^32. */
+pivbos_status pivbos_render_range(const pivbos_medium* m, const pivbos_optics* o,
+                                  const double* sources, int64_t n_sources, int64_t first_source,
+                                  int sources_on_device, int32_t rays_per_source, uint64_t seed,
+                                  uint32_t frame, int integrator, double step,
+                                  int64_t* image, int image_on_device, int64_t* stats, void* stream);
+
 /* Per-ray exit states for the parity checks: the same tracing as
  * pivbos_render, without the deposit.  ray_ids (device, int64, may be NULL
  * for "all rays in order") lists flattened ids source * rays_per_source + k;

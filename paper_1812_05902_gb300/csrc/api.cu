@@ -447,10 +447,36 @@ void pivbos_optics_destroy(pivbos_optics* o) { delete o; }
 // ---------------------------------------------------------------------------
 // render
 // ---------------------------------------------------------------------------
+static pivbos_status render_impl(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
+                                 int64_t n_sources, int64_t first_source, int sources_on_device,
+                                 int32_t rays_per_source, uint64_t seed, uint32_t frame, int integrator, double step,
+                                 int64_t* image, int image_on_device, int64_t* stats, void* stream);
+
 pivbos_status pivbos_render(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
                             int64_t n_sources, int sources_on_device, int32_t rays_per_source, uint64_t seed,
                             uint32_t frame, int integrator, double step, int64_t* image, int image_on_device,
                             int64_t* stats, void* stream)
+{
+    return render_impl(m, o, sources, n_sources, 0, sources_on_device, rays_per_source, seed, frame, integrator,
+                       step, image, image_on_device, stats, stream);
+}
+
+pivbos_status pivbos_render_range(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
+                                  int64_t n_sources, int64_t first_source, int sources_on_device,
+                                  int32_t rays_per_source, uint64_t seed, uint32_t frame, int integrator,
+                                  double step, int64_t* image, int image_on_device, int64_t* stats, void* stream)
+{
+    t_err.clear();
+    if (first_source < 0 || first_source + n_sources > 0xffffffffll)
+        return fail(PIVBOS_ERR_INVALID_ARG, "first_source %lld outside [0, 2^32 - n_sources]", (long long)first_source);
+    return render_impl(m, o, sources, n_sources, first_source, sources_on_device, rays_per_source, seed, frame,
+                       integrator, step, image, image_on_device, stats, stream);
+}
+
+static pivbos_status render_impl(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
+                                 int64_t n_sources, int64_t first_source, int sources_on_device,
+                                 int32_t rays_per_source, uint64_t seed, uint32_t frame, int integrator, double step,
+                                 int64_t* image, int image_on_device, int64_t* stats, void* stream)
 {
     t_err.clear();
     if (!image) return fail(PIVBOS_ERR_INVALID_ARG, "image is NULL");
@@ -498,6 +524,7 @@ pivbos_status pivbos_render(const pivbos_medium* m, const pivbos_optics* o, cons
         pr.p.sources = dsrc;
         pr.p.perm = perm;
         pr.p.src_df = sdf;
+        pr.p.source_offset = (uint32_t)first_source;
         e = launch_render(pr.p, integrator, dimg, stats, rays_per_cta_setting(), s);
     }
     if (e == cudaSuccess && !image_on_device)

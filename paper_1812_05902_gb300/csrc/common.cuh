@@ -58,6 +58,7 @@ struct TraceParams {
     const float2* src_df;     // [slot][3] sources in Morton order as double-float (render only)
     uint32_t n_sources;
     uint32_t rays_per_source;
+    uint32_t source_offset;   // global index of this call's first source (Philox counter)
     uint64_t seed;
     uint32_t frame;
     int max_steps;

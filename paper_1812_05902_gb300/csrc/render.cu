@@ -29,7 +29,7 @@ __device__ __forceinline__ uint32_t ray_order_key(const TraceParams& P, uint32_t
 {
     const uint32_t rps = P.rays_per_source;
     const uint32_t slot = flat / rps, k = flat - slot * rps;
-    const uint32_t sid = __ldg(P.perm + slot);
+    const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
     const float2* sp = P.src_df + 3 * (size_t)slot;
     const float sx = __ldg(sp).x, sy = __ldg(sp + 1).x, sz = __ldg(sp + 2).x;
     uint64_t w0, w1;
@@ -174,7 +174,7 @@ __device__ __forceinline__ void render_chunk(const TraceParams& P, ChunkShared& 
         if (active) {
             const uint32_t flat = (uint32_t)idx;
             const uint32_t slot = flat / rps, k = flat - slot * rps;
-            const uint32_t sid = __ldg(P.perm + slot);
+            const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
             const float2* s = P.src_df + 3 * (size_t)slot;
             const float2 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2);
             trace_ray<INTEG, CACHE>(P, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, sid, k, r, nullptr);
@@ -291,7 +291,8 @@ trace_states_kernel(const TraceParams P, const int64_t* __restrict__ ray_ids, in
     } else {
         const uint32_t sid = (uint32_t)(id / rps), k = (uint32_t)(id - (int64_t)sid * rps);
         const double* s = P.sources + 3 * (size_t)sid;
-        trace_ray<INTEG, false>(P, df_from_double(s[0]), df_from_double(s[1]), df_from_double(s[2]), sid, k, r, &st);
+        trace_ray<INTEG, false>(P, df_from_double(s[0]), df_from_double(s[1]), df_from_double(s[2]),
+                                sid + P.source_offset, k, r, &st);
     }
     out[q] = st;
 }

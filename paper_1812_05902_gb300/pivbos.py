@@ -82,6 +82,7 @@ def _load():
         "pivbos_kernel_launches": ([], I64),
         "pivbos_render_noalloc": ([P, P, P, I64, I32, U64, U32, I, D, P, P, P], I),
         "pivbos_default_tuning": ([P], I),
+        "pivbos_render_range": ([P, P, P, I64, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
         "pivbos_batch_create": ([P, I, I, P, P], I),
         "pivbos_batch_render": ([P, P], I),
         "pivbos_batch_destroy": ([P], None),
@@ -100,7 +101,7 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_sync", "pivbos_last_error", "pivbos_timing_enable", "pivbos_timing_reset",
             "pivbos_timing_read", "pivbos_version", "pivbos_kernel_launches", "pivbos_render_noalloc",
             "pivbos_default_tuning", "pivbos_batch_create", "pivbos_batch_render", "pivbos_batch_destroy",
-            "pivbos_autotune")
+            "pivbos_autotune", "pivbos_render_range")
 NOALLOC_MAX_SOURCES = 1 << 17
 
 
@@ -184,6 +185,15 @@ def pivbos_render(m, o, sources, n_sources, rays_per_source, seed, frame, integr
     st_p, _ = _addr(stats)
     _check(_lib.pivbos_render(m, o, sp, n_sources, s_dev, rays_per_source, seed, frame, integrator, step,
                               ip, i_dev, st_p, _stream(stream)))
+
+
+def pivbos_render_range(m, o, sources, n_sources, first_source, rays_per_source, seed, frame, integrator, step,
+                        image, stats=None, stream=None):
+    sp, s_dev = _addr(sources)
+    ip, i_dev = _addr(image)
+    st_p, _ = _addr(stats)
+    _check(_lib.pivbos_render_range(m, o, sp, n_sources, first_source, s_dev, rays_per_source, seed, frame,
+                                    integrator, step, ip, i_dev, st_p, _stream(stream)))
 
 
 def pivbos_render_noalloc(m, o, sources, n_sources, rays_per_source, seed, frame, integrator, step, image,

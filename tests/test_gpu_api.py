@@ -119,3 +119,20 @@ def test_host_pointer_declared_as_device_is_rejected():
                          1e-4, ctypes.c_void_p(host_img.ctypes.data), 1, None, None)
     assert st == P.ERR_INVALID_ARG
     P.pivbos_sync()
+
+
+def test_range_renders_sum_to_the_full_render():
+    import torch
+    from paper_1812_05902_gb300.shard import source_range
+    P = _P()
+    fr = scenes.c2(scale=0.001, grid=48)[0]
+    med, opt = gpu_handles(fr)
+    full, _ = gpu_render(fr, handles=(med, opt))
+    src = torch.tensor(fr.sources, dtype=torch.float64, device="cuda")
+    acc = torch.zeros((fr.optics.height, fr.optics.width), dtype=torch.int64, device="cuda")
+    for rank in range(3):
+        first, count = source_range(len(fr.sources), 3, rank)
+        P.pivbos_render_range(med.h, opt.h, src[first:first + count].contiguous(), count, first,
+                              fr.rays_per_source, fr.seed, fr.frame_index, fr.integrator, fr.step, acc)
+    P.pivbos_sync()
+    assert np.array_equal(acc.cpu().numpy(), full)
