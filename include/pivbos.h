@@ -283,6 +283,21 @@ pivbos_status pivbos_autotune(const pivbos_frame_desc* frame, int integrator, do
                               int32_t n_sample_rays, double* step_out, pivbos_tuning* tuning_out,
                               void* stream);
 
+/* ---------------------------------------------------------------------------
+ * The surrogate's network (no counterpart in the paper: a learned ray map
+ * built on the tracer).  16 inputs -> 128 -> 128 -> 128 -> 128 -> 4, ReLU on
+ * the hidden layers, BF16 tensor-core products accumulating in FP32.
+ * Parameters: PIVBOS_MLP_PARAMS floats, layer by layer W [out][in] then
+ * b [out].  These two calls run the GPU kernels on host buffers for
+ * checking: the forward (x [n][16] -> y [n][4]) and the mean-squared-error
+ * loss over n x 4 outputs with its gradient (grad [PIVBOS_MLP_PARAMS]).
+ * Synchronous; they allocate their own device memory.
+ * ------------------------------------------------------------------------- */
+#define PIVBOS_MLP_PARAMS 52228
+pivbos_status pivbos_mlp_forward(const float* params, const float* x, int32_t n, float* y);
+pivbos_status pivbos_mlp_loss_grad(const float* params, const float* x, const float* t, int32_t n,
+                                   float* grad, double* loss);
+
 /* int64 32.32 image -> float32 intensity in rays (value * 2^-32).  Device
  * pointers, n_pixels >= 0. */
 pivbos_status pivbos_image_finalize(const int64_t* image, int64_t n_pixels, float* out, void* stream);

@@ -83,6 +83,8 @@ def _load():
         "pivbos_render_noalloc": ([P, P, P, I64, I32, U64, U32, I, D, P, P, P], I),
         "pivbos_default_tuning": ([P], I),
         "pivbos_render_range": ([P, P, P, I64, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
+        "pivbos_mlp_forward": ([P, P, I32, P], I),
+        "pivbos_mlp_loss_grad": ([P, P, P, I32, P, P], I),
         "pivbos_batch_create": ([P, I, I, P, P], I),
         "pivbos_batch_render": ([P, P], I),
         "pivbos_batch_destroy": ([P], None),
@@ -101,7 +103,8 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_sync", "pivbos_last_error", "pivbos_timing_enable", "pivbos_timing_reset",
             "pivbos_timing_read", "pivbos_version", "pivbos_kernel_launches", "pivbos_render_noalloc",
             "pivbos_default_tuning", "pivbos_batch_create", "pivbos_batch_render", "pivbos_batch_destroy",
-            "pivbos_autotune", "pivbos_render_range")
+            "pivbos_autotune", "pivbos_render_range", "pivbos_mlp_forward", "pivbos_mlp_loss_grad")
+MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
 
@@ -241,6 +244,25 @@ def pivbos_autotune(desc, integrator, tol_px, n_sample_rays, stream=None):
     _check(_lib.pivbos_autotune(ctypes.byref(desc), integrator, tol_px, n_sample_rays, ctypes.byref(step),
                                 ctypes.byref(t), _stream(stream)))
     return step.value, t
+
+
+def pivbos_mlp_forward(params, x):
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.zeros((x.shape[0], 4), dtype=np.float32)
+    _check(_lib.pivbos_mlp_forward(params.ctypes.data, x.ctypes.data, x.shape[0], y.ctypes.data))
+    return y
+
+
+def pivbos_mlp_loss_grad(params, x, t):
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    g = np.zeros(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(_lib.pivbos_mlp_loss_grad(params.ctypes.data, x.ctypes.data, t.ctypes.data, x.shape[0], g.ctypes.data,
+                                     ctypes.byref(loss)))
+    return loss.value, g
 
 
 def pivbos_trace_exit_states(m, o, sources, n_sources, rays_per_source, seed, frame, integrator, step,
