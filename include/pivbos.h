@@ -298,6 +298,99 @@ pivbos_status pivbos_mlp_forward(const float* params, const float* x, int32_t n,
 pivbos_status pivbos_mlp_loss_grad(const float* params, const float* x, const float* t, int32_t n,
                                    float* grad, double* loss);
 
+/* ---------------------------------------------------------------------------
+ * Surrogate ray map (no counterpart in the paper: a learned part built on
+ * the tracer of Sec. 3.2).  For a ray with entry state E -- where its
+ * straight line meets z = max(box front, source z), and its slopes dx/dz,
+ * dy/dz -- the surrogate predicts the residual of its exit line against the
+ * straight ray (position difference on a reference plane, slope
+ * difference) as
+ *     r(E) = r_proj(E) + MLP(E, r_proj(E)),
+ * where r_proj is the first-order (Born) residual: the ray equation's
+ * dT/ds = grad n integrated along the unperturbed line, read from a table
+ * of integrals of grad n along lines through the lens pupil centre (built
+ * once per surrogate from the medium), the line cut into born_segments
+ * pieces.  The network (BF16 16 -> 128 x 4 -> 4, ReLU, FP32 accumulation)
+ * learns the correction from rays of the frame traced by the plain path
+ * (Philox counter (sample, stream, frame, 2) picks them); training runs on
+ * the GPU (tensor cores, Adam, cosine learning rate), the loss weighting
+ * each output by its measured effect on the sensor.
+ *
+ * Confidence: on held-out rays the plain tracer judges the predictor at the
+ * sensor, per entry-space bin (16 x 16 x 16 positions x 4 x 4 slopes).
+ * Bins are served in order of plain-path steps saved per unit of squared
+ * sensor error while the summed error keeps the RMS over all rays reaching
+ * the sensor within budget_margin * err_budget_px; the other rays are traced
+ * by the plain path at render time.  The report gives the same figures for
+ * the projection alone and for the straight ray.  The surrogate is tied to
+ * the frame's medium and optics (they must outlive it) and needs the lens
+ * after the box.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t n_train;        /* training rays (<= 2^31) */
+    int64_t n_val;          /* held-out rays for the confidence map (<= 2^31) */
+    int32_t epochs;
+    int32_t batch;          /* rows per step, 256..65536 */
+    float lr;               /* peak learning rate (cosine decay to 1 %) */
+    float err_budget_px;    /* RMS sensor error budget over all rays (px) */
+    float budget_margin;    /* fraction of the budget the held-out estimate may use, (0, 1] */
+    int32_t min_bin_count;  /* bins with fewer held-out rays are never served */
+    uint64_t seed;
+    double ref_plane_z;     /* residual reference plane z (m); NaN = box centre */
+    int32_t born_segments;  /* 0..64; 0 = no projection (the network alone) */
+    int32_t use_network;    /* 1, or 0 = the projection alone */
+} pivbos_surrogate_cfg;
+
+typedef struct {
+    double train_loss;                 /* MSE of the last batch (scaled targets) */
+    double train_steps;
+    double val_rms_px;                 /* held-out RMS sensor error of the served predictor on every ray
+                                          in the box (rays whose status matches the plain path's) */
+    double val_rms_px_born;            /* the same for the projection alone */
+    double val_rms_px_straight;        /* the same for the straight ray (no field) */
+    double val_rms_px_served;          /* estimated RMS over all reaching rays with the chosen bins */
+    double val_served_frac;            /* held-out box rays in served bins */
+    double val_served_frac_born;       /* the same if the projection alone were served */
+    double val_served_frac_straight;   /* the same if the straight ray were served */
+    double steps_saved_frac;           /* plain-path steps of served rays / all steps */
+    double steps_saved_frac_born;
+    double steps_saved_frac_straight;
+    double val_status_flip_frac;       /* box rays the predictor sends elsewhere (a stop, off the sensor) */
+    double n_val_reached, n_val_box;   /* held-out rays reaching the sensor; those entering the box */
+    double seconds_table, seconds_data, seconds_train, seconds_validate;
+    double table_bytes;
+    double target_rms[4];              /* RMS residuals: x, y (m) on the reference plane, slope x, y */
+    double correction_rms[4];          /* RMS of residual minus projection */
+    double sensor_px_per_unit[4];      /* RMS sensor shift per unit of each residual (loss weights) */
+} pivbos_surrogate_report;
+
+typedef struct pivbos_surrogate pivbos_surrogate;
+
+pivbos_status pivbos_surrogate_default_cfg(pivbos_surrogate_cfg* cfg);
+/* Train on `frame` (device buffers; its image and stats are not touched).
+ * Synchronous on `stream`.  Errors: INVALID_ARG (arguments, configuration),
+ * UNSUPPORTED (no medium, lens not after the box), OOM, CUDA. */
+pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integrator,
+                                     const pivbos_surrogate_cfg* cfg /* NULL = defaults */,
+                                     pivbos_surrogate** out, pivbos_surrogate_report* report, void* stream);
+/* Render `frame` (same medium and optics, any sources): the network for
+ * rays in served bins, the plain path for the rest; accumulates into the
+ * frame's image and stats as pivbos_render does.  n_fallback (may be NULL;
+ * if given, the call synchronises) receives the number of plain-traced
+ * rays. */
+pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
+                                      int64_t* n_fallback, void* stream);
+/* Per-ray sensor positions of the surrogate path for flat ray ids (device
+ * int64 [n], source-major as in pivbos_trace_exit_states): sensor_xy
+ * (device double [n][2]), flags (device int32 [n]: 0 network, 1 plain
+ * fallback, 2 never enters the box) and status (device int32 [n]).
+ * Synchronous. */
+pivbos_status pivbos_surrogate_sensor(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
+                                      const int64_t* ray_ids, int64_t n, double* sensor_xy, int32_t* flags,
+                                      int32_t* status, void* stream);
+pivbos_status pivbos_surrogate_report_get(const pivbos_surrogate* sg, pivbos_surrogate_report* out);
+void pivbos_surrogate_destroy(pivbos_surrogate* sg);
+
 /* int64 32.32 image -> float32 intensity in rays (value * 2^-32).  Device
  * pointers, n_pixels >= 0. */
 pivbos_status pivbos_image_finalize(const int64_t* image, int64_t n_pixels, float* out, void* stream);

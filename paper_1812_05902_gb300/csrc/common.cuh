@@ -56,6 +56,7 @@ struct TraceParams {
     const double* sources;    // [S][3] device (FP64 as given)
     const uint32_t* perm;     // Morton order of sources (nullptr = identity)
     const float2* src_df;     // [slot][3] sources in Morton order as double-float (render only)
+    const uint32_t* ray_list; // render only the listed flat (slot, ray) indices (nullptr = all)
     uint32_t n_sources;
     uint32_t rays_per_source;
     uint32_t source_offset;   // global index of this call's first source (Philox counter)
@@ -91,6 +92,11 @@ cudaError_t launch_render(const TraceParams& p, int integrator, int64_t* image, 
                           uint32_t rays_per_cta, cudaStream_t s);
 cudaError_t launch_trace_states(const TraceParams& p, int integrator, const int64_t* ray_ids,
                                 int64_t n_rays, pivbos_ray_state* out, cudaStream_t s);
+// Render the rays listed in p.ray_list[0, min(*count, capacity)) (count on
+// the device); persistent CTAs pop chunks of rays_per_cta list entries.
+cudaError_t launch_list(const TraceParams& p, int integrator, const unsigned long long* count, uint32_t capacity,
+                        int64_t* image, int64_t* stats, uint32_t rays_per_cta, unsigned long long* counter,
+                        cudaStream_t s);
 cudaError_t launch_batch(const BatchFrame* frames, const uint64_t* item_start, int n_frames, uint64_t total_items,
                          unsigned long long* counter, int integrator, bool cache, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_finalize(const int64_t* image, int64_t n, float* out, cudaStream_t s);

@@ -7,8 +7,6 @@ namespace pivbos {
 
 constexpr int kRenderThreads = 256;
 constexpr int kRenderMinBlocks = 3;   // CTAs per SM the register budget must allow
-constexpr int kTileW = 32;
-constexpr int kTileH = 32;
 constexpr int kMaxOrderRays = 2048;   // a CTA reorders at most this many rays
 
 __device__ __forceinline__ uint32_t spread10(uint32_t v)
@@ -46,59 +44,6 @@ __device__ __forceinline__ uint32_t ray_order_key(const TraceParams& P, uint32_t
     const float gy = fminf(fmaxf((y - P.m.origin[1].hi) * P.m.inv_h[1], 0.0f), 1023.0f);
     const uint32_t code = spread10((uint32_t)gx) | (spread10((uint32_t)gy) << 1);
     return (code << 11) | local;
-}
-
-__device__ __forceinline__ void add_q(unsigned long long* tile, int ax, int ay, int64_t* image, int W,
-                                      int gx, int gy, unsigned long long q)
-{
-    const int tx = gx - ax, ty = gy - ay;
-    if ((unsigned)tx < (unsigned)kTileW && (unsigned)ty < (unsigned)kTileH) {
-        atomicAdd(&tile[ty * kTileW + tx], q);
-    } else {
-        atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * W + gx]), q);
-    }
-}
-
-// Round-to-nearest-even of a non-negative float below 2^33 to an integer
-// with FP32/INT32 instructions only (the 64-bit float-to-integer conversion
-// runs on GB300's narrow FP64 pipe).  Below 2^23 adding 2^23 rounds to an
-// integer in the mantissa; from 2^23 up the float is already an integer.
-__device__ __forceinline__ long long round_pos_to_ll(float x)
-{
-    if (x < 8388608.0f) return (long long)(__float_as_uint(x + 8388608.0f) - 0x4B000000u);
-    const uint32_t b = __float_as_uint(x);
-    return (long long)((b & 0x7FFFFFu) | 0x800000u) << ((int)(b >> 23) - 150);
-}
-
-// Quantise the spot of one ray and add it (tile if inside, image otherwise).
-__device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
-                                            unsigned long long* tile, int ax, int ay, int64_t* image)
-{
-    SpotWindow sw;
-    spot_window(o, px, py, sw);
-    long long sum = 0, qmax = -1;
-    int imax = 0, jmax = 0;
-#pragma unroll 1
-    for (int j = 0; j < sw.ny; ++j) {
-        const float wyj = sw.wy[j] * sw.scale;
-#pragma unroll 1
-        for (int i = 0; i < sw.nx; ++i) {
-            const long long q = round_pos_to_ll(sw.wx[i] * wyj);
-            sum += q;
-            if (q > qmax) { qmax = q; imax = i; jmax = j; }
-        }
-    }
-    const long long rem = 4294967296LL - sum;
-#pragma unroll 1
-    for (int j = 0; j < sw.ny; ++j) {
-        const float wyj = sw.wy[j] * sw.scale;
-#pragma unroll 1
-        for (int i = 0; i < sw.nx; ++i) {
-            long long q = round_pos_to_ll(sw.wx[i] * wyj);
-            if (i == imax && j == jmax) q += rem;
-            if (q != 0) add_q(tile, ax, ay, image, o.W, sw.x0 + i, sw.y0 + j, (unsigned long long)q);
-        }
-    }
 }
 
 // Work: the flattened (Morton slot, ray) index space (sources in Morton order,
@@ -143,7 +88,8 @@ __device__ __forceinline__ void render_chunk(const TraceParams& P, ChunkShared& 
         uint32_t n_pow2 = 1;
         while (n_pow2 < n_here) n_pow2 <<= 1;
         for (uint32_t q = threadIdx.x; q < n_pow2; q += blockDim.x)
-            sh.order[q] = q < n_here ? ray_order_key(P, (uint32_t)first + q, q) : 0xffffffffu;
+            sh.order[q] = q < n_here ? ray_order_key(P, P.ray_list ? __ldg(P.ray_list + first + q) : (uint32_t)first + q, q)
+                                     : 0xffffffffu;
         __syncthreads();
         for (uint32_t kk = 2; kk <= n_pow2; kk <<= 1) {
             for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
@@ -172,7 +118,7 @@ __device__ __forceinline__ void render_chunk(const TraceParams& P, ChunkShared& 
         RayOut r;
         r.status = PIVBOS_RAY_MISS;
         if (active) {
-            const uint32_t flat = (uint32_t)idx;
+            const uint32_t flat = P.ray_list ? __ldg(P.ray_list + idx) : (uint32_t)idx;
             const uint32_t slot = flat / rps, k = flat - slot * rps;
             const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
             const float2* s = P.src_df + 3 * (size_t)slot;
@@ -270,6 +216,28 @@ batch_kernel(const BatchFrame* __restrict__ frames, const uint64_t* __restrict__
     }
 }
 
+// Persistent kernel over a device-side ray list (the surrogate's fallback
+// rays): chunks of rays_per_cta consecutive list entries.
+template <int INTEG, bool CACHE>
+__global__ void __launch_bounds__(kRenderThreads, CACHE ? 2 : kRenderMinBlocks)
+list_kernel(const TraceParams P, const unsigned long long* __restrict__ count, uint32_t capacity,
+            int64_t* __restrict__ image, int64_t* __restrict__ stats, uint32_t rays_per_cta,
+            unsigned long long* __restrict__ counter)
+{
+    __shared__ ChunkShared sh;
+    __shared__ unsigned long long s_item;
+    const uint64_t n = min(*count, (unsigned long long)capacity);
+    const uint64_t items = (n + rays_per_cta - 1) / rays_per_cta;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
+        __syncthreads();
+        const uint64_t it = s_item;
+        if (it >= items) break;
+        const uint64_t first = it * rays_per_cta;
+        render_chunk<INTEG, CACHE>(P, sh, first, min(first + rays_per_cta, n), image, stats);
+    }
+}
+
 template <int INTEG>
 __global__ void __launch_bounds__(128)
 trace_states_kernel(const TraceParams P, const int64_t* __restrict__ ray_ids, int64_t n,
@@ -346,6 +314,31 @@ cudaError_t launch_batch(const BatchFrame* frames, const uint64_t* item_start, i
             batch_kernel<PIVBOS_EULER, true><<<grid, kRenderThreads, 0, s>>>(frames, item_start, n_frames, total_items, counter);
         else
             batch_kernel<PIVBOS_EULER, false><<<grid, kRenderThreads, 0, s>>>(frames, item_start, n_frames, total_items, counter);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_list(const TraceParams& p, int integrator, const unsigned long long* count, uint32_t capacity,
+                        int64_t* image, int64_t* stats, uint32_t rays_per_cta, unsigned long long* counter,
+                        cudaStream_t s)
+{
+    if (rays_per_cta == 0 || rays_per_cta > (uint32_t)kMaxOrderRays) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool cache = p.cell_cache != 0;
+    const unsigned grid = (unsigned)(sms * (cache ? 2 : kRenderMinBlocks));
+    if (integrator == PIVBOS_RK4) {
+        if (cache)
+            list_kernel<PIVBOS_RK4, true><<<grid, kRenderThreads, 0, s>>>(p, count, capacity, image, stats, rays_per_cta, counter);
+        else
+            list_kernel<PIVBOS_RK4, false><<<grid, kRenderThreads, 0, s>>>(p, count, capacity, image, stats, rays_per_cta, counter);
+    } else {
+        if (cache)
+            list_kernel<PIVBOS_EULER, true><<<grid, kRenderThreads, 0, s>>>(p, count, capacity, image, stats, rays_per_cta, counter);
+        else
+            list_kernel<PIVBOS_EULER, false><<<grid, kRenderThreads, 0, s>>>(p, count, capacity, image, stats, rays_per_cta, counter);
     }
     count_launches(1);
     return cudaGetLastError();

@@ -7,6 +7,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <new>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
@@ -110,6 +113,1181 @@ pivbos_status pivbos_mlp_loss_grad(const float* params, const float* x, const fl
     if (e != cudaSuccess) return scuda(e, "mlp_loss_grad");
     *loss = lsum / ((double)n * pivbos::kMlpOut);
     return PIVBOS_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Surrogate ray map: data, training, confidence map, rendering
+// ===========================================================================
+#include "mlp_device.cuh"
+#include "trace.cuh"
+
+namespace pivbos {
+
+// Geometry and normalisation of one trained surrogate (device copy).
+struct SurrParams {
+    dfc z_lo;                       // box front (entry plane for sources in front of the box)
+    dfc z_ref;                      // reference plane of the exit-line residual
+    float cx, cy, cz, hx, hy, hz;   // box centre and half extents (feature scaling)
+    float u_scale;                  // slope scaling
+    float t_scale[4];               // network output scales: dx, dy (m) at z_ref, dux, duy
+    float b_scale[4];               // scales of the projection (Born) residual as network input
+    int nbx, nby, nbz, nbu;         // confidence bins
+    const uint32_t* bin_ok;         // bit b set: bin b is served by the network
+    int use_net;                    // 0: the projection residual alone
+    // projection table: suffix integrals of grad n along lines through the
+    // pupil centre (0, 0, aim_z), columns indexed by where they cross z_hi
+    const float4* table;            // [level][row][col][2]: {Gx, Gy, Gz, 0}, {Hx, Hy, Hz, 0}
+    int tnx, tny, tnz, born_k;      // columns, levels; segments per ray (0: no projection)
+    float t_x0, t_y0, t_inv_dx, t_inv_dy, t_inv_dz;
+    float zlo_f, zhi_f, aim_z, persp;   // persp = aim_z - z_hi
+};
+
+constexpr int kSurrBins = 16 * 16 * 16 * 4 * 4;
+
+struct Entry {
+    bool enters;
+    float f[5];    // entry x, y, z, slope x, slope y (scaled to about [-1, 1])
+    int bin;
+    df xs, ys;     // straight line at the reference plane
+    df ux, uy;     // slopes dx/dz, dy/dz of the straight ray
+    float xe, ye, ze;   // entry point (m)
+};
+
+__device__ __forceinline__ int bin_of(float f, int nb)
+{
+    const int b = (int)floorf((f + 1.0f) * 0.5f * (float)nb);
+    return min(max(b, 0), nb - 1);
+}
+
+// Entry state of a ray (source s, unit direction d): the straight line's
+// point on the plane z = max(z_lo, s_z), its slopes, the confidence bin, and
+// the straight line at the reference plane.
+__device__ __forceinline__ void surr_entry(const TraceParams& P, const SurrParams& S, df sx, df sy, df sz, df dx,
+                                           df dy, df dz, Entry& e)
+{
+    df tn;
+    e.enters = box_entry(P.m, sx, sy, sz, dx, dy, dz, tn);
+    const df inv_dz = df_rcp(dz);
+    e.ux = df_mul(dx, inv_dz);
+    e.uy = df_mul(dy, inv_dz);
+    const df ze = df_lt(sz, dfk(S.z_lo)) ? dfk(S.z_lo) : sz;
+    const df dze = df_sub(ze, sz);
+    const df xe = df_fma(e.ux, dze, sx), ye = df_fma(e.uy, dze, sy);
+    const df dzr = df_sub(dfk(S.z_ref), sz);
+    e.xs = df_fma(e.ux, dzr, sx);
+    e.ys = df_fma(e.uy, dzr, sy);
+    e.xe = xe.hi + xe.lo;
+    e.ye = ye.hi + ye.lo;
+    e.ze = ze.hi + ze.lo;
+    e.f[0] = (xe.hi - S.cx) / S.hx;
+    e.f[1] = (ye.hi - S.cy) / S.hy;
+    e.f[2] = (ze.hi - S.cz) / S.hz;
+    e.f[3] = e.ux.hi / S.u_scale;
+    e.f[4] = e.uy.hi / S.u_scale;
+    const int bu = bin_of(e.f[3], S.nbu) * S.nbu + bin_of(e.f[4], S.nbu);
+    e.bin = ((bin_of(e.f[0], S.nbx) * S.nby + bin_of(e.f[1], S.nby)) * S.nbz + bin_of(e.f[2], S.nbz)) *
+                (S.nbu * S.nbu) + bu;
+}
+
+// Table value at column coordinates (xi, eta) and depth z: bilinear across
+// columns, linear across levels; zero for columns outside the table (lines
+// that miss the box).
+__device__ __forceinline__ void table_lookup(const SurrParams& S, float xi, float eta, float z, float3& G, float3& H)
+{
+    const float fx = (xi - S.t_x0) * S.t_inv_dx, fy = (eta - S.t_y0) * S.t_inv_dy;
+    G = make_float3(0.f, 0.f, 0.f);
+    H = make_float3(0.f, 0.f, 0.f);
+    if (!(fx >= 0.0f && fy >= 0.0f && fx <= (float)(S.tnx - 1) && fy <= (float)(S.tny - 1))) return;
+    const float fz = fminf(fmaxf((z - S.zlo_f) * S.t_inv_dz, 0.0f), (float)(S.tnz - 1));
+    const int i = min((int)fx, S.tnx - 2), j = min((int)fy, S.tny - 2), l = min((int)fz, S.tnz - 2);
+    const float ax = fx - (float)i, ay = fy - (float)j, az = fz - (float)l;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int di = c & 1, dj = (c >> 1) & 1, dl = c >> 2;
+        const float w = (di ? ax : 1.0f - ax) * (dj ? ay : 1.0f - ay) * (dl ? az : 1.0f - az);
+        const float4* p = S.table + 2 * (((size_t)(l + dl) * S.tny + (j + dj)) * S.tnx + (i + di));
+        const float4 g = __ldg(p), h = __ldg(p + 1);
+        G.x = fmaf(w, g.x, G.x); G.y = fmaf(w, g.y, G.y); G.z = fmaf(w, g.z, G.z);
+        H.x = fmaf(w, h.x, H.x); H.y = fmaf(w, h.y, H.y); H.z = fmaf(w, h.z, H.z);
+    }
+}
+
+// First-order (Born) exit-line residual of the straight ray from the entry
+// point with slopes (ux, uy): dT/ds = grad n (the ray equation with
+// dt = ds / n) integrated along the unperturbed line, the line cut into
+// born_k segments, each integral taken from the table column through the
+// segment's midpoint.  r = {dx, dy at z_ref, dux, duy}.
+__device__ __forceinline__ void born_residual(const SurrParams& S, const Entry& e, float* r)
+{
+    r[0] = r[1] = r[2] = r[3] = 0.0f;
+    if (S.born_k <= 0 || !e.enters) return;
+    const float ux = e.ux.hi, uy = e.uy.hi;
+    const float dzs = (S.zhi_f - e.ze) / (float)S.born_k;
+    float3 G = make_float3(0.f, 0.f, 0.f), H = G;
+#pragma unroll 1
+    for (int k = 0; k < S.born_k; ++k) {
+        const float za = e.ze + (float)k * dzs, zb = za + dzs, zm = za + 0.5f * dzs;
+        const float c = S.persp / (S.aim_z - zm);
+        const float xi = (e.xe + ux * (zm - e.ze)) * c, eta = (e.ye + uy * (zm - e.ze)) * c;
+        float3 Ga, Ha, Gb, Hb;
+        table_lookup(S, xi, eta, za, Ga, Ha);
+        table_lookup(S, xi, eta, zb, Gb, Hb);
+        G.x += Ga.x - Gb.x; G.y += Ga.y - Gb.y; G.z += Ga.z - Gb.z;
+        H.x += Ha.x - Hb.x; H.y += Ha.y - Hb.y; H.z += Ha.z - Hb.z;
+    }
+    // slope change (T_perp - u T_z) / T_z with T = n d and ds = dz sqrt(1 + u^2)
+    const float q = 1.0f + ux * ux + uy * uy;
+    const float gx = G.x - ux * G.z, gy = G.y - uy * G.z;
+    const float hx = H.x - ux * H.z, hy = H.y - uy * H.z;
+    const float zr = S.z_ref.hi + S.z_ref.lo - S.zhi_f;
+    r[0] = q * (zr * gx - hx);
+    r[1] = q * (zr * gy - hy);
+    r[2] = q * gx;
+    r[3] = q * gy;
+}
+
+// Network input: each entry feature as a BF16 value and its BF16-rounded
+// remainder times 256 (16 significant bits in all), then the scaled
+// projection residual, zero padded.
+__device__ __forceinline__ void encode_features(const SurrParams& S, const float* f, const float* born,
+                                                __nv_bfloat16* x)
+{
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        const __nv_bfloat16 hi = __float2bfloat16(f[c]);
+        x[c] = hi;
+        x[5 + c] = __float2bfloat16((f[c] - __bfloat162float(hi)) * 256.0f);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[10 + c] = __float2bfloat16(born[c] / S.b_scale[c]);
+    x[14] = x[15] = __float2bfloat16(0.0f);
+}
+
+// Exit line from the residual r (m, m, rad, rad): a point on the reference
+// plane and the unit direction.
+__device__ __forceinline__ void surr_exit(const SurrParams& S, const Entry& e, const float* r, df& Rx, df& Ry, df& Rz,
+                                          df& dx, df& dy, df& dz)
+{
+    Rx = df_add_f(e.xs, r[0]);
+    Ry = df_add_f(e.ys, r[1]);
+    Rz = dfk(S.z_ref);
+    const df ux = df_add_f(e.ux, r[2]);
+    const df uy = df_add_f(e.uy, r[3]);
+    const df inn = df_rsqrt(df_add_f(df_add(df_sqr(ux), df_sqr(uy)), 1.0f));
+    dx = df_mul(ux, inn);
+    dy = df_mul(uy, inn);
+    dz = inn;
+}
+
+// Full residual: projection plus the network's correction (y scaled).
+__device__ __forceinline__ void surr_residual(const SurrParams& S, const float* born, const float* y, float* r)
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r[c] = born[c] + (S.use_net ? y[c] * S.t_scale[c] : 0.0f);
+}
+
+// Seeded sample of ray ids of a frame (Philox counter (q, stream, frame, 2)).
+__device__ __forceinline__ uint64_t sample_ray(const TraceParams& P, uint64_t q, uint32_t stream, uint64_t seed,
+                                               uint64_t total)
+{
+    uint64_t w0, w1;
+    philox_lens_words(q, stream, P.frame, 2ull, seed, 0ull, w0, w1);
+    return w0 % total;
+}
+
+// Source (as given, FP64 -> double-float) and direction of a ray by id.
+__device__ __forceinline__ void ray_by_id(const TraceParams& P, uint64_t id, uint32_t& sid, uint32_t& k, df& sx,
+                                          df& sy, df& sz, df& dx, df& dy, df& dz)
+{
+    const uint32_t rps = P.rays_per_source;
+    sid = (uint32_t)(id / rps);
+    k = (uint32_t)(id - (uint64_t)sid * rps);
+    const double* sp = P.sources + 3 * (size_t)sid;
+    sx = df_from_double(sp[0]);
+    sy = df_from_double(sp[1]);
+    sz = df_from_double(sp[2]);
+    ray_start(P, sx, sy, sz, sid + P.source_offset, k, dx, dy, dz);
+}
+
+// Projection table: one thread per column; the column's line is followed
+// from z_hi down to z_lo, grad n sampled (trilinear, as the tracer samples
+// it; zero outside the box) at the midpoints of `sub` sub-steps per level.
+__global__ void surr_table_kernel(const DevMedium m, SurrParams S, int sub, float4* __restrict__ table)
+{
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= S.tnx * S.tny) return;
+    const int i = col % S.tnx, j = col / S.tnx;
+    const float xi = S.t_x0 + (float)i / S.t_inv_dx, eta = S.t_y0 + (float)j / S.t_inv_dy;
+    const double lo0 = m.lo[0].hi + (double)m.lo[0].lo, hi0 = m.hi[0].hi + (double)m.hi[0].lo;
+    const double lo1 = m.lo[1].hi + (double)m.lo[1].lo, hi1 = m.hi[1].hi + (double)m.hi[1].lo;
+    const double ox = m.origin[0].hi + (double)m.origin[0].lo, oy = m.origin[1].hi + (double)m.origin[1].lo;
+    const double oz = m.origin[2].hi + (double)m.origin[2].lo;
+    const double dzl = 1.0 / S.t_inv_dz, h = dzl / sub;
+    double G[3] = {0, 0, 0}, H[3] = {0, 0, 0};
+    for (int l = S.tnz - 1; l >= 0; --l) {
+        if (l < S.tnz - 1) {
+            const double zt = S.zlo_f + (double)(l + 1) * dzl;
+            for (int q = 0; q < sub; ++q) {
+                const double z = zt - (q + 0.5) * h;
+                const double c = (S.aim_z - z) / S.persp;
+                const double x = xi * c, y = eta * c;
+                if (x < lo0 || x > hi0 || y < lo1 || y > hi1) continue;
+                const float4 v = sample_field(m, (float)((x - ox) * m.inv_h[0]), (float)((y - oy) * m.inv_h[1]),
+                                              (float)((z - oz) * m.inv_h[2]));
+                const double wz = (z - S.zhi_f) * h;
+                G[0] += v.y * h; G[1] += v.z * h; G[2] += v.w * h;
+                H[0] += v.y * wz; H[1] += v.z * wz; H[2] += v.w * wz;
+            }
+        }
+        float4* p = table + 2 * (((size_t)l * S.tny + j) * S.tnx + i);
+        p[0] = make_float4((float)G[0], (float)G[1], (float)G[2], 0.f);
+        p[1] = make_float4((float)H[0], (float)H[1], (float)H[2], 0.f);
+    }
+}
+
+// Truth (plain path) and projection residuals of one ray.
+template <int INTEG>
+__device__ __forceinline__ void truth_and_born(const TraceParams& P, const SurrParams& S, uint64_t id, Entry& e,
+                                               pivbos_ray_state& st, float* t, float* born)
+{
+    uint32_t sid, k;
+    df sx, sy, sz, dx, dy, dz;
+    ray_by_id(P, id, sid, k, sx, sy, sz, dx, dy, dz);
+    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+    born_residual(S, e, born);
+    RayOut r;
+    trace_ray<INTEG, false>(P, sx, sy, sz, sid + P.source_offset, k, r, &st);
+    t[0] = t[1] = t[2] = t[3] = 0.0f;
+    if (st.status != PIVBOS_RAY_MAXSTEP) {
+        // the exit line (straight beyond the box) against the straight ray,
+        // both taken at the reference plane
+        const double zr = df_to_double(dfk(S.z_ref));
+        const double* sp = P.sources + 3 * (size_t)sid;
+        const double uxd = df_to_double(e.ux), uyd = df_to_double(e.uy);
+        const double Dx = st.vol_dir[0] / st.vol_dir[2], Dy = st.vol_dir[1] / st.vol_dir[2];
+        const double xt = st.vol_pos[0] + (zr - st.vol_pos[2]) * Dx;
+        const double yt = st.vol_pos[1] + (zr - st.vol_pos[2]) * Dy;
+        t[0] = (float)(xt - (sp[0] + (zr - sp[2]) * uxd));
+        t[1] = (float)(yt - (sp[1] + (zr - sp[2]) * uyd));
+        t[2] = (float)(Dx - uxd);
+        t[3] = (float)(Dy - uyd);
+    }
+}
+
+// Pilot statistics on a few rays: mean squares of the truth residual, of
+// the projection residual and of their difference ([0..11]), and the sensor
+// shift per unit of each residual component by finite differences about
+// the straight ray ([12..15], [16] = rays counted).
+template <int INTEG>
+__global__ void surr_pilot_kernel(const TraceParams P, const SurrParams S, uint64_t total, int64_t n, uint64_t seed,
+                                  double dpos, double dslope, double* __restrict__ acc)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[17];
+#pragma unroll
+    for (int c = 0; c < 17; ++c) v[c] = 0.0;
+    if (q < n) {
+        Entry e;
+        pivbos_ray_state st;
+        float t[4], born[4];
+        truth_and_born<INTEG>(P, S, sample_ray(P, (uint64_t)q, 3, seed, total), e, st, t, born);
+        for (int c = 0; c < 4; ++c) {
+            v[c] = (double)t[c] * t[c];
+            v[4 + c] = (double)born[c] * born[c];
+            v[8 + c] = (double)(t[c] - born[c]) * (t[c] - born[c]);
+        }
+        double px[5], py[5];
+        bool ok = true;
+#pragma unroll 1
+        for (int c = 0; c < 5; ++c) {
+            float r[4] = {0.f, 0.f, 0.f, 0.f};
+            if (c > 0) r[c - 1] = (float)(c <= 2 ? dpos : dslope);
+            df Rx, Ry, Rz, ex, ey, ez;
+            surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
+            int status = PIVBOS_RAY_REACHED;
+            df a, b;
+            optics_to_sensor(P.o, Rx, Ry, Rz, ex, ey, ez, status, a, b);
+            ok = ok && status == PIVBOS_RAY_REACHED;
+            px[c] = df_to_double(a);
+            py[c] = df_to_double(b);
+        }
+        if (ok) {
+            for (int c = 1; c < 5; ++c) {
+                const double d = c <= 2 ? dpos : dslope;
+                const double ax = px[c] - px[0], ay = py[c] - py[0];
+                v[11 + c] = (ax * ax + ay * ay) / (d * d);
+            }
+            v[16] = 1.0;
+        }
+    }
+    for (int c = 0; c < 17; ++c) {
+        for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
+        if ((threadIdx.x & 31) == 0 && v[c] != 0.0) atomicAdd(&acc[c], v[c]);
+    }
+}
+
+// S1: samples of (encoded entry features and projection residual, scaled
+// correction truth - projection) traced by the plain path.  For held-out
+// samples also the plain sensor position, status and step count.
+template <int INTEG>
+__global__ void surr_data_kernel(const TraceParams P, const SurrParams S, uint64_t total, int64_t n, uint32_t stream,
+                                 uint64_t seed, __nv_bfloat16* __restrict__ X, float* __restrict__ T,
+                                 uint64_t* __restrict__ ids, double* __restrict__ ref_px, int* __restrict__ ref_st)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint64_t id = sample_ray(P, (uint64_t)q, stream, seed, total);
+    Entry e;
+    pivbos_ray_state st;
+    float t[4], born[4];
+    truth_and_born<INTEG>(P, S, id, e, st, t, born);
+    encode_features(S, e.f, born, X + (size_t)q * kMlpIn);
+    if (T)
+        *reinterpret_cast<float4*>(T + (size_t)q * 4) =
+            make_float4((t[0] - born[0]) / S.t_scale[0], (t[1] - born[1]) / S.t_scale[1],
+                        (t[2] - born[2]) / S.t_scale[2], (t[3] - born[3]) / S.t_scale[3]);
+    if (ids) ids[q] = id;
+    if (ref_px) {
+        ref_px[2 * q] = st.sensor_xy[0];
+        ref_px[2 * q + 1] = st.sensor_xy[1];
+        ref_st[q] = st.status | (st.steps << 3);
+    }
+}
+
+// Per-bin sums over held-out rays that reach the sensor in the plain path,
+// for three predictors: the network (projection + correction), the
+// projection alone, and the straight ray.
+struct BinAcc {
+    double* err2[3];     // squared sensor error (px^2) per predictor
+    double* steps;       // plain-path integration steps (the work a served ray saves)
+    unsigned int* cnt;
+    double* tot;         // [0] rays reaching the sensor, [1] those entering the box,
+                         // [2..4] of these, rays each predictor sends elsewhere
+};
+
+// Confidence map: the plain tracer judges each predictor at the sensor.
+// A ray whose status differs from the plain path's (one grazing a stop)
+// has no displacement: it is counted, not summed.
+__global__ void surr_eval_kernel(const TraceParams P, const SurrParams S, const uint64_t* __restrict__ ids,
+                                 const float* __restrict__ Y, const double* __restrict__ ref_px,
+                                 const int* __restrict__ ref_st, int64_t n, BinAcc acc)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    if ((ref_st[q] & 7) != PIVBOS_RAY_REACHED) return;
+    atomicAdd(&acc.tot[0], 1.0);
+    uint32_t sid, k;
+    df sx, sy, sz, dx, dy, dz;
+    ray_by_id(P, ids[q], sid, k, sx, sy, sz, dx, dy, dz);
+    Entry e;
+    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+    if (!e.enters) return;
+    atomicAdd(&acc.tot[1], 1.0);
+    float born[4], y[4];
+    born_residual(S, e, born);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[c] = Y[q * 4 + c];
+#pragma unroll 1
+    for (int v = 0; v < 3; ++v) {
+        float r[4] = {0.f, 0.f, 0.f, 0.f};
+        if (v == 0) {
+            for (int c = 0; c < 4; ++c) r[c] = born[c] + y[c] * S.t_scale[c];
+        } else if (v == 1) {
+            for (int c = 0; c < 4; ++c) r[c] = born[c];
+        }
+        df Rx, Ry, Rz, ex, ey, ez;
+        surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
+        int status = PIVBOS_RAY_REACHED;
+        df px, py;
+        optics_to_sensor(P.o, Rx, Ry, Rz, ex, ey, ez, status, px, py);
+        if (status == PIVBOS_RAY_REACHED) {
+            const double a = df_to_double(px) - ref_px[2 * q], b = df_to_double(py) - ref_px[2 * q + 1];
+            atomicAdd(&acc.err2[v][e.bin], a * a + b * b);
+        } else {
+            atomicAdd(&acc.tot[2 + v], 1.0);
+        }
+    }
+    atomicAdd(&acc.steps[e.bin], (double)(ref_st[q] >> 3));
+    atomicAdd(&acc.cnt[e.bin], 1u);
+}
+
+// Shared memory of the fused surrogate render kernel.
+struct SurrSmem {
+    mlpd::FwdSmem net;
+    __nv_bfloat16 x[256][kMlpIn];
+    float y[256][4];
+    float born[256][4];
+    float2 ray[256][6];   // source and direction (double-float)
+    int mode[256];        // 0 network, 1 fallback list, 2 straight (never enters), 3 inactive, 4 trace here
+    unsigned long long tile[kTileW * kTileH];
+    unsigned long long item;
+    unsigned long long fb_base;
+    int fb_warp[8];
+    int anchor_tid, ax, ay;
+};
+
+// S3: persistent kernel over chunks of rays of one render (sources in Morton
+// order).  Per 256 rays: entry features and projection residual -> network
+// correction (tensor cores) -> exit line -> lens and sensor -> shared tile.
+// Rays in bins the surrogate does not serve are appended, 256 at a time in
+// ray order, to the fallback list the plain tracer renders afterwards.
+template <int INTEG>
+__global__ void __launch_bounds__(256, 1)
+surr_render_kernel(const TraceParams P, const SurrParams S, const __nv_bfloat16* __restrict__ wbf,
+                   const float* __restrict__ params, int64_t* __restrict__ image, int64_t* __restrict__ stats,
+                   uint64_t total_rays, uint32_t rays_per_item, unsigned long long* __restrict__ counter,
+                   uint32_t* __restrict__ fb_ids, unsigned long long* __restrict__ fb_count, uint32_t fb_capacity)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SurrSmem& sh = *reinterpret_cast<SurrSmem*>(smem_raw);
+    if (S.use_net) mlpd::load_network(sh.net, wbf, params);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+    const uint64_t items = (total_rays + rays_per_item - 1) / rays_per_item;
+    const uint32_t rps = P.rays_per_source;
+    unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sh.item = atomicAdd(counter, 1ull);
+        for (int q = tid; q < kTileW * kTileH; q += blockDim.x) sh.tile[q] = 0ull;
+        if (tid == 0) {
+            sh.anchor_tid = 0x7fffffff;
+            sh.ax = -(1 << 28);
+            sh.ay = -(1 << 28);
+        }
+        __syncthreads();
+        const uint64_t item = sh.item;
+        if (item >= items) break;
+        const uint64_t first = item * rays_per_item;
+        const uint64_t last = min(first + rays_per_item, total_rays);
+        int ax = -(1 << 28), ay = -(1 << 28);
+        for (uint64_t base = first, sub = 0; base < last; base += 256, ++sub) {
+            // ---- features, projection and the serve / fall back decision
+            const uint64_t idx = base + tid;
+            int mode = 3;
+            Entry e;
+            e.enters = false;
+            e.f[0] = e.f[1] = e.f[2] = e.f[3] = e.f[4] = 0.0f;
+            float born[4] = {0.f, 0.f, 0.f, 0.f};
+            if (idx < last) {
+                const uint32_t flat = (uint32_t)idx;
+                const uint32_t slot = flat / rps, k = flat - slot * rps;
+                const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
+                const float2* sp = P.src_df + 3 * (size_t)slot;
+                const float2 a = __ldg(sp), b = __ldg(sp + 1), c = __ldg(sp + 2);
+                const df sx{a.x, a.y}, sy{b.x, b.y}, sz{c.x, c.y};
+                df dx, dy, dz;
+                ray_start(P, sx, sy, sz, sid, k, dx, dy, dz);
+                surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+                if (!e.enters) mode = 2;
+                else mode = ((__ldg(S.bin_ok + (e.bin >> 5)) >> (e.bin & 31)) & 1u) ? 0 : 1;
+                if (mode == 0) born_residual(S, e, born);
+                sh.ray[tid][0] = a; sh.ray[tid][1] = b; sh.ray[tid][2] = c;
+                sh.ray[tid][3] = make_float2(dx.hi, dx.lo);
+                sh.ray[tid][4] = make_float2(dy.hi, dy.lo);
+                sh.ray[tid][5] = make_float2(dz.hi, dz.lo);
+            }
+            // append the fallback rays of these 256 in ray order
+            const unsigned fbm = __ballot_sync(0xffffffffu, mode == 1);
+            if (lane == 0) sh.fb_warp[warp] = __popc(fbm);
+            __syncthreads();
+            if (tid == 0) {
+                int tot = 0;
+                for (int w = 0; w < 8; ++w) {
+                    const int c = sh.fb_warp[w];
+                    sh.fb_warp[w] = tot;
+                    tot += c;
+                }
+                sh.fb_base = tot ? atomicAdd(fb_count, (unsigned long long)tot) : 0ull;
+            }
+            __syncthreads();
+            if (mode == 1) {
+                const unsigned long long pos =
+                    sh.fb_base + (unsigned long long)(sh.fb_warp[warp] + __popc(fbm & ((1u << lane) - 1u)));
+                if (pos < fb_capacity) fb_ids[pos] = (uint32_t)idx;
+                else mode = 4;   // list full: trace it here
+            }
+            sh.mode[tid] = mode;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sh.born[tid][c] = born[c];
+            encode_features(S, e.f, born, &sh.x[tid][0]);
+            __syncthreads();
+            // ---- network: warp w runs rows [32w, 32w + 32) as two 16-row tiles
+            if (S.use_net) {
+#pragma unroll 1
+                for (int half = 0; half < 2; ++half) {
+                    const int row0 = warp * 32 + half * 16;
+                    if (!__any_sync(0xffffffffu, sh.mode[row0 + (lane & 15)] == 0)) continue;
+                    {
+                        const int r = lane >> 1, h = lane & 1;
+                        *reinterpret_cast<uint4*>(sh.net.act[warp][0] + r * mlpd::kPadH + h * 8) =
+                            *reinterpret_cast<const uint4*>(&sh.x[row0 + r][h * 8]);
+                    }
+                    __syncwarp();
+                    float y4[4];
+                    mlpd::forward_tile(sh.net, warp, y4, nullptr, 0, 0, 0);
+                    if (t4 * 2 < kMlpOut) {
+                        sh.y[row0 + g][t4 * 2] = y4[0];
+                        sh.y[row0 + g][t4 * 2 + 1] = y4[1];
+                        sh.y[row0 + g + 8][t4 * 2] = y4[2];
+                        sh.y[row0 + g + 8][t4 * 2 + 1] = y4[3];
+                    }
+                    __syncwarp();
+                }
+                __syncthreads();
+            }
+            // ---- lens, sensor and deposit
+            RayOut r;
+            r.status = PIVBOS_RAY_MISS;
+            const bool here = mode == 0 || mode == 2 || mode == 4;
+            if (here) {
+                const df sx{sh.ray[tid][0].x, sh.ray[tid][0].y}, sy{sh.ray[tid][1].x, sh.ray[tid][1].y};
+                const df sz{sh.ray[tid][2].x, sh.ray[tid][2].y};
+                df dx{sh.ray[tid][3].x, sh.ray[tid][3].y}, dy{sh.ray[tid][4].x, sh.ray[tid][4].y};
+                df dz{sh.ray[tid][5].x, sh.ray[tid][5].y};
+                if (mode == 4) {
+                    const uint32_t flat = (uint32_t)idx;
+                    const uint32_t slot = flat / rps, k = flat - slot * rps;
+                    trace_ray<INTEG, false>(P, sx, sy, sz, __ldg(P.perm + slot) + P.source_offset, k, r, nullptr);
+                } else {
+                    df Rx = sx, Ry = sy, Rz = sz;
+                    if (mode == 0) {
+                        float res[4];
+                        surr_residual(S, sh.born[tid], sh.y[tid], res);
+                        surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
+                    }
+                    r.status = PIVBOS_RAY_REACHED;
+                    optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, r.status, r.px, r.py);
+                }
+                cnt[r.status]++;
+            }
+            if (sub == 0) {
+                if (here && r.status == PIVBOS_RAY_REACHED) atomicMin(&sh.anchor_tid, tid);
+                __syncthreads();
+                if (tid == sh.anchor_tid) {
+                    float f;
+                    sh.ax = df_floor(r.px, f) - kTileW / 2;
+                    sh.ay = df_floor(r.py, f) - kTileH / 2;
+                }
+                __syncthreads();
+                ax = sh.ax;
+                ay = sh.ay;
+            }
+            if (here && r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, sh.tile, ax, ay, image);
+            __syncthreads();
+        }
+        for (int q = tid; q < kTileW * kTileH; q += blockDim.x) {
+            const unsigned long long v = sh.tile[q];
+            if (v) {
+                const int gx = ax + (q % kTileW), gy = ay + (q / kTileW);
+                atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * P.o.W + gx]), v);
+            }
+        }
+    }
+    if (stats) {
+#pragma unroll
+        for (int q = 0; q < PIVBOS_RAY_NSTATUS; ++q)
+            if (cnt[q]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[q]), (unsigned long long)cnt[q]);
+    }
+}
+
+// Per-ray surrogate sensor positions for checking (flag 0 surrogate, 1 plain
+// fallback (traced here), 2 never enters the box (straight)).
+template <int INTEG>
+__global__ void surr_sensor_kernel(const TraceParams P, const SurrParams S, const float* __restrict__ Y,
+                                   const int64_t* __restrict__ ids, int64_t n, double* __restrict__ out_px,
+                                   int* __restrict__ out_flag, int* __restrict__ out_status)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint32_t sid, k;
+    df sx, sy, sz, dx, dy, dz;
+    ray_by_id(P, (uint64_t)ids[q], sid, k, sx, sy, sz, dx, dy, dz);
+    Entry e;
+    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+    const int flag = !e.enters ? 2 : (((S.bin_ok[e.bin >> 5] >> (e.bin & 31)) & 1u) ? 0 : 1);
+    int status = PIVBOS_RAY_REACHED;
+    df px = dfv(0.f), py = dfv(0.f);
+    if (flag == 1) {
+        RayOut r;
+        trace_ray<INTEG, false>(P, sx, sy, sz, sid + P.source_offset, k, r, nullptr);
+        status = r.status;
+        px = r.px;
+        py = r.py;
+    } else {
+        df Rx = sx, Ry = sy, Rz = sz;
+        if (flag == 0) {
+            float born[4], res[4];
+            born_residual(S, e, born);
+            surr_residual(S, born, Y + q * 4, res);
+            surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
+        }
+        optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, status, px, py);
+    }
+    out_px[2 * q] = df_to_double(px);
+    out_px[2 * q + 1] = df_to_double(py);
+    out_flag[q] = flag;
+    out_status[q] = status;
+}
+
+// Encoded features of given rays (the network input of surr_sensor_kernel).
+__global__ void surr_features_kernel(const TraceParams P, const SurrParams S, const int64_t* __restrict__ ids,
+                                     int64_t n, __nv_bfloat16* __restrict__ X)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint32_t sid, k;
+    df sx, sy, sz, dx, dy, dz;
+    ray_by_id(P, (uint64_t)ids[q], sid, k, sx, sy, sz, dx, dy, dz);
+    Entry e;
+    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+    float born[4];
+    born_residual(S, e, born);
+    encode_features(S, e.f, born, X + (size_t)q * kMlpIn);
+}
+
+}  // namespace pivbos
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+#include <chrono>
+
+struct pivbos_surrogate {
+    int device = 0;
+    int integrator = PIVBOS_RK4;
+    const pivbos_medium* medium = nullptr;
+    const pivbos_optics* optics = nullptr;
+    pivbos::MlpDev net;
+    pivbos::SurrParams S;
+    uint32_t* bin_ok = nullptr;
+    float4* table = nullptr;
+    pivbos_surrogate_report rep;
+};
+
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+pivbos::dfc to_dfc2(double v)
+{
+    const float hi = (float)v;
+    return pivbos::dfc{hi, (float)(v - (double)hi)};
+}
+
+// He-uniform initial weights (bound sqrt(6/in)), zero biases; splitmix64.
+void init_params(std::vector<float>& p, uint64_t seed)
+{
+    p.assign(pivbos::kMlpParams, 0.f);
+    uint64_t x = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    auto next = [&]() {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int l = 0; l < pivbos::kMlpLayers; ++l) {
+        const int in = pivbos::mlp_in(l), out = pivbos::mlp_out(l);
+        const double bound = sqrt(6.0 / in);
+        for (int e = 0; e < in * out; ++e) p[pivbos::mlp_w_offset(l) + e] = (float)((2.0 * next() - 1.0) * bound);
+    }
+}
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    cudaError_t alloc(size_t n) { return cudaMalloc(&p, sizeof(T) * (n > 0 ? n : 1)); }
+    ~DevBuf() { cudaFree(p); }
+};
+
+// Greedy choice of served bins under a global error budget: bins in order of
+// plain-path work saved per unit of squared error, while the summed squared
+// error stays within budget2 (all in held-out sums).  Returns the served
+// bins' error, steps and ray count.
+struct Served {
+    double err2 = 0.0, steps = 0.0, rays = 0.0;
+};
+
+Served choose_bins(const std::vector<double>& err2, const std::vector<double>& steps,
+                   const std::vector<unsigned>& cnt, int min_count, double budget2, std::vector<uint32_t>* ok)
+{
+    std::vector<int> order;
+    for (int b = 0; b < (int)cnt.size(); ++b)
+        if ((int)cnt[b] >= min_count) order.push_back(b);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        // steps[a] / err2[a] > steps[b] / err2[b], without dividing by zero
+        const double l = steps[a] * err2[b], r = steps[b] * err2[a];
+        return l != r ? l > r : a < b;
+    });
+    Served sv;
+    for (int b : order) {
+        if (sv.err2 + err2[b] > budget2) continue;
+        sv.err2 += err2[b];
+        sv.steps += steps[b];
+        sv.rays += cnt[b];
+        if (ok) (*ok)[b >> 5] |= 1u << (b & 31);
+    }
+    return sv;
+}
+
+}  // namespace
+
+extern "C" {
+
+pivbos_status pivbos_surrogate_default_cfg(pivbos_surrogate_cfg* c)
+{
+    if (!c) return serr(PIVBOS_ERR_INVALID_ARG, "cfg is NULL");
+    c->n_train = 20000000;
+    c->n_val = 2000000;
+    c->epochs = 20;
+    c->batch = 16384;
+    c->lr = 3e-3f;
+    c->err_budget_px = 0.01f;
+    c->budget_margin = 0.8f;
+    c->min_bin_count = 8;
+    c->seed = 7;
+    c->ref_plane_z = NAN;
+    c->born_segments = 8;
+    c->use_network = 1;
+    return PIVBOS_OK;
+}
+
+pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integrator, const pivbos_surrogate_cfg* cfg,
+                                     pivbos_surrogate** out, pivbos_surrogate_report* report, void* stream)
+{
+    pivbos::set_last_error("");
+    if (!frame || !out) return serr(PIVBOS_ERR_INVALID_ARG, "frame and out are required");
+    *out = nullptr;
+    if (!frame->medium) return serr(PIVBOS_ERR_INVALID_ARG, "the surrogate needs a medium");
+    pivbos_surrogate_cfg c;
+    pivbos_surrogate_default_cfg(&c);
+    if (cfg) c = *cfg;
+    if (c.n_train < 256 || c.n_val < 256 || c.n_train > (1ll << 31) || c.n_val > (1ll << 31) || c.epochs < 1 ||
+        c.batch < 256 || c.batch > 65536 || !(c.lr > 0.f) || !(c.err_budget_px > 0.f) ||
+        !(c.budget_margin > 0.f && c.budget_margin <= 1.f) || c.min_bin_count < 1 ||
+        (!std::isnan(c.ref_plane_z) && !std::isfinite(c.ref_plane_z)) || c.born_segments < 0 ||
+        c.born_segments > 64 || (c.use_network != 0 && c.use_network != 1))
+        return serr(PIVBOS_ERR_INVALID_ARG, "surrogate configuration out of range");
+    pivbos::TraceParams P;
+    int dev = 0;
+    uint64_t total = 0;
+    pivbos_status st = pivbos::prepare_trace(frame->medium, frame->optics, frame->sources, frame->n_sources, 1,
+                                             frame->rays_per_source, frame->seed, frame->frame, integrator, frame->step,
+                                             &P, &dev, &total);
+    if (st) return st;
+    if (total == 0) return serr(PIVBOS_ERR_INVALID_ARG, "frame has no rays");
+    cudaStream_t s = (cudaStream_t)stream;
+    const pivbos_medium* m = frame->medium;
+    const pivbos_optics* o = frame->optics;
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = m->origin[a];
+        hi[a] = m->origin[a] + (double)(m->n[a] - 1) * m->spacing[a];
+    }
+    const double aim_z = (double)o->d.aim_z.hi + (double)o->d.aim_z.lo;
+    const double aim_r = (double)o->d.aim_r.hi + (double)o->d.aim_r.lo;
+    if (!(aim_z > hi[2])) return serr(PIVBOS_ERR_UNSUPPORTED, "the surrogate needs the lens after the density box");
+    pivbos_surrogate* sg = new (std::nothrow) pivbos_surrogate();
+    if (!sg) return serr(PIVBOS_ERR_OOM, "host allocation");
+    sg->device = dev;
+    sg->integrator = integrator;
+    sg->medium = m;
+    sg->optics = o;
+    memset(&sg->rep, 0, sizeof sg->rep);
+    pivbos_surrogate_report& R = sg->rep;
+    pivbos::SurrParams& S = sg->S;
+    memset(&S, 0, sizeof S);
+    const double z_ref = std::isnan(c.ref_plane_z) ? 0.5 * (lo[2] + hi[2]) : c.ref_plane_z;
+    S.z_lo = to_dfc2(lo[2]);
+    S.z_ref = to_dfc2(z_ref);
+    S.cx = (float)(0.5 * (lo[0] + hi[0]));
+    S.cy = (float)(0.5 * (lo[1] + hi[1]));
+    S.cz = (float)(0.5 * (lo[2] + hi[2]));
+    S.hx = (float)(0.5 * (hi[0] - lo[0]));
+    S.hy = (float)(0.5 * (hi[1] - lo[1]));
+    S.hz = (float)fmax(0.5 * (hi[2] - lo[2]), 1e-9);
+    S.u_scale = (float)((aim_r + fmax(fabs(S.cx) + S.hx, fabs(S.cy) + S.hy)) / (aim_z - hi[2]));
+    for (int q = 0; q < 4; ++q) S.t_scale[q] = S.b_scale[q] = 1.0f;
+    S.nbx = 16;
+    S.nby = 16;
+    S.nbz = 16;
+    S.nbu = 4;
+    S.use_net = c.use_network;
+    S.born_k = c.born_segments;
+    const int nbins = pivbos::kSurrBins;
+    cudaError_t e = pivbos::mlp_alloc(sg->net, 128);
+    if (e == cudaSuccess) e = cudaMalloc(&sg->bin_ok, sizeof(uint32_t) * (nbins / 32));
+    if (e != cudaSuccess) {
+        pivbos_surrogate_destroy(sg);
+        return scuda(e, "surrogate allocation");
+    }
+    // ---- projection table: columns through the pupil centre over the box's
+    // back face, one level per grid node in depth
+    const double t_start = now_s();
+    if (S.born_k > 0) {
+        const double persp = aim_z - hi[2];
+        double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+        for (int cnr = 0; cnr < 8; ++cnr) {
+            const double x = (cnr & 1) ? hi[0] : lo[0], y = (cnr & 2) ? hi[1] : lo[1], z = (cnr & 4) ? hi[2] : lo[2];
+            const double f = persp / (aim_z - z);
+            xmin = fmin(xmin, x * f); xmax = fmax(xmax, x * f);
+            ymin = fmin(ymin, y * f); ymax = fmax(ymax, y * f);
+        }
+        S.tnx = std::min(2 * (m->n[0] - 1) + 1, 1024);
+        S.tny = std::min(2 * (m->n[1] - 1) + 1, 1024);
+        S.tnz = std::max(2, std::min(m->n[2], 512));
+        S.t_x0 = (float)xmin;
+        S.t_y0 = (float)ymin;
+        S.t_inv_dx = (float)((S.tnx - 1) / fmax(xmax - xmin, 1e-12));
+        S.t_inv_dy = (float)((S.tny - 1) / fmax(ymax - ymin, 1e-12));
+        S.t_inv_dz = (float)((S.tnz - 1) / fmax(hi[2] - lo[2], 1e-12));
+        S.zlo_f = (float)lo[2];
+        S.zhi_f = (float)hi[2];
+        S.aim_z = (float)aim_z;
+        S.persp = (float)persp;
+        const size_t nodes = (size_t)S.tnx * S.tny * S.tnz;
+        e = cudaMalloc(&sg->table, nodes * 2 * sizeof(float4));
+        if (e == cudaSuccess) {
+            const double level = (hi[2] - lo[2]) / (S.tnz - 1);
+            const int sub = (int)std::min(64.0, std::max(2.0, ceil(4.0 * level / m->spacing[2])));
+            const int cols = S.tnx * S.tny;
+            pivbos::surr_table_kernel<<<(cols + 127) / 128, 128, 0, s>>>(P.m, S, sub, sg->table);
+            pivbos::count_launches(1);
+            e = cudaStreamSynchronize(s);
+        }
+        if (e != cudaSuccess) {
+            pivbos_surrogate_destroy(sg);
+            return scuda(e, "surrogate projection table");
+        }
+        S.table = sg->table;
+        R.table_bytes = (double)(nodes * 2 * sizeof(float4));
+    }
+    R.seconds_table = now_s() - t_start;
+    // ---- S1: pilot statistics, then training and held-out samples traced
+    // by the plain path
+    const double t0 = now_s();
+    DevBuf<__nv_bfloat16> Xt, Xv;
+    DevBuf<float> Tt, Yv;
+    DevBuf<uint64_t> idv;
+    DevBuf<double> refpx, pilot, accd;
+    DevBuf<int> refst;
+    DevBuf<unsigned int> bincnt;
+    e = Xt.alloc((size_t)c.n_train * pivbos::kMlpIn);
+    if (e == cudaSuccess) e = Tt.alloc((size_t)c.n_train * 4);
+    if (e == cudaSuccess) e = Xv.alloc((size_t)c.n_val * pivbos::kMlpIn);
+    if (e == cudaSuccess) e = Yv.alloc((size_t)c.n_val * 4);
+    if (e == cudaSuccess) e = idv.alloc((size_t)c.n_val);
+    if (e == cudaSuccess) e = refpx.alloc((size_t)c.n_val * 2);
+    if (e == cudaSuccess) e = refst.alloc((size_t)c.n_val);
+    if (e == cudaSuccess) e = pilot.alloc(17);
+    if (e == cudaSuccess) e = accd.alloc((size_t)4 * nbins + 5);
+    if (e == cudaSuccess) e = bincnt.alloc(nbins);
+    if (e != cudaSuccess) {
+        pivbos_surrogate_destroy(sg);
+        return scuda(e, "surrogate data allocation");
+    }
+    const int64_t n_pilot = std::min<int64_t>(c.n_val, 65536);
+    e = cudaMemsetAsync(pilot.p, 0, sizeof(double) * 17, s);
+    if (e == cudaSuccess) {
+        const unsigned blocks = (unsigned)((n_pilot + 127) / 128);
+        if (integrator == PIVBOS_RK4)
+            pivbos::surr_pilot_kernel<PIVBOS_RK4><<<blocks, 128, 0, s>>>(P, S, total, n_pilot, c.seed, 1e-6, 1e-6, pilot.p);
+        else
+            pivbos::surr_pilot_kernel<PIVBOS_EULER><<<blocks, 128, 0, s>>>(P, S, total, n_pilot, c.seed, 1e-6, 1e-6, pilot.p);
+        pivbos::count_launches(1);
+    }
+    double pm[17];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pm, pilot.p, sizeof pm, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        pivbos_surrogate_destroy(sg);
+        return scuda(e, "surrogate pilot");
+    }
+    // Scales.  Network inputs: the projection residual per component at unit
+    // RMS.  Network outputs: the correction in units of its RMS effect on
+    // the sensor (J_q px per unit, measured about the straight rays), so the
+    // loss weighs errors by what they move on the image, at about unit RMS
+    // overall.
+    double J[4], cc = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        R.target_rms[q] = sqrt(pm[q] / n_pilot);
+        const double brms = sqrt(pm[4 + q] / n_pilot);
+        R.correction_rms[q] = sqrt(pm[8 + q] / n_pilot);
+        S.b_scale[q] = (float)(brms > 1e-30 ? brms : 1.0);
+        J[q] = pm[16] > 0 ? sqrt(pm[12 + q] / pm[16]) : 0.0;
+        R.sensor_px_per_unit[q] = J[q];
+        cc += (R.correction_rms[q] * J[q]) * (R.correction_rms[q] * J[q]) / 4.0;
+    }
+    cc = sqrt(cc);
+    for (int q = 0; q < 4; ++q) {
+        double scale = (J[q] > 0 && cc > 0) ? cc / J[q] : R.correction_rms[q];
+        if (!(scale > 1e-30)) scale = 1e-30;
+        S.t_scale[q] = (float)scale;
+    }
+    auto data = [&](int64_t n, uint32_t streamid, __nv_bfloat16* X, float* T, uint64_t* ids, double* rp, int* rs) {
+        const unsigned blocks = (unsigned)((n + 127) / 128);
+        if (integrator == PIVBOS_RK4)
+            pivbos::surr_data_kernel<PIVBOS_RK4><<<blocks, 128, 0, s>>>(P, S, total, n, streamid, c.seed, X, T, ids, rp, rs);
+        else
+            pivbos::surr_data_kernel<PIVBOS_EULER><<<blocks, 128, 0, s>>>(P, S, total, n, streamid, c.seed, X, T, ids, rp, rs);
+        pivbos::count_launches(1);
+    };
+    if (c.use_network) data(c.n_train, 0, Xt.p, Tt.p, nullptr, nullptr, nullptr);
+    data(c.n_val, 1, Xv.p, nullptr, idv.p, refpx.p, refst.p);
+    e = cudaStreamSynchronize(s);
+    R.seconds_data = now_s() - t0;
+    // ---- S2: training on the GPU
+    const double t1 = now_s();
+    if (c.use_network) {
+        std::vector<float> p0;
+        init_params(p0, c.seed);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(sg->net.params, p0.data(), sizeof(float) * p0.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = pivbos::mlp_sync_bf16(sg->net, s);
+        pivbos::MlpWork w;
+        if (e == cudaSuccess) e = pivbos::mlp_work_alloc(w, c.batch);
+        const int64_t per_epoch = (c.n_train + c.batch - 1) / c.batch;
+        const int64_t steps = per_epoch * c.epochs;
+        double last_loss = 0.0;
+        for (int64_t t = 0; t < steps && e == cudaSuccess; ++t) {
+            const int64_t off = (t % per_epoch) * c.batch;
+            const int rows = (int)std::min<int64_t>(c.batch, c.n_train - off);
+            const float lr = (float)(c.lr * (0.01 + 0.99 * 0.5 * (1.0 + cos(M_PI * (double)t / (double)steps))));
+            e = pivbos::mlp_forward(sg->net, Xt.p + off * pivbos::kMlpIn, rows, w.y, &w, Tt.p + off * 4, s);
+            if (e == cudaSuccess) e = pivbos::mlp_backward(sg->net, Xt.p + off * pivbos::kMlpIn, rows, w, s);
+            if (e == cudaSuccess) e = pivbos::mlp_adam(sg->net, (int)(t + 1), lr, s);
+            if (e == cudaSuccess && t == steps - 1) {
+                double l = 0.0;
+                e = cudaMemcpyAsync(&l, w.loss, sizeof l, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                last_loss = l / ((double)rows * pivbos::kMlpOut);
+            }
+        }
+        pivbos::mlp_work_free(w);
+        R.train_loss = last_loss;
+        R.train_steps = (double)steps;
+    }
+    R.seconds_train = now_s() - t1;
+    // ---- confidence map: the plain tracer judges the predictors on held-out rays
+    const double t2 = now_s();
+    if (e == cudaSuccess) {
+        if (c.use_network) e = pivbos::mlp_forward(sg->net, Xv.p, (int)c.n_val, Yv.p, nullptr, nullptr, s);
+        else e = cudaMemsetAsync(Yv.p, 0, sizeof(float) * 4 * (size_t)c.n_val, s);
+    }
+    const size_t nacc = (size_t)4 * nbins + 5;
+    if (e == cudaSuccess) e = cudaMemsetAsync(accd.p, 0, sizeof(double) * nacc, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bincnt.p, 0, sizeof(unsigned int) * nbins, s);
+    if (e == cudaSuccess) {
+        pivbos::BinAcc acc{{accd.p, accd.p + nbins, accd.p + 2 * (size_t)nbins}, accd.p + 3 * (size_t)nbins,
+                           bincnt.p, accd.p + 4 * (size_t)nbins};
+        pivbos::surr_eval_kernel<<<(unsigned)((c.n_val + 127) / 128), 128, 0, s>>>(P, S, idv.p, Yv.p, refpx.p,
+                                                                                   refst.p, c.n_val, acc);
+        pivbos::count_launches(1);
+    }
+    std::vector<double> hd(nacc);
+    std::vector<unsigned int> hc(nbins);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), accd.p, sizeof(double) * nacc, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), bincnt.p, sizeof(unsigned) * nbins, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        pivbos_surrogate_destroy(sg);
+        return scuda(e, "surrogate training");
+    }
+    std::vector<double> err2[3];
+    for (int v = 0; v < 3; ++v) err2[v].assign(hd.begin() + (size_t)v * nbins, hd.begin() + (size_t)(v + 1) * nbins);
+    const std::vector<double> stp(hd.begin() + 3 * (size_t)nbins, hd.begin() + 4 * (size_t)nbins);
+    const double* tot = hd.data() + 4 * (size_t)nbins;
+    const double n_reached = tot[0], n_box = tot[1];
+    double all_err[3] = {0, 0, 0}, all_steps = 0.0;
+    for (int b = 0; b < nbins; ++b) {
+        for (int v = 0; v < 3; ++v) all_err[v] += err2[v][b];
+        all_steps += stp[b];
+    }
+    const double margin = c.budget_margin;
+    const double budget2 = margin * margin * (double)c.err_budget_px * c.err_budget_px * n_reached;
+    std::vector<uint32_t> ok(nbins / 32, 0u);
+    // the served predictor: the network's (projection + correction), or
+    // the projection alone without a network
+    const int vs = c.use_network ? 0 : 1;
+    Served sv[3];
+    for (int v = 0; v < 3; ++v) sv[v] = choose_bins(err2[v], stp, hc, c.min_bin_count, budget2, v == vs ? &ok : nullptr);
+    auto rms = [&](int v) { return n_box > tot[2 + v] ? sqrt(all_err[v] / (n_box - tot[2 + v])) : 0.0; };
+    R.val_rms_px = rms(vs);
+    R.val_rms_px_born = rms(1);
+    R.val_rms_px_straight = rms(2);
+    R.val_rms_px_served = n_reached > 0 ? sqrt(sv[vs].err2 / n_reached) : 0.0;
+    R.val_served_frac = n_box > 0 ? sv[vs].rays / n_box : 0.0;
+    R.val_served_frac_born = n_box > 0 ? sv[1].rays / n_box : 0.0;
+    R.val_served_frac_straight = n_box > 0 ? sv[2].rays / n_box : 0.0;
+    R.steps_saved_frac = all_steps > 0 ? sv[vs].steps / all_steps : 0.0;
+    R.steps_saved_frac_born = all_steps > 0 ? sv[1].steps / all_steps : 0.0;
+    R.steps_saved_frac_straight = all_steps > 0 ? sv[2].steps / all_steps : 0.0;
+    R.val_status_flip_frac = n_box > 0 ? tot[2 + vs] / n_box : 0.0;
+    R.n_val_reached = n_reached;
+    R.n_val_box = n_box;
+    e = cudaMemcpy(sg->bin_ok, ok.data(), sizeof(uint32_t) * ok.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        pivbos_surrogate_destroy(sg);
+        return scuda(e, "surrogate bins");
+    }
+    S.bin_ok = sg->bin_ok;
+    R.seconds_validate = now_s() - t2;
+    if (report) *report = R;
+    *out = sg;
+    return PIVBOS_OK;
+}
+
+static pivbos_status surr_prepare(const pivbos_surrogate* sg, const pivbos_frame_desc* frame, pivbos::TraceParams& P,
+                                  uint64_t& total)
+{
+    if (!sg || !frame) return serr(PIVBOS_ERR_INVALID_ARG, "surrogate and frame are required");
+    if (frame->medium != sg->medium || frame->optics != sg->optics)
+        return serr(PIVBOS_ERR_INVALID_ARG, "the frame must use the medium and optics the surrogate was trained on");
+    int dev = 0;
+    pivbos_status st = pivbos::prepare_trace(frame->medium, frame->optics, frame->sources, frame->n_sources, 1,
+                                             frame->rays_per_source, frame->seed, frame->frame, sg->integrator,
+                                             frame->step, &P, &dev, &total);
+    if (st) return st;
+    if (dev != sg->device) return serr(PIVBOS_ERR_INVALID_ARG, "surrogate belongs to device %d", sg->device);
+    return PIVBOS_OK;
+}
+
+pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_frame_desc* frame, int64_t* n_fallback,
+                                      void* stream)
+{
+    pivbos::set_last_error("");
+    pivbos::TraceParams P;
+    uint64_t total = 0;
+    pivbos_status st = surr_prepare(sg, frame, P, total);
+    if (st) return st;
+    cudaPointerAttributes a;
+    if (!frame->image || cudaPointerGetAttributes(&a, frame->image) != cudaSuccess ||
+        a.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return serr(PIVBOS_ERR_INVALID_ARG, "image must be device memory");
+    }
+    if (n_fallback) *n_fallback = 0;
+    if (total == 0) return PIVBOS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t n = (uint32_t)frame->n_sources;
+    uint32_t n_pow2 = 2;
+    while (n_pow2 < n) n_pow2 <<= 1;
+    const uint32_t capacity = (uint32_t)total;
+    const size_t off_perm = (size_t)n_pow2 * 8;
+    const size_t off_sdf = off_perm + (((size_t)n * 4 + 255) & ~(size_t)255);
+    const size_t off_cnt = off_sdf + (((size_t)n * 24 + 255) & ~(size_t)255);
+    const size_t off_fb = off_cnt + 256;
+    const size_t bytes = off_fb + (size_t)capacity * 4;
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&scratch, bytes, s);
+    if (e != cudaSuccess) return scuda(e, "surrogate render scratch");
+    uint32_t* perm = (uint32_t*)(scratch + off_perm);
+    float2* sdf = (float2*)(scratch + off_sdf);
+    // [0] render items, [1] fallback rays, [2] fallback chunks
+    unsigned long long* counters = (unsigned long long*)(scratch + off_cnt);
+    uint32_t* fb = (uint32_t*)(scratch + off_fb);
+    e = pivbos::launch_morton_sort(frame->sources, n, (uint64_t*)scratch, n_pow2, perm, sdf, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), s);
+    P.perm = perm;
+    P.src_df = sdf;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sg->device);
+    if (e == cudaSuccess) {
+        e = cudaFuncSetAttribute(pivbos::surr_render_kernel<PIVBOS_RK4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(pivbos::SurrSmem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(pivbos::surr_render_kernel<PIVBOS_EULER>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(pivbos::SurrSmem));
+    }
+    if (e == cudaSuccess) {
+        pivbos::timing_begin("surrogate_render", s);
+        if (sg->integrator == PIVBOS_RK4)
+            pivbos::surr_render_kernel<PIVBOS_RK4><<<sms, 256, sizeof(pivbos::SurrSmem), s>>>(
+                P, sg->S, sg->net.wbf, sg->net.params, frame->image, frame->stats, total, 2048u, counters, fb,
+                counters + 1, capacity);
+        else
+            pivbos::surr_render_kernel<PIVBOS_EULER><<<sms, 256, sizeof(pivbos::SurrSmem), s>>>(
+                P, sg->S, sg->net.wbf, sg->net.params, frame->image, frame->stats, total, 2048u, counters, fb,
+                counters + 1, capacity);
+        pivbos::timing_end("surrogate_render", s);
+        pivbos::count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        pivbos::TraceParams PL = P;
+        PL.ray_list = fb;
+        pivbos::timing_begin("surrogate_fallback", s);
+        e = pivbos::launch_list(PL, sg->integrator, counters + 1, capacity, frame->image, frame->stats, 2048u,
+                                counters + 2, s);
+        pivbos::timing_end("surrogate_fallback", s);
+    }
+    unsigned long long nfb = 0;
+    if (e == cudaSuccess && n_fallback) {
+        e = cudaMemcpyAsync(&nfb, counters + 1, sizeof nfb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        *n_fallback = (int64_t)nfb;
+    }
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return scuda(e, "surrogate render");
+    if (ef != cudaSuccess) return scuda(ef, "surrogate render scratch release");
+    return PIVBOS_OK;
+}
+
+pivbos_status pivbos_surrogate_sensor(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
+                                      const int64_t* ray_ids, int64_t n, double* sensor_xy, int32_t* flags,
+                                      int32_t* status, void* stream)
+{
+    pivbos::set_last_error("");
+    pivbos::TraceParams P;
+    uint64_t total = 0;
+    pivbos_status st = surr_prepare(sg, frame, P, total);
+    if (st) return st;
+    if (n < 0 || n > (1ll << 31) || (n > 0 && (!ray_ids || !sensor_xy || !flags || !status)))
+        return serr(PIVBOS_ERR_INVALID_ARG, "ray ids and outputs are required");
+    if (n == 0) return PIVBOS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf<__nv_bfloat16> X;
+    DevBuf<float> Y;
+    cudaError_t e = X.alloc((size_t)n * pivbos::kMlpIn);
+    if (e == cudaSuccess) e = Y.alloc((size_t)n * 4);
+    if (e != cudaSuccess) return scuda(e, "surrogate sensor scratch");
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    pivbos::surr_features_kernel<<<blocks, 128, 0, s>>>(P, sg->S, ray_ids, n, X.p);
+    e = pivbos::mlp_forward(sg->net, X.p, (int)n, Y.p, nullptr, nullptr, s);
+    if (e == cudaSuccess) {
+        if (sg->integrator == PIVBOS_RK4)
+            pivbos::surr_sensor_kernel<PIVBOS_RK4><<<blocks, 128, 0, s>>>(P, sg->S, Y.p, ray_ids, n, sensor_xy, flags,
+                                                                         status);
+        else
+            pivbos::surr_sensor_kernel<PIVBOS_EULER><<<blocks, 128, 0, s>>>(P, sg->S, Y.p, ray_ids, n, sensor_xy,
+                                                                           flags, status);
+        pivbos::count_launches(2);
+        e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return scuda(e, "surrogate sensor");
+    return PIVBOS_OK;
+}
+
+pivbos_status pivbos_surrogate_report_get(const pivbos_surrogate* sg, pivbos_surrogate_report* out)
+{
+    if (!sg || !out) return serr(PIVBOS_ERR_INVALID_ARG, "NULL argument");
+    *out = sg->rep;
+    return PIVBOS_OK;
+}
+
+void pivbos_surrogate_destroy(pivbos_surrogate* sg)
+{
+    if (!sg) return;
+    pivbos::mlp_free(sg->net);
+    cudaFree(sg->bin_ok);
+    cudaFree(sg->table);
+    delete sg;
 }
 
 }  // extern "C"

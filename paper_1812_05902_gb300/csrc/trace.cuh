@@ -204,6 +204,170 @@ __device__ __forceinline__ void put3(double* dst, df x, df y, df z)
     dst[2] = df_to_double(z);
 }
 
+// Sec. 3.1: the ray from source (sx, sy, sz) to its lens point, unit direction.
+__device__ __forceinline__ void ray_start(const TraceParams& P, df sx, df sy, df sz, uint32_t sid, uint32_t rid,
+                                          df& dx, df& dy, df& dz)
+{
+    const DevOptics& o = P.o;
+    uint64_t w0, w1;
+    philox_lens_words(rid, sid, P.frame, 0ull, P.seed, 0ull, w0, w1);
+    const df rr = df_mul(dfk(o.aim_r), df_sqrt(u01_df(w0)));
+    const df u2 = u01_df(w1);
+    df sn, cs;
+    df_sincospi(df{2.0f * u2.hi, 2.0f * u2.lo}, sn, cs);
+    dx = df_sub(df_mul(rr, cs), sx);
+    dy = df_sub(df_mul(rr, sn), sy);
+    dz = df_sub(dfk(o.aim_z), sz);
+    const df inv = df_rsqrt(df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz)));
+    dx = df_mul(dx, inv);
+    dy = df_mul(dy, inv);
+    dz = df_mul(dz, inv);
+}
+
+// Whether the straight ray R + t d (t >= 0) enters the density box, and the
+// parameter tn of the entry point (0 for a start inside the box).  An FP32
+// slab test decides whether and through which face; the entry parameter of
+// that face is then solved in double-float, so integration starts on the
+// face (a start shifted along the ray would shift every field sample).
+__device__ __forceinline__ bool box_entry(const DevMedium& m, df Rx, df Ry, df Rz, df dx, df dy, df dz, df& tn)
+{
+    tn = dfv(0.0f);
+    const df lo0 = dfk(m.lo[0]), lo1 = dfk(m.lo[1]), lo2 = dfk(m.lo[2]);
+    const df hi0 = dfk(m.hi[0]), hi1 = dfk(m.hi[1]), hi2 = dfk(m.hi[2]);
+    if (!df_lt(Rx, lo0) && !df_gt(Rx, hi0) && !df_lt(Ry, lo1) && !df_gt(Ry, hi1) && !df_lt(Rz, lo2) &&
+        !df_gt(Rz, hi2))
+        return true;
+    float t_near = -INFINITY, t_far = INFINITY;
+    int a_near = -1;
+    bool ok = true;
+    const float dd[3] = {dx.hi, dy.hi, dz.hi};
+    const float RR[3] = {Rx.hi, Ry.hi, Rz.hi};
+    const float LO[3] = {m.lo[0].hi, m.lo[1].hi, m.lo[2].hi};
+    const float HI[3] = {m.hi[0].hi, m.hi[1].hi, m.hi[2].hi};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (dd[a] == 0.0f) {
+            if (RR[a] < LO[a] || RR[a] > HI[a]) ok = false;
+        } else {
+            const float inv = 1.0f / dd[a];
+            const float t1 = (LO[a] - RR[a]) * inv;
+            const float t2 = (HI[a] - RR[a]) * inv;
+            const float tmin = fminf(t1, t2);
+            if (tmin > t_near) {
+                t_near = tmin;
+                a_near = a;
+            }
+            t_far = fminf(t_far, fmaxf(t1, t2));
+        }
+    }
+    if (!(ok && t_near <= t_far && t_near >= 0.0f && a_near >= 0)) return false;
+    const df Ra = a_near == 0 ? Rx : (a_near == 1 ? Ry : Rz);
+    const df da = a_near == 0 ? dx : (a_near == 1 ? dy : dz);
+    const dfc face = da.hi > 0.0f ? m.lo[a_near] : m.hi[a_near];
+    tn = df_div(df_sub(dfk(face), Ra), da);
+    if (tn.hi < 0.0f) tn = dfv(0.0f);
+    return true;
+}
+
+// Sec. 3.3 and 3.4: from a point and direction in object space through the
+// optical elements to the sensor plane.  Leaves status unchanged if the ray
+// reaches the sensor array; (R, d) end as the state at the sensor.
+__device__ __forceinline__ void optics_to_sensor(const DevOptics& o, df& Rx, df& Ry, df& Rz, df& dx, df& dy, df& dz,
+                                                 int& status, df& px, df& py)
+{
+    for (int s = 0; s < o.ns && status == PIVBOS_RAY_REACHED; ++s) {
+        const DevSurface& S = o.s[s];
+        if (!(dz.hi > 0.0f)) { status = PIVBOS_RAY_MISS; break; }
+        const df inv_dz = df_rcp(dz);
+        const df t0 = df_mul(df_sub(dfk(S.z), Rz), inv_dz);
+        if (S.type == PIVBOS_SURF_SPHERE && S.R_f != 0.0f) {
+            // vertex-relative quadratic t^2 + 2 b t + c = 0 from the point Q
+            // on the vertex plane; the vertex-side root has the smaller
+            // magnitude: t = c / (-b - sign(b) sqrt(b^2 - c))
+            const df Qx = df_fma(t0, dx, Rx), Qy = df_fma(t0, dy, Ry);
+            const df R = dfk(S.R);
+            const df b = df_sub(df_add(df_mul(dx, Qx), df_mul(dy, Qy)), df_mul(R, dz));
+            const df c = df_add(df_sqr(Qx), df_sqr(Qy));
+            const df disc = df_sub(df_sqr(b), c);
+            if (disc.hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
+            const df sq = df_sqrt(disc);
+            const df den = b.hi >= 0.0f ? df_sub(df_neg(b), sq) : df_add(df_neg(b), sq);
+            const df t1 = den.hi != 0.0f ? df_div(c, den) : dfv(0.0f);
+            if (df_add(t0, t1).hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
+            const df Hx = df_fma(t1, dx, Qx), Hy = df_fma(t1, dy, Qy), Hz = df_mul(t1, dz);
+            const df HzR = df_sub(Hz, R);
+            if (!(HzR.hi * S.R_f < 0.0f)) { status = PIVBOS_RAY_MISS; break; }
+            if (Hx.hi * Hx.hi + Hy.hi * Hy.hi > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
+            const df invR = dfk(S.invR);
+            df Nx = df_mul(Hx, invR), Ny = df_mul(Hy, invR), Nz = df_mul(HzR, invR);
+            if (Nx.hi * dx.hi + Ny.hi * dy.hi + Nz.hi * dz.hi > 0.0f) {
+                Nx = df_neg(Nx); Ny = df_neg(Ny); Nz = df_neg(Nz);
+            }
+            // Eq. 7, vector form
+            const df eta = dfk(S.eta);
+            const df ci = df_neg(df_add(df_add(df_mul(Nx, dx), df_mul(Ny, dy)), df_mul(Nz, dz)));
+            const df kk = df_sub(dfv(1.0f), df_mul(dfk(S.eta2), df_sub(dfv(1.0f), df_sqr(ci))));
+            if (kk.hi < 0.0f) { status = PIVBOS_RAY_TIR; break; }
+            const df a = df_sub(df_mul(eta, ci), df_sqrt(kk));
+            dx = df_fma(eta, dx, df_mul(a, Nx));
+            dy = df_fma(eta, dy, df_mul(a, Ny));
+            dz = df_fma(eta, dz, df_mul(a, Nz));
+            Rx = Hx;
+            Ry = Hy;
+            Rz = df_add(dfk(S.z), Hz);
+        } else {
+            if (t0.hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
+            Rx = df_fma(t0, dx, Rx);
+            Ry = df_fma(t0, dy, Ry);
+            Rz = dfk(S.z);
+            const float r2 = Rx.hi * Rx.hi + Ry.hi * Ry.hi;
+            if (S.type == PIVBOS_SURF_STOP) {
+                if (r2 > S.clear_r2) { status = PIVBOS_RAY_STOP; break; }
+            } else if (S.type == PIVBOS_SURF_IDEAL_THIN) {
+                if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
+                const df invf = dfk(S.inv_f);
+                const df ux = df_sub(df_mul(dx, inv_dz), df_mul(Rx, invf));
+                const df uy = df_sub(df_mul(dy, inv_dz), df_mul(Ry, invf));
+                const df inn = df_rsqrt(df_add_f(df_add(df_sqr(ux), df_sqr(uy)), 1.0f));
+                dx = df_mul(ux, inn);
+                dy = df_mul(uy, inn);
+                dz = inn;
+            } else {
+                if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
+                // flat surface, normal (0, 0, -1)
+                const df eta = dfk(S.eta);
+                const df kk = df_sub(dfv(1.0f), df_mul(dfk(S.eta2), df_sub(dfv(1.0f), df_sqr(dz))));
+                if (kk.hi < 0.0f) { status = PIVBOS_RAY_TIR; break; }
+                const df a = df_sub(df_mul(eta, dz), df_sqrt(kk));
+                dx = df_mul(eta, dx);
+                dy = df_mul(eta, dy);
+                dz = df_sub(df_mul(eta, dz), a);
+            }
+        }
+    }
+
+    // ---- Sec. 3.4: sensor plane -------------------------------------------
+    px = dfv(0.0f);
+    py = dfv(0.0f);
+    if (status == PIVBOS_RAY_REACHED) {
+        if (!(dz.hi > 0.0f)) {
+            status = PIVBOS_RAY_MISS;
+        } else {
+            const df t = df_mul(df_sub(dfk(o.sensor_z), Rz), df_rcp(dz));
+            if (t.hi < 0.0f) {
+                status = PIVBOS_RAY_MISS;
+            } else {
+                const df ipitch = dfk(o.inv_pitch);
+                px = df_add_f(df_mul(df_fma(t, dx, Rx), ipitch), o.half_w);
+                py = df_add_f(df_mul(df_fma(t, dy, Ry), ipitch), o.half_h);
+                const bool inx = !df_lt(px, dfv(0.0f)) && df_lt(px, dfv((float)o.W));
+                const bool iny = !df_lt(py, dfv(0.0f)) && df_lt(py, dfv((float)o.H));
+                if (!(inx && iny)) status = PIVBOS_RAY_OFF_SENSOR;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // One ray through all stages.  INTEG: PIVBOS_EULER or PIVBOS_RK4.  If st is
 // not null the full exit state is written (parity path).
@@ -216,71 +380,16 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
     const DevOptics& o = P.o;
 
     // ---- Sec. 3.1: source -> point on the lens ----------------------------
-    uint64_t w0, w1;
-    philox_lens_words(rid, sid, P.frame, 0ull, P.seed, 0ull, w0, w1);
-    const df rr = df_mul(dfk(o.aim_r), df_sqrt(u01_df(w0)));
-    const df u2 = u01_df(w1);
-    df sn, cs;
-    df_sincospi(df{2.0f * u2.hi, 2.0f * u2.lo}, sn, cs);
     df Rx = sx, Ry = sy, Rz = sz;
-    df dx = df_sub(df_mul(rr, cs), sx);
-    df dy = df_sub(df_mul(rr, sn), sy);
-    df dz = df_sub(dfk(o.aim_z), sz);
-    {
-        const df inv = df_rsqrt(df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz)));
-        dx = df_mul(dx, inv);
-        dy = df_mul(dy, inv);
-        dz = df_mul(dz, inv);
-    }
+    df dx, dy, dz;
+    ray_start(P, sx, sy, sz, sid, rid, dx, dy, dz);
     int status = PIVBOS_RAY_REACHED;
     int steps = 0;
 
     // ---- Sec. 3.2: through the density box ------------------------------
     if (m.present) {
-        const df lo0 = dfk(m.lo[0]), lo1 = dfk(m.lo[1]), lo2 = dfk(m.lo[2]);
-        const df hi0 = dfk(m.hi[0]), hi1 = dfk(m.hi[1]), hi2 = dfk(m.hi[2]);
-        const bool inside = !df_lt(Rx, lo0) && !df_gt(Rx, hi0) && !df_lt(Ry, lo1) && !df_gt(Ry, hi1) &&
-                            !df_lt(Rz, lo2) && !df_gt(Rz, hi2);
-        bool enters = inside;
-        df tn = dfv(0.0f);
-        if (!inside) {
-            // slab test on the straight line in FP32 decides whether and
-            // through which face the ray enters; the entry parameter of that
-            // face is then solved in double-float, so the integration starts
-            // on the face (a start shifted along the ray would shift every
-            // sample point of the field)
-            float t_near = -INFINITY, t_far = INFINITY;
-            int a_near = -1;
-            bool ok = true;
-            const float dd[3] = {dx.hi, dy.hi, dz.hi};
-            const float RR[3] = {Rx.hi, Ry.hi, Rz.hi};
-            const float LO[3] = {m.lo[0].hi, m.lo[1].hi, m.lo[2].hi};
-            const float HI[3] = {m.hi[0].hi, m.hi[1].hi, m.hi[2].hi};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (dd[a] == 0.0f) {
-                    if (RR[a] < LO[a] || RR[a] > HI[a]) ok = false;
-                } else {
-                    const float inv = 1.0f / dd[a];
-                    const float t1 = (LO[a] - RR[a]) * inv;
-                    const float t2 = (HI[a] - RR[a]) * inv;
-                    const float tmin = fminf(t1, t2);
-                    if (tmin > t_near) {
-                        t_near = tmin;
-                        a_near = a;
-                    }
-                    t_far = fminf(t_far, fmaxf(t1, t2));
-                }
-            }
-            if (ok && t_near <= t_far && t_near >= 0.0f && a_near >= 0) {
-                enters = true;
-                const df Ra = a_near == 0 ? Rx : (a_near == 1 ? Ry : Rz);
-                const df da = a_near == 0 ? dx : (a_near == 1 ? dy : dz);
-                const dfc face = da.hi > 0.0f ? m.lo[a_near] : m.hi[a_near];
-                tn = df_div(df_sub(dfk(face), Ra), da);
-                if (tn.hi < 0.0f) tn = dfv(0.0f);
-            }
-        }
+        df tn;
+        const bool enters = box_entry(m, Rx, Ry, Rz, dx, dy, dz, tn);
         if (enters) {
             const df R0x = df_fma(dx, tn, Rx);
             const df R0y = df_fma(dy, tn, Ry);
@@ -380,97 +489,9 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
         st->steps = steps;
     }
 
-    // ---- Sec. 3.3: optical elements in sequence ---------------------------
-    for (int s = 0; s < o.ns && status == PIVBOS_RAY_REACHED; ++s) {
-        const DevSurface& S = o.s[s];
-        if (!(dz.hi > 0.0f)) { status = PIVBOS_RAY_MISS; break; }
-        const df inv_dz = df_rcp(dz);
-        const df t0 = df_mul(df_sub(dfk(S.z), Rz), inv_dz);
-        if (S.type == PIVBOS_SURF_SPHERE && S.R_f != 0.0f) {
-            // vertex-relative quadratic t^2 + 2 b t + c = 0 from the point Q
-            // on the vertex plane; the vertex-side root has the smaller
-            // magnitude: t = c / (-b - sign(b) sqrt(b^2 - c))
-            const df Qx = df_fma(t0, dx, Rx), Qy = df_fma(t0, dy, Ry);
-            const df R = dfk(S.R);
-            const df b = df_sub(df_add(df_mul(dx, Qx), df_mul(dy, Qy)), df_mul(R, dz));
-            const df c = df_add(df_sqr(Qx), df_sqr(Qy));
-            const df disc = df_sub(df_sqr(b), c);
-            if (disc.hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
-            const df sq = df_sqrt(disc);
-            const df den = b.hi >= 0.0f ? df_sub(df_neg(b), sq) : df_add(df_neg(b), sq);
-            const df t1 = den.hi != 0.0f ? df_div(c, den) : dfv(0.0f);
-            if (df_add(t0, t1).hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
-            const df Hx = df_fma(t1, dx, Qx), Hy = df_fma(t1, dy, Qy), Hz = df_mul(t1, dz);
-            const df HzR = df_sub(Hz, R);
-            if (!(HzR.hi * S.R_f < 0.0f)) { status = PIVBOS_RAY_MISS; break; }
-            if (Hx.hi * Hx.hi + Hy.hi * Hy.hi > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
-            const df invR = dfk(S.invR);
-            df Nx = df_mul(Hx, invR), Ny = df_mul(Hy, invR), Nz = df_mul(HzR, invR);
-            if (Nx.hi * dx.hi + Ny.hi * dy.hi + Nz.hi * dz.hi > 0.0f) {
-                Nx = df_neg(Nx); Ny = df_neg(Ny); Nz = df_neg(Nz);
-            }
-            // Eq. 7, vector form
-            const df eta = dfk(S.eta);
-            const df ci = df_neg(df_add(df_add(df_mul(Nx, dx), df_mul(Ny, dy)), df_mul(Nz, dz)));
-            const df kk = df_sub(dfv(1.0f), df_mul(dfk(S.eta2), df_sub(dfv(1.0f), df_sqr(ci))));
-            if (kk.hi < 0.0f) { status = PIVBOS_RAY_TIR; break; }
-            const df a = df_sub(df_mul(eta, ci), df_sqrt(kk));
-            dx = df_fma(eta, dx, df_mul(a, Nx));
-            dy = df_fma(eta, dy, df_mul(a, Ny));
-            dz = df_fma(eta, dz, df_mul(a, Nz));
-            Rx = Hx;
-            Ry = Hy;
-            Rz = df_add(dfk(S.z), Hz);
-        } else {
-            if (t0.hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
-            Rx = df_fma(t0, dx, Rx);
-            Ry = df_fma(t0, dy, Ry);
-            Rz = dfk(S.z);
-            const float r2 = Rx.hi * Rx.hi + Ry.hi * Ry.hi;
-            if (S.type == PIVBOS_SURF_STOP) {
-                if (r2 > S.clear_r2) { status = PIVBOS_RAY_STOP; break; }
-            } else if (S.type == PIVBOS_SURF_IDEAL_THIN) {
-                if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
-                const df invf = dfk(S.inv_f);
-                const df ux = df_sub(df_mul(dx, inv_dz), df_mul(Rx, invf));
-                const df uy = df_sub(df_mul(dy, inv_dz), df_mul(Ry, invf));
-                const df inn = df_rsqrt(df_add_f(df_add(df_sqr(ux), df_sqr(uy)), 1.0f));
-                dx = df_mul(ux, inn);
-                dy = df_mul(uy, inn);
-                dz = inn;
-            } else {
-                if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
-                // flat surface, normal (0, 0, -1)
-                const df eta = dfk(S.eta);
-                const df kk = df_sub(dfv(1.0f), df_mul(dfk(S.eta2), df_sub(dfv(1.0f), df_sqr(dz))));
-                if (kk.hi < 0.0f) { status = PIVBOS_RAY_TIR; break; }
-                const df a = df_sub(df_mul(eta, dz), df_sqrt(kk));
-                dx = df_mul(eta, dx);
-                dy = df_mul(eta, dy);
-                dz = df_sub(df_mul(eta, dz), a);
-            }
-        }
-    }
-
-    // ---- Sec. 3.4: sensor plane -------------------------------------------
-    df px = dfv(0.0f), py = dfv(0.0f);
-    if (status == PIVBOS_RAY_REACHED) {
-        if (!(dz.hi > 0.0f)) {
-            status = PIVBOS_RAY_MISS;
-        } else {
-            const df t = df_mul(df_sub(dfk(o.sensor_z), Rz), df_rcp(dz));
-            if (t.hi < 0.0f) {
-                status = PIVBOS_RAY_MISS;
-            } else {
-                const df ipitch = dfk(o.inv_pitch);
-                px = df_add_f(df_mul(df_fma(t, dx, Rx), ipitch), o.half_w);
-                py = df_add_f(df_mul(df_fma(t, dy, Ry), ipitch), o.half_h);
-                const bool inx = !df_lt(px, dfv(0.0f)) && df_lt(px, dfv((float)o.W));
-                const bool iny = !df_lt(py, dfv(0.0f)) && df_lt(py, dfv((float)o.H));
-                if (!(inx && iny)) status = PIVBOS_RAY_OFF_SENSOR;
-            }
-        }
-    }
+    // ---- Sec. 3.3-3.4: optical elements and the sensor plane --------------
+    df px, py;
+    optics_to_sensor(o, Rx, Ry, Rz, dx, dy, dz, status, px, py);
     if (st) {
         st->sensor_xy[0] = df_to_double(px);
         st->sensor_xy[1] = df_to_double(py);
@@ -528,5 +549,62 @@ __device__ __forceinline__ void spot_window(const DevOptics& o, df px, df py, Sp
     axis_weights(py, o.win3, o.H, o.inv_sqrt2_sigma, sw.y0, sw.ny, sw.wy, sy);
     sw.scale = 4294967296.0f / (sx * sy);
 }
+
+constexpr int kTileW = 32;
+constexpr int kTileH = 32;
+
+__device__ __forceinline__ void add_q(unsigned long long* tile, int ax, int ay, int64_t* image, int W,
+                                      int gx, int gy, unsigned long long q)
+{
+    const int tx = gx - ax, ty = gy - ay;
+    if ((unsigned)tx < (unsigned)kTileW && (unsigned)ty < (unsigned)kTileH) {
+        atomicAdd(&tile[ty * kTileW + tx], q);
+    } else {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * W + gx]), q);
+    }
+}
+
+// Round-to-nearest-even of a non-negative float below 2^33 to an integer
+// with FP32/INT32 instructions only (the 64-bit float-to-integer conversion
+// runs on GB300's narrow FP64 pipe).  Below 2^23 adding 2^23 rounds to an
+// integer in the mantissa; from 2^23 up the float is already an integer.
+__device__ __forceinline__ long long round_pos_to_ll(float x)
+{
+    if (x < 8388608.0f) return (long long)(__float_as_uint(x + 8388608.0f) - 0x4B000000u);
+    const uint32_t b = __float_as_uint(x);
+    return (long long)((b & 0x7FFFFFu) | 0x800000u) << ((int)(b >> 23) - 150);
+}
+
+// Quantise the spot of one ray and add it (tile if inside, image otherwise).
+__device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
+                                            unsigned long long* tile, int ax, int ay, int64_t* image)
+{
+    SpotWindow sw;
+    spot_window(o, px, py, sw);
+    long long sum = 0, qmax = -1;
+    int imax = 0, jmax = 0;
+#pragma unroll 1
+    for (int j = 0; j < sw.ny; ++j) {
+        const float wyj = sw.wy[j] * sw.scale;
+#pragma unroll 1
+        for (int i = 0; i < sw.nx; ++i) {
+            const long long q = round_pos_to_ll(sw.wx[i] * wyj);
+            sum += q;
+            if (q > qmax) { qmax = q; imax = i; jmax = j; }
+        }
+    }
+    const long long rem = 4294967296LL - sum;
+#pragma unroll 1
+    for (int j = 0; j < sw.ny; ++j) {
+        const float wyj = sw.wy[j] * sw.scale;
+#pragma unroll 1
+        for (int i = 0; i < sw.nx; ++i) {
+            long long q = round_pos_to_ll(sw.wx[i] * wyj);
+            if (i == imax && j == jmax) q += rem;
+            if (q != 0) add_q(tile, ax, ay, image, o.W, sw.x0 + i, sw.y0 + j, (unsigned long long)q);
+        }
+    }
+}
+
 
 }  // namespace pivbos

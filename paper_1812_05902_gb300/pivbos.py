@@ -51,6 +51,32 @@ class pivbos_tuning(ctypes.Structure):
                 ("use_graph", ctypes.c_int32)]
 
 
+class pivbos_surrogate_cfg(ctypes.Structure):
+    _fields_ = [("n_train", ctypes.c_int64), ("n_val", ctypes.c_int64), ("epochs", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("err_budget_px", ctypes.c_float),
+                ("budget_margin", ctypes.c_float), ("min_bin_count", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("ref_plane_z", ctypes.c_double), ("born_segments", ctypes.c_int32),
+                ("use_network", ctypes.c_int32)]
+
+
+_REPORT_SCALARS = ("train_loss", "train_steps", "val_rms_px", "val_rms_px_born", "val_rms_px_straight",
+                   "val_rms_px_served", "val_served_frac", "val_served_frac_born", "val_served_frac_straight",
+                   "steps_saved_frac", "steps_saved_frac_born", "steps_saved_frac_straight",
+                   "val_status_flip_frac", "n_val_reached", "n_val_box", "seconds_table", "seconds_data",
+                   "seconds_train", "seconds_validate", "table_bytes")
+_REPORT_VECTORS = ("target_rms", "correction_rms", "sensor_px_per_unit")
+
+
+class pivbos_surrogate_report(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in _REPORT_SCALARS] + [(n, ctypes.c_double * 4) for n in _REPORT_VECTORS]
+
+    def as_dict(self):
+        d = {n: getattr(self, n) for n in _REPORT_SCALARS}
+        for n in _REPORT_VECTORS:
+            d[n] = list(getattr(self, n))
+        return d
+
+
 class PivbosError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("pivbos status %d: %s" % (status, msg))
@@ -89,6 +115,12 @@ def _load():
         "pivbos_batch_render": ([P, P], I),
         "pivbos_batch_destroy": ([P], None),
         "pivbos_autotune": ([P, I, D, I32, P, P, P], I),
+        "pivbos_surrogate_default_cfg": ([P], I),
+        "pivbos_surrogate_train": ([P, I, P, P, P, P], I),
+        "pivbos_surrogate_render": ([P, P, P, P], I),
+        "pivbos_surrogate_sensor": ([P, P, P, I64, P, P, P, P], I),
+        "pivbos_surrogate_report_get": ([P, P], I),
+        "pivbos_surrogate_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -103,7 +135,9 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_sync", "pivbos_last_error", "pivbos_timing_enable", "pivbos_timing_reset",
             "pivbos_timing_read", "pivbos_version", "pivbos_kernel_launches", "pivbos_render_noalloc",
             "pivbos_default_tuning", "pivbos_batch_create", "pivbos_batch_render", "pivbos_batch_destroy",
-            "pivbos_autotune", "pivbos_render_range", "pivbos_mlp_forward", "pivbos_mlp_loss_grad")
+            "pivbos_autotune", "pivbos_render_range", "pivbos_mlp_forward", "pivbos_mlp_loss_grad",
+            "pivbos_surrogate_default_cfg", "pivbos_surrogate_train", "pivbos_surrogate_render",
+            "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
@@ -263,6 +297,46 @@ def pivbos_mlp_loss_grad(params, x, t):
     _check(_lib.pivbos_mlp_loss_grad(params.ctypes.data, x.ctypes.data, t.ctypes.data, x.shape[0], g.ctypes.data,
                                      ctypes.byref(loss)))
     return loss.value, g
+
+
+def pivbos_surrogate_default_cfg():
+    c = pivbos_surrogate_cfg()
+    _check(_lib.pivbos_surrogate_default_cfg(ctypes.byref(c)))
+    return c
+
+
+def pivbos_surrogate_train(desc, integrator, cfg=None, stream=None):
+    """Train a surrogate on a frame; returns (handle, report)."""
+    out = ctypes.c_void_p()
+    rep = pivbos_surrogate_report()
+    _check(_lib.pivbos_surrogate_train(ctypes.byref(desc), integrator, ctypes.byref(cfg) if cfg else None,
+                                       ctypes.byref(out), ctypes.byref(rep), _stream(stream)))
+    return out, rep
+
+
+def pivbos_surrogate_render(sg, desc, count_fallback=False, stream=None):
+    """Render a frame with the surrogate; returns the number of plain-traced
+    rays when count_fallback (the call then synchronises), else None."""
+    n = ctypes.c_int64()
+    _check(_lib.pivbos_surrogate_render(sg, ctypes.byref(desc), ctypes.byref(n) if count_fallback else None,
+                                        _stream(stream)))
+    return n.value if count_fallback else None
+
+
+def pivbos_surrogate_sensor(sg, desc, ray_ids, sensor_xy, flags, status, stream=None):
+    rp, _ = _addr(ray_ids)
+    _check(_lib.pivbos_surrogate_sensor(sg, ctypes.byref(desc), rp, int(ray_ids.numel()), _addr(sensor_xy)[0],
+                                        _addr(flags)[0], _addr(status)[0], _stream(stream)))
+
+
+def pivbos_surrogate_report_get(sg):
+    rep = pivbos_surrogate_report()
+    _check(_lib.pivbos_surrogate_report_get(sg, ctypes.byref(rep)))
+    return rep
+
+
+def pivbos_surrogate_destroy(sg):
+    _lib.pivbos_surrogate_destroy(sg)
 
 
 def pivbos_trace_exit_states(m, o, sources, n_sources, rays_per_source, seed, frame, integrator, step,

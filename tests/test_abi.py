@@ -45,9 +45,11 @@ def test_struct_layouts_match_header(P):
 #include <stddef.h>
 #include "pivbos.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(pivbos_surface), offsetof(pivbos_surface, clear_radius),
-         sizeof(pivbos_ray_state), offsetof(pivbos_ray_state, status), sizeof(pivbos_frame_desc),
-         offsetof(pivbos_frame_desc, stats), sizeof(pivbos_tuning));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(pivbos_surface),
+         offsetof(pivbos_surface, clear_radius), sizeof(pivbos_ray_state), offsetof(pivbos_ray_state, status),
+         sizeof(pivbos_frame_desc), offsetof(pivbos_frame_desc, stats), sizeof(pivbos_tuning),
+         sizeof(pivbos_surrogate_cfg), offsetof(pivbos_surrogate_cfg, ref_plane_z),
+         sizeof(pivbos_surrogate_report), offsetof(pivbos_surrogate_report, target_rms));
   return 0;
 }
 """
@@ -64,6 +66,40 @@ int main(void) {
     assert vals[4] == ctypes.sizeof(P.pivbos_frame_desc)
     assert vals[5] == P.pivbos_frame_desc.stats.offset
     assert vals[6] == ctypes.sizeof(P.pivbos_tuning)
+    assert vals[7] == ctypes.sizeof(P.pivbos_surrogate_cfg)
+    assert vals[8] == P.pivbos_surrogate_cfg.ref_plane_z.offset
+    assert vals[9] == ctypes.sizeof(P.pivbos_surrogate_report)
+    assert vals[10] == P.pivbos_surrogate_report.target_rms.offset
+
+
+def test_surrogate_arguments_without_a_device(P):
+    L = P.lib()
+    assert L.pivbos_surrogate_default_cfg(None) == P.ERR_INVALID_ARG
+    cfg = P.pivbos_surrogate_default_cfg()
+    assert cfg.n_train == 20_000_000 and cfg.batch == 16384 and np.isnan(cfg.ref_plane_z)
+    assert cfg.born_segments == 8 and cfg.use_network == 1
+    assert abs(cfg.err_budget_px - 0.01) < 1e-9
+    out = ctypes.c_void_p()
+    rep = P.pivbos_surrogate_report()
+    assert L.pivbos_surrogate_train(None, 1, None, ctypes.byref(out), None, None) == P.ERR_INVALID_ARG
+    fake = ctypes.c_void_p(1)  # never dereferenced: the configuration check fails first
+    desc = P.pivbos_frame_desc(fake, fake, fake, 1, 1, 0, 0, 1e-4, fake, None)
+    no_medium = P.pivbos_frame_desc(None, fake, fake, 1, 1, 0, 0, 1e-4, fake, None)
+    assert L.pivbos_surrogate_train(ctypes.byref(no_medium), 1, None, ctypes.byref(out), None,
+                                    None) == P.ERR_INVALID_ARG
+    for field, value in (("batch", 100), ("batch", 1 << 17), ("n_train", 10), ("epochs", 0), ("lr", 0.0),
+                         ("err_budget_px", -1.0), ("budget_margin", 1.5), ("min_bin_count", 0),
+                         ("ref_plane_z", float("inf")), ("born_segments", -1), ("born_segments", 65),
+                         ("use_network", 2)):
+        bad = P.pivbos_surrogate_default_cfg()
+        setattr(bad, field, value)
+        assert L.pivbos_surrogate_train(ctypes.byref(desc), 1, ctypes.byref(bad), ctypes.byref(out),
+                                        ctypes.byref(rep), None) == P.ERR_INVALID_ARG, field
+        assert "configuration" in P.pivbos_last_error()
+    assert L.pivbos_surrogate_render(None, ctypes.byref(desc), None, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_surrogate_sensor(None, ctypes.byref(desc), None, 0, None, None, None, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_surrogate_report_get(None, ctypes.byref(rep)) == P.ERR_INVALID_ARG
+    L.pivbos_surrogate_destroy(None)
 
 
 def test_argument_errors_without_a_device(P):

@@ -1,0 +1,214 @@
+"""The surrogate ray map on a reduced Tomo-PIV workload (particles inside a
+100 x 100 x 30 mm turbulence box, 128^3 grid, 10^7 rays): training on the
+GPU, the confidence map, what the trained network gains (over the straight
+ray and over the first-order projection it corrects), the error of the
+surrogate path against the plain tracer and the oracle, and images rendered
+through the fallback list."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_05902_gb300 import scenes
+from gpu_helpers import gpu_handles, gpu_states, oracle_states
+
+pytestmark = pytest.mark.gpu
+
+BUDGET_PX = 0.01
+
+
+def _cfg(P, **kw):
+    cfg = P.pivbos_surrogate_default_cfg()
+    cfg.n_train = 4_000_000
+    cfg.n_val = 2_000_000
+    cfg.epochs = 10
+    cfg.err_budget_px = BUDGET_PX
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+@pytest.fixture(scope="module")
+def trained():
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    frame = scenes.c4(scale=0.01, grid=128)[0]
+    med, opt = gpu_handles(frame)
+    src = torch.tensor(frame.sources, dtype=torch.float64, device="cuda")
+    img = torch.zeros((frame.optics.height, frame.optics.width), dtype=torch.int64, device="cuda")
+    st = torch.zeros(P.RAY_NSTATUS, dtype=torch.int64, device="cuda")
+    desc = P.frame_desc(med.h, opt.h, src, len(frame.sources), frame.rays_per_source, frame.frame_index,
+                        frame.seed, frame.step, img, st)
+    sg, rep = P.pivbos_surrogate_train(desc, frame.integrator, _cfg(P))
+    yield frame, (med, opt), src, img, st, desc, sg, rep
+    P.pivbos_surrogate_destroy(sg)
+
+
+def test_training_report_and_gain_over_projection_and_straight_rays(trained):
+    frame, _, _, _, _, _, sg, rep = trained
+    r = rep.as_dict()
+    print(r)
+    assert np.isfinite(r["train_loss"]) and r["train_loss"] < 1.0
+    assert r["n_val_box"] > 0.99 * r["n_val_reached"] > 0             # the particles sit inside the box
+    assert r["val_status_flip_frac"] < 1e-3                           # only rays grazing a stop
+    # without a field model the budget cannot be met on every ray
+    assert r["val_rms_px_straight"] > BUDGET_PX
+    # the projection captures most of the displacement; the network's
+    # correction does not make it worse
+    assert r["val_rms_px_born"] < 0.5 * r["val_rms_px_straight"]
+    assert r["val_rms_px"] <= 1.05 * r["val_rms_px_born"]
+    assert r["val_served_frac"] >= r["val_served_frac_born"] - 0.01
+    assert r["val_served_frac"] > r["val_served_frac_straight"]
+    assert r["steps_saved_frac"] > r["steps_saved_frac_straight"]
+    assert r["val_rms_px_served"] <= BUDGET_PX * 0.8 * (1 + 1e-9)
+
+
+def test_network_alone_gains_over_straight_rays(trained):
+    """Without the projection the network is the only field model: at the same
+    budget it must serve more rays and save more steps than the straight ray."""
+    from paper_1812_05902_gb300 import pivbos as P
+    frame, _, _, _, _, desc, _, _ = trained
+    sg, rep = P.pivbos_surrogate_train(desc, frame.integrator, _cfg(P, born_segments=0))
+    try:
+        r = rep.as_dict()
+        print(r)
+        assert r["val_rms_px"] < 0.8 * r["val_rms_px_straight"]
+        assert r["val_served_frac"] > r["val_served_frac_straight"] + 0.05
+        assert r["steps_saved_frac"] > r["steps_saved_frac_straight"] + 0.05
+    finally:
+        P.pivbos_surrogate_destroy(sg)
+
+
+def _sample_ids(frame, n, seed):
+    total = len(frame.sources) * frame.rays_per_source
+    return np.random.default_rng(seed).choice(total, n, replace=False).astype(np.int64)
+
+
+def _surrogate_sensor(trained, ids):
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    frame, _, _, _, _, desc, sg, _ = trained
+    ids_t = torch.tensor(ids, device="cuda")
+    xy = torch.empty((len(ids), 2), dtype=torch.float64, device="cuda")
+    flags = torch.empty(len(ids), dtype=torch.int32, device="cuda")
+    status = torch.empty(len(ids), dtype=torch.int32, device="cuda")
+    P.pivbos_surrogate_sensor(sg, desc, ids_t, xy, flags, status)
+    return xy.cpu().numpy(), flags.cpu().numpy(), status.cpu().numpy()
+
+
+def test_surrogate_error_against_plain_tracer_and_oracle(trained):
+    frame, handles = trained[0], trained[1]
+    ids = _sample_ids(frame, 400_000, 11)     # rays the training never chose on purpose
+    xy, flags, status = _surrogate_sensor(trained, ids)
+    plain = gpu_states(frame, ids, handles)
+    both = (status == 0) & (plain["status"] == 0)
+    assert both.mean() > 0.99
+    d = xy[both] - plain["sensor_xy"][both]
+    rms = np.sqrt((d ** 2).sum(1).mean())
+    served = flags[both] == 0
+    print("rms vs plain %.5f px, served %.3f" % (rms, served.mean()))
+    assert rms <= BUDGET_PX
+    assert served.mean() > 0.05
+    # fallback rays are the plain tracer's own result
+    fb = flags[both] == 1
+    assert np.max(np.abs(d[fb])) < 1e-9
+    # against the oracle on a sample the CPU traces in seconds
+    sub = ids[:4000]
+    o = oracle_states(frame, sub)
+    ok = (status[:4000] == 0) & (o["status"] == 0)
+    do = xy[:4000][ok] - o["sensor_xy"][ok]
+    rms_o = np.sqrt((do ** 2).sum(1).mean())
+    print("rms vs oracle %.5f px over %d rays" % (rms_o, ok.sum()))
+    assert rms_o <= 1.5 * BUDGET_PX    # a 4,000-ray sample of a <= 0.8-budget estimate
+
+
+def test_surrogate_render_image(trained):
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    frame, handles, src, img, st, desc, sg, rep = trained
+    img.zero_()
+    st.zero_()
+    n_fb = P.pivbos_surrogate_render(sg, desc, count_fallback=True)
+    total = len(frame.sources) * frame.rays_per_source
+    stats = st.cpu().numpy()
+    assert stats.sum() == total
+    assert img.sum().item() == stats[0] * (1 << 32)        # every reaching ray deposits exactly 2^32
+    served = 1.0 - n_fb / total
+    assert abs(served - rep.val_served_frac) < 0.05         # the render serves what the map promised
+    # against the plain render: same rays reach the sensor (up to rays grazing a stop)
+    ref = torch.zeros_like(img)
+    ref_st = torch.zeros_like(st)
+    P.pivbos_render(handles[0].h, handles[1].h, src, len(frame.sources), frame.rays_per_source, frame.seed,
+                    frame.frame_index, frame.integrator, frame.step, ref, ref_st)
+    P.pivbos_sync()
+    rs = ref_st.cpu().numpy()
+    assert abs(int(stats[0]) - int(rs[0])) <= 1e-4 * total
+    a = img.double()
+    b = ref.double()
+    rel = (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+    print("image rel L2 vs plain %.4f, fallback %d of %d" % (rel, n_fb, total))
+    assert rel < 0.05
+
+
+def test_nothing_served_equals_plain_render():
+    """With a budget no bin meets, every ray goes through the fallback list:
+    the image must be the plain render's, bit for bit."""
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    frame = scenes.c4(scale=0.001, grid=64)[0]
+    med, opt = gpu_handles(frame)
+    src = torch.tensor(frame.sources, dtype=torch.float64, device="cuda")
+    img = torch.zeros((frame.optics.height, frame.optics.width), dtype=torch.int64, device="cuda")
+    st = torch.zeros(P.RAY_NSTATUS, dtype=torch.int64, device="cuda")
+    desc = P.frame_desc(med.h, opt.h, src, len(frame.sources), frame.rays_per_source, frame.frame_index,
+                        frame.seed, frame.step, img, st)
+    cfg = P.pivbos_surrogate_default_cfg()
+    cfg.n_train = 65536
+    cfg.n_val = 65536
+    cfg.epochs = 1
+    cfg.batch = 65536
+    cfg.err_budget_px = 1e-12
+    sg, rep = P.pivbos_surrogate_train(desc, frame.integrator, cfg)
+    try:
+        assert rep.val_served_frac == 0.0
+        n_fb = P.pivbos_surrogate_render(sg, desc, count_fallback=True)
+        total = len(frame.sources) * frame.rays_per_source
+        assert n_fb == total
+        ref = torch.zeros_like(img)
+        ref_st = torch.zeros_like(st)
+        P.pivbos_render(med.h, opt.h, src, len(frame.sources), frame.rays_per_source, frame.seed,
+                        frame.frame_index, frame.integrator, frame.step, ref, ref_st)
+        P.pivbos_sync()
+        assert torch.equal(img, ref)
+        assert torch.equal(st, ref_st)
+        # a second frame with other sources through the same surrogate
+        other = torch.flip(src, [0]).contiguous()
+        img.zero_()
+        st.zero_()
+        desc2 = P.frame_desc(med.h, opt.h, other, len(frame.sources), frame.rays_per_source, 5, frame.seed,
+                             frame.step, img, st)
+        P.pivbos_surrogate_render(sg, desc2)
+        ref.zero_()
+        ref_st.zero_()
+        P.pivbos_render(med.h, opt.h, other, len(frame.sources), frame.rays_per_source, frame.seed, 5,
+                        frame.integrator, frame.step, ref, ref_st)
+        P.pivbos_sync()
+        assert torch.equal(img, ref)
+    finally:
+        P.pivbos_surrogate_destroy(sg)
+
+
+def test_surrogate_rejects_other_medium_and_host_image(trained):
+    import ctypes
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    frame, handles, src, img, st, desc, sg, _ = trained
+    other_med, _ = gpu_handles(frame)
+    bad = P.frame_desc(other_med.h, handles[1].h, src, len(frame.sources), frame.rays_per_source, 0, frame.seed,
+                       frame.step, img, st)
+    with pytest.raises(P.PivbosError):
+        P.pivbos_surrogate_render(sg, bad)
+    host_img = torch.zeros_like(img, device="cpu")
+    bad2 = P.frame_desc(handles[0].h, handles[1].h, src, len(frame.sources), frame.rays_per_source, 0,
+                        frame.seed, frame.step, host_img, st)
+    with pytest.raises(P.PivbosError):
+        P.pivbos_surrogate_render(sg, bad2)
