@@ -12,6 +12,14 @@ finalisation.  Inputs are resident on the GPU when the timed region starts;
 L2 is flushed between timed steps.  The e2e figure runs the same step through
 the C ABI with host buffers (host density and sources in, host image out).
 
+--surrogate (workload C4, Tomo-PIV scale, 10^9 rays per image) trains the
+surrogate ray map on the image (outside the timed region), then times the
+plain render and the surrogate render (projection + network for served
+rays, plain tracer for the rest) of the same image, and measures the
+surrogate path's RMS sensor error against the plain tracer (10^6 sampled
+rays) and the oracle (a few thousand rays).  The default run adds the same
+figures, with fewer steps, under the "surrogate" key of its line.
+
 --impl reference times the CPU oracle (the paper's method written plainly in
 FP64 C) on a bounded sample of the same workload on the host cores.
 """
@@ -360,6 +368,12 @@ def run_gpu(args, rank, world):
     msteps = [mean_steps(P, fr, opt, meds[i], src_d[i]) for i, fr in enumerate(frames)]
     rf = roofline(frames, msteps, render_ms, render_n, clk.get("sm_max_mhz"),
                   recorded_traffic(args.workload) if args.scale == 1.0 else None)
+    sur = None
+    if world == 1 and args.workload == "c1" and not args.no_surrogate:
+        try:
+            sur = run_surrogate(args, rank, world, steps=max(2, min(args.steps, 3)), warmup=1, embedded=True)
+        except Exception as exc:   # reported, never hidden
+            sur = {"error": "%s: %s" % (type(exc).__name__, exc)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, threads, done, t = oracle_sample(frames, seconds_target=12.0)
@@ -378,6 +392,184 @@ def run_gpu(args, rank, world):
                        "parallelism": "replicas (weak)" if world > 1 else "single GPU"},
             "gpu_launches": int(launches), "clocks": clk, "roofline": rf, "e2e": e2e, "cpu_baseline": cpu,
             "impl": "pivbos",
+        }
+        if sur is not None:
+            out["surrogate"] = sur
+        print(json.dumps(out), flush=True)
+
+
+MLP_FLOP_PER_RAY = 2 * (16 * 128 + 3 * 128 * 128 + 128 * 4)   # one forward of the surrogate network
+
+
+def run_surrogate(args, rank, world, steps, warmup, embedded):
+    """C4 with the surrogate: returns the measurement as a dict."""
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    fr = _frames("c4", args.scale)[0]
+    fr.seed = fr.seed + 1000003 * rank
+    med = P.Medium(fr.medium, rho=torch.tensor(fr.medium.rho, device=dev))
+    opt = P.Optics(fr.optics)
+    W, H = fr.optics.width, fr.optics.height
+    src = torch.tensor(fr.sources, dtype=torch.float64, device=dev)
+    img = torch.zeros((H, W), dtype=torch.int64, device=dev)
+    fimg = torch.empty((H, W), dtype=torch.float32, device=dev)
+    stats = torch.zeros(P.RAY_NSTATUS, dtype=torch.int64, device=dev)
+    desc = P.frame_desc(med.h, opt.h, src, len(fr.sources), fr.rays_per_source, fr.frame_index, fr.seed, fr.step,
+                        img, stats)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    sg, rep = P.pivbos_surrogate_train(desc, fr.integrator, P.pivbos_surrogate_default_cfg())
+    train_wall = time.perf_counter() - t0
+
+    def plain_step():
+        img.zero_()
+        P.pivbos_render(med.h, opt.h, src, len(fr.sources), fr.rays_per_source, fr.seed, fr.frame_index,
+                        fr.integrator, fr.step, img, stats)
+        P.pivbos_image_finalize(img, H * W, fimg)
+
+    def surrogate_step():
+        img.zero_()
+        P.pivbos_surrogate_render(sg, desc)
+        P.pivbos_image_finalize(img, H * W, fimg)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        timed.launches0 = P.pivbos_kernel_launches()
+        ev = []
+        for _ in range(steps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    try:
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
+        time.sleep(0.3)
+        ms_plain = timed(plain_step)
+        P.pivbos_timing_reset()
+        P.pivbos_timing_enable(True)
+        ms_sur = timed(surrogate_step)
+        launches = P.pivbos_kernel_launches() - timed.launches0
+        P.pivbos_timing_enable(False)
+        clk = clocks.stop()
+        k_ms, k_n = P.pivbos_timing_read("surrogate_render")
+        f_ms, f_n = P.pivbos_timing_read("surrogate_fallback")
+        n_fb = P.pivbos_surrogate_render(sg, desc, count_fallback=True)
+        # error of the surrogate path: against the plain tracer on 10^6 rays,
+        # against the oracle on a few thousand of them
+        ids = np.random.default_rng(777).choice(fr.n_rays, 1_000_000, replace=False).astype(np.int64)
+        ids_t = torch.tensor(ids, device=dev)
+        xy = torch.empty((len(ids), 2), dtype=torch.float64, device=dev)
+        flags = torch.empty(len(ids), dtype=torch.int32, device=dev)
+        sst = torch.empty(len(ids), dtype=torch.int32, device=dev)
+        P.pivbos_surrogate_sensor(sg, desc, ids_t, xy, flags, sst)
+        out = torch.empty(len(ids) * P.RAY_STATE.itemsize, dtype=torch.uint8, device=dev)
+        P.pivbos_trace_exit_states(med.h, opt.h, src, len(fr.sources), fr.rays_per_source, fr.seed,
+                                   fr.frame_index, fr.integrator, fr.step, ids_t, len(ids), out)
+        P.pivbos_sync()
+        plain = np.frombuffer(out.cpu().numpy().tobytes(), dtype=P.RAY_STATE)
+        xy, flags, sst = xy.cpu().numpy(), flags.cpu().numpy(), sst.cpu().numpy()
+        ok = (sst == 0) & (plain["status"] == 0)
+        d = xy[ok] - plain["sensor_xy"][ok]
+        rms_plain = float(np.sqrt((d ** 2).sum(1).mean()))
+        n_or = 3000
+        om = oracle.Medium.from_scene(fr.medium)
+        oo = oracle.Optics.from_scene(fr.optics)
+        ost = oracle.trace_many(om, oo, fr.sources, fr.rays_per_source, ids[:n_or], fr.seed, fr.frame_index,
+                                fr.integrator, fr.step)
+        ok_o = (sst[:n_or] == 0) & (ost["status"] == 0)
+        do = xy[:n_or][ok_o] - ost["sensor_xy"][ok_o]
+        rms_oracle = float(np.sqrt((do ** 2).sum(1).mean()))
+        e2e = None
+        if not embedded and not args.no_e2e:
+            # sources from pinned host memory in, the float image out, every step
+            src_h = torch.tensor(fr.sources, dtype=torch.float64).pin_memory()
+            img_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+
+            def e2e_step():
+                src.copy_(src_h, non_blocking=True)
+                surrogate_step()
+                img_h.copy_(fimg, non_blocking=True)
+
+            e2e_step()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for _ in range(max(1, steps)):
+                e2e_step()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t1
+            e2e = {"value": fr.n_rays * max(1, steps) * world / dt, "unit": "rays/s",
+                   "h2d_bytes_per_step": int(src_h.numel() * 8), "d2h_bytes_per_step": int(H * W * 4)}
+    finally:
+        P.pivbos_surrogate_destroy(sg)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_plain, ms_sur], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_plain, ms_sur = float(t[0]), float(t[1])
+    rays = fr.n_rays
+    v_plain = rays * steps * world / (ms_plain * 1e-3)
+    v_sur = rays * steps * world / (ms_sur * 1e-3)
+    served = rays - n_fb
+    k_launch_s = k_ms / max(k_n, 1) * 1e-3
+    peaks, src_kind = _peaks()
+    peak_tf = peaks.get("bf16_tflops", 1900.0)
+    achieved = served * MLP_FLOP_PER_RAY / k_launch_s / 1e12 if k_n else None
+    res = {
+        "workload": WORKLOAD_NAMES["c4"], "rays_per_step": rays,
+        "plain_rays_per_s": v_plain, "surrogate_rays_per_s": v_sur, "speedup": v_sur / v_plain,
+        "ms_per_step_plain": ms_plain / steps, "ms_per_step_surrogate": ms_sur / steps,
+        "rms_err_px_vs_plain": rms_plain, "rms_err_px_vs_oracle": rms_oracle, "oracle_rays": int(ok_o.sum()),
+        "sampled_rays": int(ok.sum()), "budget_px": 0.01,
+        "served_frac": served / rays, "fallback_rays": int(n_fb),
+        "surrogate_kernel_ms": k_ms / max(k_n, 1), "fallback_kernel_ms": f_ms / max(f_n, 1),
+        "train_seconds": train_wall, "report": rep.as_dict(),
+        "roofline": ({"bound": "tensor", "achieved": round(achieved, 2), "peak": peak_tf, "unit": "TFLOP/s",
+                      "frac": round(achieved / peak_tf, 4), "traffic": None, "kernel": "surr_render_kernel",
+                      "op": "BF16 MLP forward, %d FLOP per served ray" % MLP_FLOP_PER_RAY,
+                      "peak_source": "%s bf16_tflops" % src_kind} if achieved else None),
+        "clocks": clk, "gpu_launches": int(launches), "steps": steps, "warmup": warmup, "e2e": e2e,
+    }
+    return res
+
+
+def run_surrogate_line(args, rank, world):
+    """--surrogate: the C4 line with the surrogate path as the value."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1812_05902_gb300 import build as libbuild
+    libbuild.build()
+    res = run_surrogate(args, rank, world, steps=args.steps, warmup=args.warmup, embedded=False)
+    fr = _frames("c4", args.scale)[0]
+    e2e = res.pop("e2e")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, threads, done, t = oracle_sample([fr], seconds_target=12.0)
+        cpu = {"value": v, "unit": "rays/s", "cores": threads, "kind": "oracle",
+               "sample": "first %d rays (source order) of the image, %.1f s of CPU work (plain method)" % (done, t)}
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": res["surrogate_rays_per_s"], "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step_surrogate"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 network / f32 projection and optics (double-float pairs)", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES["c4"] + " - surrogate path", "name": "c4-surrogate",
+                       "rays_per_step": res["rays_per_step"], "l2": "flushed between steps",
+                       "parallelism": "replicas (weak)" if world > 1 else "single GPU"},
+            "gpu_launches": res["gpu_launches"], "clocks": res["clocks"], "roofline": res["roofline"],
+            "e2e": e2e, "cpu_baseline": cpu, "impl": "pivbos", "surrogate": res,
         }
         print(json.dumps(out), flush=True)
 
@@ -449,6 +641,8 @@ def main():
     ap.add_argument("--workload", default="c1", choices=sorted(WORKLOAD_NAMES))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the C4 surrogate figures of the default line")
+    ap.add_argument("--surrogate", action="store_true", help="C4 with the surrogate path as the value")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (profiling captures only; the JSON line says so)")
     args = ap.parse_args()
@@ -461,7 +655,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        if args.workload == "c3":
+        if args.surrogate:
+            run_surrogate_line(args, rank, world)
+        elif args.workload == "c3":
             run_batch(args, rank, world)
         else:
             run_gpu(args, rank, world)

@@ -2,10 +2,12 @@
 // (dX and dW per layer) and Adam.  Warp-level BF16 mma.sync m16n8k16 with
 // ldmatrix operand loads from shared memory, FP32 accumulation.
 #include <math.h>
+#include <stdlib.h>
 
 #include "common.cuh"
 #include "mlp.cuh"
 #include "mlp_device.cuh"
+#include "mlp_tc.cuh"
 
 namespace pivbos {
 namespace {
@@ -249,6 +251,84 @@ __global__ void mlp_tobf16_kernel(const float* __restrict__ p, __nv_bfloat16* __
     if (local < mlp_in(l) * mlp_out(l)) wbf[mlp_wbf_offset(l) + local] = __float2bfloat16(p[i]);
 }
 
+// Inference forward on tcgen05: persistent CTAs of one warpgroup, one
+// 128-row tile at a time, five MMA / epilogue rounds per tile.
+__global__ void __launch_bounds__(128, 1)
+mlp_fwd_tc_kernel(const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ params,
+                  const __nv_bfloat16* __restrict__ X, int n, float* __restrict__ Y, int* __restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    mlptc::Net& S = *reinterpret_cast<mlptc::Net*>(smem);
+    unsigned char* A = smem + ((sizeof(mlptc::Net) + 127) / 128) * 128;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    mlptc::load_net(S, wbf, params);
+    if (warp == 0) umma::tmem_alloc(&tmem_base, 128);
+    if (tid == 0) umma::mbar_init(&bar, 1);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t row_tmem = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t a_saddr = umma::smem_addr(A);
+    uint32_t parity = 0;
+    bool failed = false;
+    const int tiles = (n + mlptc::kRows - 1) / mlptc::kRows;
+    for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+        const int row = t * mlptc::kRows + tid;
+        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+        if (row < n) {
+            lo = *reinterpret_cast<const uint4*>(X + (size_t)row * kMlpIn);
+            hi = *reinterpret_cast<const uint4*>(X + (size_t)row * kMlpIn + 8);
+        }
+        mlptc::store_input_row(A, tid, lo, hi);
+#pragma unroll 1
+        for (int l = 0; l < kMlpLayers; ++l) {
+            umma::fence_async_smem();
+            umma::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                umma::fence_after_sync();
+                mlptc::issue_layer(S, l, a_saddr, tmem);
+                umma::commit(&bar);
+            }
+            const bool ok = umma::mbar_wait(&bar, parity, mlptc::kWaitLimit);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            parity ^= 1u;
+            umma::fence_after_sync();
+            if (l < kMlpLayers - 1) {
+                mlptc::epilogue_hidden(row_tmem, S.bias[l], A, tid);
+            } else {
+                float y[kMlpOut];
+                mlptc::epilogue_out(row_tmem, S.bias4, y);
+                if (row < n) *reinterpret_cast<float4*>(Y + (size_t)row * 4) = make_float4(y[0], y[1], y[2], y[3]);
+            }
+        }
+    }
+    if (failed) {
+        // report, then give the MMAs in flight a second bounded wait before
+        // the accumulator memory is released
+        if (tid == 0) {
+            atomicExch(status, (int)PIVBOS_ERR_DEVICE_TIMEOUT);
+            umma::mbar_wait(&bar, parity, mlptc::kWaitLimit);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, 128);
+    }
+}
+
+// The operand tile is followed by 32 KB of slack: every address the tensor
+// core can form from an operand descriptor stays inside the allocation.
+size_t tc_smem() { return ((sizeof(mlptc::Net) + 127) / 128) * 128 + 2 * mlptc::kTileBytes; }
+
 int sm_count()
 {
     int dev = 0, sms = 0;
@@ -271,11 +351,15 @@ cudaError_t mlp_alloc(MlpDev& d, int splits)
     if (e == cudaSuccess) e = cudaMalloc(&d.grad, sizeof(float) * kMlpParams);
     if (e == cudaSuccess) e = cudaMalloc(&d.wbf, sizeof(__nv_bfloat16) * kMlpWeights);
     if (e == cudaSuccess) e = cudaMalloc(&d.partial, sizeof(float) * (size_t)splits * (kMlpHidden * kMlpHidden + kMlpHidden));
+    if (e == cudaSuccess) e = cudaMalloc(&d.status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(d.m, 0, sizeof(float) * kMlpParams);
     if (e == cudaSuccess) e = cudaMemset(d.v, 0, sizeof(float) * kMlpParams);
     static bool attrs = false;
     if (e == cudaSuccess && !attrs) {
         e = cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FwdSmem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mlp_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem());
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(mlp_dx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dx_smem());
         if (e == cudaSuccess)
@@ -287,6 +371,8 @@ cudaError_t mlp_alloc(MlpDev& d, int splits)
 
 void mlp_free(MlpDev& d)
 {
+    cudaFree(d.status);
+    d.status = nullptr;
     cudaFree(d.params);
     cudaFree(d.m);
     cudaFree(d.v);
@@ -322,10 +408,41 @@ cudaError_t mlp_sync_bf16(const MlpDev& d, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t mlp_forward_tc(const MlpDev& d, const __nv_bfloat16* X, int n, float* Y, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int tiles = (n + mlptc::kRows - 1) / mlptc::kRows;
+    const int grid = min(sm_count(), tiles);
+    timing_begin("mlp_forward_tc", s);
+    mlp_fwd_tc_kernel<<<grid, 128, tc_smem(), s>>>(d.wbf, d.params, X, n, Y, d.status);
+    timing_end("mlp_forward_tc", s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int mlp_status(const MlpDev& d)
+{
+    int v = 0;
+    if (!d.status || cudaMemcpy(&v, d.status, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+    if (v) cudaMemset(d.status, 0, sizeof(int));
+    return v;
+}
+
+static bool use_tc()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("PIVBOS_MLP_TC");
+        v = (e && atoi(e) == 0) ? 0 : 1;
+    }
+    return v == 1;
+}
+
 cudaError_t mlp_forward(const MlpDev& d, const __nv_bfloat16* X, int n, float* Y, MlpWork* work, const float* T,
                         cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
+    if (!work && use_tc()) return mlp_forward_tc(d, X, n, Y, s);
     const int tiles = (n + 15) / 16;
     const int grid = min(sm_count(), (tiles + 7) / 8);
     if (work && T) {

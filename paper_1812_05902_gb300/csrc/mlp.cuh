@@ -43,6 +43,7 @@ struct MlpDev {
     __nv_bfloat16* wbf = nullptr;  // BF16 weights [kMlpWeights]
     float* partial = nullptr;      // dW/db partial sums [splits][max layer params]
     int splits = 0;
+    int* status = nullptr;         // device word: nonzero after a tensor-core wait gave up
 };
 
 // Training workspace for batches of up to max_rows rows.
@@ -66,6 +67,13 @@ cudaError_t mlp_sync_bf16(const MlpDev& d, cudaStream_t s);
 // ([n][4] FP32), the loss sum and dL/dY go to work.loss / work.dz[0].
 cudaError_t mlp_forward(const MlpDev& d, const __nv_bfloat16* X, int n, float* Y, MlpWork* work, const float* T,
                         cudaStream_t s);
+// Inference forward on the fifth-generation tensor cores (tcgen05, TMEM
+// accumulators), 128-row tiles.  Same inputs and outputs as mlp_forward
+// without work; mlp_forward uses it for inference.
+cudaError_t mlp_forward_tc(const MlpDev& d, const __nv_bfloat16* X, int n, float* Y, cudaStream_t s);
+// PIVBOS_OK, or PIVBOS_ERR_DEVICE_TIMEOUT if a tensor-core wait gave up
+// since the last call (synchronises with the device; clears the word).
+int mlp_status(const MlpDev& d);
 // Backward after a training forward: gradients of the mean loss into d.grad.
 cudaError_t mlp_backward(MlpDev& d, const __nv_bfloat16* X, int n, MlpWork& work, cudaStream_t s);
 // One Adam step (t counts from 1) on all parameters, then the BF16 copies.

@@ -92,6 +92,7 @@ pivbos_status pivbos_mlp_forward(const float* params, const float* x, int32_t n,
     if (e == cudaSuccess) e = cudaMemcpy(y, dy, sizeof(float) * (size_t)n * pivbos::kMlpOut, cudaMemcpyDeviceToHost);
     cudaFree(dy);
     if (e != cudaSuccess) return scuda(e, "mlp_forward");
+    if (pivbos::mlp_status(B.d)) return serr(PIVBOS_ERR_DEVICE_TIMEOUT, "mlp_forward: a tensor-core wait gave up");
     return PIVBOS_OK;
 }
 
