@@ -337,7 +337,9 @@ typedef struct {
     int32_t min_bin_count;  /* bins with fewer held-out rays are never served */
     uint64_t seed;
     double ref_plane_z;     /* residual reference plane z (m); NaN = box centre */
-    int32_t born_segments;  /* 0..64; 0 = no projection (the network alone) */
+    int32_t born_segments;  /* 0..64; 0 = no projection (the network alone); -1 = the smallest of
+                               1, 2, 4, ..., 32 whose projection alone keeps the pilot rays' RMS
+                               sensor error within budget_margin * err_budget_px / 2 */
     int32_t use_network;    /* 1, or 0 = the projection alone */
 } pivbos_surrogate_cfg;
 
@@ -359,6 +361,8 @@ typedef struct {
     double n_val_reached, n_val_box;   /* held-out rays reaching the sensor; those entering the box */
     double seconds_table, seconds_data, seconds_train, seconds_validate;
     double table_bytes;
+    double born_segments;              /* segment count used */
+    double pilot_rms_px_born_k[6];     /* pilot RMS sensor error of the projection with 1, 2, 4, ..., 32 segments */
     double target_rms[4];              /* RMS residuals: x, y (m) on the reference plane, slope x, y */
     double correction_rms[4];          /* RMS of residual minus projection */
     double sensor_px_per_unit[4];      /* RMS sensor shift per unit of each residual (loss weights) */

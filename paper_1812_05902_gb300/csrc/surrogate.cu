@@ -121,7 +121,7 @@ pivbos_status pivbos_mlp_loss_grad(const float* params, const float* x, const fl
 // ===========================================================================
 // Surrogate ray map: data, training, confidence map, rendering
 // ===========================================================================
-#include "mlp_device.cuh"
+#include "mlp_tc.cuh"
 #include "trace.cuh"
 
 namespace pivbos {
@@ -378,17 +378,23 @@ __device__ __forceinline__ void truth_and_born(const TraceParams& P, const SurrP
 }
 
 // Pilot statistics on a few rays: mean squares of the truth residual, of
-// the projection residual and of their difference ([0..11]), and the sensor
+// the projection residual and of their difference ([0..11]), the sensor
 // shift per unit of each residual component by finite differences about
-// the straight ray ([12..15], [16] = rays counted).
+// the straight ray ([12..15], [16] = rays counted), and for each candidate
+// segment count kc = 1, 2, 4, ..., the squared sensor error of the
+// projection alone against the plain path ([17 + c], [17 + kPilotK] =
+// rays compared).
+constexpr int kPilotK = 6;   // candidates 1, 2, 4, 8, 16, 32
+
 template <int INTEG>
 __global__ void surr_pilot_kernel(const TraceParams P, const SurrParams S, uint64_t total, int64_t n, uint64_t seed,
                                   double dpos, double dslope, double* __restrict__ acc)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double v[17];
+    constexpr int NV = 18 + kPilotK;
+    double v[NV];
 #pragma unroll
-    for (int c = 0; c < 17; ++c) v[c] = 0.0;
+    for (int c = 0; c < NV; ++c) v[c] = 0.0;
     if (q < n) {
         Entry e;
         pivbos_ray_state st;
@@ -422,8 +428,31 @@ __global__ void surr_pilot_kernel(const TraceParams P, const SurrParams S, uint6
             }
             v[16] = 1.0;
         }
+        if (S.born_k != 0 && e.enters && st.status == PIVBOS_RAY_REACHED) {
+            bool all = true;
+            double err[kPilotK];
+#pragma unroll 1
+            for (int c = 0; c < kPilotK; ++c) {
+                SurrParams Sk = S;
+                Sk.born_k = 1 << c;
+                float r[4];
+                born_residual(Sk, e, r);
+                df Rx, Ry, Rz, ex, ey, ez;
+                surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
+                int status = PIVBOS_RAY_REACHED;
+                df a, b;
+                optics_to_sensor(P.o, Rx, Ry, Rz, ex, ey, ez, status, a, b);
+                all = all && status == PIVBOS_RAY_REACHED;
+                const double dx = df_to_double(a) - st.sensor_xy[0], dy = df_to_double(b) - st.sensor_xy[1];
+                err[c] = dx * dx + dy * dy;
+            }
+            if (all) {
+                for (int c = 0; c < kPilotK; ++c) v[17 + c] = err[c];
+                v[17 + kPilotK] = 1.0;
+            }
+        }
     }
-    for (int c = 0; c < 17; ++c) {
+    for (int c = 0; c < NV; ++c) {
         for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
         if ((threadIdx.x & 31) == 0 && v[c] != 0.0) atomicAdd(&acc[c], v[c]);
     }
@@ -516,8 +545,8 @@ __global__ void surr_eval_kernel(const TraceParams P, const SurrParams S, const 
 
 // Shared memory of the fused surrogate render kernel.
 struct SurrSmem {
-    mlpd::FwdSmem net;
-    __nv_bfloat16 x[256][kMlpIn];
+    mlptc::Net net;
+    alignas(128) unsigned char a[2][mlptc::kTileBytes];   // network operand of the two 128-ray tiles
     float y[256][4];
     float born[256][4];
     float2 ray[256][6];   // source and direction (double-float)
@@ -525,15 +554,20 @@ struct SurrSmem {
     unsigned long long tile[kTileW * kTileH];
     unsigned long long item;
     unsigned long long fb_base;
+    uint64_t bar[2];
+    uint32_t tmem_base;
+    int wg_failed[2];
     int fb_warp[8];
     int anchor_tid, ax, ay;
 };
 
 // S3: persistent kernel over chunks of rays of one render (sources in Morton
-// order).  Per 256 rays: entry features and projection residual -> network
-// correction (tensor cores) -> exit line -> lens and sensor -> shared tile.
-// Rays in bins the surrogate does not serve are appended, 256 at a time in
-// ray order, to the fallback list the plain tracer renders afterwards.
+// order).  Per 256 rays: entry features and projection residual (written
+// straight into the network operand) -> network correction on tcgen05 (two
+// 128-row tiles, accumulators in TMEM, warpgroup g runs tile g's epilogues)
+// -> exit line -> lens and sensor -> shared tile.  Rays in bins the
+// surrogate does not serve are appended, 256 at a time in ray order, to the
+// fallback list the plain tracer renders afterwards.
 template <int INTEG>
 __global__ void __launch_bounds__(256, 1)
 surr_render_kernel(const TraceParams P, const SurrParams S, const __nv_bfloat16* __restrict__ wbf,
@@ -541,10 +575,26 @@ surr_render_kernel(const TraceParams P, const SurrParams S, const __nv_bfloat16*
                    uint64_t total_rays, uint32_t rays_per_item, unsigned long long* __restrict__ counter,
                    uint32_t* __restrict__ fb_ids, unsigned long long* __restrict__ fb_count, uint32_t fb_capacity)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SurrSmem& sh = *reinterpret_cast<SurrSmem*>(smem_raw);
-    if (S.use_net) mlpd::load_network(sh.net, wbf, params);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = warp >> 2, row = tid & 127;   // tile and row of this thread's ray
+    if (S.use_net) mlptc::load_net(sh.net, wbf, params);
+    if (warp == 0) umma::tmem_alloc(&sh.tmem_base, 256);
+    if (tid == 0) {
+        umma::mbar_init(&sh.bar[0], 1);
+        umma::mbar_init(&sh.bar[1], 1);
+        sh.wg_failed[0] = sh.wg_failed[1] = 0;
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = sh.tmem_base;
+    const uint32_t d_tmem = tmem + (uint32_t)(grp * 128);   // this warpgroup's accumulator columns
+    const uint32_t row_tmem = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t a_saddr = umma::smem_addr(sh.a[grp]);
+    uint32_t parity = 0;   // of this warpgroup's mbarrier
+    bool failed = false;
     const uint64_t items = (total_rays + rays_per_item - 1) / rays_per_item;
     const uint32_t rps = P.rays_per_source;
     unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
@@ -559,7 +609,7 @@ surr_render_kernel(const TraceParams P, const SurrParams S, const __nv_bfloat16*
         }
         __syncthreads();
         const uint64_t item = sh.item;
-        if (item >= items) break;
+        if (item >= items || failed) break;
         const uint64_t first = item * rays_per_item;
         const uint64_t last = min(first + rays_per_item, total_rays);
         int ax = -(1 << 28), ay = -(1 << 28);
@@ -612,31 +662,40 @@ surr_render_kernel(const TraceParams P, const SurrParams S, const __nv_bfloat16*
             sh.mode[tid] = mode;
 #pragma unroll
             for (int c = 0; c < 4; ++c) sh.born[tid][c] = born[c];
-            encode_features(S, e.f, born, &sh.x[tid][0]);
-            __syncthreads();
-            // ---- network: warp w runs rows [32w, 32w + 32) as two 16-row tiles
-            if (S.use_net) {
-#pragma unroll 1
-                for (int half = 0; half < 2; ++half) {
-                    const int row0 = warp * 32 + half * 16;
-                    if (!__any_sync(0xffffffffu, sh.mode[row0 + (lane & 15)] == 0)) continue;
-                    {
-                        const int r = lane >> 1, h = lane & 1;
-                        *reinterpret_cast<uint4*>(sh.net.act[warp][0] + r * mlpd::kPadH + h * 8) =
-                            *reinterpret_cast<const uint4*>(&sh.x[row0 + r][h * 8]);
-                    }
-                    __syncwarp();
-                    float y4[4];
-                    mlpd::forward_tile(sh.net, warp, y4, nullptr, 0, 0, 0);
-                    if (t4 * 2 < kMlpOut) {
-                        sh.y[row0 + g][t4 * 2] = y4[0];
-                        sh.y[row0 + g][t4 * 2 + 1] = y4[1];
-                        sh.y[row0 + g + 8][t4 * 2] = y4[2];
-                        sh.y[row0 + g + 8][t4 * 2 + 1] = y4[3];
-                    }
-                    __syncwarp();
+            // ---- network on tcgen05 (skipped when no ray of the 256 is served).
+            // Warpgroup g runs tile g on its own: its leader issues each
+            // layer, all 128 threads wait on the tile's mbarrier and run the
+            // epilogue, so one tile's MMAs overlap the other's epilogue.
+            if (__syncthreads_or(S.use_net && mode == 0)) {
+                {
+                    __align__(16) __nv_bfloat16 x[kMlpIn];
+                    encode_features(S, e.f, born, x);
+                    mlptc::store_input_row(sh.a[grp], row, *reinterpret_cast<const uint4*>(&x[0]),
+                                           *reinterpret_cast<const uint4*>(&x[8]));
                 }
-                __syncthreads();
+#pragma unroll 1
+                for (int l = 0; l < kMlpLayers; ++l) {
+                    umma::fence_async_smem();
+                    umma::fence_before_sync();
+                    umma::named_sync(1 + grp, 128);
+                    if (row == 0) {
+                        umma::fence_after_sync();
+                        mlptc::issue_layer(sh.net, l, a_saddr, d_tmem);
+                        umma::commit(&sh.bar[grp]);
+                    }
+                    const bool ok = umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit);
+                    if (!ok) sh.wg_failed[grp] = 1;
+                    umma::named_sync(1 + grp, 128);
+                    if (sh.wg_failed[grp]) break;
+                    parity ^= 1u;
+                    umma::fence_after_sync();
+                    if (l < kMlpLayers - 1) mlptc::epilogue_hidden2(row_tmem, sh.net.bias[l], sh.a[grp], row);
+                    else mlptc::epilogue_out(row_tmem, sh.net.bias4, sh.y[tid]);
+                }
+                if (__syncthreads_or(sh.wg_failed[grp] != 0)) {
+                    failed = true;
+                    break;
+                }
             }
             // ---- lens, sensor and deposit
             RayOut r;
@@ -686,10 +745,22 @@ surr_render_kernel(const TraceParams P, const SurrParams S, const __nv_bfloat16*
             }
         }
     }
+    if (failed && row == 0) {
+        // report, then give the MMAs in flight a second bounded wait before
+        // the accumulator memory is released
+        atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_DEVICE_TIMEOUT);
+        if (sh.wg_failed[grp]) umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit);
+    }
     if (stats) {
 #pragma unroll
         for (int q = 0; q < PIVBOS_RAY_NSTATUS; ++q)
             if (cnt[q]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[q]), (unsigned long long)cnt[q]);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, 256);
     }
 }
 
@@ -854,7 +925,7 @@ pivbos_status pivbos_surrogate_default_cfg(pivbos_surrogate_cfg* c)
     c->min_bin_count = 8;
     c->seed = 7;
     c->ref_plane_z = NAN;
-    c->born_segments = 8;
+    c->born_segments = -1;
     c->use_network = 1;
     return PIVBOS_OK;
 }
@@ -872,8 +943,8 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
     if (c.n_train < 256 || c.n_val < 256 || c.n_train > (1ll << 31) || c.n_val > (1ll << 31) || c.epochs < 1 ||
         c.batch < 256 || c.batch > 65536 || !(c.lr > 0.f) || !(c.err_budget_px > 0.f) ||
         !(c.budget_margin > 0.f && c.budget_margin <= 1.f) || c.min_bin_count < 1 ||
-        (!std::isnan(c.ref_plane_z) && !std::isfinite(c.ref_plane_z)) || c.born_segments < 0 ||
-        c.born_segments > 64 || (c.use_network != 0 && c.use_network != 1))
+        (!std::isnan(c.ref_plane_z) && !std::isfinite(c.ref_plane_z)) ||
+        c.born_segments < -1 || c.born_segments > 64 || (c.use_network != 0 && c.use_network != 1))
         return serr(PIVBOS_ERR_INVALID_ARG, "surrogate configuration out of range");
     pivbos::TraceParams P;
     int dev = 0;
@@ -920,7 +991,9 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
     S.nbz = 16;
     S.nbu = 4;
     S.use_net = c.use_network;
-    S.born_k = c.born_segments;
+    // -1: chosen below from the pilot rays; until then the table is built
+    // and the pilot runs with a nonzero count
+    S.born_k = c.born_segments < 0 ? 8 : c.born_segments;
     const int nbins = pivbos::kSurrBins;
     cudaError_t e = pivbos::mlp_alloc(sg->net, 128);
     if (e == cudaSuccess) e = cudaMalloc(&sg->bin_ok, sizeof(uint32_t) * (nbins / 32));
@@ -986,7 +1059,7 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
     if (e == cudaSuccess) e = idv.alloc((size_t)c.n_val);
     if (e == cudaSuccess) e = refpx.alloc((size_t)c.n_val * 2);
     if (e == cudaSuccess) e = refst.alloc((size_t)c.n_val);
-    if (e == cudaSuccess) e = pilot.alloc(17);
+    if (e == cudaSuccess) e = pilot.alloc(18 + pivbos::kPilotK);
     if (e == cudaSuccess) e = accd.alloc((size_t)4 * nbins + 5);
     if (e == cudaSuccess) e = bincnt.alloc(nbins);
     if (e != cudaSuccess) {
@@ -994,7 +1067,8 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
         return scuda(e, "surrogate data allocation");
     }
     const int64_t n_pilot = std::min<int64_t>(c.n_val, 65536);
-    e = cudaMemsetAsync(pilot.p, 0, sizeof(double) * 17, s);
+    const int npv = 18 + pivbos::kPilotK;
+    e = cudaMemsetAsync(pilot.p, 0, sizeof(double) * npv, s);
     if (e == cudaSuccess) {
         const unsigned blocks = (unsigned)((n_pilot + 127) / 128);
         if (integrator == PIVBOS_RK4)
@@ -1003,12 +1077,54 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
             pivbos::surr_pilot_kernel<PIVBOS_EULER><<<blocks, 128, 0, s>>>(P, S, total, n_pilot, c.seed, 1e-6, 1e-6, pilot.p);
         pivbos::count_launches(1);
     }
-    double pm[17];
+    double pm[18 + pivbos::kPilotK];
     if (e == cudaSuccess) e = cudaMemcpyAsync(pm, pilot.p, sizeof pm, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         pivbos_surrogate_destroy(sg);
         return scuda(e, "surrogate pilot");
+    }
+    // Segment count: the smallest candidate whose projection alone keeps
+    // the pilot's RMS sensor error within half the budget the held-out
+    // estimate may use (the network corrects part of the rest), else the
+    // largest candidate.
+    if (c.born_segments < 0) {
+        const double nk = pm[17 + pivbos::kPilotK];
+        const double goal = 0.5 * c.budget_margin * c.err_budget_px;
+        int kc = pivbos::kPilotK - 1;
+        for (int q = 0; q < pivbos::kPilotK; ++q)
+            if (nk > 0 && sqrt(pm[17 + q] / nk) <= goal) {
+                kc = q;
+                break;
+            }
+        S.born_k = 1 << kc;
+        if (kc != 3) {   // the pilot's moments used 8 segments: redo them with the chosen count
+            e = cudaMemsetAsync(pilot.p, 0, sizeof(double) * npv, s);
+            if (e == cudaSuccess) {
+                const unsigned blocks = (unsigned)((n_pilot + 127) / 128);
+                if (integrator == PIVBOS_RK4)
+                    pivbos::surr_pilot_kernel<PIVBOS_RK4><<<blocks, 128, 0, s>>>(P, S, total, n_pilot, c.seed, 1e-6,
+                                                                                1e-6, pilot.p);
+                else
+                    pivbos::surr_pilot_kernel<PIVBOS_EULER><<<blocks, 128, 0, s>>>(P, S, total, n_pilot, c.seed,
+                                                                                  1e-6, 1e-6, pilot.p);
+                pivbos::count_launches(1);
+            }
+            double keep[pivbos::kPilotK + 1];
+            for (int q = 0; q <= pivbos::kPilotK; ++q) keep[q] = pm[17 + q];
+            if (e == cudaSuccess) e = cudaMemcpyAsync(pm, pilot.p, sizeof pm, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            for (int q = 0; q <= pivbos::kPilotK; ++q) pm[17 + q] = keep[q];
+            if (e != cudaSuccess) {
+                pivbos_surrogate_destroy(sg);
+                return scuda(e, "surrogate pilot");
+            }
+        }
+    }
+    R.born_segments = S.born_k;
+    {
+        const double nk = pm[17 + pivbos::kPilotK];
+        for (int q = 0; q < pivbos::kPilotK; ++q) R.pilot_rms_px_born_k[q] = nk > 0 ? sqrt(pm[17 + q] / nk) : 0.0;
     }
     // Scales.  Network inputs: the projection residual per component at unit
     // RMS.  Network outputs: the correction in units of its RMS effect on

@@ -63,16 +63,18 @@ _REPORT_SCALARS = ("train_loss", "train_steps", "val_rms_px", "val_rms_px_born",
                    "val_rms_px_served", "val_served_frac", "val_served_frac_born", "val_served_frac_straight",
                    "steps_saved_frac", "steps_saved_frac_born", "steps_saved_frac_straight",
                    "val_status_flip_frac", "n_val_reached", "n_val_box", "seconds_table", "seconds_data",
-                   "seconds_train", "seconds_validate", "table_bytes")
-_REPORT_VECTORS = ("target_rms", "correction_rms", "sensor_px_per_unit")
+                   "seconds_train", "seconds_validate", "table_bytes", "born_segments")
+_REPORT_VECTORS = (("pilot_rms_px_born_k", 6), ("target_rms", 4), ("correction_rms", 4),
+                   ("sensor_px_per_unit", 4))
 
 
 class pivbos_surrogate_report(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in _REPORT_SCALARS] + [(n, ctypes.c_double * 4) for n in _REPORT_VECTORS]
+    _fields_ = ([(n, ctypes.c_double) for n in _REPORT_SCALARS] +
+                [(n, ctypes.c_double * k) for n, k in _REPORT_VECTORS])
 
     def as_dict(self):
         d = {n: getattr(self, n) for n in _REPORT_SCALARS}
-        for n in _REPORT_VECTORS:
+        for n, _ in _REPORT_VECTORS:
             d[n] = list(getattr(self, n))
         return d
 
