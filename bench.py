@@ -154,25 +154,31 @@ ISSUE_LANES_PER_SM = 128
 N_SM = 152
 
 
-def kernel_source_hash():
-    import glob
+# the sources each profiled kernel is compiled from
+KERNEL_SOURCES = {
+    "render": ("render.cu", "trace.cuh", "df64.cuh", "common.cuh"),
+    "surrogate": ("surrogate.cu", "mlp_tc.cuh", "umma.cuh", "mlp.cuh", "trace.cuh", "df64.cuh", "common.cuh"),
+}
+
+
+def kernel_source_hash(kind="render"):
     import hashlib
     h = hashlib.sha256()
-    for path in sorted(glob.glob(os.path.join(ROOT, "paper_1812_05902_gb300", "csrc", "*"))):
-        with open(path, "rb") as f:
+    for name in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_1812_05902_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per render launch from the committed ncu record, or None
-    when the record is for another workload or the kernels changed since."""
+def recorded_traffic(record, kind="render"):
+    """DRAM bytes per launch from a committed ncu record (profiles/<record>.json),
+    or None when the kernel's sources changed since it was taken."""
     try:
-        with open(os.path.join(ROOT, "profiles", "render_%s_traffic.json" % workload)) as f:
+        with open(os.path.join(ROOT, "profiles", record + ".json")) as f:
             rec = json.load(f)
     except Exception:
         return None
-    if rec.get("source_hash") != kernel_source_hash():
+    if rec.get("source_hash") != kernel_source_hash(kind):
         return None
     return int(rec["dram_bytes_read"] + rec["dram_bytes_write"])
 
@@ -367,7 +373,7 @@ def run_gpu(args, rank, world):
 
     msteps = [mean_steps(P, fr, opt, meds[i], src_d[i]) for i, fr in enumerate(frames)]
     rf = roofline(frames, msteps, render_ms, render_n, clk.get("sm_max_mhz"),
-                  recorded_traffic(args.workload) if args.scale == 1.0 else None)
+                  recorded_traffic("render_%s_traffic" % args.workload) if args.scale == 1.0 else None)
     sur = None
     if world == 1 and args.workload == "c1" and not args.no_surrogate:
         try:
@@ -401,13 +407,14 @@ def run_gpu(args, rank, world):
 MLP_FLOP_PER_RAY = 2 * (16 * 128 + 3 * 128 * 128 + 128 * 4)   # one forward of the surrogate network
 
 
-def run_surrogate(args, rank, world, steps, warmup, embedded):
-    """C4 with the surrogate: returns the measurement as a dict."""
+def run_surrogate(args, rank, world, steps, warmup, embedded, workload="c4"):
+    """A workload with the surrogate (C4, or the C2 BOS field): returns the
+    measurement as a dict."""
     import torch
     from paper_1812_05902_gb300 import pivbos as P
     import oracle
     dev = torch.device("cuda", torch.cuda.current_device())
-    fr = _frames("c4", args.scale)[0]
+    fr = _frames(workload, args.scale)[0]
     fr.seed = fr.seed + 1000003 * rank
     med = P.Medium(fr.medium, rho=torch.tensor(fr.medium.rho, device=dev))
     opt = P.Optics(fr.optics)
@@ -527,7 +534,7 @@ def run_surrogate(args, rank, world, steps, warmup, embedded):
     peak_tf = peaks.get("bf16_tflops", 1900.0)
     achieved = served * MLP_FLOP_PER_RAY / k_launch_s / 1e12 if k_n else None
     res = {
-        "workload": WORKLOAD_NAMES["c4"], "rays_per_step": rays,
+        "workload": WORKLOAD_NAMES[workload], "name": workload, "rays_per_step": rays,
         "plain_rays_per_s": v_plain, "surrogate_rays_per_s": v_sur, "speedup": v_sur / v_plain,
         "ms_per_step_plain": ms_plain / steps, "ms_per_step_surrogate": ms_sur / steps,
         "rms_err_px_vs_plain": rms_plain, "rms_err_px_vs_oracle": rms_oracle, "oracle_rays": int(ok_o.sum()),
@@ -536,7 +543,9 @@ def run_surrogate(args, rank, world, steps, warmup, embedded):
         "surrogate_kernel_ms": k_ms / max(k_n, 1), "fallback_kernel_ms": f_ms / max(f_n, 1),
         "train_seconds": train_wall, "report": rep.as_dict(),
         "roofline": ({"bound": "tensor", "achieved": round(achieved, 2), "peak": peak_tf, "unit": "TFLOP/s",
-                      "frac": round(achieved / peak_tf, 4), "traffic": None, "kernel": "surr_render_kernel",
+                      "frac": round(achieved / peak_tf, 4),
+                      "traffic": (recorded_traffic("surrogate_%s_traffic" % workload, "surrogate")
+                                  if args.scale == 1.0 else None), "kernel": "surr_render_kernel",
                       "op": "BF16 MLP forward, %d FLOP per served ray" % MLP_FLOP_PER_RAY,
                       "peak_source": "%s bf16_tflops" % src_kind} if achieved else None),
         "clocks": clk, "gpu_launches": int(launches), "steps": steps, "warmup": warmup, "e2e": e2e,
@@ -551,8 +560,9 @@ def run_surrogate_line(args, rank, world):
     torch.cuda.set_device(local)
     from paper_1812_05902_gb300 import build as libbuild
     libbuild.build()
-    res = run_surrogate(args, rank, world, steps=args.steps, warmup=args.warmup, embedded=False)
-    fr = _frames("c4", args.scale)[0]
+    wl = args.workload if args.workload in ("c2", "c4") else "c4"
+    res = run_surrogate(args, rank, world, steps=args.steps, warmup=args.warmup, embedded=False, workload=wl)
+    fr = _frames(wl, args.scale)[0]
     e2e = res.pop("e2e")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -565,7 +575,7 @@ def run_surrogate_line(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step_surrogate"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 network / f32 projection and optics (double-float pairs)", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAMES["c4"] + " - surrogate path", "name": "c4-surrogate",
+            "config": {"workload": WORKLOAD_NAMES[wl] + " - surrogate path", "name": wl + "-surrogate",
                        "rays_per_step": res["rays_per_step"], "l2": "flushed between steps",
                        "parallelism": "replicas (weak)" if world > 1 else "single GPU"},
             "gpu_launches": res["gpu_launches"], "clocks": res["clocks"], "roofline": res["roofline"],
@@ -642,7 +652,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the C4 surrogate figures of the default line")
-    ap.add_argument("--surrogate", action="store_true", help="C4 with the surrogate path as the value")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="the surrogate path as the value (workload c4, the default here, or c2)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (profiling captures only; the JSON line says so)")
     args = ap.parse_args()
