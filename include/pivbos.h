@@ -341,6 +341,10 @@ typedef struct {
                                1, 2, 4, ..., 32 whose projection alone keeps the pilot rays' RMS
                                sensor error within budget_margin * err_budget_px / 2 */
     int32_t use_network;    /* 1, or 0 = the projection alone */
+    int32_t table_columns_per_cell;  /* projection-table columns per grid spacing across the box, 1..8, at
+                                        most 2048 per axis; 0 = the densest of 4, 2, 1 whose table fits
+                                        in 16 GiB */
+    int32_t table_levels_per_cell;   /* table levels per grid spacing in depth, 1..4 (1); at most 1024 */
 } pivbos_surrogate_cfg;
 
 typedef struct {
@@ -362,6 +366,7 @@ typedef struct {
     double seconds_table, seconds_data, seconds_train, seconds_validate;
     double table_bytes;
     double born_segments;              /* segment count used */
+    double table_columns_per_cell;     /* table columns per grid spacing used */
     double pilot_rms_px_born_k[6];     /* pilot RMS sensor error of the projection with 1, 2, 4, ..., 32 segments */
     double target_rms[4];              /* RMS residuals: x, y (m) on the reference plane, slope x, y */
     double correction_rms[4];          /* RMS of residual minus projection */

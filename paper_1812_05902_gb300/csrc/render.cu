@@ -7,45 +7,6 @@ namespace pivbos {
 
 constexpr int kRenderThreads = 256;
 constexpr int kRenderMinBlocks = 3;   // CTAs per SM the register budget must allow
-constexpr int kMaxOrderRays = 2048;   // a CTA reorders at most this many rays
-
-__device__ __forceinline__ uint32_t spread10(uint32_t v)
-{
-    v &= 0x3ffu;
-    v = (v | (v << 16)) & 0x030000ffu;
-    v = (v | (v << 8)) & 0x0300f00fu;
-    v = (v | (v << 4)) & 0x030c30c3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
-}
-
-// Ordering key of a ray: Morton code of the grid cell where its straight
-// line from the source to its lens point crosses the mid-plane of the box
-// (FP32 throughout -- only the order of tracing depends on it), above the
-// ray's index within the CTA.
-__device__ __forceinline__ uint32_t ray_order_key(const TraceParams& P, uint32_t flat, uint32_t local)
-{
-    const uint32_t rps = P.rays_per_source;
-    const uint32_t slot = flat / rps, k = flat - slot * rps;
-    const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
-    const float2* sp = P.src_df + 3 * (size_t)slot;
-    const float sx = __ldg(sp).x, sy = __ldg(sp + 1).x, sz = __ldg(sp + 2).x;
-    uint64_t w0, w1;
-    philox_lens_words(k, sid, P.frame, 0ull, P.seed, 0ull, w0, w1);
-    const float u1 = ((float)(uint32_t)(w0 >> 40) + 0.5f) * 0x1p-24f;
-    const float u2 = ((float)(uint32_t)(w1 >> 40) + 0.5f) * 0x1p-24f;
-    float sn, cs;
-    sincospif(2.0f * u2, &sn, &cs);
-    const float r = P.o.aim_r.hi * sqrtf(u1);
-    const float dz = P.o.aim_z.hi - sz;
-    const float t = dz != 0.0f ? fminf(fmaxf((P.m.z_key - sz) / dz, 0.0f), 1.0f) : 0.0f;
-    const float x = fmaf(r * cs - sx, t, sx), y = fmaf(r * sn - sy, t, sy);
-    const float gx = fminf(fmaxf((x - P.m.origin[0].hi) * P.m.inv_h[0], 0.0f), 1023.0f);
-    const float gy = fminf(fmaxf((y - P.m.origin[1].hi) * P.m.inv_h[1], 0.0f), 1023.0f);
-    const uint32_t code = spread10((uint32_t)gx) | (spread10((uint32_t)gy) << 1);
-    return (code << 11) | local;
-}
-
 // Work: the flattened (Morton slot, ray) index space (sources in Morton order,
 // read as double-float from P.src_df) is cut into chunks of
 // rays_per_cta consecutive rays; a CTA takes one chunk, so its rays come
@@ -84,29 +45,7 @@ __device__ __forceinline__ void render_chunk(const TraceParams& P, ChunkShared& 
     // instead of the whole cone of a source.
     const uint32_t n_here = (uint32_t)(last - first);
     const bool reorder = P.reorder && n_here <= (uint32_t)kMaxOrderRays;
-    if (reorder) {
-        uint32_t n_pow2 = 1;
-        while (n_pow2 < n_here) n_pow2 <<= 1;
-        for (uint32_t q = threadIdx.x; q < n_pow2; q += blockDim.x)
-            sh.order[q] = q < n_here ? ray_order_key(P, P.ray_list ? __ldg(P.ray_list + first + q) : (uint32_t)first + q, q)
-                                     : 0xffffffffu;
-        __syncthreads();
-        for (uint32_t kk = 2; kk <= n_pow2; kk <<= 1) {
-            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-                for (uint32_t t = threadIdx.x; t < n_pow2 / 2; t += blockDim.x) {
-                    const uint32_t i = 2 * t - (t & (j - 1));
-                    const uint32_t l = i + j;
-                    const bool up = (i & kk) == 0;
-                    const uint32_t a = sh.order[i], b = sh.order[l];
-                    if ((a > b) == up) {
-                        sh.order[i] = b;
-                        sh.order[l] = a;
-                    }
-                }
-                __syncthreads();
-            }
-        }
-    }
+    if (reorder) order_chunk(P, sh.order, first, n_here);
     // one uniform loop over the chunk's rays; after the first round every
     // thread's first hit is known and the lowest-thread hit anchors the tile
     const int rounds = (int)((n_here + blockDim.x - 1) / blockDim.x);

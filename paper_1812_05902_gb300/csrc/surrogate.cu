@@ -215,33 +215,41 @@ __device__ __forceinline__ void table_lookup(const SurrParams& S, float xi, floa
     }
 }
 
-// First-order (Born) exit-line residual of the straight ray from the entry
-// point with slopes (ux, uy): dT/ds = grad n (the ray equation with
-// dt = ds / n) integrated along the unperturbed line, the line cut into
-// born_k segments, each integral taken from the table column through the
-// segment's midpoint.  r = {dx, dy at z_ref, dux, duy}.
+// Projection (Born-type) exit-line residual of a ray from its entry point
+// with straight slopes (ux, uy): dT/ds = grad n (the ray equation with
+// dt = ds / n) integrated along the line cut into born_k segments, each
+// segment's integrals taken from the table column through the segment's
+// midpoint.  The midpoint is moved by the displacement the earlier segments
+// have already produced, so the integrals follow the deflected path
+// (first-order accurate in each segment, self-consistent along the ray).
+// r = {dx, dy at z_ref, dux, duy}.
 __device__ __forceinline__ void born_residual(const SurrParams& S, const Entry& e, float* r)
 {
     r[0] = r[1] = r[2] = r[3] = 0.0f;
     if (S.born_k <= 0 || !e.enters) return;
     const float ux = e.ux.hi, uy = e.uy.hi;
+    const float q = 1.0f + ux * ux + uy * uy;   // slope change (T_perp - u T_z) / T_z with T = n d, ds = dz sqrt(1+u^2)
     const float dzs = (S.zhi_f - e.ze) / (float)S.born_k;
-    float3 G = make_float3(0.f, 0.f, 0.f), H = G;
+    // accumulated slope-change integrals of the segments done so far:
+    // gx, gy = sum of (G_perp - u G_z); hx, hy = the same with weight (z - z_hi)
+    float gx = 0.f, gy = 0.f, hx = 0.f, hy = 0.f;
 #pragma unroll 1
     for (int k = 0; k < S.born_k; ++k) {
         const float za = e.ze + (float)k * dzs, zb = za + dzs, zm = za + 0.5f * dzs;
+        // displacement at zm from the earlier segments' kinks
+        const float dxm = q * ((zm - S.zhi_f) * gx - hx), dym = q * ((zm - S.zhi_f) * gy - hy);
         const float c = S.persp / (S.aim_z - zm);
-        const float xi = (e.xe + ux * (zm - e.ze)) * c, eta = (e.ye + uy * (zm - e.ze)) * c;
+        const float xi = (e.xe + ux * (zm - e.ze) + dxm) * c, eta = (e.ye + uy * (zm - e.ze) + dym) * c;
         float3 Ga, Ha, Gb, Hb;
         table_lookup(S, xi, eta, za, Ga, Ha);
         table_lookup(S, xi, eta, zb, Gb, Hb);
-        G.x += Ga.x - Gb.x; G.y += Ga.y - Gb.y; G.z += Ga.z - Gb.z;
-        H.x += Ha.x - Hb.x; H.y += Ha.y - Hb.y; H.z += Ha.z - Hb.z;
+        const float Gx = Ga.x - Gb.x, Gy = Ga.y - Gb.y, Gz = Ga.z - Gb.z;
+        const float Hx = Ha.x - Hb.x, Hy = Ha.y - Hb.y, Hz = Ha.z - Hb.z;
+        gx += Gx - ux * Gz;
+        gy += Gy - uy * Gz;
+        hx += Hx - ux * Hz;
+        hy += Hy - uy * Hz;
     }
-    // slope change (T_perp - u T_z) / T_z with T = n d and ds = dz sqrt(1 + u^2)
-    const float q = 1.0f + ux * ux + uy * uy;
-    const float gx = G.x - ux * G.z, gy = G.y - uy * G.z;
-    const float hx = H.x - ux * H.z, hy = H.y - uy * H.z;
     const float zr = S.z_ref.hi + S.z_ref.lo - S.zhi_f;
     r[0] = q * (zr * gx - hx);
     r[1] = q * (zr * gy - hy);
@@ -552,6 +560,7 @@ struct SurrSmem {
     float2 ray[256][6];   // source and direction (double-float)
     int mode[256];        // 0 network, 1 fallback list, 2 straight (never enters), 3 inactive, 4 trace here
     unsigned long long tile[kTileW * kTileH];
+    uint32_t order[kMaxOrderRays];   // the item's rays in mid-plane Morton order (dense media)
     unsigned long long item;
     unsigned long long fb_base;
     uint64_t bar[2];
@@ -612,16 +621,24 @@ surr_render_kernel(const TraceParams P, const SurrParams S, const __nv_bfloat16*
         if (item >= items || failed) break;
         const uint64_t first = item * rays_per_item;
         const uint64_t last = min(first + rays_per_item, total_rays);
+        const uint32_t n_here = (uint32_t)(last - first);
+        // with many projection segments per ray the item's rays are taken in
+        // the order of where they cross the box mid-plane, so a warp's table
+        // gathers share columns (with few, the sort costs more than it saves)
+        const bool reorder = P.reorder && S.born_k >= 8 && n_here <= (uint32_t)kMaxOrderRays;
+        if (reorder) order_chunk(P, sh.order, first, n_here);
         int ax = -(1 << 28), ay = -(1 << 28);
         for (uint64_t base = first, sub = 0; base < last; base += 256, ++sub) {
             // ---- features, projection and the serve / fall back decision
-            const uint64_t idx = base + tid;
+            const uint32_t pos_in_item = (uint32_t)(base - first) + (uint32_t)tid;
+            const bool active = pos_in_item < n_here;
+            const uint64_t idx = first + (reorder && active ? (sh.order[pos_in_item] & 0x7ffu) : pos_in_item);
             int mode = 3;
             Entry e;
             e.enters = false;
             e.f[0] = e.f[1] = e.f[2] = e.f[3] = e.f[4] = 0.0f;
             float born[4] = {0.f, 0.f, 0.f, 0.f};
-            if (idx < last) {
+            if (active) {
                 const uint32_t flat = (uint32_t)idx;
                 const uint32_t slot = flat / rps, k = flat - slot * rps;
                 const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
@@ -927,6 +944,8 @@ pivbos_status pivbos_surrogate_default_cfg(pivbos_surrogate_cfg* c)
     c->ref_plane_z = NAN;
     c->born_segments = -1;
     c->use_network = 1;
+    c->table_columns_per_cell = 0;
+    c->table_levels_per_cell = 1;
     return PIVBOS_OK;
 }
 
@@ -944,7 +963,9 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
         c.batch < 256 || c.batch > 65536 || !(c.lr > 0.f) || !(c.err_budget_px > 0.f) ||
         !(c.budget_margin > 0.f && c.budget_margin <= 1.f) || c.min_bin_count < 1 ||
         (!std::isnan(c.ref_plane_z) && !std::isfinite(c.ref_plane_z)) ||
-        c.born_segments < -1 || c.born_segments > 64 || (c.use_network != 0 && c.use_network != 1))
+        c.born_segments < -1 || c.born_segments > 64 || (c.use_network != 0 && c.use_network != 1) ||
+        c.table_columns_per_cell < 0 || c.table_columns_per_cell > 8 || c.table_levels_per_cell < 1 ||
+        c.table_levels_per_cell > 4)
         return serr(PIVBOS_ERR_INVALID_ARG, "surrogate configuration out of range");
     pivbos::TraceParams P;
     int dev = 0;
@@ -1013,9 +1034,22 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
             xmin = fmin(xmin, x * f); xmax = fmax(xmax, x * f);
             ymin = fmin(ymin, y * f); ymax = fmax(ymax, y * f);
         }
-        S.tnx = std::min(2 * (m->n[0] - 1) + 1, 1024);
-        S.tny = std::min(2 * (m->n[1] - 1) + 1, 1024);
-        S.tnz = std::max(2, std::min(m->n[2], 512));
+        const int lpc = c.table_levels_per_cell;
+        S.tnz = std::max(2, std::min(lpc * (m->n[2] - 1) + 1, 1024));
+        // columns per grid spacing: as configured, or the densest of 4, 2, 1
+        // whose table fits in 16 GiB (lateral interpolation of the column
+        // integrals is the projection's accuracy limit)
+        int cpc = c.table_columns_per_cell;
+        if (cpc == 0) {
+            for (cpc = 4; cpc > 1; cpc /= 2) {
+                const double cols = (double)std::min(cpc * (m->n[0] - 1) + 1, 2048) *
+                                    (double)std::min(cpc * (m->n[1] - 1) + 1, 2048);
+                if (cols * S.tnz * 2 * sizeof(float4) <= 16.0 * (1ull << 30)) break;
+            }
+        }
+        S.tnx = std::min(cpc * (m->n[0] - 1) + 1, 2048);
+        S.tny = std::min(cpc * (m->n[1] - 1) + 1, 2048);
+        R.table_columns_per_cell = cpc;
         S.t_x0 = (float)xmin;
         S.t_y0 = (float)ymin;
         S.t_inv_dx = (float)((S.tnx - 1) / fmax(xmax - xmin, 1e-12));

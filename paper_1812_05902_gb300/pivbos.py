@@ -56,14 +56,16 @@ class pivbos_surrogate_cfg(ctypes.Structure):
                 ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("err_budget_px", ctypes.c_float),
                 ("budget_margin", ctypes.c_float), ("min_bin_count", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("ref_plane_z", ctypes.c_double), ("born_segments", ctypes.c_int32),
-                ("use_network", ctypes.c_int32)]
+                ("use_network", ctypes.c_int32), ("table_columns_per_cell", ctypes.c_int32),
+                ("table_levels_per_cell", ctypes.c_int32)]
 
 
 _REPORT_SCALARS = ("train_loss", "train_steps", "val_rms_px", "val_rms_px_born", "val_rms_px_straight",
                    "val_rms_px_served", "val_served_frac", "val_served_frac_born", "val_served_frac_straight",
                    "steps_saved_frac", "steps_saved_frac_born", "steps_saved_frac_straight",
                    "val_status_flip_frac", "n_val_reached", "n_val_box", "seconds_table", "seconds_data",
-                   "seconds_train", "seconds_validate", "table_bytes", "born_segments")
+                   "seconds_train", "seconds_validate", "table_bytes", "born_segments",
+                   "table_columns_per_cell")
 _REPORT_VECTORS = (("pilot_rms_px_born_k", 6), ("target_rms", 4), ("correction_rms", 4),
                    ("sensor_px_per_unit", 4))
 

@@ -90,7 +90,8 @@ def test_surrogate_arguments_without_a_device(P):
     for field, value in (("batch", 100), ("batch", 1 << 17), ("n_train", 10), ("epochs", 0), ("lr", 0.0),
                          ("err_budget_px", -1.0), ("budget_margin", 1.5), ("min_bin_count", 0),
                          ("ref_plane_z", float("inf")), ("born_segments", -2), ("born_segments", 65),
-                         ("use_network", 2)):
+                         ("use_network", 2), ("table_columns_per_cell", -1), ("table_columns_per_cell", 9),
+                         ("table_levels_per_cell", 5)):
         bad = P.pivbos_surrogate_default_cfg()
         setattr(bad, field, value)
         assert L.pivbos_surrogate_train(ctypes.byref(desc), 1, ctypes.byref(bad), ctypes.byref(out),
