@@ -446,6 +446,7 @@ def run_surrogate(args, rank, world, steps, warmup, embedded, workload="c4"):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
+        P.pivbos_timing_reset()   # kernel timings of the timed steps only
         timed.launches0 = P.pivbos_kernel_launches()
         ev = []
         for _ in range(steps):
@@ -470,7 +471,9 @@ def run_surrogate(args, rank, world, steps, warmup, embedded, workload="c4"):
         launches = P.pivbos_kernel_launches() - timed.launches0
         P.pivbos_timing_enable(False)
         clk = clocks.stop()
-        k_ms, k_n = P.pivbos_timing_read("surrogate_render")
+        k_ms, k_n = P.pivbos_timing_read("surrogate_net")
+        p_ms, p_n = P.pivbos_timing_read("surrogate_prep")
+        q_ms, q_n = P.pivbos_timing_read("surrogate_finish")
         f_ms, f_n = P.pivbos_timing_read("surrogate_fallback")
         n_fb = P.pivbos_surrogate_render(sg, desc, count_fallback=True)
         # error of the surrogate path: against the plain tracer on 10^6 rays,
@@ -529,7 +532,7 @@ def run_surrogate(args, rank, world, steps, warmup, embedded, workload="c4"):
     v_plain = rays * steps * world / (ms_plain * 1e-3)
     v_sur = rays * steps * world / (ms_sur * 1e-3)
     served = rays - n_fb
-    k_launch_s = k_ms / max(k_n, 1) * 1e-3
+    k_launch_s = k_ms / steps * 1e-3   # the network kernels of one render
     peaks, src_kind = _peaks()
     peak_tf = peaks.get("bf16_tflops", 1900.0)
     achieved = served * MLP_FLOP_PER_RAY / k_launch_s / 1e12 if k_n else None
@@ -540,13 +543,14 @@ def run_surrogate(args, rank, world, steps, warmup, embedded, workload="c4"):
         "rms_err_px_vs_plain": rms_plain, "rms_err_px_vs_oracle": rms_oracle, "oracle_rays": int(ok_o.sum()),
         "sampled_rays": int(ok.sum()), "budget_px": 0.01,
         "served_frac": served / rays, "fallback_rays": int(n_fb),
-        "surrogate_kernel_ms": k_ms / max(k_n, 1), "fallback_kernel_ms": f_ms / max(f_n, 1),
+        "kernel_ms_per_render": {"prep": p_ms / steps, "net": k_ms / steps, "finish": q_ms / steps,
+                                 "fallback": f_ms / max(f_n, 1)},
         "train_seconds": train_wall, "report": rep.as_dict(),
         "roofline": ({"bound": "tensor", "achieved": round(achieved, 2), "peak": peak_tf, "unit": "TFLOP/s",
                       "frac": round(achieved / peak_tf, 4),
                       "traffic": (recorded_traffic("surrogate_%s_traffic" % workload, "surrogate")
-                                  if args.scale == 1.0 else None), "kernel": "surr_render_kernel",
-                      "op": "BF16 MLP forward, %d FLOP per served ray" % MLP_FLOP_PER_RAY,
+                                  if args.scale == 1.0 else None), "kernel": "surr_net_kernel",
+                      "op": "BF16 MLP forward (tcgen05), %d FLOP per served ray" % MLP_FLOP_PER_RAY,
                       "peak_source": "%s bf16_tflops" % src_kind} if achieved else None),
         "clocks": clk, "gpu_launches": int(launches), "steps": steps, "warmup": warmup, "e2e": e2e,
     }

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -551,88 +552,72 @@ __global__ void surr_eval_kernel(const TraceParams P, const SurrParams S, const 
     atomicAdd(&acc.cnt[e.bin], 1u);
 }
 
-// Shared memory of the fused surrogate render kernel.
-struct SurrSmem {
-    mlptc::Net net;
-    alignas(128) unsigned char a[2][mlptc::kTileBytes];   // network operand of the two 128-ray tiles
-    float y[256][4];
-    float born[256][4];
-    float2 ray[256][6];   // source and direction (double-float)
-    int mode[256];        // 0 network, 1 fallback list, 2 straight (never enters), 3 inactive, 4 trace here
-    unsigned long long tile[kTileW * kTileH];
-    uint32_t order[kMaxOrderRays];   // the item's rays in mid-plane Morton order (dense media)
-    unsigned long long item;
-    unsigned long long fb_base;
-    uint64_t bar[2];
-    uint32_t tmem_base;
-    int wg_failed[2];
-    int fb_warp[8];
-    int anchor_tid, ax, ay;
+// ---------------------------------------------------------------------------
+// Surrogate render in three kernels over chunks of the frame's rays:
+// prep (features, projection, serve / fall back) -> network (tcgen05) ->
+// finish (exit line, optics, tile deposit).  Each runs at its own
+// occupancy; the served rays pass between them in ray order.
+// ---------------------------------------------------------------------------
+struct ServedList {
+    uint32_t* ids;              // flat ray index; top bit: never enters the box (straight)
+    __nv_bfloat16* X;           // [capacity][16] network input
+    float4* B;                  // [capacity] projection residual
+    float4* R;                  // [capacity] full residual (projection + correction)
+    float4* L;                  // [capacity][2] straight line: x, y at z_ref and slopes, double-float
+    unsigned long long* count;  // rays appended
+    uint32_t capacity;
 };
 
-// S3: persistent kernel over chunks of rays of one render (sources in Morton
-// order).  Per 256 rays: entry features and projection residual (written
-// straight into the network operand) -> network correction on tcgen05 (two
-// 128-row tiles, accumulators in TMEM, warpgroup g runs tile g's epilogues)
-// -> exit line -> lens and sensor -> shared tile.  Rays in bins the
-// surrogate does not serve are appended, 256 at a time in ray order, to the
-// fallback list the plain tracer renders afterwards.
-template <int INTEG>
-__global__ void __launch_bounds__(256, 1)
-surr_render_kernel(const TraceParams P, const SurrParams S, const __nv_bfloat16* __restrict__ wbf,
-                   const float* __restrict__ params, int64_t* __restrict__ image, int64_t* __restrict__ stats,
-                   uint64_t total_rays, uint32_t rays_per_item, unsigned long long* __restrict__ counter,
-                   uint32_t* __restrict__ fb_ids, unsigned long long* __restrict__ fb_count, uint32_t fb_capacity)
+constexpr uint32_t kStraightBit = 0x80000000u;
+
+// Append the calling CTA's flagged lanes (one atomic per CTA); returns this
+// thread's slot (meaningful where flag is set).  All threads call it.
+__device__ __forceinline__ unsigned long long block_append(bool flag, unsigned long long* counter, int* warp_off,
+                                                           unsigned long long* base)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    SurrSmem& sh = *reinterpret_cast<SurrSmem*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int grp = warp >> 2, row = tid & 127;   // tile and row of this thread's ray
-    if (S.use_net) mlptc::load_net(sh.net, wbf, params);
-    if (warp == 0) umma::tmem_alloc(&sh.tmem_base, 256);
-    if (tid == 0) {
-        umma::mbar_init(&sh.bar[0], 1);
-        umma::mbar_init(&sh.bar[1], 1);
-        sh.wg_failed[0] = sh.wg_failed[1] = 0;
-    }
-    umma::fence_before_sync();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
     __syncthreads();
-    umma::fence_after_sync();
-    const uint32_t tmem = sh.tmem_base;
-    const uint32_t d_tmem = tmem + (uint32_t)(grp * 128);   // this warpgroup's accumulator columns
-    const uint32_t row_tmem = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const uint32_t a_saddr = umma::smem_addr(sh.a[grp]);
-    uint32_t parity = 0;   // of this warpgroup's mbarrier
-    bool failed = false;
-    const uint64_t items = (total_rays + rays_per_item - 1) / rays_per_item;
-    const uint32_t rps = P.rays_per_source;
-    unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) sh.item = atomicAdd(counter, 1ull);
-        for (int q = tid; q < kTileW * kTileH; q += blockDim.x) sh.tile[q] = 0ull;
-        if (tid == 0) {
-            sh.anchor_tid = 0x7fffffff;
-            sh.ax = -(1 << 28);
-            sh.ay = -(1 << 28);
+    if (lane == 0) warp_off[warp] = __popc(m);
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int c = warp_off[w];
+            warp_off[w] = tot;
+            tot += c;
         }
-        __syncthreads();
-        const uint64_t item = sh.item;
-        if (item >= items || failed) break;
-        const uint64_t first = item * rays_per_item;
-        const uint64_t last = min(first + rays_per_item, total_rays);
-        const uint32_t n_here = (uint32_t)(last - first);
-        // with many projection segments per ray the item's rays are taken in
-        // the order of where they cross the box mid-plane, so a warp's table
-        // gathers share columns (with few, the sort costs more than it saves)
-        const bool reorder = P.reorder && S.born_k >= 8 && n_here <= (uint32_t)kMaxOrderRays;
-        if (reorder) order_chunk(P, sh.order, first, n_here);
-        int ax = -(1 << 28), ay = -(1 << 28);
-        for (uint64_t base = first, sub = 0; base < last; base += 256, ++sub) {
-            // ---- features, projection and the serve / fall back decision
-            const uint32_t pos_in_item = (uint32_t)(base - first) + (uint32_t)tid;
-            const bool active = pos_in_item < n_here;
-            const uint64_t idx = first + (reorder && active ? (sh.order[pos_in_item] & 0x7ffu) : pos_in_item);
+        *base = tot ? atomicAdd(counter, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    return *base + (unsigned long long)(warp_off[warp] + __popc(m & ((1u << lane) - 1u)));
+}
+
+// Prep: rays [c0, c1) of the Morton-ordered (slot, ray) space, 256 per CTA
+// round; served rays (and rays that never enter the box) go to the served
+// list with their network input and projection residual, the others to the
+// fallback list.
+__global__ void __launch_bounds__(256)
+surr_prep_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t c1, ServedList sv,
+                 uint32_t* __restrict__ fb_ids, unsigned long long* __restrict__ fb_count, uint32_t fb_capacity)
+{
+    __shared__ int warp_off[8];
+    __shared__ unsigned long long base;
+    __shared__ uint32_t order[kMaxOrderRays];
+    const uint32_t rps = P.rays_per_source;
+    // items of kMaxOrderRays rays; with many projection segments per ray an
+    // item's rays are taken in the order of where they cross the box
+    // mid-plane, so a warp's table gathers share columns
+    const uint64_t items = (c1 - c0 + kMaxOrderRays - 1) / kMaxOrderRays;
+    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const uint64_t first = c0 + it * kMaxOrderRays;
+        const uint32_t n_here = (uint32_t)(min(first + kMaxOrderRays, c1) - first);
+        const bool reorder = P.reorder && S.born_k >= 8;
+        if (reorder) order_chunk(P, order, first, n_here);
+        for (uint32_t r0 = 0; r0 < n_here; r0 += 256) {
+            const uint32_t pos = r0 + threadIdx.x;
+            const bool active = pos < n_here;
+            const uint64_t idx = first + (reorder && active ? (order[pos] & 0x7ffu) : pos);
             int mode = 3;
             Entry e;
             e.enters = false;
@@ -644,140 +629,199 @@ surr_render_kernel(const TraceParams P, const SurrParams S, const __nv_bfloat16*
                 const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
                 const float2* sp = P.src_df + 3 * (size_t)slot;
                 const float2 a = __ldg(sp), b = __ldg(sp + 1), c = __ldg(sp + 2);
-                const df sx{a.x, a.y}, sy{b.x, b.y}, sz{c.x, c.y};
                 df dx, dy, dz;
-                ray_start(P, sx, sy, sz, sid, k, dx, dy, dz);
-                surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+                ray_start(P, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, sid, k, dx, dy, dz);
+                surr_entry(P, S, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, dx, dy, dz, e);
                 if (!e.enters) mode = 2;
                 else mode = ((__ldg(S.bin_ok + (e.bin >> 5)) >> (e.bin & 31)) & 1u) ? 0 : 1;
                 if (mode == 0) born_residual(S, e, born);
-                sh.ray[tid][0] = a; sh.ray[tid][1] = b; sh.ray[tid][2] = c;
-                sh.ray[tid][3] = make_float2(dx.hi, dx.lo);
-                sh.ray[tid][4] = make_float2(dy.hi, dy.lo);
-                sh.ray[tid][5] = make_float2(dz.hi, dz.lo);
             }
-            // append the fallback rays of these 256 in ray order
-            const unsigned fbm = __ballot_sync(0xffffffffu, mode == 1);
-            if (lane == 0) sh.fb_warp[warp] = __popc(fbm);
-            __syncthreads();
-            if (tid == 0) {
-                int tot = 0;
-                for (int w = 0; w < 8; ++w) {
-                    const int c = sh.fb_warp[w];
-                    sh.fb_warp[w] = tot;
-                    tot += c;
-                }
-                sh.fb_base = tot ? atomicAdd(fb_count, (unsigned long long)tot) : 0ull;
-            }
-            __syncthreads();
-            if (mode == 1) {
-                const unsigned long long pos =
-                    sh.fb_base + (unsigned long long)(sh.fb_warp[warp] + __popc(fbm & ((1u << lane) - 1u)));
-                if (pos < fb_capacity) fb_ids[pos] = (uint32_t)idx;
-                else mode = 4;   // list full: trace it here
-            }
-            sh.mode[tid] = mode;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) sh.born[tid][c] = born[c];
-            // ---- network on tcgen05 (skipped when no ray of the 256 is served).
-            // Warpgroup g runs tile g on its own: its leader issues each
-            // layer, all 128 threads wait on the tile's mbarrier and run the
-            // epilogue, so one tile's MMAs overlap the other's epilogue.
-            if (__syncthreads_or(S.use_net && mode == 0)) {
-                {
+            const unsigned long long ps = block_append(mode == 0 || mode == 2, sv.count, warp_off, &base);
+            if (mode == 0 || mode == 2) {
+                if (ps < sv.capacity) {
+                    sv.ids[ps] = (uint32_t)idx | (mode == 2 ? kStraightBit : 0u);
                     __align__(16) __nv_bfloat16 x[kMlpIn];
                     encode_features(S, e.f, born, x);
-                    mlptc::store_input_row(sh.a[grp], row, *reinterpret_cast<const uint4*>(&x[0]),
-                                           *reinterpret_cast<const uint4*>(&x[8]));
-                }
-#pragma unroll 1
-                for (int l = 0; l < kMlpLayers; ++l) {
-                    umma::fence_async_smem();
-                    umma::fence_before_sync();
-                    umma::named_sync(1 + grp, 128);
-                    if (row == 0) {
-                        umma::fence_after_sync();
-                        mlptc::issue_layer(sh.net, l, a_saddr, d_tmem);
-                        umma::commit(&sh.bar[grp]);
-                    }
-                    const bool ok = umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit);
-                    if (!ok) sh.wg_failed[grp] = 1;
-                    umma::named_sync(1 + grp, 128);
-                    if (sh.wg_failed[grp]) break;
-                    parity ^= 1u;
-                    umma::fence_after_sync();
-                    if (l < kMlpLayers - 1) mlptc::epilogue_hidden2(row_tmem, sh.net.bias[l], sh.a[grp], row);
-                    else mlptc::epilogue_out(row_tmem, sh.net.bias4, sh.y[tid]);
-                }
-                if (__syncthreads_or(sh.wg_failed[grp] != 0)) {
-                    failed = true;
-                    break;
-                }
-            }
-            // ---- lens, sensor and deposit
-            RayOut r;
-            r.status = PIVBOS_RAY_MISS;
-            const bool here = mode == 0 || mode == 2 || mode == 4;
-            if (here) {
-                const df sx{sh.ray[tid][0].x, sh.ray[tid][0].y}, sy{sh.ray[tid][1].x, sh.ray[tid][1].y};
-                const df sz{sh.ray[tid][2].x, sh.ray[tid][2].y};
-                df dx{sh.ray[tid][3].x, sh.ray[tid][3].y}, dy{sh.ray[tid][4].x, sh.ray[tid][4].y};
-                df dz{sh.ray[tid][5].x, sh.ray[tid][5].y};
-                if (mode == 4) {
-                    const uint32_t flat = (uint32_t)idx;
-                    const uint32_t slot = flat / rps, k = flat - slot * rps;
-                    trace_ray<INTEG, false>(P, sx, sy, sz, __ldg(P.perm + slot) + P.source_offset, k, r, nullptr);
+                    uint4* xr = reinterpret_cast<uint4*>(sv.X + ps * kMlpIn);
+                    xr[0] = *reinterpret_cast<const uint4*>(&x[0]);
+                    xr[1] = *reinterpret_cast<const uint4*>(&x[8]);
+                    sv.B[ps] = make_float4(born[0], born[1], born[2], born[3]);
+                    sv.L[2 * ps] = make_float4(e.xs.hi, e.xs.lo, e.ys.hi, e.ys.lo);
+                    sv.L[2 * ps + 1] = make_float4(e.ux.hi, e.ux.lo, e.uy.hi, e.uy.lo);
                 } else {
-                    df Rx = sx, Ry = sy, Rz = sz;
-                    if (mode == 0) {
-                        float res[4];
-                        surr_residual(S, sh.born[tid], sh.y[tid], res);
-                        surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
-                    }
-                    r.status = PIVBOS_RAY_REACHED;
-                    optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, r.status, r.px, r.py);
+                    atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_OVERFLOW);   // cannot happen: capacity = chunk
                 }
-                cnt[r.status]++;
             }
-            if (sub == 0) {
-                if (here && r.status == PIVBOS_RAY_REACHED) atomicMin(&sh.anchor_tid, tid);
-                __syncthreads();
-                if (tid == sh.anchor_tid) {
-                    float f;
-                    sh.ax = df_floor(r.px, f) - kTileW / 2;
-                    sh.ay = df_floor(r.py, f) - kTileH / 2;
-                }
-                __syncthreads();
-                ax = sh.ax;
-                ay = sh.ay;
-            }
-            if (here && r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, sh.tile, ax, ay, image);
-            __syncthreads();
-        }
-        for (int q = tid; q < kTileW * kTileH; q += blockDim.x) {
-            const unsigned long long v = sh.tile[q];
-            if (v) {
-                const int gx = ax + (q % kTileW), gy = ay + (q / kTileW);
-                atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * P.o.W + gx]), v);
+            const unsigned long long pf = block_append(mode == 1, fb_count, warp_off, &base);
+            if (mode == 1) {
+                if (pf < fb_capacity) fb_ids[pf] = (uint32_t)idx;
+                else atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_OVERFLOW);   // cannot happen: capacity = rays
             }
         }
+        __syncthreads();   // order[] is rewritten by the next item
     }
-    if (failed && row == 0) {
-        // report, then give the MMAs in flight a second bounded wait before
-        // the accumulator memory is released
-        atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_DEVICE_TIMEOUT);
-        if (sh.wg_failed[grp]) umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit);
+}
+
+// Network over the served list on tcgen05: three warpgroups per CTA, each
+// running its own 128-row tiles (its own operand buffer, TMEM columns and
+// mbarrier), so tiles of different warpgroups overlap.  R = B + y * scale.
+constexpr int kNetGroups = 3;
+struct NetSmem {
+    mlptc::Net net;
+    alignas(128) unsigned char a[kNetGroups][mlptc::kTileBytes];
+    uint64_t bar[kNetGroups];
+    uint32_t tmem_base;
+    int failed[kNetGroups];
+};
+
+__global__ void __launch_bounds__(128 * kNetGroups, 1)
+surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ params,
+                ServedList sv, int* __restrict__ status_word)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    NetSmem& sh = *reinterpret_cast<NetSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, grp = warp >> 2, row = tid & 127;
+    mlptc::load_net(sh.net, wbf, params);
+    if (warp == 0) umma::tmem_alloc(&sh.tmem_base, 512);
+    if (tid < kNetGroups) {
+        umma::mbar_init(&sh.bar[tid], 1);
+        sh.failed[tid] = 0;
     }
-    if (stats) {
-#pragma unroll
-        for (int q = 0; q < PIVBOS_RAY_NSTATUS; ++q)
-            if (cnt[q]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[q]), (unsigned long long)cnt[q]);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t d_tmem = sh.tmem_base + (uint32_t)(grp * 128);
+    const uint32_t row_tmem = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t a_saddr = umma::smem_addr(sh.a[grp]);
+    const uint64_t n = min(*sv.count, (unsigned long long)sv.capacity);
+    const uint64_t tiles = (n + mlptc::kRows - 1) / mlptc::kRows;
+    uint32_t parity = 0;
+    for (uint64_t t = (uint64_t)blockIdx.x * kNetGroups + grp; t < tiles; t += (uint64_t)gridDim.x * kNetGroups) {
+        const uint64_t r = t * mlptc::kRows + row;
+        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+        if (r < n) {
+            const uint4* xr = reinterpret_cast<const uint4*>(sv.X + r * kMlpIn);
+            lo = xr[0];
+            hi = xr[1];
+        }
+        mlptc::store_input_row(sh.a[grp], row, lo, hi);
+        bool bad = false;
+#pragma unroll 1
+        for (int l = 0; l < kMlpLayers; ++l) {
+            umma::fence_async_smem();
+            umma::fence_before_sync();
+            umma::named_sync(1 + grp, 128);
+            if (row == 0) {
+                umma::fence_after_sync();
+                mlptc::issue_layer(sh.net, l, a_saddr, d_tmem);
+                umma::commit(&sh.bar[grp]);
+            }
+            if (!umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit)) sh.failed[grp] = 1;
+            umma::named_sync(1 + grp, 128);
+            if (sh.failed[grp]) {
+                bad = true;
+                break;
+            }
+            parity ^= 1u;
+            umma::fence_after_sync();
+            if (l < kMlpLayers - 1) {
+                mlptc::epilogue_hidden2(row_tmem, sh.net.bias[l], sh.a[grp], row);
+            } else {
+                float y[kMlpOut];
+                mlptc::epilogue_out(row_tmem, sh.net.bias4, y);
+                if (r < n) {
+                    const float4 b = sv.B[r];
+                    sv.R[r] = make_float4(b.x + y[0] * S.t_scale[0], b.y + y[1] * S.t_scale[1],
+                                          b.z + y[2] * S.t_scale[2], b.w + y[3] * S.t_scale[3]);
+                }
+            }
+        }
+        if (bad) break;
+    }
+    if (sh.failed[grp] && row == 0) {
+        atomicCAS(status_word, 0, (int)PIVBOS_ERR_DEVICE_TIMEOUT);
+        umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit);
     }
     umma::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
         umma::fence_after_sync();
-        umma::tmem_dealloc(tmem, 256);
+        umma::tmem_dealloc(sh.tmem_base, 512);
+    }
+}
+
+// Finish: the served list in chunks of 256 consecutive entries (one round of
+// the prep kernel's rays: a few neighbouring sources), each chunk deposited
+// into a shared tile anchored at its first hit.
+__global__ void __launch_bounds__(256, 3)
+surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const float4* __restrict__ resid,
+                   int64_t* __restrict__ image, int64_t* __restrict__ stats, unsigned long long* __restrict__ counter)
+{
+    __shared__ unsigned long long tile[kTileW * kTileH];
+    __shared__ unsigned long long s_item;
+    __shared__ int anchor_tid, sax, say;
+    const int tid = threadIdx.x;
+    const uint64_t n = min(*sv.count, (unsigned long long)sv.capacity);
+    const uint64_t items = (n + 255) / 256;
+    unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
+    for (;;) {
+        if (tid == 0) {
+            s_item = atomicAdd(counter, 1ull);
+            anchor_tid = 0x7fffffff;
+        }
+        for (int q = tid; q < kTileW * kTileH; q += blockDim.x) tile[q] = 0ull;
+        __syncthreads();
+        const uint64_t it = s_item;
+        if (it >= items) break;
+        const uint64_t pos = it * 256 + tid;
+        RayOut r;
+        r.status = PIVBOS_RAY_MISS;
+        const bool active = pos < n;
+        if (active) {
+            // the straight line from the prep kernel, plus the residual (none
+            // for a ray that never enters the box)
+            const float4 l0 = sv.L[2 * pos], l1 = sv.L[2 * pos + 1];
+            Entry e;
+            e.xs = df{l0.x, l0.y};
+            e.ys = df{l0.z, l0.w};
+            e.ux = df{l1.x, l1.y};
+            e.uy = df{l1.z, l1.w};
+            float res[4] = {0.f, 0.f, 0.f, 0.f};
+            if (!(sv.ids[pos] & kStraightBit)) {
+                const float4 rv = resid[pos];
+                res[0] = rv.x; res[1] = rv.y; res[2] = rv.z; res[3] = rv.w;
+            }
+            df Rx, Ry, Rz, dx, dy, dz;
+            surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
+            r.status = PIVBOS_RAY_REACHED;
+            optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, r.status, r.px, r.py);
+            cnt[r.status]++;
+            if (r.status == PIVBOS_RAY_REACHED) atomicMin(&anchor_tid, tid);
+        }
+        __syncthreads();
+        if (tid == anchor_tid) {
+            float f;
+            sax = df_floor(r.px, f) - kTileW / 2;
+            say = df_floor(r.py, f) - kTileH / 2;
+        }
+        __syncthreads();
+        const int ax = anchor_tid == 0x7fffffff ? -(1 << 28) : sax;
+        const int ay = anchor_tid == 0x7fffffff ? -(1 << 28) : say;
+        if (active && r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, tile, ax, ay, image);
+        __syncthreads();
+        for (int q = tid; q < kTileW * kTileH; q += blockDim.x) {
+            const unsigned long long v = tile[q];
+            if (v) {
+                const int gx = ax + (q % kTileW), gy = ay + (q / kTileW);
+                atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * P.o.W + gx]), v);
+            }
+        }
+        __syncthreads();
+    }
+    if (stats) {
+#pragma unroll
+        for (int q = 0; q < PIVBOS_RAY_NSTATUS; ++q)
+            if (cnt[q]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[q]), (unsigned long long)cnt[q]);
     }
 }
 
@@ -1350,25 +1394,53 @@ pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_f
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sg->device);
     if (e == cudaSuccess) {
-        e = cudaFuncSetAttribute(pivbos::surr_render_kernel<PIVBOS_RK4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(pivbos::SurrSmem));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pivbos::surr_render_kernel<PIVBOS_EULER>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(pivbos::SurrSmem));
-    }
-    if (e == cudaSuccess) {
-        pivbos::timing_begin("surrogate_render", s);
-        if (sg->integrator == PIVBOS_RK4)
-            pivbos::surr_render_kernel<PIVBOS_RK4><<<sms, 256, sizeof(pivbos::SurrSmem), s>>>(
-                P, sg->S, sg->net.wbf, sg->net.params, frame->image, frame->stats, total, 2048u, counters, fb,
-                counters + 1, capacity);
-        else
-            pivbos::surr_render_kernel<PIVBOS_EULER><<<sms, 256, sizeof(pivbos::SurrSmem), s>>>(
-                P, sg->S, sg->net.wbf, sg->net.params, frame->image, frame->stats, total, 2048u, counters, fb,
-                counters + 1, capacity);
-        pivbos::timing_end("surrogate_render", s);
-        pivbos::count_launches(1);
-        e = cudaGetLastError();
+        // three kernels per chunk of up to 2^26 rays: prep -> network -> finish
+        const uint64_t chunk = std::min<uint64_t>(total, 1ull << 26);
+        pivbos::ServedList sv;
+        char* sbuf = nullptr;
+        const size_t off_count = ((size_t)chunk * 100 + 255) & ~(size_t)255;
+        const size_t sbytes = off_count + 256;
+        e = cudaMallocAsync((void**)&sbuf, sbytes, s);
+        if (e == cudaSuccess) {
+            sv.X = (__nv_bfloat16*)sbuf;
+            sv.B = (float4*)(sbuf + (size_t)chunk * 32);
+            sv.R = (float4*)(sbuf + (size_t)chunk * 48);
+            sv.L = (float4*)(sbuf + (size_t)chunk * 64);
+            sv.ids = (uint32_t*)(sbuf + (size_t)chunk * 96);
+            sv.count = (unsigned long long*)(sbuf + off_count);   // [0] served, [1] finish items
+            sv.capacity = (uint32_t)chunk;
+            static bool attr = false;
+            if (!attr) {
+                e = cudaFuncSetAttribute(pivbos::surr_net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(pivbos::NetSmem));
+                attr = e == cudaSuccess;
+            }
+            for (uint64_t c0 = 0; c0 < total && e == cudaSuccess; c0 += chunk) {
+                const uint64_t c1 = std::min(total, c0 + chunk);
+                e = cudaMemsetAsync(sv.count, 0, 2 * sizeof(unsigned long long), s);
+                if (e != cudaSuccess) break;
+                const uint64_t items = (c1 - c0 + pivbos::kMaxOrderRays - 1) / pivbos::kMaxOrderRays;
+                pivbos::timing_begin("surrogate_prep", s);
+                pivbos::surr_prep_kernel<<<(unsigned)std::min<uint64_t>(items, (uint64_t)sms * 6), 256, 0, s>>>(
+                    P, sg->S, c0, c1, sv, fb, counters + 1, capacity);
+                pivbos::timing_end("surrogate_prep", s);
+                if (sg->S.use_net) {
+                    pivbos::timing_begin("surrogate_net", s);
+                    pivbos::surr_net_kernel<<<sms, 128 * pivbos::kNetGroups, sizeof(pivbos::NetSmem), s>>>(
+                        sg->S, sg->net.wbf, sg->net.params, sv, P.status_word);
+                    pivbos::timing_end("surrogate_net", s);
+                }
+                pivbos::timing_begin("surrogate_finish", s);
+                pivbos::surr_finish_kernel<<<sms * 4, 256, 0, s>>>(P, sg->S, sv, sg->S.use_net ? sv.R : sv.B,
+                                                                    frame->image, frame->stats, sv.count + 1);
+                pivbos::timing_end("surrogate_finish", s);
+                pivbos::count_launches(sg->S.use_net ? 3 : 2);
+                e = cudaGetLastError();
+            }
+
+            cudaError_t ef = cudaFreeAsync(sbuf, s);
+            if (e == cudaSuccess) e = ef;
+        }
     }
     if (e == cudaSuccess) {
         pivbos::TraceParams PL = P;
