@@ -696,15 +696,29 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
     const uint64_t n = min(*sv.count, (unsigned long long)sv.capacity);
     const uint64_t tiles = (n + mlptc::kRows - 1) / mlptc::kRows;
     uint32_t parity = 0;
-    for (uint64_t t = (uint64_t)blockIdx.x * kNetGroups + grp; t < tiles; t += (uint64_t)gridDim.x * kNetGroups) {
+    const uint64_t stride = (uint64_t)gridDim.x * kNetGroups;
+    // this thread's input row and projection residual, loaded one tile ahead
+    // so the loads overlap the previous tile's five layers
+    auto load_row = [&](uint64_t t, uint4& lo, uint4& hi, float4& b) {
         const uint64_t r = t * mlptc::kRows + row;
-        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
-        if (r < n) {
+        lo = make_uint4(0u, 0u, 0u, 0u);
+        hi = lo;
+        b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < tiles && r < n) {
             const uint4* xr = reinterpret_cast<const uint4*>(sv.X + r * kMlpIn);
-            lo = xr[0];
-            hi = xr[1];
+            lo = __ldcs(xr);
+            hi = __ldcs(xr + 1);
+            b = __ldcs(sv.B + r);
         }
-        mlptc::store_input_row(sh.a[grp], row, lo, hi);
+    };
+    uint4 nlo, nhi;
+    float4 nb;
+    load_row((uint64_t)blockIdx.x * kNetGroups + grp, nlo, nhi, nb);
+    for (uint64_t t = (uint64_t)blockIdx.x * kNetGroups + grp; t < tiles; t += stride) {
+        const uint64_t r = t * mlptc::kRows + row;
+        const float4 b = nb;
+        mlptc::store_input_row(sh.a[grp], row, nlo, nhi);
+        load_row(t + stride, nlo, nhi, nb);
         bool bad = false;
 #pragma unroll 1
         for (int l = 0; l < kMlpLayers; ++l) {
@@ -729,11 +743,9 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
             } else {
                 float y[kMlpOut];
                 mlptc::epilogue_out(row_tmem, sh.net.bias4, y);
-                if (r < n) {
-                    const float4 b = sv.B[r];
-                    sv.R[r] = make_float4(b.x + y[0] * S.t_scale[0], b.y + y[1] * S.t_scale[1],
-                                          b.z + y[2] * S.t_scale[2], b.w + y[3] * S.t_scale[3]);
-                }
+                if (r < n)
+                    __stcs(sv.R + r, make_float4(b.x + y[0] * S.t_scale[0], b.y + y[1] * S.t_scale[1],
+                                                 b.z + y[2] * S.t_scale[2], b.w + y[3] * S.t_scale[3]));
             }
         }
         if (bad) break;
