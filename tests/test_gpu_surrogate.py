@@ -212,3 +212,47 @@ def test_surrogate_rejects_other_medium_and_host_image(trained):
                         frame.seed, frame.step, host_img, st)
     with pytest.raises(P.PivbosError):
         P.pivbos_surrogate_render(sg, bad2)
+
+
+def test_render_path_matches_per_ray_positions():
+    """The render path (prep -> tcgen05 network -> finish, plus the plain
+    fallback list) against the per-ray API: every ray's surrogate sensor
+    position deposited by the oracle's Eq. 8 deposit must give the render's
+    image (up to the FP32-versus-FP64 spot weights) and the same status
+    counts."""
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    frame = scenes.c4(scale=0.001, grid=64)[0]
+    med, opt = gpu_handles(frame)
+    src = torch.tensor(frame.sources, dtype=torch.float64, device="cuda")
+    img = torch.zeros((frame.optics.height, frame.optics.width), dtype=torch.int64, device="cuda")
+    st = torch.zeros(P.RAY_NSTATUS, dtype=torch.int64, device="cuda")
+    desc = P.frame_desc(med.h, opt.h, src, len(frame.sources), frame.rays_per_source, frame.frame_index,
+                        frame.seed, frame.step, img, st)
+    cfg = _cfg(P, n_train=1_000_000, n_val=400_000, epochs=3, min_bin_count=2, err_budget_px=0.002)
+    sg, rep = P.pivbos_surrogate_train(desc, frame.integrator, cfg)
+    try:
+        n_fb = P.pivbos_surrogate_render(sg, desc, count_fallback=True)
+        total = frame.n_rays
+        assert n_fb < total                # the served path is exercised
+        ids = torch.arange(total, dtype=torch.int64, device="cuda")
+        xy = torch.empty((total, 2), dtype=torch.float64, device="cuda")
+        flags = torch.empty(total, dtype=torch.int32, device="cuda")
+        status = torch.empty(total, dtype=torch.int32, device="cuda")
+        P.pivbos_surrogate_sensor(sg, desc, ids, xy, flags, status)
+        xy, flags, status = xy.cpu().numpy(), flags.cpu().numpy(), status.cpu().numpy()
+    finally:
+        P.pivbos_surrogate_destroy(sg)
+    assert int((flags == 1).sum()) == n_fb
+    stats = st.cpu().numpy()
+    for code in range(P.RAY_NSTATUS):
+        assert stats[code] == int((status == code).sum()), code
+    oo = oracle.Optics.from_scene(frame.optics)
+    ref = np.zeros((frame.optics.height, frame.optics.width), dtype=np.int64)
+    for (px, py) in xy[status == 0]:
+        oracle.deposit(oo, float(px), float(py), ref)
+    got = img.cpu().numpy()
+    assert got.sum() == ref.sum() == stats[0] * (1 << 32)
+    rel = np.linalg.norm((got - ref).astype(np.float64)) / np.linalg.norm(ref.astype(np.float64))
+    print("render vs per-ray positions: rel L2 %.2e, %d fallback of %d" % (rel, n_fb, total))
+    assert rel < 1e-5
