@@ -79,10 +79,17 @@ __device__ __forceinline__ void issue_layer(const Net& S, int l, uint32_t a_sadd
     const uint32_t w = l < 4 ? umma::smem_addr(S.wh[l - 1]) : umma::smem_addr(S.w4);
     const uint32_t lbo_w = l < 4 ? kLboW : kLboW4;
     const uint32_t idesc = umma::make_idesc_bf16(kRows, l < 4 ? kMlpHidden : kOutN);
-#pragma unroll 1
-    for (int ks = 0; ks < kMlpHidden / 16; ++ks)
-        umma::mma_bf16(d_tmem, umma::make_desc(a_saddr + ks * 2 * kLboA, kLboA, 128),
-                       umma::make_desc(w + ks * 2 * lbo_w, lbo_w, 128), idesc, ks > 0);
+    // successive K steps advance both start addresses by two core matrices
+    // along K: add (2 * LBO) >> 4 to the descriptors' address fields
+    uint64_t ad = umma::make_desc(a_saddr, kLboA, 128);
+    uint64_t bd = umma::make_desc(w, lbo_w, 128);
+    const uint64_t ainc = (2 * kLboA) >> 4, binc = (2 * lbo_w) >> 4;
+#pragma unroll
+    for (int ks = 0; ks < kMlpHidden / 16; ++ks) {
+        umma::mma_bf16(d_tmem, ad, bd, idesc, ks > 0);
+        ad += ainc;
+        bd += binc;
+    }
 }
 
 // Hidden-layer epilogue of this thread's row r: ReLU(D + b) as BF16 into the

@@ -729,8 +729,12 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
                 umma::fence_after_sync();
                 mlptc::issue_layer(sh.net, l, a_saddr, d_tmem);
                 umma::commit(&sh.bar[grp]);
+                // one thread polls; the rest of its warp parks at __syncwarp and
+                // the other warps at the named barrier, leaving the issue slots
+                // to the other warpgroups' epilogues
+                if (!umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit)) sh.failed[grp] = 1;
             }
-            if (!umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit)) sh.failed[grp] = 1;
+            __syncwarp();
             umma::named_sync(1 + grp, 128);
             if (sh.failed[grp]) {
                 bad = true;
