@@ -157,7 +157,8 @@ N_SM = 152
 # the sources each profiled kernel is compiled from
 KERNEL_SOURCES = {
     "render": ("render.cu", "trace.cuh", "df64.cuh", "common.cuh"),
-    "surrogate": ("surrogate.cu", "mlp_tc.cuh", "umma.cuh", "mlp.cuh", "trace.cuh", "df64.cuh", "common.cuh"),
+    "surrogate": ("surrogate.cu", "surrogate_kernels.cuh", "mlp_tc.cuh", "umma.cuh", "mlp.cuh", "trace.cuh",
+                  "df64.cuh", "common.cuh"),
 }
 
 
@@ -188,6 +189,12 @@ def ops_per_ray(frame, mean_steps):
     return OPS_RAY_BASE + surf + OPS_STEP[frame.integrator] * mean_steps
 
 
+# field gathers: 8 corners x 16 B per evaluation of D; RK4 evaluates 3 times per step
+GATHER_BYTES_PER_EVAL = 8 * 16
+EVALS_PER_STEP = {scenes.RK4: 3, scenes.EULER: 1}
+L1_BYTES_PER_CLK_PER_SM = 128
+
+
 def roofline(frames, mean_steps, render_ms, render_launches, sm_max_mhz, traffic=None):
     if render_launches == 0:
         return None
@@ -195,12 +202,23 @@ def roofline(frames, mean_steps, render_ms, render_launches, sm_max_mhz, traffic
     rays = sum(f.n_rays for f in frames) / len(frames)
     ops = sum(ops_per_ray(f, ms) * f.n_rays for f, ms in zip(frames, mean_steps)) / len(frames)
     achieved = ops / t / 1e12
-    peak = N_SM * ISSUE_LANES_PER_SM * (sm_max_mhz or 2070.0) * 1e6 / 1e12
-    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic,
-            "kernel": "render_kernel", "op": "FP32/INT32 lane operation (1 per lane instruction)",
-            "peak_source": "issue rate derived from 152 SMs x 128 lanes x max SM clock",
-            "ops_per_ray": round(ops / rays, 1), "launch_ms": round(t * 1e3, 4), "rays_per_launch": int(rays)}
+    clk = (sm_max_mhz or 2070.0) * 1e6
+    peak = N_SM * ISSUE_LANES_PER_SM * clk / 1e12
+    out = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+           "frac": round(achieved / peak, 4), "traffic": traffic,
+           "kernel": "render_kernel", "op": "FP32/INT32 lane operation (1 per lane instruction)",
+           "peak_source": "issue rate derived from 152 SMs x 128 lanes x max SM clock",
+           "ops_per_ray": round(ops / rays, 1), "launch_ms": round(t * 1e3, 4), "rays_per_launch": int(rays)}
+    if all(f.medium is not None for f in frames):
+        # the same launch against the L1 data path, for the field gathers
+        gbytes = sum(GATHER_BYTES_PER_EVAL * EVALS_PER_STEP[f.integrator] * ms * f.n_rays
+                     for f, ms in zip(frames, mean_steps)) / len(frames)
+        gpeak = N_SM * L1_BYTES_PER_CLK_PER_SM * clk / 1e9
+        out["gather"] = {"bound": "l1", "achieved": round(gbytes / t / 1e9, 1), "peak": round(gpeak, 1),
+                         "unit": "GB/s", "frac": round(gbytes / t / 1e9 / gpeak, 4),
+                         "bytes_per_ray": round(gbytes / rays, 1),
+                         "peak_source": "152 SMs x 128 B/clk L1 data path x max SM clock"}
+    return out
 
 
 def mean_steps(P, frame, opt, med, src_d, n=65536):

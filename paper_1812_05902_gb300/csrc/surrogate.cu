@@ -119,784 +119,7 @@ pivbos_status pivbos_mlp_loss_grad(const float* params, const float* x, const fl
 
 }  // extern "C"
 
-// ===========================================================================
-// Surrogate ray map: data, training, confidence map, rendering
-// ===========================================================================
-#include "mlp_tc.cuh"
-#include "trace.cuh"
-
-namespace pivbos {
-
-// Geometry and normalisation of one trained surrogate (device copy).
-struct SurrParams {
-    dfc z_lo;                       // box front (entry plane for sources in front of the box)
-    dfc z_ref;                      // reference plane of the exit-line residual
-    float cx, cy, cz, hx, hy, hz;   // box centre and half extents (feature scaling)
-    float u_scale;                  // slope scaling
-    float t_scale[4];               // network output scales: dx, dy (m) at z_ref, dux, duy
-    float b_scale[4];               // scales of the projection (Born) residual as network input
-    int nbx, nby, nbz, nbu;         // confidence bins
-    const uint32_t* bin_ok;         // bit b set: bin b is served by the network
-    int use_net;                    // 0: the projection residual alone
-    // projection table: suffix integrals of grad n along lines through the
-    // pupil centre (0, 0, aim_z), columns indexed by where they cross z_hi
-    const float4* table;            // [level][row][col][2]: {Gx, Gy, Gz, 0}, {Hx, Hy, Hz, 0}
-    int tnx, tny, tnz, born_k;      // columns, levels; segments per ray (0: no projection)
-    float t_x0, t_y0, t_inv_dx, t_inv_dy, t_inv_dz;
-    float zlo_f, zhi_f, aim_z, persp;   // persp = aim_z - z_hi
-};
-
-constexpr int kSurrBins = 16 * 16 * 16 * 4 * 4;
-
-struct Entry {
-    bool enters;
-    float f[5];    // entry x, y, z, slope x, slope y (scaled to about [-1, 1])
-    int bin;
-    df xs, ys;     // straight line at the reference plane
-    df ux, uy;     // slopes dx/dz, dy/dz of the straight ray
-    float xe, ye, ze;   // entry point (m)
-};
-
-__device__ __forceinline__ int bin_of(float f, int nb)
-{
-    const int b = (int)floorf((f + 1.0f) * 0.5f * (float)nb);
-    return min(max(b, 0), nb - 1);
-}
-
-// Entry state of a ray (source s, unit direction d): the straight line's
-// point on the plane z = max(z_lo, s_z), its slopes, the confidence bin, and
-// the straight line at the reference plane.
-__device__ __forceinline__ void surr_entry(const TraceParams& P, const SurrParams& S, df sx, df sy, df sz, df dx,
-                                           df dy, df dz, Entry& e)
-{
-    df tn;
-    e.enters = box_entry(P.m, sx, sy, sz, dx, dy, dz, tn);
-    const df inv_dz = df_rcp(dz);
-    e.ux = df_mul(dx, inv_dz);
-    e.uy = df_mul(dy, inv_dz);
-    const df ze = df_lt(sz, dfk(S.z_lo)) ? dfk(S.z_lo) : sz;
-    const df dze = df_sub(ze, sz);
-    const df xe = df_fma(e.ux, dze, sx), ye = df_fma(e.uy, dze, sy);
-    const df dzr = df_sub(dfk(S.z_ref), sz);
-    e.xs = df_fma(e.ux, dzr, sx);
-    e.ys = df_fma(e.uy, dzr, sy);
-    e.xe = xe.hi + xe.lo;
-    e.ye = ye.hi + ye.lo;
-    e.ze = ze.hi + ze.lo;
-    e.f[0] = (xe.hi - S.cx) / S.hx;
-    e.f[1] = (ye.hi - S.cy) / S.hy;
-    e.f[2] = (ze.hi - S.cz) / S.hz;
-    e.f[3] = e.ux.hi / S.u_scale;
-    e.f[4] = e.uy.hi / S.u_scale;
-    const int bu = bin_of(e.f[3], S.nbu) * S.nbu + bin_of(e.f[4], S.nbu);
-    e.bin = ((bin_of(e.f[0], S.nbx) * S.nby + bin_of(e.f[1], S.nby)) * S.nbz + bin_of(e.f[2], S.nbz)) *
-                (S.nbu * S.nbu) + bu;
-}
-
-// Table value at column coordinates (xi, eta) and depth z: bilinear across
-// columns, linear across levels; zero for columns outside the table (lines
-// that miss the box).
-__device__ __forceinline__ void table_lookup(const SurrParams& S, float xi, float eta, float z, float3& G, float3& H)
-{
-    const float fx = (xi - S.t_x0) * S.t_inv_dx, fy = (eta - S.t_y0) * S.t_inv_dy;
-    G = make_float3(0.f, 0.f, 0.f);
-    H = make_float3(0.f, 0.f, 0.f);
-    if (!(fx >= 0.0f && fy >= 0.0f && fx <= (float)(S.tnx - 1) && fy <= (float)(S.tny - 1))) return;
-    const float fz = fminf(fmaxf((z - S.zlo_f) * S.t_inv_dz, 0.0f), (float)(S.tnz - 1));
-    const int i = min((int)fx, S.tnx - 2), j = min((int)fy, S.tny - 2), l = min((int)fz, S.tnz - 2);
-    const float ax = fx - (float)i, ay = fy - (float)j, az = fz - (float)l;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int di = c & 1, dj = (c >> 1) & 1, dl = c >> 2;
-        const float w = (di ? ax : 1.0f - ax) * (dj ? ay : 1.0f - ay) * (dl ? az : 1.0f - az);
-        const float4* p = S.table + 2 * (((size_t)(l + dl) * S.tny + (j + dj)) * S.tnx + (i + di));
-        const float4 g = __ldg(p), h = __ldg(p + 1);
-        G.x = fmaf(w, g.x, G.x); G.y = fmaf(w, g.y, G.y); G.z = fmaf(w, g.z, G.z);
-        H.x = fmaf(w, h.x, H.x); H.y = fmaf(w, h.y, H.y); H.z = fmaf(w, h.z, H.z);
-    }
-}
-
-// Projection (Born-type) exit-line residual of a ray from its entry point
-// with straight slopes (ux, uy): dT/ds = grad n (the ray equation with
-// dt = ds / n) integrated along the line cut into born_k segments, each
-// segment's integrals taken from the table column through the segment's
-// midpoint.  The midpoint is moved by the displacement the earlier segments
-// have already produced, so the integrals follow the deflected path
-// (first-order accurate in each segment, self-consistent along the ray).
-// r = {dx, dy at z_ref, dux, duy}.
-__device__ __forceinline__ void born_residual(const SurrParams& S, const Entry& e, float* r)
-{
-    r[0] = r[1] = r[2] = r[3] = 0.0f;
-    if (S.born_k <= 0 || !e.enters) return;
-    const float ux = e.ux.hi, uy = e.uy.hi;
-    const float q = 1.0f + ux * ux + uy * uy;   // slope change (T_perp - u T_z) / T_z with T = n d, ds = dz sqrt(1+u^2)
-    const float dzs = (S.zhi_f - e.ze) / (float)S.born_k;
-    // accumulated slope-change integrals of the segments done so far:
-    // gx, gy = sum of (G_perp - u G_z); hx, hy = the same with weight (z - z_hi)
-    float gx = 0.f, gy = 0.f, hx = 0.f, hy = 0.f;
-#pragma unroll 1
-    for (int k = 0; k < S.born_k; ++k) {
-        const float za = e.ze + (float)k * dzs, zb = za + dzs, zm = za + 0.5f * dzs;
-        // displacement at zm from the earlier segments' kinks
-        const float dxm = q * ((zm - S.zhi_f) * gx - hx), dym = q * ((zm - S.zhi_f) * gy - hy);
-        const float c = S.persp / (S.aim_z - zm);
-        const float xi = (e.xe + ux * (zm - e.ze) + dxm) * c, eta = (e.ye + uy * (zm - e.ze) + dym) * c;
-        float3 Ga, Ha, Gb, Hb;
-        table_lookup(S, xi, eta, za, Ga, Ha);
-        table_lookup(S, xi, eta, zb, Gb, Hb);
-        const float Gx = Ga.x - Gb.x, Gy = Ga.y - Gb.y, Gz = Ga.z - Gb.z;
-        const float Hx = Ha.x - Hb.x, Hy = Ha.y - Hb.y, Hz = Ha.z - Hb.z;
-        gx += Gx - ux * Gz;
-        gy += Gy - uy * Gz;
-        hx += Hx - ux * Hz;
-        hy += Hy - uy * Hz;
-    }
-    const float zr = S.z_ref.hi + S.z_ref.lo - S.zhi_f;
-    r[0] = q * (zr * gx - hx);
-    r[1] = q * (zr * gy - hy);
-    r[2] = q * gx;
-    r[3] = q * gy;
-}
-
-// Network input: each entry feature as a BF16 value and its BF16-rounded
-// remainder times 256 (16 significant bits in all), then the scaled
-// projection residual, zero padded.
-__device__ __forceinline__ void encode_features(const SurrParams& S, const float* f, const float* born,
-                                                __nv_bfloat16* x)
-{
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-        const __nv_bfloat16 hi = __float2bfloat16(f[c]);
-        x[c] = hi;
-        x[5 + c] = __float2bfloat16((f[c] - __bfloat162float(hi)) * 256.0f);
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) x[10 + c] = __float2bfloat16(born[c] / S.b_scale[c]);
-    x[14] = x[15] = __float2bfloat16(0.0f);
-}
-
-// Exit line from the residual r (m, m, rad, rad): a point on the reference
-// plane and the unit direction.
-__device__ __forceinline__ void surr_exit(const SurrParams& S, const Entry& e, const float* r, df& Rx, df& Ry, df& Rz,
-                                          df& dx, df& dy, df& dz)
-{
-    Rx = df_add_f(e.xs, r[0]);
-    Ry = df_add_f(e.ys, r[1]);
-    Rz = dfk(S.z_ref);
-    const df ux = df_add_f(e.ux, r[2]);
-    const df uy = df_add_f(e.uy, r[3]);
-    const df inn = df_rsqrt(df_add_f(df_add(df_sqr(ux), df_sqr(uy)), 1.0f));
-    dx = df_mul(ux, inn);
-    dy = df_mul(uy, inn);
-    dz = inn;
-}
-
-// Full residual: projection plus the network's correction (y scaled).
-__device__ __forceinline__ void surr_residual(const SurrParams& S, const float* born, const float* y, float* r)
-{
-#pragma unroll
-    for (int c = 0; c < 4; ++c) r[c] = born[c] + (S.use_net ? y[c] * S.t_scale[c] : 0.0f);
-}
-
-// Seeded sample of ray ids of a frame (Philox counter (q, stream, frame, 2)).
-__device__ __forceinline__ uint64_t sample_ray(const TraceParams& P, uint64_t q, uint32_t stream, uint64_t seed,
-                                               uint64_t total)
-{
-    uint64_t w0, w1;
-    philox_lens_words(q, stream, P.frame, 2ull, seed, 0ull, w0, w1);
-    return w0 % total;
-}
-
-// Source (as given, FP64 -> double-float) and direction of a ray by id.
-__device__ __forceinline__ void ray_by_id(const TraceParams& P, uint64_t id, uint32_t& sid, uint32_t& k, df& sx,
-                                          df& sy, df& sz, df& dx, df& dy, df& dz)
-{
-    const uint32_t rps = P.rays_per_source;
-    sid = (uint32_t)(id / rps);
-    k = (uint32_t)(id - (uint64_t)sid * rps);
-    const double* sp = P.sources + 3 * (size_t)sid;
-    sx = df_from_double(sp[0]);
-    sy = df_from_double(sp[1]);
-    sz = df_from_double(sp[2]);
-    ray_start(P, sx, sy, sz, sid + P.source_offset, k, dx, dy, dz);
-}
-
-// Projection table: one thread per column; the column's line is followed
-// from z_hi down to z_lo, grad n sampled (trilinear, as the tracer samples
-// it; zero outside the box) at the midpoints of `sub` sub-steps per level.
-__global__ void surr_table_kernel(const DevMedium m, SurrParams S, int sub, float4* __restrict__ table)
-{
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= S.tnx * S.tny) return;
-    const int i = col % S.tnx, j = col / S.tnx;
-    const float xi = S.t_x0 + (float)i / S.t_inv_dx, eta = S.t_y0 + (float)j / S.t_inv_dy;
-    const double lo0 = m.lo[0].hi + (double)m.lo[0].lo, hi0 = m.hi[0].hi + (double)m.hi[0].lo;
-    const double lo1 = m.lo[1].hi + (double)m.lo[1].lo, hi1 = m.hi[1].hi + (double)m.hi[1].lo;
-    const double ox = m.origin[0].hi + (double)m.origin[0].lo, oy = m.origin[1].hi + (double)m.origin[1].lo;
-    const double oz = m.origin[2].hi + (double)m.origin[2].lo;
-    const double dzl = 1.0 / S.t_inv_dz, h = dzl / sub;
-    double G[3] = {0, 0, 0}, H[3] = {0, 0, 0};
-    for (int l = S.tnz - 1; l >= 0; --l) {
-        if (l < S.tnz - 1) {
-            const double zt = S.zlo_f + (double)(l + 1) * dzl;
-            for (int q = 0; q < sub; ++q) {
-                const double z = zt - (q + 0.5) * h;
-                const double c = (S.aim_z - z) / S.persp;
-                const double x = xi * c, y = eta * c;
-                if (x < lo0 || x > hi0 || y < lo1 || y > hi1) continue;
-                const float4 v = sample_field(m, (float)((x - ox) * m.inv_h[0]), (float)((y - oy) * m.inv_h[1]),
-                                              (float)((z - oz) * m.inv_h[2]));
-                const double wz = (z - S.zhi_f) * h;
-                G[0] += v.y * h; G[1] += v.z * h; G[2] += v.w * h;
-                H[0] += v.y * wz; H[1] += v.z * wz; H[2] += v.w * wz;
-            }
-        }
-        float4* p = table + 2 * (((size_t)l * S.tny + j) * S.tnx + i);
-        p[0] = make_float4((float)G[0], (float)G[1], (float)G[2], 0.f);
-        p[1] = make_float4((float)H[0], (float)H[1], (float)H[2], 0.f);
-    }
-}
-
-// Truth (plain path) and projection residuals of one ray.
-template <int INTEG>
-__device__ __forceinline__ void truth_and_born(const TraceParams& P, const SurrParams& S, uint64_t id, Entry& e,
-                                               pivbos_ray_state& st, float* t, float* born)
-{
-    uint32_t sid, k;
-    df sx, sy, sz, dx, dy, dz;
-    ray_by_id(P, id, sid, k, sx, sy, sz, dx, dy, dz);
-    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
-    born_residual(S, e, born);
-    RayOut r;
-    trace_ray<INTEG, false>(P, sx, sy, sz, sid + P.source_offset, k, r, &st);
-    t[0] = t[1] = t[2] = t[3] = 0.0f;
-    if (st.status != PIVBOS_RAY_MAXSTEP) {
-        // the exit line (straight beyond the box) against the straight ray,
-        // both taken at the reference plane
-        const double zr = df_to_double(dfk(S.z_ref));
-        const double* sp = P.sources + 3 * (size_t)sid;
-        const double uxd = df_to_double(e.ux), uyd = df_to_double(e.uy);
-        const double Dx = st.vol_dir[0] / st.vol_dir[2], Dy = st.vol_dir[1] / st.vol_dir[2];
-        const double xt = st.vol_pos[0] + (zr - st.vol_pos[2]) * Dx;
-        const double yt = st.vol_pos[1] + (zr - st.vol_pos[2]) * Dy;
-        t[0] = (float)(xt - (sp[0] + (zr - sp[2]) * uxd));
-        t[1] = (float)(yt - (sp[1] + (zr - sp[2]) * uyd));
-        t[2] = (float)(Dx - uxd);
-        t[3] = (float)(Dy - uyd);
-    }
-}
-
-// Pilot statistics on a few rays: mean squares of the truth residual, of
-// the projection residual and of their difference ([0..11]), the sensor
-// shift per unit of each residual component by finite differences about
-// the straight ray ([12..15], [16] = rays counted), and for each candidate
-// segment count kc = 1, 2, 4, ..., the squared sensor error of the
-// projection alone against the plain path ([17 + c], [17 + kPilotK] =
-// rays compared).
-constexpr int kPilotK = 6;   // candidates 1, 2, 4, 8, 16, 32
-
-template <int INTEG>
-__global__ void surr_pilot_kernel(const TraceParams P, const SurrParams S, uint64_t total, int64_t n, uint64_t seed,
-                                  double dpos, double dslope, double* __restrict__ acc)
-{
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    constexpr int NV = 18 + kPilotK;
-    double v[NV];
-#pragma unroll
-    for (int c = 0; c < NV; ++c) v[c] = 0.0;
-    if (q < n) {
-        Entry e;
-        pivbos_ray_state st;
-        float t[4], born[4];
-        truth_and_born<INTEG>(P, S, sample_ray(P, (uint64_t)q, 3, seed, total), e, st, t, born);
-        for (int c = 0; c < 4; ++c) {
-            v[c] = (double)t[c] * t[c];
-            v[4 + c] = (double)born[c] * born[c];
-            v[8 + c] = (double)(t[c] - born[c]) * (t[c] - born[c]);
-        }
-        double px[5], py[5];
-        bool ok = true;
-#pragma unroll 1
-        for (int c = 0; c < 5; ++c) {
-            float r[4] = {0.f, 0.f, 0.f, 0.f};
-            if (c > 0) r[c - 1] = (float)(c <= 2 ? dpos : dslope);
-            df Rx, Ry, Rz, ex, ey, ez;
-            surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
-            int status = PIVBOS_RAY_REACHED;
-            df a, b;
-            optics_to_sensor(P.o, Rx, Ry, Rz, ex, ey, ez, status, a, b);
-            ok = ok && status == PIVBOS_RAY_REACHED;
-            px[c] = df_to_double(a);
-            py[c] = df_to_double(b);
-        }
-        if (ok) {
-            for (int c = 1; c < 5; ++c) {
-                const double d = c <= 2 ? dpos : dslope;
-                const double ax = px[c] - px[0], ay = py[c] - py[0];
-                v[11 + c] = (ax * ax + ay * ay) / (d * d);
-            }
-            v[16] = 1.0;
-        }
-        if (S.born_k != 0 && e.enters && st.status == PIVBOS_RAY_REACHED) {
-            bool all = true;
-            double err[kPilotK];
-#pragma unroll 1
-            for (int c = 0; c < kPilotK; ++c) {
-                SurrParams Sk = S;
-                Sk.born_k = 1 << c;
-                float r[4];
-                born_residual(Sk, e, r);
-                df Rx, Ry, Rz, ex, ey, ez;
-                surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
-                int status = PIVBOS_RAY_REACHED;
-                df a, b;
-                optics_to_sensor(P.o, Rx, Ry, Rz, ex, ey, ez, status, a, b);
-                all = all && status == PIVBOS_RAY_REACHED;
-                const double dx = df_to_double(a) - st.sensor_xy[0], dy = df_to_double(b) - st.sensor_xy[1];
-                err[c] = dx * dx + dy * dy;
-            }
-            if (all) {
-                for (int c = 0; c < kPilotK; ++c) v[17 + c] = err[c];
-                v[17 + kPilotK] = 1.0;
-            }
-        }
-    }
-    for (int c = 0; c < NV; ++c) {
-        for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
-        if ((threadIdx.x & 31) == 0 && v[c] != 0.0) atomicAdd(&acc[c], v[c]);
-    }
-}
-
-// S1: samples of (encoded entry features and projection residual, scaled
-// correction truth - projection) traced by the plain path.  For held-out
-// samples also the plain sensor position, status and step count.
-template <int INTEG>
-__global__ void surr_data_kernel(const TraceParams P, const SurrParams S, uint64_t total, int64_t n, uint32_t stream,
-                                 uint64_t seed, __nv_bfloat16* __restrict__ X, float* __restrict__ T,
-                                 uint64_t* __restrict__ ids, double* __restrict__ ref_px, int* __restrict__ ref_st)
-{
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    const uint64_t id = sample_ray(P, (uint64_t)q, stream, seed, total);
-    Entry e;
-    pivbos_ray_state st;
-    float t[4], born[4];
-    truth_and_born<INTEG>(P, S, id, e, st, t, born);
-    encode_features(S, e.f, born, X + (size_t)q * kMlpIn);
-    if (T)
-        *reinterpret_cast<float4*>(T + (size_t)q * 4) =
-            make_float4((t[0] - born[0]) / S.t_scale[0], (t[1] - born[1]) / S.t_scale[1],
-                        (t[2] - born[2]) / S.t_scale[2], (t[3] - born[3]) / S.t_scale[3]);
-    if (ids) ids[q] = id;
-    if (ref_px) {
-        ref_px[2 * q] = st.sensor_xy[0];
-        ref_px[2 * q + 1] = st.sensor_xy[1];
-        ref_st[q] = st.status | (st.steps << 3);
-    }
-}
-
-// Per-bin sums over held-out rays that reach the sensor in the plain path,
-// for three predictors: the network (projection + correction), the
-// projection alone, and the straight ray.
-struct BinAcc {
-    double* err2[3];     // squared sensor error (px^2) per predictor
-    double* steps;       // plain-path integration steps (the work a served ray saves)
-    unsigned int* cnt;
-    double* tot;         // [0] rays reaching the sensor, [1] those entering the box,
-                         // [2..4] of these, rays each predictor sends elsewhere
-};
-
-// Confidence map: the plain tracer judges each predictor at the sensor.
-// A ray whose status differs from the plain path's (one grazing a stop)
-// has no displacement: it is counted, not summed.
-__global__ void surr_eval_kernel(const TraceParams P, const SurrParams S, const uint64_t* __restrict__ ids,
-                                 const float* __restrict__ Y, const double* __restrict__ ref_px,
-                                 const int* __restrict__ ref_st, int64_t n, BinAcc acc)
-{
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    if ((ref_st[q] & 7) != PIVBOS_RAY_REACHED) return;
-    atomicAdd(&acc.tot[0], 1.0);
-    uint32_t sid, k;
-    df sx, sy, sz, dx, dy, dz;
-    ray_by_id(P, ids[q], sid, k, sx, sy, sz, dx, dy, dz);
-    Entry e;
-    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
-    if (!e.enters) return;
-    atomicAdd(&acc.tot[1], 1.0);
-    float born[4], y[4];
-    born_residual(S, e, born);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) y[c] = Y[q * 4 + c];
-#pragma unroll 1
-    for (int v = 0; v < 3; ++v) {
-        float r[4] = {0.f, 0.f, 0.f, 0.f};
-        if (v == 0) {
-            for (int c = 0; c < 4; ++c) r[c] = born[c] + y[c] * S.t_scale[c];
-        } else if (v == 1) {
-            for (int c = 0; c < 4; ++c) r[c] = born[c];
-        }
-        df Rx, Ry, Rz, ex, ey, ez;
-        surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
-        int status = PIVBOS_RAY_REACHED;
-        df px, py;
-        optics_to_sensor(P.o, Rx, Ry, Rz, ex, ey, ez, status, px, py);
-        if (status == PIVBOS_RAY_REACHED) {
-            const double a = df_to_double(px) - ref_px[2 * q], b = df_to_double(py) - ref_px[2 * q + 1];
-            atomicAdd(&acc.err2[v][e.bin], a * a + b * b);
-        } else {
-            atomicAdd(&acc.tot[2 + v], 1.0);
-        }
-    }
-    atomicAdd(&acc.steps[e.bin], (double)(ref_st[q] >> 3));
-    atomicAdd(&acc.cnt[e.bin], 1u);
-}
-
-// ---------------------------------------------------------------------------
-// Surrogate render in three kernels over chunks of the frame's rays:
-// prep (features, projection, serve / fall back) -> network (tcgen05) ->
-// finish (exit line, optics, tile deposit).  Each runs at its own
-// occupancy; the served rays pass between them in ray order.
-// ---------------------------------------------------------------------------
-struct ServedList {
-    uint32_t* ids;              // flat ray index; top bit: never enters the box (straight)
-    __nv_bfloat16* X;           // [capacity][16] network input
-    float4* B;                  // [capacity] projection residual
-    float4* R;                  // [capacity] full residual (projection + correction)
-    float4* L;                  // [capacity][2] straight line: x, y at z_ref and slopes, double-float
-    unsigned long long* count;  // rays appended
-    uint32_t capacity;
-};
-
-constexpr uint32_t kStraightBit = 0x80000000u;
-
-// Append the calling CTA's flagged lanes (one atomic per CTA); returns this
-// thread's slot (meaningful where flag is set).  All threads call it.
-__device__ __forceinline__ unsigned long long block_append(bool flag, unsigned long long* counter, int* warp_off,
-                                                           unsigned long long* base)
-{
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-    const unsigned m = __ballot_sync(0xffffffffu, flag);
-    __syncthreads();
-    if (lane == 0) warp_off[warp] = __popc(m);
-    __syncthreads();
-    if (tid == 0) {
-        int tot = 0;
-        for (int w = 0; w < nw; ++w) {
-            const int c = warp_off[w];
-            warp_off[w] = tot;
-            tot += c;
-        }
-        *base = tot ? atomicAdd(counter, (unsigned long long)tot) : 0ull;
-    }
-    __syncthreads();
-    return *base + (unsigned long long)(warp_off[warp] + __popc(m & ((1u << lane) - 1u)));
-}
-
-// Prep: rays [c0, c1) of the Morton-ordered (slot, ray) space, 256 per CTA
-// round; served rays (and rays that never enter the box) go to the served
-// list with their network input and projection residual, the others to the
-// fallback list.
-__global__ void __launch_bounds__(256)
-surr_prep_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t c1, ServedList sv,
-                 uint32_t* __restrict__ fb_ids, unsigned long long* __restrict__ fb_count, uint32_t fb_capacity)
-{
-    __shared__ int warp_off[8];
-    __shared__ unsigned long long base;
-    __shared__ uint32_t order[kMaxOrderRays];
-    const uint32_t rps = P.rays_per_source;
-    // items of kMaxOrderRays rays; with many projection segments per ray an
-    // item's rays are taken in the order of where they cross the box
-    // mid-plane, so a warp's table gathers share columns
-    const uint64_t items = (c1 - c0 + kMaxOrderRays - 1) / kMaxOrderRays;
-    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
-        const uint64_t first = c0 + it * kMaxOrderRays;
-        const uint32_t n_here = (uint32_t)(min(first + kMaxOrderRays, c1) - first);
-        const bool reorder = P.reorder && S.born_k >= 8;
-        if (reorder) order_chunk(P, order, first, n_here);
-        for (uint32_t r0 = 0; r0 < n_here; r0 += 256) {
-            const uint32_t pos = r0 + threadIdx.x;
-            const bool active = pos < n_here;
-            const uint64_t idx = first + (reorder && active ? (order[pos] & 0x7ffu) : pos);
-            int mode = 3;
-            Entry e;
-            e.enters = false;
-            e.f[0] = e.f[1] = e.f[2] = e.f[3] = e.f[4] = 0.0f;
-            float born[4] = {0.f, 0.f, 0.f, 0.f};
-            if (active) {
-                const uint32_t flat = (uint32_t)idx;
-                const uint32_t slot = flat / rps, k = flat - slot * rps;
-                const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
-                const float2* sp = P.src_df + 3 * (size_t)slot;
-                const float2 a = __ldg(sp), b = __ldg(sp + 1), c = __ldg(sp + 2);
-                df dx, dy, dz;
-                ray_start(P, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, sid, k, dx, dy, dz);
-                surr_entry(P, S, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, dx, dy, dz, e);
-                if (!e.enters) mode = 2;
-                else mode = ((__ldg(S.bin_ok + (e.bin >> 5)) >> (e.bin & 31)) & 1u) ? 0 : 1;
-                if (mode == 0) born_residual(S, e, born);
-            }
-            const unsigned long long ps = block_append(mode == 0 || mode == 2, sv.count, warp_off, &base);
-            if (mode == 0 || mode == 2) {
-                if (ps < sv.capacity) {
-                    sv.ids[ps] = (uint32_t)idx | (mode == 2 ? kStraightBit : 0u);
-                    __align__(16) __nv_bfloat16 x[kMlpIn];
-                    encode_features(S, e.f, born, x);
-                    uint4* xr = reinterpret_cast<uint4*>(sv.X + ps * kMlpIn);
-                    xr[0] = *reinterpret_cast<const uint4*>(&x[0]);
-                    xr[1] = *reinterpret_cast<const uint4*>(&x[8]);
-                    sv.B[ps] = make_float4(born[0], born[1], born[2], born[3]);
-                    sv.L[2 * ps] = make_float4(e.xs.hi, e.xs.lo, e.ys.hi, e.ys.lo);
-                    sv.L[2 * ps + 1] = make_float4(e.ux.hi, e.ux.lo, e.uy.hi, e.uy.lo);
-                } else {
-                    atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_OVERFLOW);   // cannot happen: capacity = chunk
-                }
-            }
-            const unsigned long long pf = block_append(mode == 1, fb_count, warp_off, &base);
-            if (mode == 1) {
-                if (pf < fb_capacity) fb_ids[pf] = (uint32_t)idx;
-                else atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_OVERFLOW);   // cannot happen: capacity = rays
-            }
-        }
-        __syncthreads();   // order[] is rewritten by the next item
-    }
-}
-
-// Network over the served list on tcgen05: three warpgroups per CTA, each
-// running its own 128-row tiles (its own operand buffer, TMEM columns and
-// mbarrier), so tiles of different warpgroups overlap.  R = B + y * scale.
-constexpr int kNetGroups = 3;
-struct NetSmem {
-    mlptc::Net net;
-    alignas(128) unsigned char a[kNetGroups][mlptc::kTileBytes];
-    uint64_t bar[kNetGroups];
-    uint32_t tmem_base;
-    int failed[kNetGroups];
-};
-
-__global__ void __launch_bounds__(128 * kNetGroups, 1)
-surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ params,
-                ServedList sv, int* __restrict__ status_word)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    NetSmem& sh = *reinterpret_cast<NetSmem*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, grp = warp >> 2, row = tid & 127;
-    mlptc::load_net(sh.net, wbf, params);
-    if (warp == 0) umma::tmem_alloc(&sh.tmem_base, 512);
-    if (tid < kNetGroups) {
-        umma::mbar_init(&sh.bar[tid], 1);
-        sh.failed[tid] = 0;
-    }
-    umma::fence_before_sync();
-    __syncthreads();
-    umma::fence_after_sync();
-    const uint32_t d_tmem = sh.tmem_base + (uint32_t)(grp * 128);
-    const uint32_t row_tmem = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const uint32_t a_saddr = umma::smem_addr(sh.a[grp]);
-    const uint64_t n = min(*sv.count, (unsigned long long)sv.capacity);
-    const uint64_t tiles = (n + mlptc::kRows - 1) / mlptc::kRows;
-    uint32_t parity = 0;
-    const uint64_t stride = (uint64_t)gridDim.x * kNetGroups;
-    // this thread's input row and projection residual, loaded one tile ahead
-    // so the loads overlap the previous tile's five layers
-    auto load_row = [&](uint64_t t, uint4& lo, uint4& hi, float4& b) {
-        const uint64_t r = t * mlptc::kRows + row;
-        lo = make_uint4(0u, 0u, 0u, 0u);
-        hi = lo;
-        b = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t < tiles && r < n) {
-            const uint4* xr = reinterpret_cast<const uint4*>(sv.X + r * kMlpIn);
-            lo = __ldcs(xr);
-            hi = __ldcs(xr + 1);
-            b = __ldcs(sv.B + r);
-        }
-    };
-    uint4 nlo, nhi;
-    float4 nb;
-    load_row((uint64_t)blockIdx.x * kNetGroups + grp, nlo, nhi, nb);
-    for (uint64_t t = (uint64_t)blockIdx.x * kNetGroups + grp; t < tiles; t += stride) {
-        const uint64_t r = t * mlptc::kRows + row;
-        const float4 b = nb;
-        mlptc::store_input_row(sh.a[grp], row, nlo, nhi);
-        load_row(t + stride, nlo, nhi, nb);
-        bool bad = false;
-#pragma unroll 1
-        for (int l = 0; l < kMlpLayers; ++l) {
-            umma::fence_async_smem();
-            umma::fence_before_sync();
-            umma::named_sync(1 + grp, 128);
-            if (row == 0) {
-                umma::fence_after_sync();
-                mlptc::issue_layer(sh.net, l, a_saddr, d_tmem);
-                umma::commit(&sh.bar[grp]);
-                // one thread polls; the rest of its warp parks at __syncwarp and
-                // the other warps at the named barrier, leaving the issue slots
-                // to the other warpgroups' epilogues
-                if (!umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit)) sh.failed[grp] = 1;
-            }
-            __syncwarp();
-            umma::named_sync(1 + grp, 128);
-            if (sh.failed[grp]) {
-                bad = true;
-                break;
-            }
-            parity ^= 1u;
-            umma::fence_after_sync();
-            if (l < kMlpLayers - 1) {
-                mlptc::epilogue_hidden2(row_tmem, sh.net.bias[l], sh.a[grp], row);
-            } else {
-                float y[kMlpOut];
-                mlptc::epilogue_out(row_tmem, sh.net.bias4, y);
-                if (r < n)
-                    __stcs(sv.R + r, make_float4(b.x + y[0] * S.t_scale[0], b.y + y[1] * S.t_scale[1],
-                                                 b.z + y[2] * S.t_scale[2], b.w + y[3] * S.t_scale[3]));
-            }
-        }
-        if (bad) break;
-    }
-    if (sh.failed[grp] && row == 0) {
-        atomicCAS(status_word, 0, (int)PIVBOS_ERR_DEVICE_TIMEOUT);
-        umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit);
-    }
-    umma::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) {
-        umma::fence_after_sync();
-        umma::tmem_dealloc(sh.tmem_base, 512);
-    }
-}
-
-// Finish: the served list in chunks of 256 consecutive entries (one round of
-// the prep kernel's rays: a few neighbouring sources), each chunk deposited
-// into a shared tile anchored at its first hit.
-__global__ void __launch_bounds__(256, 3)
-surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const float4* __restrict__ resid,
-                   int64_t* __restrict__ image, int64_t* __restrict__ stats, unsigned long long* __restrict__ counter)
-{
-    __shared__ unsigned long long tile[kTileW * kTileH];
-    __shared__ unsigned long long s_item;
-    __shared__ int anchor_tid, sax, say;
-    const int tid = threadIdx.x;
-    const uint64_t n = min(*sv.count, (unsigned long long)sv.capacity);
-    const uint64_t items = (n + 255) / 256;
-    unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
-    for (;;) {
-        if (tid == 0) {
-            s_item = atomicAdd(counter, 1ull);
-            anchor_tid = 0x7fffffff;
-        }
-        for (int q = tid; q < kTileW * kTileH; q += blockDim.x) tile[q] = 0ull;
-        __syncthreads();
-        const uint64_t it = s_item;
-        if (it >= items) break;
-        const uint64_t pos = it * 256 + tid;
-        RayOut r;
-        r.status = PIVBOS_RAY_MISS;
-        const bool active = pos < n;
-        if (active) {
-            // the straight line from the prep kernel, plus the residual (none
-            // for a ray that never enters the box)
-            const float4 l0 = sv.L[2 * pos], l1 = sv.L[2 * pos + 1];
-            Entry e;
-            e.xs = df{l0.x, l0.y};
-            e.ys = df{l0.z, l0.w};
-            e.ux = df{l1.x, l1.y};
-            e.uy = df{l1.z, l1.w};
-            float res[4] = {0.f, 0.f, 0.f, 0.f};
-            if (!(sv.ids[pos] & kStraightBit)) {
-                const float4 rv = resid[pos];
-                res[0] = rv.x; res[1] = rv.y; res[2] = rv.z; res[3] = rv.w;
-            }
-            df Rx, Ry, Rz, dx, dy, dz;
-            surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
-            r.status = PIVBOS_RAY_REACHED;
-            optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, r.status, r.px, r.py);
-            cnt[r.status]++;
-            if (r.status == PIVBOS_RAY_REACHED) atomicMin(&anchor_tid, tid);
-        }
-        __syncthreads();
-        if (tid == anchor_tid) {
-            float f;
-            sax = df_floor(r.px, f) - kTileW / 2;
-            say = df_floor(r.py, f) - kTileH / 2;
-        }
-        __syncthreads();
-        const int ax = anchor_tid == 0x7fffffff ? -(1 << 28) : sax;
-        const int ay = anchor_tid == 0x7fffffff ? -(1 << 28) : say;
-        if (active && r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, tile, ax, ay, image);
-        __syncthreads();
-        for (int q = tid; q < kTileW * kTileH; q += blockDim.x) {
-            const unsigned long long v = tile[q];
-            if (v) {
-                const int gx = ax + (q % kTileW), gy = ay + (q / kTileW);
-                atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * P.o.W + gx]), v);
-            }
-        }
-        __syncthreads();
-    }
-    if (stats) {
-#pragma unroll
-        for (int q = 0; q < PIVBOS_RAY_NSTATUS; ++q)
-            if (cnt[q]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[q]), (unsigned long long)cnt[q]);
-    }
-}
-
-// Per-ray surrogate sensor positions for checking (flag 0 surrogate, 1 plain
-// fallback (traced here), 2 never enters the box (straight)).
-template <int INTEG>
-__global__ void surr_sensor_kernel(const TraceParams P, const SurrParams S, const float* __restrict__ Y,
-                                   const int64_t* __restrict__ ids, int64_t n, double* __restrict__ out_px,
-                                   int* __restrict__ out_flag, int* __restrict__ out_status)
-{
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    uint32_t sid, k;
-    df sx, sy, sz, dx, dy, dz;
-    ray_by_id(P, (uint64_t)ids[q], sid, k, sx, sy, sz, dx, dy, dz);
-    Entry e;
-    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
-    const int flag = !e.enters ? 2 : (((S.bin_ok[e.bin >> 5] >> (e.bin & 31)) & 1u) ? 0 : 1);
-    int status = PIVBOS_RAY_REACHED;
-    df px = dfv(0.f), py = dfv(0.f);
-    if (flag == 1) {
-        RayOut r;
-        trace_ray<INTEG, false>(P, sx, sy, sz, sid + P.source_offset, k, r, nullptr);
-        status = r.status;
-        px = r.px;
-        py = r.py;
-    } else {
-        df Rx = sx, Ry = sy, Rz = sz;
-        if (flag == 0) {
-            float born[4], res[4];
-            born_residual(S, e, born);
-            surr_residual(S, born, Y + q * 4, res);
-            surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
-        }
-        optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, status, px, py);
-    }
-    out_px[2 * q] = df_to_double(px);
-    out_px[2 * q + 1] = df_to_double(py);
-    out_flag[q] = flag;
-    out_status[q] = status;
-}
-
-// Encoded features of given rays (the network input of surr_sensor_kernel).
-__global__ void surr_features_kernel(const TraceParams P, const SurrParams S, const int64_t* __restrict__ ids,
-                                     int64_t n, __nv_bfloat16* __restrict__ X)
-{
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    uint32_t sid, k;
-    df sx, sy, sz, dx, dy, dz;
-    ray_by_id(P, (uint64_t)ids[q], sid, k, sx, sy, sz, dx, dy, dz);
-    Entry e;
-    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
-    float born[4];
-    born_residual(S, e, born);
-    encode_features(S, e.f, born, X + (size_t)q * kMlpIn);
-}
-
-}  // namespace pivbos
+#include "surrogate_kernels.cuh"
 
 // ---------------------------------------------------------------------------
 // host side
