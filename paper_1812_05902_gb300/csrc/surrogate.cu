@@ -357,6 +357,7 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
             return scuda(e, "surrogate projection table");
         }
         S.table = sg->table;
+        S.table_h = sg->table + nodes;
         R.table_bytes = (double)(nodes * 2 * sizeof(float4));
     }
     R.seconds_table = now_s() - t_start;

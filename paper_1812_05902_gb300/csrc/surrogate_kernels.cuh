@@ -24,7 +24,8 @@ struct SurrParams {
     int use_net;                    // 0: the projection residual alone
     // projection table: suffix integrals of grad n along lines through the
     // pupil centre (0, 0, aim_z), columns indexed by where they cross z_hi
-    const float4* table;            // [level][row][col][2]: {Gx, Gy, Gz, 0}, {Hx, Hy, Hz, 0}
+    const float4* table;            // G plane [level][row][col] {Gx, Gy, Gz, 0}, then the H plane
+    const float4* table_h;          //   {Hx, Hy, Hz, 0} (= table + nodes)
     int tnx, tny, tnz, born_k;      // columns, levels; segments per ray (0: no projection)
     float t_x0, t_y0, t_inv_dx, t_inv_dy, t_inv_dz;
     float zlo_f, zhi_f, aim_z, persp;   // persp = aim_z - z_hi
@@ -79,7 +80,8 @@ __device__ __forceinline__ void surr_entry(const TraceParams& P, const SurrParam
 
 // Table value at column coordinates (xi, eta) and depth z: bilinear across
 // columns, linear across levels; zero for columns outside the table (lines
-// that miss the box).
+// that miss the box).  H only when WANT_H.
+template <bool WANT_H>
 __device__ __forceinline__ void table_lookup(const SurrParams& S, float xi, float eta, float z, float3& G, float3& H)
 {
     const float fx = (xi - S.t_x0) * S.t_inv_dx, fy = (eta - S.t_y0) * S.t_inv_dy;
@@ -93,10 +95,13 @@ __device__ __forceinline__ void table_lookup(const SurrParams& S, float xi, floa
     for (int c = 0; c < 8; ++c) {
         const int di = c & 1, dj = (c >> 1) & 1, dl = c >> 2;
         const float w = (di ? ax : 1.0f - ax) * (dj ? ay : 1.0f - ay) * (dl ? az : 1.0f - az);
-        const float4* p = S.table + 2 * (((size_t)(l + dl) * S.tny + (j + dj)) * S.tnx + (i + di));
-        const float4 g = __ldg(p), h = __ldg(p + 1);
+        const size_t node = ((size_t)(l + dl) * S.tny + (j + dj)) * S.tnx + (i + di);
+        const float4 g = __ldg(S.table + node);
         G.x = fmaf(w, g.x, G.x); G.y = fmaf(w, g.y, G.y); G.z = fmaf(w, g.z, G.z);
-        H.x = fmaf(w, h.x, H.x); H.y = fmaf(w, h.y, H.y); H.z = fmaf(w, h.z, H.z);
+        if constexpr (WANT_H) {
+            const float4 h = __ldg(S.table_h + node);
+            H.x = fmaf(w, h.x, H.x); H.y = fmaf(w, h.y, H.y); H.z = fmaf(w, h.z, H.z);
+        }
     }
 }
 
@@ -107,7 +112,9 @@ __device__ __forceinline__ void table_lookup(const SurrParams& S, float xi, floa
 // midpoint.  The midpoint is moved by the displacement the earlier segments
 // have already produced, so the integrals follow the deflected path
 // (first-order accurate in each segment, self-consistent along the ray).
-// r = {dx, dy at z_ref, dux, duy}.
+// With 8 or more segments a segment's first moment H is taken as its
+// midpoint offset times G (the table's H plane is read only for fewer,
+// longer segments).  r = {dx, dy at z_ref, dux, duy}.
 __device__ __forceinline__ void born_residual(const SurrParams& S, const Entry& e, float* r)
 {
     r[0] = r[1] = r[2] = r[3] = 0.0f;
@@ -126,10 +133,18 @@ __device__ __forceinline__ void born_residual(const SurrParams& S, const Entry& 
         const float c = S.persp / (S.aim_z - zm);
         const float xi = (e.xe + ux * (zm - e.ze) + dxm) * c, eta = (e.ye + uy * (zm - e.ze) + dym) * c;
         float3 Ga, Ha, Gb, Hb;
-        table_lookup(S, xi, eta, za, Ga, Ha);
-        table_lookup(S, xi, eta, zb, Gb, Hb);
+        float Hx, Hy, Hz;
+        if (S.born_k >= 8) {
+            table_lookup<false>(S, xi, eta, za, Ga, Ha);
+            table_lookup<false>(S, xi, eta, zb, Gb, Hb);
+            const float zo = zm - S.zhi_f;
+            Hx = zo * (Ga.x - Gb.x); Hy = zo * (Ga.y - Gb.y); Hz = zo * (Ga.z - Gb.z);
+        } else {
+            table_lookup<true>(S, xi, eta, za, Ga, Ha);
+            table_lookup<true>(S, xi, eta, zb, Gb, Hb);
+            Hx = Ha.x - Hb.x; Hy = Ha.y - Hb.y; Hz = Ha.z - Hb.z;
+        }
         const float Gx = Ga.x - Gb.x, Gy = Ga.y - Gb.y, Gz = Ga.z - Gb.z;
-        const float Hx = Ha.x - Hb.x, Hy = Ha.y - Hb.y, Hz = Ha.z - Hb.z;
         gx += Gx - ux * Gz;
         gy += Gy - uy * Gz;
         hx += Hx - ux * Hz;
@@ -235,9 +250,9 @@ __global__ void surr_table_kernel(const DevMedium m, SurrParams S, int sub, floa
                 H[0] += v.y * wz; H[1] += v.z * wz; H[2] += v.w * wz;
             }
         }
-        float4* p = table + 2 * (((size_t)l * S.tny + j) * S.tnx + i);
-        p[0] = make_float4((float)G[0], (float)G[1], (float)G[2], 0.f);
-        p[1] = make_float4((float)H[0], (float)H[1], (float)H[2], 0.f);
+        const size_t node = ((size_t)l * S.tny + j) * S.tnx + i;
+        table[node] = make_float4((float)G[0], (float)G[1], (float)G[2], 0.f);
+        table[(size_t)S.tnx * S.tny * S.tnz + node] = make_float4((float)H[0], (float)H[1], (float)H[2], 0.f);
     }
 }
 
