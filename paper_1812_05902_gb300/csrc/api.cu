@@ -118,16 +118,35 @@ uint32_t next_pow2(uint32_t v)
     return p;
 }
 
-uint32_t rays_per_cta_setting()
+}  // namespace
+
+// Rays per CTA of a render: PIVBOS_RAYS_PER_CTA if set, else 2048 in a
+// dense medium (where a CTA reorders up to 2048 rays) and 1024 otherwise.
+uint32_t rays_per_cta_setting(const TraceParams& p)
 {
-    static uint32_t v = 0;
-    if (v == 0) {
+    static long v = -1;
+    if (v < 0) {
         const char* s = getenv("PIVBOS_RAYS_PER_CTA");
-        long x = s ? strtol(s, nullptr, 10) : 0;
-        v = (x >= 256 && x <= (1 << 20)) ? (uint32_t)x : 2048u;
+        const long x = s ? strtol(s, nullptr, 10) : 0;
+        v = (x >= 256 && x <= (1 << 20)) ? x : 0;
     }
-    return v;
+    return v ? (uint32_t)v : (p.reorder ? 2048u : 1024u);
 }
+
+// Gather strategy for a medium: reorder a CTA's rays when a ray makes many
+// field evaluations (the box depth in steps times the stages per step); keep
+// the last cell's corners in registers when, in addition, a step is short
+// against every grid spacing, so that consecutive stages mostly fall in one
+// cell (PIVBOS_CELL_CACHE overrides).
+void choose_gather(const pivbos_medium* m, double step, int integrator, TraceParams& p)
+{
+    const double evals = (double)(m->n[2] - 1) * m->spacing[2] / step * (integrator == PIVBOS_RK4 ? 3.0 : 1.0);
+    p.reorder = evals >= 64.0 ? 1 : 0;
+    const double hmin = fmin(m->spacing[0], fmin(m->spacing[1], m->spacing[2]));
+    p.cell_cache = tuning_cell_cache(p.reorder && step < 0.75 * hmin);
+}
+
+namespace {
 
 // Common validation and parameter assembly for render / trace_exit_states.
 struct Prepared {
@@ -183,11 +202,7 @@ pivbos_status prepare(const pivbos_medium* m, const pivbos_optics* o, const doub
         if (ms > 2.0e9) return fail(PIVBOS_ERR_UNSUPPORTED, "step too small for the box (%g steps)", ms);
         p.max_steps = (int)ms;
         p.m.z_key = (float)(m->origin[2] + 0.5 * (double)(m->n[2] - 1) * m->spacing[2]);
-        // reorder rays for gather locality when a ray makes many field
-        // evaluations (the box depth in steps times the stages per step)
-        const double evals = (double)(m->n[2] - 1) * m->spacing[2] / step * (integrator == PIVBOS_RK4 ? 3.0 : 1.0);
-        p.reorder = evals >= 64.0 ? 1 : 0;
-        p.cell_cache = pivbos::tuning_cell_cache(p.reorder);
+        choose_gather(m, step, integrator, p);
     }
     p.o = o->d;
     p.sources = sources;
@@ -525,7 +540,7 @@ static pivbos_status render_impl(const pivbos_medium* m, const pivbos_optics* o,
         pr.p.perm = perm;
         pr.p.src_df = sdf;
         pr.p.source_offset = (uint32_t)first_source;
-        e = launch_render(pr.p, integrator, dimg, stats, rays_per_cta_setting(), s);
+        e = launch_render(pr.p, integrator, dimg, stats, rays_per_cta_setting(pr.p), s);
     }
     if (e == cudaSuccess && !image_on_device)
         e = cudaMemcpyAsync(image, dimg, img_bytes, cudaMemcpyDeviceToHost, s);

@@ -148,11 +148,7 @@ extern "C" pivbos_status pivbos_render_noalloc(const pivbos_medium* m, const piv
         if (ms > 2.0e9) return err(PIVBOS_ERR_UNSUPPORTED, "step too small for the box (%g steps)", ms);
         p.max_steps = (int)ms;
         p.m.z_key = (float)(m->origin[2] + 0.5 * (double)(m->n[2] - 1) * m->spacing[2]);
-        // reorder rays for gather locality when a ray makes many field
-        // evaluations (the box depth in steps times the stages per step)
-        const double evals = (double)(m->n[2] - 1) * m->spacing[2] / step * (integrator == PIVBOS_RK4 ? 3.0 : 1.0);
-        p.reorder = evals >= 64.0 ? 1 : 0;
-        p.cell_cache = pivbos::tuning_cell_cache(p.reorder);
+        pivbos::choose_gather(m, step, integrator, p);
     }
     p.o = o->d;
     p.sources = sources;
@@ -181,7 +177,7 @@ extern "C" pivbos_status pivbos_render_noalloc(const pivbos_medium* m, const piv
     if (e != cudaSuccess) return err(PIVBOS_ERR_CUDA, "sort: %s", cudaGetErrorString(e));
     p.perm = perm;
     p.src_df = src_df;
-    e = pivbos::launch_render(p, integrator, image, stats, 2048u, s);
+    e = pivbos::launch_render(p, integrator, image, stats, pivbos::rays_per_cta_setting(p), s);
     if (e != cudaSuccess) return err(PIVBOS_ERR_CUDA, "render: %s", cudaGetErrorString(e));
     return PIVBOS_OK;
 }
