@@ -256,3 +256,47 @@ def test_render_path_matches_per_ray_positions():
     rel = np.linalg.norm((got - ref).astype(np.float64)) / np.linalg.norm(ref.astype(np.float64))
     print("render vs per-ray positions: rel L2 %.2e, %d fallback of %d" % (rel, n_fb, total))
     assert rel < 1e-5
+
+
+def test_bos_slab_with_first_order_integrator():
+    """The surrogate on the BOS linear-gradient slab (dots in front of the box,
+    the first-order integrator, an ideal lens): every ray served, the error
+    against the plain path within the budget, and far below the straight
+    ray's; the image totals consistent with the per-ray status counts."""
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    frame = scenes.c0(scale=0.25, rays_per_source=100)[0]      # 32 x 32 dots x 100 rays, Euler 0.1 mm
+    assert frame.integrator == scenes.EULER
+    med, opt = gpu_handles(frame)
+    src = torch.tensor(frame.sources, dtype=torch.float64, device="cuda")
+    img = torch.zeros((frame.optics.height, frame.optics.width), dtype=torch.int64, device="cuda")
+    st = torch.zeros(P.RAY_NSTATUS, dtype=torch.int64, device="cuda")
+    desc = P.frame_desc(med.h, opt.h, src, len(frame.sources), frame.rays_per_source, frame.frame_index,
+                        frame.seed, frame.step, img, st)
+    sg, rep = P.pivbos_surrogate_train(desc, frame.integrator,
+                                       _cfg(P, n_train=1_000_000, n_val=400_000, epochs=4, min_bin_count=2))
+    try:
+        r = rep.as_dict()
+        print(r)
+        assert r["val_served_frac"] > 0.99
+        assert r["val_rms_px"] < 0.2 * r["val_rms_px_straight"]
+        n_fb = P.pivbos_surrogate_render(sg, desc, count_fallback=True)
+        stats = st.cpu().numpy()
+        assert stats.sum() == frame.n_rays
+        assert img.sum().item() == stats[0] * (1 << 32)
+        ids = np.arange(0, frame.n_rays, 7, dtype=np.int64)
+        ids_t = torch.tensor(ids, device="cuda")
+        xy = torch.empty((len(ids), 2), dtype=torch.float64, device="cuda")
+        flags = torch.empty(len(ids), dtype=torch.int32, device="cuda")
+        status = torch.empty(len(ids), dtype=torch.int32, device="cuda")
+        P.pivbos_surrogate_sensor(sg, desc, ids_t, xy, flags, status)
+    finally:
+        P.pivbos_surrogate_destroy(sg)
+    plain = gpu_states(frame, ids, (med, opt))
+    xy, status = xy.cpu().numpy(), status.cpu().numpy()
+    ok = (status == 0) & (plain["status"] == 0)
+    assert ok.mean() > 0.99
+    d = xy[ok] - plain["sensor_xy"][ok]
+    rms = float(np.sqrt((d ** 2).sum(1).mean()))
+    print("BOS slab: rms vs plain %.2e px, %d fallback of %d" % (rms, n_fb, frame.n_rays))
+    assert rms <= BUDGET_PX
