@@ -323,8 +323,9 @@ pivbos_status pivbos_mlp_loss_grad(const float* params, const float* x, const fl
  * the sensor within budget_margin * err_budget_px; the other rays are traced
  * by the plain path at render time.  The report gives the same figures for
  * the projection alone and for the straight ray.  The surrogate is tied to
- * the frame's medium and optics (they must outlive it) and needs the lens
- * after the box.
+ * the frame's medium and optics (they must outlive it; a refill of the
+ * medium makes later surrogate calls fail with INVALID_ARG) and needs the
+ * lens after the box.
  * ------------------------------------------------------------------------- */
 typedef struct {
     int64_t n_train;        /* training rays (<= 2^31) */

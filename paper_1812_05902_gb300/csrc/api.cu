@@ -361,7 +361,9 @@ pivbos_status pivbos_medium_refill(pivbos_medium* m, const float* rho, int rho_o
         st = check_device_ptr(rho, dev, "rho");
         if (st) return st;
     }
-    return medium_fill(m, rho, rho_on_device, (cudaStream_t)stream);
+    st = medium_fill(m, rho, rho_on_device, (cudaStream_t)stream);
+    if (st == PIVBOS_OK) ++m->version;
+    return st;
 }
 
 void pivbos_medium_destroy(pivbos_medium* m)

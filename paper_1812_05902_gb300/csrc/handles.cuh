@@ -11,6 +11,7 @@ struct pivbos_medium {
     double K;
     float4* field;
     float* rho_scratch;   // device copy of host rho during a (re)fill
+    uint64_t version = 0; // incremented by every refill (derived data, e.g. a surrogate, records it)
 };
 
 struct pivbos_optics {

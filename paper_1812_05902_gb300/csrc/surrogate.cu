@@ -130,6 +130,7 @@ struct pivbos_surrogate {
     int device = 0;
     int integrator = PIVBOS_RK4;
     const pivbos_medium* medium = nullptr;
+    uint64_t medium_version = 0;   // the medium's version when trained
     const pivbos_optics* optics = nullptr;
     pivbos::MlpDev net;
     pivbos::SurrParams S;
@@ -274,6 +275,7 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
     sg->device = dev;
     sg->integrator = integrator;
     sg->medium = m;
+    sg->medium_version = m->version;
     sg->optics = o;
     memset(&sg->rep, 0, sizeof sg->rep);
     pivbos_surrogate_report& R = sg->rep;
@@ -584,6 +586,8 @@ static pivbos_status surr_prepare(const pivbos_surrogate* sg, const pivbos_frame
     if (!sg || !frame) return serr(PIVBOS_ERR_INVALID_ARG, "surrogate and frame are required");
     if (frame->medium != sg->medium || frame->optics != sg->optics)
         return serr(PIVBOS_ERR_INVALID_ARG, "the frame must use the medium and optics the surrogate was trained on");
+    if (sg->medium->version != sg->medium_version)
+        return serr(PIVBOS_ERR_INVALID_ARG, "the medium was refilled after the surrogate was trained");
     int dev = 0;
     pivbos_status st = pivbos::prepare_trace(frame->medium, frame->optics, frame->sources, frame->n_sources, 1,
                                              frame->rays_per_source, frame->seed, frame->frame, sg->integrator,

@@ -197,6 +197,26 @@ def test_nothing_served_equals_plain_render():
         P.pivbos_surrogate_destroy(sg)
 
 
+def test_surrogate_rejects_a_refilled_medium():
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    frame = scenes.c4(scale=0.001, grid=64)[0]
+    med, opt = gpu_handles(frame)
+    src = torch.tensor(frame.sources, dtype=torch.float64, device="cuda")
+    img = torch.zeros((frame.optics.height, frame.optics.width), dtype=torch.int64, device="cuda")
+    desc = P.frame_desc(med.h, opt.h, src, len(frame.sources), frame.rays_per_source, 0, frame.seed,
+                        frame.step, img)
+    sg, _ = P.pivbos_surrogate_train(desc, frame.integrator, _cfg(P, n_train=65536, n_val=65536, epochs=1,
+                                                                   batch=65536))
+    try:
+        P.pivbos_surrogate_render(sg, desc)
+        med.refill(torch.tensor(frame.medium.rho, device="cuda"))
+        with pytest.raises(P.PivbosError, match="refilled"):
+            P.pivbos_surrogate_render(sg, desc)
+    finally:
+        P.pivbos_surrogate_destroy(sg)
+
+
 def test_surrogate_rejects_other_medium_and_host_image(trained):
     import ctypes
     import torch
