@@ -262,8 +262,12 @@ typedef struct pivbos_batch pivbos_batch;
 /* Defaults: 2048 rays per item, no cell cache, 3 CTAs per SM, graphs on. */
 pivbos_status pivbos_default_tuning(pivbos_tuning* out);
 
+/* tuning NULL: the defaults, except that the cell cache (with 2 CTAs per
+ * SM) is used when dense frames (>= 64 field evaluations per ray) whose
+ * smallest grid spacing exceeds 4/3 of the step carry most of the estimated
+ * work. */
 pivbos_status pivbos_batch_create(const pivbos_frame_desc* frames, int n_frames, int integrator,
-                                  const pivbos_tuning* tuning /* NULL = defaults */, pivbos_batch** out);
+                                  const pivbos_tuning* tuning, pivbos_batch** out);
 pivbos_status pivbos_batch_render(pivbos_batch* b, void* stream);
 void pivbos_batch_destroy(pivbos_batch* b);
 

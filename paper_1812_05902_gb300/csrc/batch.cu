@@ -148,7 +148,6 @@ pivbos_status pivbos_batch_create(const pivbos_frame_desc* frames, int n_frames,
         fr[f].stats = d.stats;
         fr[f].rays_per_cta = (uint32_t)t.rays_per_cta;
         fr[f].total_rays = total;
-        fr[f].p.cell_cache = t.cell_cache;
         // estimated work: rays x (field evaluations expected per ray + fixed part)
         double evals = 0.0;
         if (d.medium) {
@@ -157,6 +156,21 @@ pivbos_status pivbos_batch_create(const pivbos_frame_desc* frames, int n_frames,
         }
         cost[f] = (double)total * (30.0 + evals);
     }
+    if (!tuning) {
+        // without a tuning: the cell cache (and 2 CTAs per SM) when frames
+        // whose geometry favours it (see the render's gather choice) carry
+        // most of the estimated work
+        double with = 0.0, all = 0.0;
+        for (int f = 0; f < n_frames; ++f) {
+            all += cost[f];
+            if (fr[f].p.cell_cache) with += cost[f];
+        }
+        if (all > 0.0 && with >= 0.5 * all) {
+            t.cell_cache = 1;
+            t.ctas_per_sm = 2;
+        }
+    }
+    for (int f = 0; f < n_frames; ++f) fr[f].p.cell_cache = t.cell_cache;
     pivbos_batch* b = new (std::nothrow) pivbos_batch();
     if (!b) return berr(PIVBOS_ERR_OOM, "host allocation");
     b->device = dev;
