@@ -355,8 +355,8 @@ cudaError_t mlp_alloc(MlpDev& d, int splits)
     if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(d.m, 0, sizeof(float) * kMlpParams);
     if (e == cudaSuccess) e = cudaMemset(d.v, 0, sizeof(float) * kMlpParams);
-    static bool attrs = false;
-    if (e == cudaSuccess && !attrs) {
+    // the shared-memory limits are per device: set them on every allocation
+    if (e == cudaSuccess) {
         e = cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FwdSmem));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(mlp_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem());
@@ -364,7 +364,6 @@ cudaError_t mlp_alloc(MlpDev& d, int splits)
             e = cudaFuncSetAttribute(mlp_dx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dx_smem());
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(mlp_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem());
-        attrs = e == cudaSuccess;
     }
     return e;
 }

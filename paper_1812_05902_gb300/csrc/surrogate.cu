@@ -653,12 +653,9 @@ pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_f
             sv.ids = (uint32_t*)(sbuf + (size_t)chunk * 96);
             sv.count = (unsigned long long*)(sbuf + off_count);   // [0] served, [1] finish items
             sv.capacity = (uint32_t)chunk;
-            static bool attr = false;
-            if (!attr) {
-                e = cudaFuncSetAttribute(pivbos::surr_net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(pivbos::NetSmem));
-                attr = e == cudaSuccess;
-            }
+            // per device, so set on every render (cheap)
+            e = cudaFuncSetAttribute(pivbos::surr_net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(pivbos::NetSmem));
             for (uint64_t c0 = 0; c0 < total && e == cudaSuccess; c0 += chunk) {
                 const uint64_t c1 = std::min(total, c0 + chunk);
                 e = cudaMemsetAsync(sv.count, 0, 2 * sizeof(unsigned long long), s);
