@@ -197,6 +197,20 @@ __device__ __forceinline__ void surr_residual(const SurrParams& S, const float* 
     for (int c = 0; c < 4; ++c) r[c] = born[c] + (S.use_net ? y[c] * S.t_scale[c] : 0.0f);
 }
 
+// Sensor position of a surrogate exit line: the lens and sensor in FP32
+// (the surrogate's own error, ~1e-3 px, is far above their rounding; the
+// plain path keeps double-float optics for its 1e-5 px parity).
+__device__ __forceinline__ void surr_optics(const DevOptics& o, df Rx, df Ry, df Rz, df dx, df dy, df dz,
+                                            int& status, df& px, df& py)
+{
+    float x = Rx.hi + Rx.lo, y = Ry.hi + Ry.lo, z = Rz.hi + Rz.lo;
+    float ux = dx.hi + dx.lo, uy = dy.hi + dy.lo, uz = dz.hi + dz.lo;
+    float fx, fy;
+    optics_to_sensor<F32Ops>(o, x, y, z, ux, uy, uz, status, fx, fy);
+    px = dfv(fx);
+    py = dfv(fy);
+}
+
 // Seeded sample of ray ids of a frame (Philox counter (q, stream, frame, 2)).
 __device__ __forceinline__ uint64_t sample_ray(const TraceParams& P, uint64_t q, uint32_t stream, uint64_t seed,
                                                uint64_t total)
@@ -349,7 +363,7 @@ __global__ void surr_pilot_kernel(const TraceParams P, const SurrParams S, uint6
                 surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
                 int status = PIVBOS_RAY_REACHED;
                 df a, b;
-                optics_to_sensor(P.o, Rx, Ry, Rz, ex, ey, ez, status, a, b);
+                surr_optics(P.o, Rx, Ry, Rz, ex, ey, ez, status, a, b);
                 all = all && status == PIVBOS_RAY_REACHED;
                 const double dx = df_to_double(a) - st.sensor_xy[0], dy = df_to_double(b) - st.sensor_xy[1];
                 err[c] = dx * dx + dy * dy;
@@ -439,7 +453,7 @@ __global__ void surr_eval_kernel(const TraceParams P, const SurrParams S, const 
         surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
         int status = PIVBOS_RAY_REACHED;
         df px, py;
-        optics_to_sensor(P.o, Rx, Ry, Rz, ex, ey, ez, status, px, py);
+        surr_optics(P.o, Rx, Ry, Rz, ex, ey, ez, status, px, py);
         if (status == PIVBOS_RAY_REACHED) {
             const double a = df_to_double(px) - ref_px[2 * q], b = df_to_double(py) - ref_px[2 * q + 1];
             atomicAdd(&acc.err2[v][e.bin], a * a + b * b);
@@ -709,7 +723,7 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
             df Rx, Ry, Rz, dx, dy, dz;
             surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
             r.status = PIVBOS_RAY_REACHED;
-            optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, r.status, r.px, r.py);
+            surr_optics(P.o, Rx, Ry, Rz, dx, dy, dz, r.status, r.px, r.py);
             cnt[r.status]++;
             if (r.status == PIVBOS_RAY_REACHED) atomicMin(&anchor_tid, tid);
         }
@@ -771,7 +785,7 @@ __global__ void surr_sensor_kernel(const TraceParams P, const SurrParams S, cons
             surr_residual(S, born, Y + q * 4, res);
             surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
         }
-        optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, status, px, py);
+        surr_optics(P.o, Rx, Ry, Rz, dx, dy, dz, status, px, py);
     }
     out_px[2 * q] = df_to_double(px);
     out_px[2 * q + 1] = df_to_double(py);

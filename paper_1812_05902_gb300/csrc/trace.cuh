@@ -272,96 +272,142 @@ __device__ __forceinline__ bool box_entry(const DevMedium& m, df Rx, df Ry, df R
 // Sec. 3.3 and 3.4: from a point and direction in object space through the
 // optical elements to the sensor plane.  Leaves status unchanged if the ray
 // reaches the sensor array; (R, d) end as the state at the sensor.
-__device__ __forceinline__ void optics_to_sensor(const DevOptics& o, df& Rx, df& Ry, df& Rz, df& dx, df& dy, df& dz,
-                                                 int& status, df& px, df& py)
+//
+// Written once over a number type: N = DfOps (double-float, the exact
+// path) or F32Ops (FP32, for the surrogate's approximate exit lines, whose
+// error budget is a thousand times looser); DfOps maps every operation onto
+// the double-float function it names.
+struct DfOps {
+    using T = df;
+    static __device__ __forceinline__ T k(dfc c) { return dfk(c); }
+    static __device__ __forceinline__ T v(float a) { return dfv(a); }
+    static __device__ __forceinline__ float hi(T a) { return a.hi; }
+    static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return df_sub(a, b); }
+    static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+    static __device__ __forceinline__ T fma(T a, T b, T c) { return df_fma(a, b, c); }
+    static __device__ __forceinline__ T sqr(T a) { return df_sqr(a); }
+    static __device__ __forceinline__ T sqrt(T a) { return df_sqrt(a); }
+    static __device__ __forceinline__ T div(T a, T b) { return df_div(a, b); }
+    static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
+    static __device__ __forceinline__ T rsqrt(T a) { return df_rsqrt(a); }
+    static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
+    static __device__ __forceinline__ T add_f(T a, float b) { return df_add_f(a, b); }
+    static __device__ __forceinline__ bool lt(T a, T b) { return df_lt(a, b); }
+};
+struct F32Ops {
+    using T = float;
+    static __device__ __forceinline__ T k(dfc c) { return c.hi + c.lo; }
+    static __device__ __forceinline__ T v(float a) { return a; }
+    static __device__ __forceinline__ float hi(T a) { return a; }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T fma(T a, T b, T c) { return fmaf(a, b, c); }
+    static __device__ __forceinline__ T sqr(T a) { return a * a; }
+    static __device__ __forceinline__ T sqrt(T a) { return sqrtf(a); }
+    static __device__ __forceinline__ T div(T a, T b) { return a / b; }
+    static __device__ __forceinline__ T rcp(T a) { return 1.0f / a; }
+    static __device__ __forceinline__ T rsqrt(T a) { return rsqrtf(a); }
+    static __device__ __forceinline__ T neg(T a) { return -a; }
+    static __device__ __forceinline__ T add_f(T a, float b) { return a + b; }
+    static __device__ __forceinline__ bool lt(T a, T b) { return a < b; }
+};
+
+template <class N = DfOps>
+__device__ __forceinline__ void optics_to_sensor(const DevOptics& o, typename N::T& Rx, typename N::T& Ry,
+                                                 typename N::T& Rz, typename N::T& dx, typename N::T& dy,
+                                                 typename N::T& dz, int& status, typename N::T& px,
+                                                 typename N::T& py)
 {
+    using T = typename N::T;
     for (int s = 0; s < o.ns && status == PIVBOS_RAY_REACHED; ++s) {
         const DevSurface& S = o.s[s];
-        if (!(dz.hi > 0.0f)) { status = PIVBOS_RAY_MISS; break; }
-        const df inv_dz = df_rcp(dz);
-        const df t0 = df_mul(df_sub(dfk(S.z), Rz), inv_dz);
+        if (!(N::hi(dz) > 0.0f)) { status = PIVBOS_RAY_MISS; break; }
+        const T inv_dz = N::rcp(dz);
+        const T t0 = N::mul(N::sub(N::k(S.z), Rz), inv_dz);
         if (S.type == PIVBOS_SURF_SPHERE && S.R_f != 0.0f) {
             // vertex-relative quadratic t^2 + 2 b t + c = 0 from the point Q
             // on the vertex plane; the vertex-side root has the smaller
             // magnitude: t = c / (-b - sign(b) sqrt(b^2 - c))
-            const df Qx = df_fma(t0, dx, Rx), Qy = df_fma(t0, dy, Ry);
-            const df R = dfk(S.R);
-            const df b = df_sub(df_add(df_mul(dx, Qx), df_mul(dy, Qy)), df_mul(R, dz));
-            const df c = df_add(df_sqr(Qx), df_sqr(Qy));
-            const df disc = df_sub(df_sqr(b), c);
-            if (disc.hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
-            const df sq = df_sqrt(disc);
-            const df den = b.hi >= 0.0f ? df_sub(df_neg(b), sq) : df_add(df_neg(b), sq);
-            const df t1 = den.hi != 0.0f ? df_div(c, den) : dfv(0.0f);
-            if (df_add(t0, t1).hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
-            const df Hx = df_fma(t1, dx, Qx), Hy = df_fma(t1, dy, Qy), Hz = df_mul(t1, dz);
-            const df HzR = df_sub(Hz, R);
-            if (!(HzR.hi * S.R_f < 0.0f)) { status = PIVBOS_RAY_MISS; break; }
-            if (Hx.hi * Hx.hi + Hy.hi * Hy.hi > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
-            const df invR = dfk(S.invR);
-            df Nx = df_mul(Hx, invR), Ny = df_mul(Hy, invR), Nz = df_mul(HzR, invR);
-            if (Nx.hi * dx.hi + Ny.hi * dy.hi + Nz.hi * dz.hi > 0.0f) {
-                Nx = df_neg(Nx); Ny = df_neg(Ny); Nz = df_neg(Nz);
+            const T Qx = N::fma(t0, dx, Rx), Qy = N::fma(t0, dy, Ry);
+            const T R = N::k(S.R);
+            const T b = N::sub(N::add(N::mul(dx, Qx), N::mul(dy, Qy)), N::mul(R, dz));
+            const T c = N::add(N::sqr(Qx), N::sqr(Qy));
+            const T disc = N::sub(N::sqr(b), c);
+            if (N::hi(disc) < 0.0f) { status = PIVBOS_RAY_MISS; break; }
+            const T sq = N::sqrt(disc);
+            const T den = N::hi(b) >= 0.0f ? N::sub(N::neg(b), sq) : N::add(N::neg(b), sq);
+            const T t1 = N::hi(den) != 0.0f ? N::div(c, den) : N::v(0.0f);
+            if (N::hi(N::add(t0, t1)) < 0.0f) { status = PIVBOS_RAY_MISS; break; }
+            const T Hx = N::fma(t1, dx, Qx), Hy = N::fma(t1, dy, Qy), Hz = N::mul(t1, dz);
+            const T HzR = N::sub(Hz, R);
+            if (!(N::hi(HzR) * S.R_f < 0.0f)) { status = PIVBOS_RAY_MISS; break; }
+            if (N::hi(Hx) * N::hi(Hx) + N::hi(Hy) * N::hi(Hy) > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
+            const T invR = N::k(S.invR);
+            T Nx = N::mul(Hx, invR), Ny = N::mul(Hy, invR), Nz = N::mul(HzR, invR);
+            if (N::hi(Nx) * N::hi(dx) + N::hi(Ny) * N::hi(dy) + N::hi(Nz) * N::hi(dz) > 0.0f) {
+                Nx = N::neg(Nx); Ny = N::neg(Ny); Nz = N::neg(Nz);
             }
             // Eq. 7, vector form
-            const df eta = dfk(S.eta);
-            const df ci = df_neg(df_add(df_add(df_mul(Nx, dx), df_mul(Ny, dy)), df_mul(Nz, dz)));
-            const df kk = df_sub(dfv(1.0f), df_mul(dfk(S.eta2), df_sub(dfv(1.0f), df_sqr(ci))));
-            if (kk.hi < 0.0f) { status = PIVBOS_RAY_TIR; break; }
-            const df a = df_sub(df_mul(eta, ci), df_sqrt(kk));
-            dx = df_fma(eta, dx, df_mul(a, Nx));
-            dy = df_fma(eta, dy, df_mul(a, Ny));
-            dz = df_fma(eta, dz, df_mul(a, Nz));
+            const T eta = N::k(S.eta);
+            const T ci = N::neg(N::add(N::add(N::mul(Nx, dx), N::mul(Ny, dy)), N::mul(Nz, dz)));
+            const T kk = N::sub(N::v(1.0f), N::mul(N::k(S.eta2), N::sub(N::v(1.0f), N::sqr(ci))));
+            if (N::hi(kk) < 0.0f) { status = PIVBOS_RAY_TIR; break; }
+            const T a = N::sub(N::mul(eta, ci), N::sqrt(kk));
+            dx = N::fma(eta, dx, N::mul(a, Nx));
+            dy = N::fma(eta, dy, N::mul(a, Ny));
+            dz = N::fma(eta, dz, N::mul(a, Nz));
             Rx = Hx;
             Ry = Hy;
-            Rz = df_add(dfk(S.z), Hz);
+            Rz = N::add(N::k(S.z), Hz);
         } else {
-            if (t0.hi < 0.0f) { status = PIVBOS_RAY_MISS; break; }
-            Rx = df_fma(t0, dx, Rx);
-            Ry = df_fma(t0, dy, Ry);
-            Rz = dfk(S.z);
-            const float r2 = Rx.hi * Rx.hi + Ry.hi * Ry.hi;
+            if (N::hi(t0) < 0.0f) { status = PIVBOS_RAY_MISS; break; }
+            Rx = N::fma(t0, dx, Rx);
+            Ry = N::fma(t0, dy, Ry);
+            Rz = N::k(S.z);
+            const float r2 = N::hi(Rx) * N::hi(Rx) + N::hi(Ry) * N::hi(Ry);
             if (S.type == PIVBOS_SURF_STOP) {
                 if (r2 > S.clear_r2) { status = PIVBOS_RAY_STOP; break; }
             } else if (S.type == PIVBOS_SURF_IDEAL_THIN) {
                 if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
-                const df invf = dfk(S.inv_f);
-                const df ux = df_sub(df_mul(dx, inv_dz), df_mul(Rx, invf));
-                const df uy = df_sub(df_mul(dy, inv_dz), df_mul(Ry, invf));
-                const df inn = df_rsqrt(df_add_f(df_add(df_sqr(ux), df_sqr(uy)), 1.0f));
-                dx = df_mul(ux, inn);
-                dy = df_mul(uy, inn);
+                const T invf = N::k(S.inv_f);
+                const T ux = N::sub(N::mul(dx, inv_dz), N::mul(Rx, invf));
+                const T uy = N::sub(N::mul(dy, inv_dz), N::mul(Ry, invf));
+                const T inn = N::rsqrt(N::add_f(N::add(N::sqr(ux), N::sqr(uy)), 1.0f));
+                dx = N::mul(ux, inn);
+                dy = N::mul(uy, inn);
                 dz = inn;
             } else {
                 if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
                 // flat surface, normal (0, 0, -1)
-                const df eta = dfk(S.eta);
-                const df kk = df_sub(dfv(1.0f), df_mul(dfk(S.eta2), df_sub(dfv(1.0f), df_sqr(dz))));
-                if (kk.hi < 0.0f) { status = PIVBOS_RAY_TIR; break; }
-                const df a = df_sub(df_mul(eta, dz), df_sqrt(kk));
-                dx = df_mul(eta, dx);
-                dy = df_mul(eta, dy);
-                dz = df_sub(df_mul(eta, dz), a);
+                const T eta = N::k(S.eta);
+                const T kk = N::sub(N::v(1.0f), N::mul(N::k(S.eta2), N::sub(N::v(1.0f), N::sqr(dz))));
+                if (N::hi(kk) < 0.0f) { status = PIVBOS_RAY_TIR; break; }
+                const T a = N::sub(N::mul(eta, dz), N::sqrt(kk));
+                dx = N::mul(eta, dx);
+                dy = N::mul(eta, dy);
+                dz = N::sub(N::mul(eta, dz), a);
             }
         }
     }
 
     // ---- Sec. 3.4: sensor plane -------------------------------------------
-    px = dfv(0.0f);
-    py = dfv(0.0f);
+    px = N::v(0.0f);
+    py = N::v(0.0f);
     if (status == PIVBOS_RAY_REACHED) {
-        if (!(dz.hi > 0.0f)) {
+        if (!(N::hi(dz) > 0.0f)) {
             status = PIVBOS_RAY_MISS;
         } else {
-            const df t = df_mul(df_sub(dfk(o.sensor_z), Rz), df_rcp(dz));
-            if (t.hi < 0.0f) {
+            const T t = N::mul(N::sub(N::k(o.sensor_z), Rz), N::rcp(dz));
+            if (N::hi(t) < 0.0f) {
                 status = PIVBOS_RAY_MISS;
             } else {
-                const df ipitch = dfk(o.inv_pitch);
-                px = df_add_f(df_mul(df_fma(t, dx, Rx), ipitch), o.half_w);
-                py = df_add_f(df_mul(df_fma(t, dy, Ry), ipitch), o.half_h);
-                const bool inx = !df_lt(px, dfv(0.0f)) && df_lt(px, dfv((float)o.W));
-                const bool iny = !df_lt(py, dfv(0.0f)) && df_lt(py, dfv((float)o.H));
+                const T ipitch = N::k(o.inv_pitch);
+                px = N::add_f(N::mul(N::fma(t, dx, Rx), ipitch), o.half_w);
+                py = N::add_f(N::mul(N::fma(t, dy, Ry), ipitch), o.half_h);
+                const bool inx = !N::lt(px, N::v(0.0f)) && N::lt(px, N::v((float)o.W));
+                const bool iny = !N::lt(py, N::v(0.0f)) && N::lt(py, N::v((float)o.H));
                 if (!(inx && iny)) status = PIVBOS_RAY_OFF_SENSOR;
             }
         }
