@@ -48,34 +48,90 @@ __device__ __forceinline__ int bin_of(float f, int nb)
     return min(max(b, 0), nb - 1);
 }
 
-// Entry state of a ray (source s, unit direction d): the straight line's
-// point on the plane z = max(z_lo, s_z), its slopes, the confidence bin, and
-// the straight line at the reference plane.
-__device__ __forceinline__ void surr_entry(const TraceParams& P, const SurrParams& S, df sx, df sy, df sz, df dx,
-                                           df dy, df dz, Entry& e)
+// The surrogate path's ray in FP32: the lens point from the same Philox
+// words as the plain path (Sec. 3.1), rounded to FP32 (the surrogate's model
+// error, ~1e-3 px, is far above what FP32 rays change: ~1e-5 px).
+__device__ __forceinline__ void ray_start_f(const TraceParams& P, float sx, float sy, float sz, uint32_t sid,
+                                            uint32_t rid, float& dx, float& dy, float& dz)
 {
-    df tn;
-    e.enters = box_entry(P.m, sx, sy, sz, dx, dy, dz, tn);
-    const df inv_dz = df_rcp(dz);
-    e.ux = df_mul(dx, inv_dz);
-    e.uy = df_mul(dy, inv_dz);
-    const df ze = df_lt(sz, dfk(S.z_lo)) ? dfk(S.z_lo) : sz;
-    const df dze = df_sub(ze, sz);
-    const df xe = df_fma(e.ux, dze, sx), ye = df_fma(e.uy, dze, sy);
-    const df dzr = df_sub(dfk(S.z_ref), sz);
-    e.xs = df_fma(e.ux, dzr, sx);
-    e.ys = df_fma(e.uy, dzr, sy);
-    e.xe = xe.hi + xe.lo;
-    e.ye = ye.hi + ye.lo;
-    e.ze = ze.hi + ze.lo;
-    e.f[0] = (xe.hi - S.cx) / S.hx;
-    e.f[1] = (ye.hi - S.cy) / S.hy;
-    e.f[2] = (ze.hi - S.cz) / S.hz;
-    e.f[3] = e.ux.hi / S.u_scale;
-    e.f[4] = e.uy.hi / S.u_scale;
+    uint64_t w0, w1;
+    philox_lens_words(rid, sid, P.frame, 0ull, P.seed, 0ull, w0, w1);
+    const df u1 = u01_df(w0), u2 = u01_df(w1);
+    const float r = (P.o.aim_r.hi + P.o.aim_r.lo) * sqrtf(u1.hi + u1.lo);
+    float sn, cs;
+    sincospif(2.0f * (u2.hi + u2.lo), &sn, &cs);
+    dx = r * cs - sx;
+    dy = r * sn - sy;
+    dz = (P.o.aim_z.hi + P.o.aim_z.lo) - sz;
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv;
+    dy *= inv;
+    dz *= inv;
+}
+
+// Whether the straight ray meets the box (slab test, FP32).
+__device__ __forceinline__ bool box_entry_f(const DevMedium& m, float Rx, float Ry, float Rz, float dx, float dy,
+                                            float dz)
+{
+    const float R[3] = {Rx, Ry, Rz}, d[3] = {dx, dy, dz};
+    float t_near = 0.0f, t_far = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = m.lo[a].hi + m.lo[a].lo, hi = m.hi[a].hi + m.hi[a].lo;
+        if (d[a] == 0.0f) {
+            if (R[a] < lo || R[a] > hi) return false;
+        } else {
+            const float inv = 1.0f / d[a];
+            const float t1 = (lo - R[a]) * inv, t2 = (hi - R[a]) * inv;
+            t_near = fmaxf(t_near, fminf(t1, t2));
+            t_far = fminf(t_far, fmaxf(t1, t2));
+        }
+    }
+    return t_near <= t_far;
+}
+
+// Entry state of the FP32 ray of (source s, ray k): the straight line's
+// point on the plane z = max(z_lo, s_z) and its slopes (the network's
+// features), the confidence bin, and the straight line at the reference
+// plane.
+__device__ __forceinline__ void surr_entry_f(const TraceParams& P, const SurrParams& S, float sx, float sy, float sz,
+                                             uint32_t sid, uint32_t k, Entry& e)
+{
+    float dx, dy, dz;
+    ray_start_f(P, sx, sy, sz, sid, k, dx, dy, dz);
+    e.enters = box_entry_f(P.m, sx, sy, sz, dx, dy, dz);
+    const float ux = dx / dz, uy = dy / dz;
+    const float zlo = S.z_lo.hi + S.z_lo.lo, zr = S.z_ref.hi + S.z_ref.lo;
+    const float ze = sz < zlo ? zlo : sz;
+    e.xe = fmaf(ux, ze - sz, sx);
+    e.ye = fmaf(uy, ze - sz, sy);
+    e.ze = ze;
+    e.ux = dfv(ux);
+    e.uy = dfv(uy);
+    e.xs = dfv(fmaf(ux, zr - sz, sx));
+    e.ys = dfv(fmaf(uy, zr - sz, sy));
+    e.f[0] = (e.xe - S.cx) / S.hx;
+    e.f[1] = (e.ye - S.cy) / S.hy;
+    e.f[2] = (ze - S.cz) / S.hz;
+    e.f[3] = ux / S.u_scale;
+    e.f[4] = uy / S.u_scale;
     const int bu = bin_of(e.f[3], S.nbu) * S.nbu + bin_of(e.f[4], S.nbu);
     e.bin = ((bin_of(e.f[0], S.nbx) * S.nby + bin_of(e.f[1], S.nby)) * S.nbz + bin_of(e.f[2], S.nbz)) *
                 (S.nbu * S.nbu) + bu;
+}
+
+// Source (FP64 as given -> double-float) and FP32 entry state of a ray by id.
+__device__ __forceinline__ void surr_ray_by_id(const TraceParams& P, const SurrParams& S, uint64_t id, uint32_t& sid,
+                                               uint32_t& k, df& sx, df& sy, df& sz, Entry& e)
+{
+    const uint32_t rps = P.rays_per_source;
+    sid = (uint32_t)(id / rps);
+    k = (uint32_t)(id - (uint64_t)sid * rps);
+    const double* sp = P.sources + 3 * (size_t)sid;
+    sx = df_from_double(sp[0]);
+    sy = df_from_double(sp[1]);
+    sz = df_from_double(sp[2]);
+    surr_entry_f(P, S, sx.hi + sx.lo, sy.hi + sy.lo, sz.hi + sz.lo, sid + P.source_offset, k, e);
 }
 
 // Table value at column coordinates (xi, eta) and depth z: bilinear across
@@ -220,20 +276,6 @@ __device__ __forceinline__ uint64_t sample_ray(const TraceParams& P, uint64_t q,
     return w0 % total;
 }
 
-// Source (as given, FP64 -> double-float) and direction of a ray by id.
-__device__ __forceinline__ void ray_by_id(const TraceParams& P, uint64_t id, uint32_t& sid, uint32_t& k, df& sx,
-                                          df& sy, df& sz, df& dx, df& dy, df& dz)
-{
-    const uint32_t rps = P.rays_per_source;
-    sid = (uint32_t)(id / rps);
-    k = (uint32_t)(id - (uint64_t)sid * rps);
-    const double* sp = P.sources + 3 * (size_t)sid;
-    sx = df_from_double(sp[0]);
-    sy = df_from_double(sp[1]);
-    sz = df_from_double(sp[2]);
-    ray_start(P, sx, sy, sz, sid + P.source_offset, k, dx, dy, dz);
-}
-
 // Projection table: one thread per column; the column's line is followed
 // from z_hi down to z_lo, grad n sampled (trilinear, as the tracer samples
 // it; zero outside the box) at the midpoints of `sub` sub-steps per level.
@@ -276,26 +318,23 @@ __device__ __forceinline__ void truth_and_born(const TraceParams& P, const SurrP
                                                pivbos_ray_state& st, float* t, float* born)
 {
     uint32_t sid, k;
-    df sx, sy, sz, dx, dy, dz;
-    ray_by_id(P, id, sid, k, sx, sy, sz, dx, dy, dz);
-    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+    df sx, sy, sz;
+    surr_ray_by_id(P, S, id, sid, k, sx, sy, sz, e);
     born_residual(S, e, born);
     RayOut r;
-    trace_ray<INTEG, false>(P, sx, sy, sz, sid + P.source_offset, k, r, &st);
+    trace_ray<INTEG, false>(P, sx, sy, sz, sid + P.source_offset, k, r, &st);   // the plain path's ray
     t[0] = t[1] = t[2] = t[3] = 0.0f;
     if (st.status != PIVBOS_RAY_MAXSTEP) {
-        // the exit line (straight beyond the box) against the straight ray,
-        // both taken at the reference plane
+        // the exit line (straight beyond the box) against the surrogate's
+        // straight ray, both taken at the reference plane
         const double zr = df_to_double(dfk(S.z_ref));
-        const double* sp = P.sources + 3 * (size_t)sid;
-        const double uxd = df_to_double(e.ux), uyd = df_to_double(e.uy);
         const double Dx = st.vol_dir[0] / st.vol_dir[2], Dy = st.vol_dir[1] / st.vol_dir[2];
         const double xt = st.vol_pos[0] + (zr - st.vol_pos[2]) * Dx;
         const double yt = st.vol_pos[1] + (zr - st.vol_pos[2]) * Dy;
-        t[0] = (float)(xt - (sp[0] + (zr - sp[2]) * uxd));
-        t[1] = (float)(yt - (sp[1] + (zr - sp[2]) * uyd));
-        t[2] = (float)(Dx - uxd);
-        t[3] = (float)(Dy - uyd);
+        t[0] = (float)(xt - df_to_double(e.xs));
+        t[1] = (float)(yt - df_to_double(e.ys));
+        t[2] = (float)(Dx - df_to_double(e.ux));
+        t[3] = (float)(Dy - df_to_double(e.uy));
     }
 }
 
@@ -431,10 +470,9 @@ __global__ void surr_eval_kernel(const TraceParams P, const SurrParams S, const 
     if ((ref_st[q] & 7) != PIVBOS_RAY_REACHED) return;
     atomicAdd(&acc.tot[0], 1.0);
     uint32_t sid, k;
-    df sx, sy, sz, dx, dy, dz;
-    ray_by_id(P, ids[q], sid, k, sx, sy, sz, dx, dy, dz);
+    df sx, sy, sz;
     Entry e;
-    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+    surr_ray_by_id(P, S, ids[q], sid, k, sx, sy, sz, e);
     if (!e.enters) return;
     atomicAdd(&acc.tot[1], 1.0);
     float born[4], y[4];
@@ -542,9 +580,7 @@ surr_prep_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t 
                 const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
                 const float2* sp = P.src_df + 3 * (size_t)slot;
                 const float2 a = __ldg(sp), b = __ldg(sp + 1), c = __ldg(sp + 2);
-                df dx, dy, dz;
-                ray_start(P, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, sid, k, dx, dy, dz);
-                surr_entry(P, S, df{a.x, a.y}, df{b.x, b.y}, df{c.x, c.y}, dx, dy, dz, e);
+                surr_entry_f(P, S, a.x + a.y, b.x + b.y, c.x + c.y, sid, k, e);
                 if (!e.enters) mode = 2;
                 else mode = ((__ldg(S.bin_ok + (e.bin >> 5)) >> (e.bin & 31)) & 1u) ? 0 : 1;
                 if (mode == 0) born_residual(S, e, born);
@@ -764,10 +800,9 @@ __global__ void surr_sensor_kernel(const TraceParams P, const SurrParams S, cons
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     uint32_t sid, k;
-    df sx, sy, sz, dx, dy, dz;
-    ray_by_id(P, (uint64_t)ids[q], sid, k, sx, sy, sz, dx, dy, dz);
+    df sx, sy, sz;
     Entry e;
-    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+    surr_ray_by_id(P, S, (uint64_t)ids[q], sid, k, sx, sy, sz, e);
     const int flag = !e.enters ? 2 : (((S.bin_ok[e.bin >> 5] >> (e.bin & 31)) & 1u) ? 0 : 1);
     int status = PIVBOS_RAY_REACHED;
     df px = dfv(0.f), py = dfv(0.f);
@@ -778,13 +813,16 @@ __global__ void surr_sensor_kernel(const TraceParams P, const SurrParams S, cons
         px = r.px;
         py = r.py;
     } else {
-        df Rx = sx, Ry = sy, Rz = sz;
+        // the straight line (a ray that never enters the box) or the
+        // surrogate's exit line, as the render's finish kernel takes them
+        float res[4] = {0.f, 0.f, 0.f, 0.f};
         if (flag == 0) {
-            float born[4], res[4];
+            float born[4];
             born_residual(S, e, born);
             surr_residual(S, born, Y + q * 4, res);
-            surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
         }
+        df Rx, Ry, Rz, dx, dy, dz;
+        surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
         surr_optics(P.o, Rx, Ry, Rz, dx, dy, dz, status, px, py);
     }
     out_px[2 * q] = df_to_double(px);
@@ -800,10 +838,9 @@ __global__ void surr_features_kernel(const TraceParams P, const SurrParams S, co
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     uint32_t sid, k;
-    df sx, sy, sz, dx, dy, dz;
-    ray_by_id(P, (uint64_t)ids[q], sid, k, sx, sy, sz, dx, dy, dz);
+    df sx, sy, sz;
     Entry e;
-    surr_entry(P, S, sx, sy, sz, dx, dy, dz, e);
+    surr_ray_by_id(P, S, (uint64_t)ids[q], sid, k, sx, sy, sz, e);
     float born[4];
     born_residual(S, e, born);
     encode_features(S, e.f, born, X + (size_t)q * kMlpIn);
