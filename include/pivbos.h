@@ -290,7 +290,9 @@ pivbos_status pivbos_autotune(const pivbos_frame_desc* frame, int integrator, do
 /* ---------------------------------------------------------------------------
  * The surrogate's network (no counterpart in the paper: a learned ray map
  * built on the tracer).  16 inputs -> 128 -> 128 -> 128 -> 128 -> 4, ReLU on
- * the hidden layers, BF16 tensor-core products accumulating in FP32.
+ * the hidden layers, BF16 tensor-core products accumulating in FP32.  Inputs
+ * 14 and 15 are reserved and must be zero: the inference kernels use them
+ * to carry the first layer's bias through the tensor core.
  * Parameters: PIVBOS_MLP_PARAMS floats, layer by layer W [out][in] then
  * b [out].  These two calls run the GPU kernels on host buffers for
  * checking: the forward (x [n][16] -> y [n][4]) and the mean-squared-error

@@ -252,28 +252,31 @@ __global__ void mlp_tobf16_kernel(const float* __restrict__ p, __nv_bfloat16* __
 }
 
 // Inference forward on tcgen05: persistent CTAs of one warpgroup, one
-// 128-row tile at a time, five MMA / epilogue rounds per tile.
+// 128-row tile at a time, five MMA / epilogue rounds per tile; activations
+// and accumulator in tensor memory (columns [0, 256)).
 __global__ void __launch_bounds__(128, 1)
 mlp_fwd_tc_kernel(const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ params,
                   const __nv_bfloat16* __restrict__ X, int n, float* __restrict__ Y, int* __restrict__ status)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     mlptc::Net& S = *reinterpret_cast<mlptc::Net*>(smem);
-    unsigned char* A = smem + ((sizeof(mlptc::Net) + 127) / 128) * 128;
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_base;
+    __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5;
     mlptc::load_net(S, wbf, params);
-    if (warp == 0) umma::tmem_alloc(&tmem_base, 128);
-    if (tid == 0) umma::mbar_init(&bar, 1);
+    if (warp == 0) umma::tmem_alloc(&tmem_base, mlptc::kTileCols);
+    if (tid == 0) {
+        umma::mbar_init(&bar, 1);
+        failed = 0;
+    }
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    const uint32_t tmem = tmem_base;
-    const uint32_t row_tmem = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint32_t a_saddr = umma::smem_addr(A);
+    const uint32_t d_tmem = tmem_base, a_tmem = tmem_base + mlptc::kACol;
+    const uint32_t lane = (uint32_t)(warp * 32) << 16;
+    mlptc::store_constants(a_tmem + lane);
     uint32_t parity = 0;
-    bool failed = false;
     const int tiles = (n + mlptc::kRows - 1) / mlptc::kRows;
     for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
         const int row = t * mlptc::kRows + tid;
@@ -282,52 +285,45 @@ mlp_fwd_tc_kernel(const __nv_bfloat16* __restrict__ wbf, const float* __restrict
             lo = *reinterpret_cast<const uint4*>(X + (size_t)row * kMlpIn);
             hi = *reinterpret_cast<const uint4*>(X + (size_t)row * kMlpIn + 8);
         }
-        mlptc::store_input_row(A, tid, lo, hi);
+        mlptc::store_input(a_tmem + lane, lo, hi);
 #pragma unroll 1
         for (int l = 0; l < kMlpLayers; ++l) {
-            umma::fence_async_smem();
             umma::fence_before_sync();
             __syncthreads();
             if (tid == 0) {
                 umma::fence_after_sync();
-                mlptc::issue_layer(S, l, a_saddr, tmem);
+                mlptc::issue_layer(S, l, a_tmem, d_tmem);
                 umma::commit(&bar);
+                if (!umma::mbar_wait(&bar, parity, mlptc::kWaitLimit)) failed = 1;
             }
-            const bool ok = umma::mbar_wait(&bar, parity, mlptc::kWaitLimit);
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
+            __syncthreads();
+            if (failed) break;
             parity ^= 1u;
             umma::fence_after_sync();
             if (l < kMlpLayers - 1) {
-                mlptc::epilogue_hidden(row_tmem, S.bias[l], A, tid);
+                mlptc::epilogue_hidden(d_tmem + lane, a_tmem + lane);
             } else {
                 float y[kMlpOut];
-                mlptc::epilogue_out(row_tmem, S.bias4, y);
+                mlptc::epilogue_out(d_tmem + lane, y);
                 if (row < n) *reinterpret_cast<float4*>(Y + (size_t)row * 4) = make_float4(y[0], y[1], y[2], y[3]);
             }
         }
     }
-    if (failed) {
+    if (failed && tid == 0) {
         // report, then give the MMAs in flight a second bounded wait before
-        // the accumulator memory is released
-        if (tid == 0) {
-            atomicExch(status, (int)PIVBOS_ERR_DEVICE_TIMEOUT);
-            umma::mbar_wait(&bar, parity, mlptc::kWaitLimit);
-        }
+        // the tensor memory is released
+        atomicExch(status, (int)PIVBOS_ERR_DEVICE_TIMEOUT);
+        umma::mbar_wait(&bar, parity, mlptc::kWaitLimit);
     }
     umma::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
         umma::fence_after_sync();
-        umma::tmem_dealloc(tmem, 128);
+        umma::tmem_dealloc(tmem_base, mlptc::kTileCols);
     }
 }
 
-// The operand tile is followed by 32 KB of slack: every address the tensor
-// core can form from an operand descriptor stays inside the allocation.
-size_t tc_smem() { return ((sizeof(mlptc::Net) + 127) / 128) * 128 + 2 * mlptc::kTileBytes; }
+size_t tc_smem() { return sizeof(mlptc::Net); }
 
 int sm_count()
 {

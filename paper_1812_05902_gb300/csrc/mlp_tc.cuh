@@ -1,9 +1,18 @@
 // The surrogate network's forward pass on the fifth-generation tensor cores:
-// 128-row tiles, weights resident in shared memory as K-major core-matrix
-// operands, one 128 x 128 (or 128 x 16) FP32 accumulator per layer in
-// tensor memory, and an epilogue (bias, ReLU, BF16) from tensor memory back
-// into the next layer's shared-memory operand.  One warpgroup (4 warps)
-// owns a tile: warp w reads accumulator lanes (rows) 32w .. 32w + 31.
+// 128-row tiles; weights resident in shared memory as K-major core-matrix
+// operands (B); each tile's activations (A) and accumulator (D) in tensor
+// memory.  Per tile and layer one tcgen05.mma chain D = A * W^T, then an
+// epilogue (ReLU, BF16) from D back into A with tcgen05.ld / tcgen05.st --
+// no shared-memory traffic besides the weights, which the tensor core reads.
+//
+// The biases ride in the MMA: A carries two constant ones (inputs 14 and 15
+// of the first layer, K columns 128 and 129 of the others) and W the bias
+// split into a BF16 leading part and a BF16 remainder (about 16 significant
+// bits), so the epilogue is a plain ReLU and convert.  Inputs 14 and 15 of
+// the network are therefore reserved (zero in every caller).
+//
+// One warpgroup (4 warps) owns a tile: warp w reads and writes TMEM lanes
+// (rows) 32w .. 32w + 31.  TMEM columns of a tile: D [0, 128), A [128, 200).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -14,142 +23,124 @@
 namespace pivbos {
 namespace mlptc {
 
-constexpr int kRows = 128;                                 // rows per tile (MMA M)
-constexpr int kGroups = kRows / 8;                         // row groups of an A tile
-constexpr uint32_t kTileBytes = kRows * kMlpHidden * 2;    // A operand of one tile (K up to 128)
-constexpr int kOutN = 16;                                  // output layer N (4 used)
-constexpr uint32_t kLboA = kGroups * 128;                  // K-direction core-matrix stride of A
-constexpr uint32_t kLboW = (kMlpHidden / 8) * 128;         // the same for a 128-row weight matrix
-constexpr uint32_t kLboW4 = (kOutN / 8) * 128;             // ... and for the 16-row output weights
-constexpr uint32_t kWaitLimit = 1u << 20;                  // mbarrier polls before giving up
+constexpr int kRows = 128;                          // rows per tile (MMA M)
+constexpr int kKh = 144;                            // K of layers 1-4: 128 activations, 2 ones, 14 zeros
+constexpr int kOutN = 16;                           // output layer N (4 used)
+constexpr uint32_t kTileCols = 256;                 // TMEM columns per tile (D 128 + A 72, rounded up)
+constexpr uint32_t kACol = 128;                     // first A column of a tile
+constexpr uint32_t kLboW = (kMlpHidden / 8) * 128;  // K-direction core-matrix stride of a 128-row weight matrix
+constexpr uint32_t kLboW4 = (kOutN / 8) * 128;      // ... of the 16-row output weights
+constexpr uint32_t kOnes = 0x3F803F80u;             // two BF16 ones
+constexpr uint32_t kWaitLimit = 1u << 20;           // mbarrier polls before giving up
 
 struct Net {
-    alignas(128) unsigned char w0[kMlpHidden * kMlpIn * 2];
-    alignas(128) unsigned char wh[3][kMlpHidden * kMlpHidden * 2];
-    alignas(128) unsigned char w4[kOutN * kMlpHidden * 2];
-    float bias[4][kMlpHidden];
-    float bias4[kOutN];
+    alignas(128) unsigned char w0[kMlpHidden * kMlpIn * 2];    // K 16: inputs 0-13, bias lead, bias rest
+    alignas(128) unsigned char wh[3][kMlpHidden * kKh * 2];
+    alignas(128) unsigned char w4[kOutN * kKh * 2];
 };
 
-// Weights (BF16 [out][in] per layer in wbf) and biases (FP32 master) into
-// shared memory, 16 bytes at a time.
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// Weights (BF16 [out][in] per layer in wbf) and the split biases (FP32
+// master in params) into shared memory, 16 bytes (8 K elements) at a time.
 __device__ inline void load_net(Net& S, const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ params)
 {
-    for (int e = threadIdx.x; e < kMlpHidden * (kMlpIn / 8); e += blockDim.x) {
-        const int n = e / (kMlpIn / 8), c = e % (kMlpIn / 8);
-        *reinterpret_cast<uint4*>(S.w0 + umma::kmajor_offset(n, c * 8, kMlpHidden / 8)) =
-            *reinterpret_cast<const uint4*>(wbf + mlp_wbf_offset(0) + n * kMlpIn + c * 8);
-    }
-    for (int l = 1; l <= 3; ++l)
-        for (int e = threadIdx.x; e < kMlpHidden * (kMlpHidden / 8); e += blockDim.x) {
-            const int n = e / (kMlpHidden / 8), c = e % (kMlpHidden / 8);
-            *reinterpret_cast<uint4*>(S.wh[l - 1] + umma::kmajor_offset(n, c * 8, kMlpHidden / 8)) =
-                *reinterpret_cast<const uint4*>(wbf + mlp_wbf_offset(l) + n * kMlpHidden + c * 8);
+    for (int e = threadIdx.x; e < kMlpHidden * 2; e += blockDim.x) {
+        const int n = e >> 1, c = e & 1;
+        uint4 v = *reinterpret_cast<const uint4*>(wbf + mlp_wbf_offset(0) + n * kMlpIn + c * 8);
+        if (c == 1) {   // K 14, 15: the bias
+            const float b = params[mlp_w_offset(0) + kMlpIn * kMlpHidden + n];
+            const __nv_bfloat16 lead = __float2bfloat16(b);
+            v.w = pack2(lead, __float2bfloat16(b - __bfloat162float(lead)));
         }
-    for (int e = threadIdx.x; e < kOutN * (kMlpHidden / 8); e += blockDim.x) {
-        const int n = e / (kMlpHidden / 8), c = e % (kMlpHidden / 8);
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (n < kMlpOut) v = *reinterpret_cast<const uint4*>(wbf + mlp_wbf_offset(4) + n * kMlpHidden + c * 8);
-        *reinterpret_cast<uint4*>(S.w4 + umma::kmajor_offset(n, c * 8, kOutN / 8)) = v;
+        *reinterpret_cast<uint4*>(S.w0 + umma::kmajor_offset(n, c * 8, kMlpHidden / 8)) = v;
     }
-    for (int e = threadIdx.x; e < 4 * kMlpHidden; e += blockDim.x) {
-        const int l = e / kMlpHidden, o = e % kMlpHidden;
-        S.bias[l][o] = params[mlp_w_offset(l) + mlp_in(l) * mlp_out(l) + o];
+    for (int l = 1; l <= 4; ++l) {
+        const int N = l < 4 ? kMlpHidden : kOutN, nout = mlp_out(l);
+        unsigned char* W = l < 4 ? S.wh[l - 1] : S.w4;
+        for (int e = threadIdx.x; e < N * (kKh / 8); e += blockDim.x) {
+            const int n = e / (kKh / 8), c = e % (kKh / 8);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (n < nout) {
+                if (c < kMlpHidden / 8) {
+                    v = *reinterpret_cast<const uint4*>(wbf + mlp_wbf_offset(l) + n * kMlpHidden + c * 8);
+                } else if (c == kMlpHidden / 8) {   // K 128, 129: the bias
+                    const float b = params[mlp_w_offset(l) + kMlpHidden * nout + n];
+                    const __nv_bfloat16 lead = __float2bfloat16(b);
+                    v.x = pack2(lead, __float2bfloat16(b - __bfloat162float(lead)));
+                }
+            }
+            *reinterpret_cast<uint4*>(W + umma::kmajor_offset(n, c * 8, N / 8)) = v;
+        }
     }
-    for (int o = threadIdx.x; o < kOutN; o += blockDim.x)
-        S.bias4[o] = o < kMlpOut ? params[mlp_w_offset(4) + kMlpHidden * kMlpOut + o] : 0.0f;
 }
 
-// Row r of the input tile: 16 BF16 features.
-__device__ __forceinline__ void store_input_row(unsigned char* A, int r, uint4 lo, uint4 hi)
+// The constant K columns of a tile's A (ones at K 128 and 129, zeros up to
+// 143); written once per lane, before the first tile.
+__device__ __forceinline__ void store_constants(uint32_t a_lane)
 {
-    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, 0, kGroups)) = lo;
-    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, 8, kGroups)) = hi;
+    const uint32_t c[8] = {kOnes, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    umma::tmem_st8(a_lane + kMlpHidden / 2, c);
+    umma::tmem_wait_st();
 }
 
-// Issue layer l of one tile (one thread): D[tmem] = A * W_l^T.
-__device__ __forceinline__ void issue_layer(const Net& S, int l, uint32_t a_saddr, uint32_t d_tmem)
+// This thread's input row: 14 BF16 features, then the two ones of the bias.
+__device__ __forceinline__ void store_input(uint32_t a_lane, uint4 lo, uint4 hi)
+{
+    const uint32_t x[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, kOnes};
+    umma::tmem_st8(a_lane, x);
+    umma::tmem_wait_st();
+}
+
+// Issue layer l of one tile (one thread): D = A * W_l^T.
+__device__ __forceinline__ void issue_layer(const Net& S, int l, uint32_t a_tmem, uint32_t d_tmem)
 {
     if (l == 0) {
-        umma::mma_bf16(d_tmem, umma::make_desc(a_saddr, kLboA, 128),
-                       umma::make_desc(umma::smem_addr(S.w0), kLboW, 128), umma::make_idesc_bf16(kRows, kMlpHidden),
-                       false);
+        umma::mma_bf16_ts(d_tmem, a_tmem, umma::make_desc(umma::smem_addr(S.w0), kLboW, 128),
+                          umma::make_idesc_bf16(kRows, kMlpHidden), false);
         return;
     }
     const uint32_t w = l < 4 ? umma::smem_addr(S.wh[l - 1]) : umma::smem_addr(S.w4);
     const uint32_t lbo_w = l < 4 ? kLboW : kLboW4;
     const uint32_t idesc = umma::make_idesc_bf16(kRows, l < 4 ? kMlpHidden : kOutN);
-    // successive K steps advance both start addresses by two core matrices
-    // along K: add (2 * LBO) >> 4 to the descriptors' address fields
-    uint64_t ad = umma::make_desc(a_saddr, kLboA, 128);
+    // each K step (16 elements) takes 8 A columns and advances the weights'
+    // descriptor by two core matrices along K
     uint64_t bd = umma::make_desc(w, lbo_w, 128);
-    const uint64_t ainc = (2 * kLboA) >> 4, binc = (2 * lbo_w) >> 4;
+    const uint64_t binc = (2 * lbo_w) >> 4;
 #pragma unroll
-    for (int ks = 0; ks < kMlpHidden / 16; ++ks) {
-        umma::mma_bf16(d_tmem, ad, bd, idesc, ks > 0);
-        ad += ainc;
+    for (int ks = 0; ks < kKh / 16; ++ks) {
+        umma::mma_bf16_ts(d_tmem, a_tmem + 8 * ks, bd, idesc, ks > 0);
         bd += binc;
     }
 }
 
-// Hidden-layer epilogue of this thread's row r: ReLU(D + b) as BF16 into the
-// next layer's A operand.
-__device__ __forceinline__ void epilogue_hidden(uint32_t row_tmem, const float* __restrict__ bias, unsigned char* A,
-                                                int r)
-{
-#pragma unroll 1
-    for (int c0 = 0; c0 < kMlpHidden; c0 += 32) {
-        float v[32];
-        umma::tmem_ld32(row_tmem + (uint32_t)c0, v);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            uint32_t p[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = j * 8 + q * 2;
-                const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(v[i] + bias[c0 + i], 0.0f),
-                                                               fmaxf(v[i + 1] + bias[c0 + i + 1], 0.0f));
-                p[q] = *reinterpret_cast<const uint32_t*>(&h);
-            }
-            *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, c0 + j * 8, kGroups)) =
-                make_uint4(p[0], p[1], p[2], p[3]);
-        }
-    }
-}
-
-// The same with two 32-column loads in flight per wait and the ReLU folded
-// into the BF16 conversion.
-__device__ __forceinline__ void epilogue_hidden2(uint32_t row_tmem, const float* __restrict__ bias, unsigned char* A,
-                                                 int r)
+// Hidden-layer epilogue of this thread's row: ReLU(D) as BF16 into A.
+__device__ __forceinline__ void epilogue_hidden(uint32_t d_lane, uint32_t a_lane)
 {
 #pragma unroll 1
     for (int c0 = 0; c0 < kMlpHidden; c0 += 64) {
         uint32_t u[64];
-        umma::tmem_ld32_nowait(row_tmem + (uint32_t)c0, u);
-        umma::tmem_ld32_nowait(row_tmem + (uint32_t)c0 + 32, u + 32);
+        umma::tmem_ld32_nowait(d_lane + (uint32_t)c0, u);
+        umma::tmem_ld32_nowait(d_lane + (uint32_t)c0 + 32, u + 32);
         umma::tmem_wait();
+        uint32_t p[32];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            uint32_t p[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = j * 8 + q * 2;
-                p[q] = umma::relu_bf16x2(__uint_as_float(u[i]) + bias[c0 + i],
-                                         __uint_as_float(u[i + 1]) + bias[c0 + i + 1]);
-            }
-            *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, c0 + j * 8, kGroups)) =
-                make_uint4(p[0], p[1], p[2], p[3]);
-        }
+        for (int q = 0; q < 32; ++q) p[q] = umma::relu_bf16x2(__uint_as_float(u[2 * q]), __uint_as_float(u[2 * q + 1]));
+        umma::tmem_st32(a_lane + (uint32_t)(c0 / 2), p);
     }
+    umma::tmem_wait_st();
 }
 
 // Output epilogue: the 4 outputs of this thread's row.
-__device__ __forceinline__ void epilogue_out(uint32_t row_tmem, const float* __restrict__ bias4, float* y)
+__device__ __forceinline__ void epilogue_out(uint32_t d_lane, float* y)
 {
     float v[8];
-    umma::tmem_ld8(row_tmem, v);
+    umma::tmem_ld8(d_lane, v);
 #pragma unroll
-    for (int c = 0; c < kMlpOut; ++c) y[c] = v[c] + bias4[c];
+    for (int c = 0; c < kMlpOut; ++c) y[c] = v[c];
 }
 
 }  // namespace mlptc

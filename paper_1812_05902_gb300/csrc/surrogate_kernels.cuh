@@ -611,13 +611,13 @@ surr_prep_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t 
     }
 }
 
-// Network over the served list on tcgen05: three warpgroups per CTA, each
-// running its own 128-row tiles (its own operand buffer, TMEM columns and
-// mbarrier), so tiles of different warpgroups overlap.  R = B + y * scale.
-constexpr int kNetGroups = 3;
+// Network over the served list on tcgen05: two warpgroups per CTA, each
+// running its own 128-row tiles (TMEM columns [256g, 256g + 256), its own
+// mbarrier), so one tile's MMAs overlap the other's epilogue; the next
+// tile's inputs are loaded during the current one.  R = B + y * scale.
+constexpr int kNetGroups = 2;
 struct NetSmem {
     mlptc::Net net;
-    alignas(128) unsigned char a[kNetGroups][mlptc::kTileBytes];
     uint64_t bar[kNetGroups];
     uint32_t tmem_base;
     int failed[kNetGroups];
@@ -631,7 +631,7 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
     NetSmem& sh = *reinterpret_cast<NetSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, grp = warp >> 2, row = tid & 127;
     mlptc::load_net(sh.net, wbf, params);
-    if (warp == 0) umma::tmem_alloc(&sh.tmem_base, 512);
+    if (warp == 0) umma::tmem_alloc(&sh.tmem_base, mlptc::kTileCols * kNetGroups);
     if (tid < kNetGroups) {
         umma::mbar_init(&sh.bar[tid], 1);
         sh.failed[tid] = 0;
@@ -639,15 +639,14 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    const uint32_t d_tmem = sh.tmem_base + (uint32_t)(grp * 128);
-    const uint32_t row_tmem = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const uint32_t a_saddr = umma::smem_addr(sh.a[grp]);
+    const uint32_t d_tmem = sh.tmem_base + (uint32_t)grp * mlptc::kTileCols, a_tmem = d_tmem + mlptc::kACol;
+    const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
+    mlptc::store_constants(a_tmem + lane);
     const uint64_t n = min(*sv.count, (unsigned long long)sv.capacity);
     const uint64_t tiles = (n + mlptc::kRows - 1) / mlptc::kRows;
     uint32_t parity = 0;
     const uint64_t stride = (uint64_t)gridDim.x * kNetGroups;
     // this thread's input row and projection residual, loaded one tile ahead
-    // so the loads overlap the previous tile's five layers
     auto load_row = [&](uint64_t t, uint4& lo, uint4& hi, float4& b) {
         const uint64_t r = t * mlptc::kRows + row;
         lo = make_uint4(0u, 0u, 0u, 0u);
@@ -666,21 +665,20 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
     for (uint64_t t = (uint64_t)blockIdx.x * kNetGroups + grp; t < tiles; t += stride) {
         const uint64_t r = t * mlptc::kRows + row;
         const float4 b = nb;
-        mlptc::store_input_row(sh.a[grp], row, nlo, nhi);
+        mlptc::store_input(a_tmem + lane, nlo, nhi);
         load_row(t + stride, nlo, nhi, nb);
         bool bad = false;
 #pragma unroll 1
         for (int l = 0; l < kMlpLayers; ++l) {
-            umma::fence_async_smem();
             umma::fence_before_sync();
             umma::named_sync(1 + grp, 128);
             if (row == 0) {
                 umma::fence_after_sync();
-                mlptc::issue_layer(sh.net, l, a_saddr, d_tmem);
+                mlptc::issue_layer(sh.net, l, a_tmem, d_tmem);
                 umma::commit(&sh.bar[grp]);
                 // one thread polls; the rest of its warp parks at __syncwarp and
                 // the other warps at the named barrier, leaving the issue slots
-                // to the other warpgroups' epilogues
+                // to the other warpgroup's epilogue
                 if (!umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit)) sh.failed[grp] = 1;
             }
             __syncwarp();
@@ -692,10 +690,10 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
             parity ^= 1u;
             umma::fence_after_sync();
             if (l < kMlpLayers - 1) {
-                mlptc::epilogue_hidden2(row_tmem, sh.net.bias[l], sh.a[grp], row);
+                mlptc::epilogue_hidden(d_tmem + lane, a_tmem + lane);
             } else {
                 float y[kMlpOut];
-                mlptc::epilogue_out(row_tmem, sh.net.bias4, y);
+                mlptc::epilogue_out(d_tmem + lane, y);
                 if (r < n)
                     __stcs(sv.R + r, make_float4(b.x + y[0] * S.t_scale[0], b.y + y[1] * S.t_scale[1],
                                                  b.z + y[2] * S.t_scale[2], b.w + y[3] * S.t_scale[3]));
@@ -711,7 +709,7 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
     __syncthreads();
     if (warp == 0) {
         umma::fence_after_sync();
-        umma::tmem_dealloc(sh.tmem_base, 512);
+        umma::tmem_dealloc(sh.tmem_base, mlptc::kTileCols * kNetGroups);
     }
 }
 
