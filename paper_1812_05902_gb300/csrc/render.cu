@@ -6,7 +6,8 @@
 namespace pivbos {
 
 constexpr int kRenderThreads = 256;
-constexpr int kRenderMinBlocks = 3;   // CTAs per SM the register budget must allow
+constexpr int kRenderMinBlocks = 4;   // CTAs per SM the register budget must allow
+constexpr int kBatchMinBlocks = 3;    // ... for the persistent batch kernel (4 would spill 112 B)
 // Work: the flattened (Morton slot, ray) index space (sources in Morton order,
 // read as double-float from P.src_df) is cut into chunks of
 // rays_per_cta consecutive rays; a CTA takes one chunk, so its rays come
@@ -117,7 +118,7 @@ render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restr
 // frame by frame in the order the host chose (largest work first); the
 // frame's parameters are copied to shared memory once per item.
 template <int INTEG, bool CACHE>
-__global__ void __launch_bounds__(kRenderThreads, CACHE ? 2 : kRenderMinBlocks)
+__global__ void __launch_bounds__(kRenderThreads, CACHE ? 2 : kBatchMinBlocks)
 batch_kernel(const BatchFrame* __restrict__ frames, const uint64_t* __restrict__ item_start, int n_frames,
              uint64_t total_items, unsigned long long* __restrict__ counter)
 {

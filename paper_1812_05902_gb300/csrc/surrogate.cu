@@ -291,7 +291,11 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
     S.hy = (float)(0.5 * (hi[1] - lo[1]));
     S.hz = (float)fmax(0.5 * (hi[2] - lo[2]), 1e-9);
     S.u_scale = (float)((aim_r + fmax(fabs(S.cx) + S.hx, fabs(S.cy) + S.hy)) / (aim_z - hi[2]));
-    for (int q = 0; q < 4; ++q) S.t_scale[q] = S.b_scale[q] = 1.0f;
+    S.inv_h[0] = 1.0f / S.hx;
+    S.inv_h[1] = 1.0f / S.hy;
+    S.inv_h[2] = 1.0f / S.hz;
+    S.inv_u_scale = 1.0f / S.u_scale;
+    for (int q = 0; q < 4; ++q) S.t_scale[q] = S.b_scale[q] = S.inv_b_scale[q] = 1.0f;
     S.nbx = 16;
     S.nby = 16;
     S.nbz = 16;
@@ -457,6 +461,7 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
         const double brms = sqrt(pm[4 + q] / n_pilot);
         R.correction_rms[q] = sqrt(pm[8 + q] / n_pilot);
         S.b_scale[q] = (float)(brms > 1e-30 ? brms : 1.0);
+        S.inv_b_scale[q] = 1.0f / S.b_scale[q];
         J[q] = pm[16] > 0 ? sqrt(pm[12 + q] / pm[16]) : 0.0;
         R.sensor_px_per_unit[q] = J[q];
         cc += (R.correction_rms[q] * J[q]) * (R.correction_rms[q] * J[q]) / 4.0;
@@ -642,7 +647,7 @@ pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_f
         const uint64_t chunk = std::min<uint64_t>(total, 1ull << 26);
         pivbos::ServedList sv;
         char* sbuf = nullptr;
-        const size_t off_count = ((size_t)chunk * 100 + 255) & ~(size_t)255;
+        const size_t off_count = ((size_t)chunk * 84 + 255) & ~(size_t)255;
         const size_t sbytes = off_count + 256;
         e = cudaMallocAsync((void**)&sbuf, sbytes, s);
         if (e == cudaSuccess) {
@@ -650,7 +655,7 @@ pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_f
             sv.B = (float4*)(sbuf + (size_t)chunk * 32);
             sv.R = (float4*)(sbuf + (size_t)chunk * 48);
             sv.L = (float4*)(sbuf + (size_t)chunk * 64);
-            sv.ids = (uint32_t*)(sbuf + (size_t)chunk * 96);
+            sv.ids = (uint32_t*)(sbuf + (size_t)chunk * 80);
             sv.count = (unsigned long long*)(sbuf + off_count);   // [0] served, [1] finish items
             sv.capacity = (uint32_t)chunk;
             // per device, so set on every render (cheap)

@@ -17,6 +17,8 @@ struct SurrParams {
     dfc z_ref;                      // reference plane of the exit-line residual
     float cx, cy, cz, hx, hy, hz;   // box centre and half extents (feature scaling)
     float u_scale;                  // slope scaling
+    float inv_h[3], inv_u_scale;    // 1 / hx, 1 / hy, 1 / hz, 1 / u_scale
+    float inv_b_scale[4];           // 1 / b_scale
     float t_scale[4];               // network output scales: dx, dy (m) at z_ref, dux, duy
     float b_scale[4];               // scales of the projection (Born) residual as network input
     int nbx, nby, nbz, nbu;         // confidence bins
@@ -37,8 +39,8 @@ struct Entry {
     bool enters;
     float f[5];    // entry x, y, z, slope x, slope y (scaled to about [-1, 1])
     int bin;
-    df xs, ys;     // straight line at the reference plane
-    df ux, uy;     // slopes dx/dz, dy/dz of the straight ray
+    float xs, ys;  // straight line at the reference plane
+    float ux, uy;  // slopes dx/dz, dy/dz of the straight ray
     float xe, ye, ze;   // entry point (m)
 };
 
@@ -100,21 +102,22 @@ __device__ __forceinline__ void surr_entry_f(const TraceParams& P, const SurrPar
     float dx, dy, dz;
     ray_start_f(P, sx, sy, sz, sid, k, dx, dy, dz);
     e.enters = box_entry_f(P.m, sx, sy, sz, dx, dy, dz);
-    const float ux = dx / dz, uy = dy / dz;
+    const float idz = 1.0f / dz;
+    const float ux = dx * idz, uy = dy * idz;
     const float zlo = S.z_lo.hi + S.z_lo.lo, zr = S.z_ref.hi + S.z_ref.lo;
     const float ze = sz < zlo ? zlo : sz;
     e.xe = fmaf(ux, ze - sz, sx);
     e.ye = fmaf(uy, ze - sz, sy);
     e.ze = ze;
-    e.ux = dfv(ux);
-    e.uy = dfv(uy);
-    e.xs = dfv(fmaf(ux, zr - sz, sx));
-    e.ys = dfv(fmaf(uy, zr - sz, sy));
-    e.f[0] = (e.xe - S.cx) / S.hx;
-    e.f[1] = (e.ye - S.cy) / S.hy;
-    e.f[2] = (ze - S.cz) / S.hz;
-    e.f[3] = ux / S.u_scale;
-    e.f[4] = uy / S.u_scale;
+    e.ux = ux;
+    e.uy = uy;
+    e.xs = fmaf(ux, zr - sz, sx);
+    e.ys = fmaf(uy, zr - sz, sy);
+    e.f[0] = (e.xe - S.cx) * S.inv_h[0];
+    e.f[1] = (e.ye - S.cy) * S.inv_h[1];
+    e.f[2] = (ze - S.cz) * S.inv_h[2];
+    e.f[3] = ux * S.inv_u_scale;
+    e.f[4] = uy * S.inv_u_scale;
     const int bu = bin_of(e.f[3], S.nbu) * S.nbu + bin_of(e.f[4], S.nbu);
     e.bin = ((bin_of(e.f[0], S.nbx) * S.nby + bin_of(e.f[1], S.nby)) * S.nbz + bin_of(e.f[2], S.nbz)) *
                 (S.nbu * S.nbu) + bu;
@@ -175,7 +178,7 @@ __device__ __forceinline__ void born_residual(const SurrParams& S, const Entry& 
 {
     r[0] = r[1] = r[2] = r[3] = 0.0f;
     if (S.born_k <= 0 || !e.enters) return;
-    const float ux = e.ux.hi, uy = e.uy.hi;
+    const float ux = e.ux, uy = e.uy;
     const float q = 1.0f + ux * ux + uy * uy;   // slope change (T_perp - u T_z) / T_z with T = n d, ds = dz sqrt(1+u^2)
     const float dzs = (S.zhi_f - e.ze) / (float)S.born_k;
     // accumulated slope-change integrals of the segments done so far:
@@ -226,20 +229,21 @@ __device__ __forceinline__ void encode_features(const SurrParams& S, const float
         x[5 + c] = __float2bfloat16((f[c] - __bfloat162float(hi)) * 256.0f);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) x[10 + c] = __float2bfloat16(born[c] / S.b_scale[c]);
+    for (int c = 0; c < 4; ++c) x[10 + c] = __float2bfloat16(born[c] * S.inv_b_scale[c]);
     x[14] = x[15] = __float2bfloat16(0.0f);
 }
 
 // Exit line from the residual r (m, m, rad, rad): a point on the reference
-// plane and the unit direction.
+// plane and the unit direction, in double-float (the pilot's finite
+// differences of the sensor position).
 __device__ __forceinline__ void surr_exit(const SurrParams& S, const Entry& e, const float* r, df& Rx, df& Ry, df& Rz,
                                           df& dx, df& dy, df& dz)
 {
-    Rx = df_add_f(e.xs, r[0]);
-    Ry = df_add_f(e.ys, r[1]);
+    Rx = df_add_f(dfv(e.xs), r[0]);
+    Ry = df_add_f(dfv(e.ys), r[1]);
     Rz = dfk(S.z_ref);
-    const df ux = df_add_f(e.ux, r[2]);
-    const df uy = df_add_f(e.uy, r[3]);
+    const df ux = df_add_f(dfv(e.ux), r[2]);
+    const df uy = df_add_f(dfv(e.uy), r[3]);
     const df inn = df_rsqrt(df_add_f(df_add(df_sqr(ux), df_sqr(uy)), 1.0f));
     dx = df_mul(ux, inn);
     dy = df_mul(uy, inn);
@@ -253,16 +257,20 @@ __device__ __forceinline__ void surr_residual(const SurrParams& S, const float* 
     for (int c = 0; c < 4; ++c) r[c] = born[c] + (S.use_net ? y[c] * S.t_scale[c] : 0.0f);
 }
 
-// Sensor position of a surrogate exit line: the lens and sensor in FP32
-// (the surrogate's own error, ~1e-3 px, is far above their rounding; the
-// plain path keeps double-float optics for its 1e-5 px parity).
-__device__ __forceinline__ void surr_optics(const DevOptics& o, df Rx, df Ry, df Rz, df dx, df dy, df dz,
-                                            int& status, df& px, df& py)
+// Sensor position of a surrogate ray: its straight line (xs, ys at z_ref,
+// slopes ux, uy) plus the residual r gives the exit line, which passes the
+// lens and reaches the sensor in FP32 (the surrogate's own error, ~1e-3 px,
+// is far above their rounding; the plain path keeps double-float optics for
+// its 1e-5 px parity).  status: PIVBOS_RAY_REACHED on entry.
+__device__ __forceinline__ void surr_sensor(const DevOptics& o, const SurrParams& S, float xs, float ys, float ux,
+                                            float uy, const float* r, int& status, df& px, df& py)
 {
-    float x = Rx.hi + Rx.lo, y = Ry.hi + Ry.lo, z = Rz.hi + Rz.lo;
-    float ux = dx.hi + dx.lo, uy = dy.hi + dy.lo, uz = dz.hi + dz.lo;
+    float x = xs + r[0], y = ys + r[1], z = S.z_ref.hi + S.z_ref.lo;
+    const float vx = ux + r[2], vy = uy + r[3];
+    const float inn = rsqrtf(fmaf(vx, vx, fmaf(vy, vy, 1.0f)));
+    float dx = vx * inn, dy = vy * inn, dz = inn;
     float fx, fy;
-    optics_to_sensor<F32Ops>(o, x, y, z, ux, uy, uz, status, fx, fy);
+    optics_to_sensor<F32Ops>(o, x, y, z, dx, dy, dz, status, fx, fy);
     px = dfv(fx);
     py = dfv(fy);
 }
@@ -331,10 +339,10 @@ __device__ __forceinline__ void truth_and_born(const TraceParams& P, const SurrP
         const double Dx = st.vol_dir[0] / st.vol_dir[2], Dy = st.vol_dir[1] / st.vol_dir[2];
         const double xt = st.vol_pos[0] + (zr - st.vol_pos[2]) * Dx;
         const double yt = st.vol_pos[1] + (zr - st.vol_pos[2]) * Dy;
-        t[0] = (float)(xt - df_to_double(e.xs));
-        t[1] = (float)(yt - df_to_double(e.ys));
-        t[2] = (float)(Dx - df_to_double(e.ux));
-        t[3] = (float)(Dy - df_to_double(e.uy));
+        t[0] = (float)(xt - (double)e.xs);
+        t[1] = (float)(yt - (double)e.ys);
+        t[2] = (float)(Dx - (double)e.ux);
+        t[3] = (float)(Dy - (double)e.uy);
     }
 }
 
@@ -398,11 +406,9 @@ __global__ void surr_pilot_kernel(const TraceParams P, const SurrParams S, uint6
                 Sk.born_k = 1 << c;
                 float r[4];
                 born_residual(Sk, e, r);
-                df Rx, Ry, Rz, ex, ey, ez;
-                surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
                 int status = PIVBOS_RAY_REACHED;
                 df a, b;
-                surr_optics(P.o, Rx, Ry, Rz, ex, ey, ez, status, a, b);
+                surr_sensor(P.o, S, e.xs, e.ys, e.ux, e.uy, r, status, a, b);
                 all = all && status == PIVBOS_RAY_REACHED;
                 const double dx = df_to_double(a) - st.sensor_xy[0], dy = df_to_double(b) - st.sensor_xy[1];
                 err[c] = dx * dx + dy * dy;
@@ -487,11 +493,9 @@ __global__ void surr_eval_kernel(const TraceParams P, const SurrParams S, const 
         } else if (v == 1) {
             for (int c = 0; c < 4; ++c) r[c] = born[c];
         }
-        df Rx, Ry, Rz, ex, ey, ez;
-        surr_exit(S, e, r, Rx, Ry, Rz, ex, ey, ez);
         int status = PIVBOS_RAY_REACHED;
         df px, py;
-        surr_optics(P.o, Rx, Ry, Rz, ex, ey, ez, status, px, py);
+        surr_sensor(P.o, S, e.xs, e.ys, e.ux, e.uy, r, status, px, py);
         if (status == PIVBOS_RAY_REACHED) {
             const double a = df_to_double(px) - ref_px[2 * q], b = df_to_double(py) - ref_px[2 * q + 1];
             atomicAdd(&acc.err2[v][e.bin], a * a + b * b);
@@ -514,34 +518,42 @@ struct ServedList {
     __nv_bfloat16* X;           // [capacity][16] network input
     float4* B;                  // [capacity] projection residual
     float4* R;                  // [capacity] full residual (projection + correction)
-    float4* L;                  // [capacity][2] straight line: x, y at z_ref and slopes, double-float
+    float4* L;                  // [capacity] straight line: x, y at z_ref and slopes x, y
     unsigned long long* count;  // rays appended
     uint32_t capacity;
 };
 
 constexpr uint32_t kStraightBit = 0x80000000u;
 
-// Append the calling CTA's flagged lanes (one atomic per CTA); returns this
-// thread's slot (meaningful where flag is set).  All threads call it.
-__device__ __forceinline__ unsigned long long block_append(bool flag, unsigned long long* counter, int* warp_off,
-                                                           unsigned long long* base)
+// Append the calling CTA's lanes to one of two lists (flag a: list A, flag
+// b: list B; at most one of them set per lane), with one atomic per CTA and
+// list; returns this thread's slot in its list (meaningful where a flag is
+// set).  All threads call it; blockDim.x <= 256.
+__device__ __forceinline__ unsigned long long block_append2(bool fa, bool fb, unsigned long long* count_a,
+                                                            unsigned long long* count_b, int (*warp_off)[8],
+                                                            unsigned long long* base)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-    const unsigned m = __ballot_sync(0xffffffffu, flag);
-    __syncthreads();
-    if (lane == 0) warp_off[warp] = __popc(m);
-    __syncthreads();
-    if (tid == 0) {
-        int tot = 0;
-        for (int w = 0; w < nw; ++w) {
-            const int c = warp_off[w];
-            warp_off[w] = tot;
-            tot += c;
-        }
-        *base = tot ? atomicAdd(counter, (unsigned long long)tot) : 0ull;
+    const unsigned ma = __ballot_sync(0xffffffffu, fa), mb = __ballot_sync(0xffffffffu, fb);
+    __syncthreads();   // every thread has read the previous call's offsets
+    if (lane == 0) {
+        warp_off[0][warp] = __popc(ma);
+        warp_off[1][warp] = __popc(mb);
     }
     __syncthreads();
-    return *base + (unsigned long long)(warp_off[warp] + __popc(m & ((1u << lane) - 1u)));
+    if (tid < 2) {
+        int tot = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int c = warp_off[tid][w];
+            warp_off[tid][w] = tot;
+            tot += c;
+        }
+        base[tid] = tot ? atomicAdd(tid ? count_b : count_a, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    const int l = fb ? 1 : 0;
+    const unsigned m = fb ? mb : ma;
+    return base[l] + (unsigned long long)(warp_off[l][warp] + __popc(m & ((1u << lane) - 1u)));
 }
 
 // Prep: rays [c0, c1) of the Morton-ordered (slot, ray) space, 256 per CTA
@@ -552,8 +564,8 @@ __global__ void __launch_bounds__(256)
 surr_prep_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t c1, ServedList sv,
                  uint32_t* __restrict__ fb_ids, unsigned long long* __restrict__ fb_count, uint32_t fb_capacity)
 {
-    __shared__ int warp_off[8];
-    __shared__ unsigned long long base;
+    __shared__ int warp_off[2][8];
+    __shared__ unsigned long long base[2];
     __shared__ uint32_t order[kMaxOrderRays];
     const uint32_t rps = P.rays_per_source;
     // items of kMaxOrderRays rays; with many projection segments per ray an
@@ -585,25 +597,28 @@ surr_prep_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t 
                 else mode = ((__ldg(S.bin_ok + (e.bin >> 5)) >> (e.bin & 31)) & 1u) ? 0 : 1;
                 if (mode == 0) born_residual(S, e, born);
             }
-            const unsigned long long ps = block_append(mode == 0 || mode == 2, sv.count, warp_off, &base);
+            // served and straight rays to the served list, the rest to the
+            // fallback list
+            const unsigned long long ps = block_append2(mode == 0 || mode == 2, mode == 1, sv.count, fb_count,
+                                                        warp_off, base);
             if (mode == 0 || mode == 2) {
                 if (ps < sv.capacity) {
-                    sv.ids[ps] = (uint32_t)idx | (mode == 2 ? kStraightBit : 0u);
+                    // streaming stores: the lists pass through HBM once,
+                    // leaving L2 to the projection table
+                    __stcs(sv.ids + ps, (uint32_t)idx | (mode == 2 ? kStraightBit : 0u));
                     __align__(16) __nv_bfloat16 x[kMlpIn];
                     encode_features(S, e.f, born, x);
                     uint4* xr = reinterpret_cast<uint4*>(sv.X + ps * kMlpIn);
-                    xr[0] = *reinterpret_cast<const uint4*>(&x[0]);
-                    xr[1] = *reinterpret_cast<const uint4*>(&x[8]);
-                    sv.B[ps] = make_float4(born[0], born[1], born[2], born[3]);
-                    sv.L[2 * ps] = make_float4(e.xs.hi, e.xs.lo, e.ys.hi, e.ys.lo);
-                    sv.L[2 * ps + 1] = make_float4(e.ux.hi, e.ux.lo, e.uy.hi, e.uy.lo);
+                    __stcs(xr, *reinterpret_cast<const uint4*>(&x[0]));
+                    __stcs(xr + 1, *reinterpret_cast<const uint4*>(&x[8]));
+                    __stcs(sv.B + ps, make_float4(born[0], born[1], born[2], born[3]));
+                    __stcs(sv.L + ps, make_float4(e.xs, e.ys, e.ux, e.uy));
                 } else {
                     atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_OVERFLOW);   // cannot happen: capacity = chunk
                 }
             }
-            const unsigned long long pf = block_append(mode == 1, fb_count, warp_off, &base);
             if (mode == 1) {
-                if (pf < fb_capacity) fb_ids[pf] = (uint32_t)idx;
+                if (ps < fb_capacity) fb_ids[ps] = (uint32_t)idx;
                 else atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_OVERFLOW);   // cannot happen: capacity = rays
             }
         }
@@ -743,21 +758,14 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
         if (active) {
             // the straight line from the prep kernel, plus the residual (none
             // for a ray that never enters the box)
-            const float4 l0 = sv.L[2 * pos], l1 = sv.L[2 * pos + 1];
-            Entry e;
-            e.xs = df{l0.x, l0.y};
-            e.ys = df{l0.z, l0.w};
-            e.ux = df{l1.x, l1.y};
-            e.uy = df{l1.z, l1.w};
+            const float4 l = __ldcs(sv.L + pos);
             float res[4] = {0.f, 0.f, 0.f, 0.f};
-            if (!(sv.ids[pos] & kStraightBit)) {
-                const float4 rv = resid[pos];
+            if (!(__ldcs(sv.ids + pos) & kStraightBit)) {
+                const float4 rv = __ldcs(resid + pos);
                 res[0] = rv.x; res[1] = rv.y; res[2] = rv.z; res[3] = rv.w;
             }
-            df Rx, Ry, Rz, dx, dy, dz;
-            surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
             r.status = PIVBOS_RAY_REACHED;
-            surr_optics(P.o, Rx, Ry, Rz, dx, dy, dz, r.status, r.px, r.py);
+            surr_sensor(P.o, S, l.x, l.y, l.z, l.w, res, r.status, r.px, r.py);
             cnt[r.status]++;
             if (r.status == PIVBOS_RAY_REACHED) atomicMin(&anchor_tid, tid);
         }
@@ -819,9 +827,7 @@ __global__ void surr_sensor_kernel(const TraceParams P, const SurrParams S, cons
             born_residual(S, e, born);
             surr_residual(S, born, Y + q * 4, res);
         }
-        df Rx, Ry, Rz, dx, dy, dz;
-        surr_exit(S, e, res, Rx, Ry, Rz, dx, dy, dz);
-        surr_optics(P.o, Rx, Ry, Rz, dx, dy, dz, status, px, py);
+        surr_sensor(P.o, S, e.xs, e.ys, e.ux, e.uy, res, status, px, py);
     }
     out_px[2 * q] = df_to_double(px);
     out_px[2 * q + 1] = df_to_double(py);

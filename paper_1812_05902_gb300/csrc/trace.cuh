@@ -112,17 +112,11 @@ __device__ __forceinline__ float3 eval_D(const DevMedium& m, float gx, float gy,
 // wherever the point is in the grid.
 __device__ __forceinline__ void cell_split(float gh, float gl, int N, int& i, float& f)
 {
+    // Branch-free: below the grid (or NaN) the cell is 0 and the fraction
+    // saturates to 0, above it the cell is N-2 and the fraction saturates to 1.
     const float s = gh + gl;
-    if (!(s > 0.0f)) {           // also catches NaN
-        i = 0;
-        f = 0.0f;
-    } else if (s >= (float)(N - 1)) {
-        i = N - 2;
-        f = 1.0f;
-    } else {
-        i = min((int)s, N - 2);
-        f = fminf(fmaxf(__fadd_rn(__fsub_rn(gh, (float)i), gl), 0.0f), 1.0f);
-    }
+    i = min(max((int)s, 0), N - 2);
+    f = __saturatef(__fadd_rn(__fsub_rn(gh, (float)i), gl));
 }
 
 // Corners of the last cell a ray sampled.  Consecutive Runge-Kutta stages
@@ -485,7 +479,7 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
                 float sTx = 0.f, sTy = 0.f, sTz = 0.f;   // sum of wT * K
                 float kx = 0.f, ky = 0.f, kz = 0.f;      // K of the previous stage
                 constexpr int kStages = INTEG == PIVBOS_RK4 ? 3 : 1;
-#pragma unroll 1
+#pragma unroll
                 for (int sg = 0; sg < kStages; ++sg) {
                     const float cT = sg == 0 ? 0.f : (sg == 1 ? 0.5f : 1.f);
                     const float cK = sg == 0 ? 0.f : (sg == 1 ? 0.125f : 0.5f);
