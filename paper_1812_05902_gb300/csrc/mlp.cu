@@ -286,7 +286,8 @@ mlp_fwd_tc_kernel(const __nv_bfloat16* __restrict__ wbf, const float* __restrict
             hi = *reinterpret_cast<const uint4*>(X + (size_t)row * kMlpIn + 8);
         }
         mlptc::store_input(a_tmem + lane, lo, hi);
-#pragma unroll 1
+        // unrolled: each layer's descriptors and epilogue are fixed at compile time
+#pragma unroll
         for (int l = 0; l < kMlpLayers; ++l) {
             umma::fence_before_sync();
             __syncthreads();

@@ -117,18 +117,20 @@ __device__ __forceinline__ void issue_layer(const Net& S, int l, uint32_t a_tmem
     }
 }
 
-// Hidden-layer epilogue of this thread's row: ReLU(D) as BF16 into A.
+// Hidden-layer epilogue of this thread's row: ReLU(D) as BF16 into A (all
+// 128 columns loaded before one wait, so the loads' latency is paid once).
 __device__ __forceinline__ void epilogue_hidden(uint32_t d_lane, uint32_t a_lane)
 {
-#pragma unroll 1
+    uint32_t u[kMlpHidden];
+#pragma unroll
+    for (int c0 = 0; c0 < kMlpHidden; c0 += 32) umma::tmem_ld32_nowait(d_lane + (uint32_t)c0, u + c0);
+    umma::tmem_wait();
+#pragma unroll
     for (int c0 = 0; c0 < kMlpHidden; c0 += 64) {
-        uint32_t u[64];
-        umma::tmem_ld32_nowait(d_lane + (uint32_t)c0, u);
-        umma::tmem_ld32_nowait(d_lane + (uint32_t)c0 + 32, u + 32);
-        umma::tmem_wait();
         uint32_t p[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) p[q] = umma::relu_bf16x2(__uint_as_float(u[2 * q]), __uint_as_float(u[2 * q + 1]));
+        for (int q = 0; q < 32; ++q)
+            p[q] = umma::relu_bf16x2(__uint_as_float(u[c0 + 2 * q]), __uint_as_float(u[c0 + 2 * q + 1]));
         umma::tmem_st32(a_lane + (uint32_t)(c0 / 2), p);
     }
     umma::tmem_wait_st();

@@ -635,7 +635,6 @@ struct NetSmem {
     mlptc::Net net;
     uint64_t bar[kNetGroups];
     uint32_t tmem_base;
-    int failed[kNetGroups];
 };
 
 __global__ void __launch_bounds__(128 * kNetGroups, 1)
@@ -647,10 +646,7 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
     const int tid = threadIdx.x, warp = tid >> 5, grp = warp >> 2, row = tid & 127;
     mlptc::load_net(sh.net, wbf, params);
     if (warp == 0) umma::tmem_alloc(&sh.tmem_base, mlptc::kTileCols * kNetGroups);
-    if (tid < kNetGroups) {
-        umma::mbar_init(&sh.bar[tid], 1);
-        sh.failed[tid] = 0;
-    }
+    if (tid < kNetGroups) umma::mbar_init(&sh.bar[tid], 1);
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
@@ -677,16 +673,18 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
     uint4 nlo, nhi;
     float4 nb;
     load_row((uint64_t)blockIdx.x * kNetGroups + grp, nlo, nhi, nb);
+    bool bad = false;   // a wait of this warpgroup gave up
     for (uint64_t t = (uint64_t)blockIdx.x * kNetGroups + grp; t < tiles; t += stride) {
         const uint64_t r = t * mlptc::kRows + row;
         const float4 b = nb;
         mlptc::store_input(a_tmem + lane, nlo, nhi);
         load_row(t + stride, nlo, nhi, nb);
-        bool bad = false;
-#pragma unroll 1
+        // unrolled: each layer's descriptors and epilogue are fixed at compile time
+#pragma unroll
         for (int l = 0; l < kMlpLayers; ++l) {
             umma::fence_before_sync();
             umma::named_sync(1 + grp, 128);
+            bool timed_out = false;
             if (row == 0) {
                 umma::fence_after_sync();
                 mlptc::issue_layer(sh.net, l, a_tmem, d_tmem);
@@ -694,11 +692,11 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
                 // one thread polls; the rest of its warp parks at __syncwarp and
                 // the other warps at the named barrier, leaving the issue slots
                 // to the other warpgroup's epilogue
-                if (!umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit)) sh.failed[grp] = 1;
+                timed_out = !umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit);
             }
             __syncwarp();
-            umma::named_sync(1 + grp, 128);
-            if (sh.failed[grp]) {
+            // the barrier also tells the warpgroup whether the wait gave up
+            if (umma::named_sync_or(1 + grp, 128, timed_out)) {
                 bad = true;
                 break;
             }
@@ -716,7 +714,9 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
         }
         if (bad) break;
     }
-    if (sh.failed[grp] && row == 0) {
+    if (bad && row == 0) {
+        // report, then give the MMAs in flight a second bounded wait before
+        // the tensor memory is released
         atomicCAS(status_word, 0, (int)PIVBOS_ERR_DEVICE_TIMEOUT);
         umma::mbar_wait(&sh.bar[grp], parity, mlptc::kWaitLimit);
     }

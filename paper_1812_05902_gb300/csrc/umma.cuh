@@ -195,6 +195,22 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t count)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Named barrier over `count` threads that also returns the OR of `pred`
+// over them (one instruction: the barrier carries the flag).
+__device__ __forceinline__ bool named_sync_or(uint32_t id, uint32_t count, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
 // ReLU of two FP32 values packed as BF16x2 (lo in the low half).
 __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi)
 {
