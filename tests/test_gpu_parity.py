@@ -86,3 +86,16 @@ def test_full_size_c2_sampled():
     fr = scenes.c2()[0]
     ids = _sample_ids(fr, 1500, seed=3)
     compare_states(gpu_states(fr, ids), oracle_states(fr, ids), fr.optics.pitch, vol_scale(fr))
+
+
+def test_full_size_c4_sampled_and_totals():
+    """The surrogate workload's plain render at full size (256^3 turbulence,
+    1e9 rays, 2048^2 sensor): sampled rays against the oracle, and the exact
+    intensity total of the whole render."""
+    fr = scenes.c4()[0]
+    ids = _sample_ids(fr, 1500, seed=5)
+    compare_states(gpu_states(fr, ids), oracle_states(fr, ids), fr.optics.pitch, vol_scale(fr))
+    img_g, st_g = gpu_render(fr)
+    assert st_g.sum() == fr.n_rays
+    assert img_g.sum() == int(st_g[0]) << 32
+    assert st_g[0] > 0.5 * fr.n_rays
