@@ -346,7 +346,7 @@ typedef struct {
     double ref_plane_z;     /* residual reference plane z (m); NaN = box centre */
     int32_t born_segments;  /* 0..64; 0 = no projection (the network alone); -1 = the smallest of
                                1, 2, 4, ..., 32 whose projection alone keeps the pilot rays' RMS
-                               sensor error within budget_margin * err_budget_px / 2 */
+                               sensor error within 0.8 * budget_margin * err_budget_px */
     int32_t use_network;    /* 1, or 0 = the projection alone */
     int32_t table_columns_per_cell;  /* projection-table columns per grid spacing across the box, 1..8, at
                                         most 2048 per axis; 0 = the densest of 4, 2, 1 whose table fits

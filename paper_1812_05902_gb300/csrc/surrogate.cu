@@ -409,12 +409,13 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
         return scuda(e, "surrogate pilot");
     }
     // Segment count: the smallest candidate whose projection alone keeps
-    // the pilot's RMS sensor error within half the budget the held-out
-    // estimate may use (the network corrects part of the rest), else the
-    // largest candidate.
+    // the pilot's RMS sensor error within 80 % of the budget the held-out
+    // estimate may use (the network corrects part of it and the confidence
+    // map turns away what is left over), else the largest candidate.  Each
+    // halving of the segments halves the render's table lookups.
     if (c.born_segments < 0) {
         const double nk = pm[17 + pivbos::kPilotK];
-        const double goal = 0.5 * c.budget_margin * c.err_budget_px;
+        const double goal = 0.8 * c.budget_margin * c.err_budget_px;
         int kc = pivbos::kPilotK - 1;
         for (int q = 0; q < pivbos::kPilotK; ++q)
             if (nk > 0 && sqrt(pm[17 + q] / nk) <= goal) {
