@@ -93,6 +93,8 @@ def lib():
             L.om_render.argtypes = [P, P, P, I64, ctypes.c_int32, I64, I64, U64, U32, I, D, P, P, I]
             L.om_trace_many.argtypes = [P, P, P, ctypes.c_int32, P, I64, U64, U32, I, D, P, I]
             L.om_threads.restype = I
+            L.om_line_gradient_integral.argtypes = [P, P, P, P]
+            L.om_line_gradient_integral.restype = I
             _lib = L
     return _lib
 
@@ -148,6 +150,7 @@ class Medium:
         self.dims = (nx, ny, nz)
         o = np.ascontiguousarray(origin, dtype=np.float64)
         h = np.ascontiguousarray(spacing, dtype=np.float64)
+        self.origin, self.spacing = tuple(float(v) for v in o), tuple(float(v) for v in h)
         self.h = lib().om_medium_build(_ptr(self.rho), nx, ny, nz, _ptr(o), _ptr(h), float(K))
         if not self.h:
             raise ValueError("oracle medium needs at least 2 nodes per axis")
@@ -168,6 +171,10 @@ class Medium:
         g = np.zeros((len(pts), 3))
         lib().om_sample_many(self.h, _ptr(pts), len(pts), _ptr(dn), _ptr(g))
         return dn, g
+
+    def z_mid(self):
+        """z of the mid-plane of the box"""
+        return self.origin[2] + 0.5 * (self.dims[2] - 1) * self.spacing[2]
 
     def max_steps(self, step):
         return lib().om_max_steps(self.h, step)
@@ -254,6 +261,98 @@ def render_frame(frame, image=None, first_ray=0, ray_count=None, threads=0):
     return render(med, opt, frame.sources, frame.rays_per_source, frame.seed, frame.frame_index,
                   frame.integrator, frame.step, image=image, first_ray=first_ray,
                   ray_count=ray_count, threads=threads)
+
+
+# --------------------------------------------------------------------------
+# Sec. 4: the simulated BOS experiment (per-dot displacements, Eq. 9, and
+# the regular-grid map the paper draws them on)
+# --------------------------------------------------------------------------
+def line_gradient_integral(medium, s, c):
+    """Integral over z of the sampled (dn/dx, dn/dy) along the line from s
+    toward c, over its part inside the box (``om_line_gradient_integral``).
+    Returns (integral [2], pieces)."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    out = np.zeros(2)
+    k = lib().om_line_gradient_integral(medium.h, _ptr(s), _ptr(c), _ptr(out))
+    return out, k
+
+
+def eq9_displacements(medium, dots, aim_z, magnification, n_object, pitch):
+    """Eq. 9 for every dot, in pixels of the sensor frame.
+
+    Delta X = (M Z_D / n0) * integral of grad n dz, the integral taken along
+    the dot's chief ray (toward the centre of the lens at z = aim_z), Z_D
+    from the dot to the mid-plane of the box.  A ray bent by epsilon seems to
+    come from a dot shifted by -Z_D epsilon; the lens inverts the real image
+    (the sensor frame is not flipped), so the dot's image moves by
+    +M Z_D epsilon."""
+    dots = np.ascontiguousarray(dots, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((len(dots), 2))
+    zm = medium.z_mid()
+    for q, d in enumerate(dots):
+        I, _ = line_gradient_integral(medium, d, (0.0, 0.0, aim_z))
+        out[q] = magnification * (zm - d[2]) * I / n_object / pitch
+    return out
+
+
+def bos_displacements(medium, optics, dots, rays_per_dot, seed, frame, integrator, step, threads=0,
+                      dot_ids=None):
+    """Sec. 4: every ray of a dot traced through the medium and, with the same
+    lens point, through the uniform medium; over the rays that reach the
+    sensor both times: the mean sensor position without the medium
+    (centroid, px), the mean of (with - without) (displacement, px) and the
+    number of such pairs.  Dots without a pair get NaN.  dot_ids (optional)
+    restricts the result to those dots of the set (ray k of dot d keeps its
+    lens point)."""
+    dots = np.ascontiguousarray(dots, dtype=np.float64).reshape(-1, 3)
+    sel = np.arange(len(dots), dtype=np.int64) if dot_ids is None else np.asarray(dot_ids, dtype=np.int64)
+    n = len(sel)
+    ids = (sel[:, None] * int(rays_per_dot) + np.arange(int(rays_per_dot))[None, :]).ravel()
+    a = trace_many(medium, optics, dots, rays_per_dot, ids, seed, frame, integrator, step, threads)
+    b = trace_many(None, optics, dots, rays_per_dot, ids, seed, frame, integrator, step, threads)
+    ok = ((a["status"] == REACHED) & (b["status"] == REACHED)).reshape(n, rays_per_dot)
+    pa = a["sensor_xy"].reshape(n, rays_per_dot, 2)
+    pb = b["sensor_xy"].reshape(n, rays_per_dot, 2)
+    cnt = ok.sum(1)
+    centroid = np.full((n, 2), np.nan)
+    disp = np.full((n, 2), np.nan)
+    for q in range(n):
+        if cnt[q]:
+            centroid[q] = pb[q][ok[q]].mean(0)
+            disp[q] = (pa[q][ok[q]] - pb[q][ok[q]]).mean(0)
+    return centroid, disp, cnt.astype(np.int32)
+
+
+def regrid_bilinear(xy, values, grid_w, grid_h, x0, y0, cell, min_weight=0.0):
+    """Sec. 4: scattered per-dot values onto a regular grid by bilinear
+    interpolation.  Reading: a point at grid coordinates (u, v) =
+    ((x - x0) / cell, (y - y0) / cell) inside [0, W-1] x [0, H-1] gives the
+    four nodes of its cell its value with the bilinear weights
+    (1-fu)(1-fv), fu(1-fv), (1-fu)fv, fu fv; a node holds the weighted mean
+    of what it received, NaN if its summed weight is zero or below
+    min_weight.  Returns (values [H, W, 2], weight [H, W])."""
+    xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+    values = np.asarray(values, dtype=np.float64).reshape(-1, 2)
+    acc = np.zeros((grid_h, grid_w, 2))
+    wsum = np.zeros((grid_h, grid_w))
+    for (x, y), v in zip(xy, values):
+        if not (np.isfinite(v).all() and np.isfinite(x) and np.isfinite(y)):
+            continue
+        u, t = (x - x0) / cell, (y - y0) / cell
+        if not (0.0 <= u <= grid_w - 1 and 0.0 <= t <= grid_h - 1):
+            continue
+        i = min(int(np.floor(u)), grid_w - 2)
+        j = min(int(np.floor(t)), grid_h - 2)
+        fu, fv = u - i, t - j
+        for di, dj, w in ((0, 0, (1 - fu) * (1 - fv)), (1, 0, fu * (1 - fv)),
+                          (0, 1, (1 - fu) * fv), (1, 1, fu * fv)):
+            acc[j + dj, i + di] += w * v
+            wsum[j + dj, i + di] += w
+    out = np.full((grid_h, grid_w, 2), np.nan)
+    keep = (wsum > 0.0) & (wsum >= min_weight)
+    out[keep] = acc[keep] / wsum[keep][:, None]
+    return out, wsum
 
 
 def threads() -> int:

@@ -17,6 +17,7 @@
  *                                         the first-order scheme of Sec. 3.2
  *   om_trace (optics part) .............. Sec. 3.3, Eq. 7 (Snell), apertures
  *   om_trace (sensor) / om_deposit ...... Sec. 3.4, Eq. 8 (diffraction spot)
+ *   om_line_gradient_integral ........... Sec. 4, Eq. 9 (BOS theory deflection)
  *
  * Readings where the paper is silent (box faces, final step, windows,
  * quantisation, ideal lens) are documented at each function.
@@ -628,6 +629,85 @@ void om_trace_many(const om_medium *m, const om_optics *o, const double *sources
         uint32_t k = (uint32_t)(r % rays_per_source);
         om_trace(m, o, &sources[3 * s], seed, (uint32_t)s, k, frame, integrator, step, &out[q]);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 9 (Sec. 4): the BOS theory deflection needs the integral over depth  */
+/* of the transverse gradient of n, Delta X = (M Z_D / n0) * int grad n dz.  */
+/* Reading: the integral runs along the straight line from a dot s toward   */
+/* the point c (the centre of the lens), over the part of that line inside  */
+/* the density box and between s and c, of the trilinearly sampled dn/dx    */
+/* and dn/dy (the same samples the tracer uses), with respect to z.         */
+/* Between two consecutive crossings of node planes the sample is a         */
+/* product of three linear functions of z, a cubic; each such piece is      */
+/* integrated with three-point Gauss-Legendre quadrature, which is exact    */
+/* for polynomials of degree five or less.  Returns the number of pieces    */
+/* (0: the line misses the box; -1: the line is parallel to the sensor).    */
+/* ------------------------------------------------------------------------ */
+static int om_cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+int om_line_gradient_integral(const om_medium *m, const double s[3], const double c[3], double out[2])
+{
+    out[0] = 0.0;
+    out[1] = 0.0;
+    if (c[2] == s[2]) return -1;
+    /* x(z) = s_x + a_x (z - s_z), y(z) = s_y + a_y (z - s_z) */
+    double a[3];
+    a[0] = (c[0] - s[0]) / (c[2] - s[2]);
+    a[1] = (c[1] - s[1]) / (c[2] - s[2]);
+    a[2] = 1.0;
+    double z0 = fmin(s[2], c[2]), z1 = fmax(s[2], c[2]);
+    for (int ax = 0; ax < 3; ++ax) {
+        double lo = m->origin[ax], hi = m->origin[ax] + (double)(m->n[ax] - 1) * m->spacing[ax];
+        if (a[ax] == 0.0) {
+            if (s[ax] < lo || s[ax] > hi) return 0;
+            continue;
+        }
+        /* z where coordinate ax equals lo and hi */
+        double za = s[2] + (lo - s[ax]) / a[ax];
+        double zb = s[2] + (hi - s[ax]) / a[ax];
+        z0 = fmax(z0, fmin(za, zb));
+        z1 = fmin(z1, fmax(za, zb));
+    }
+    if (!(z1 > z0)) return 0;
+    /* breakpoints: the ends and every crossing of a node plane in between */
+    int cap = 2 + m->n[0] + m->n[1] + m->n[2];
+    double *zs = (double *)malloc((size_t)cap * sizeof(double));
+    int nz = 0;
+    zs[nz++] = z0;
+    zs[nz++] = z1;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (a[ax] == 0.0) continue;
+        for (int i = 0; i < m->n[ax]; ++i) {
+            double plane = m->origin[ax] + (double)i * m->spacing[ax];
+            double zc = s[2] + (plane - s[ax]) / a[ax];
+            if (zc > z0 && zc < z1) zs[nz++] = zc;
+        }
+    }
+    qsort(zs, (size_t)nz, sizeof(double), om_cmp_double);
+    const double xg[3] = { -sqrt(0.6), 0.0, sqrt(0.6) };
+    const double wg[3] = { 5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0 };
+    int pieces = 0;
+    for (int q = 0; q + 1 < nz; ++q) {
+        double za = zs[q], zb = zs[q + 1];
+        if (!(zb > za)) continue;
+        double mid = 0.5 * (za + zb), half = 0.5 * (zb - za);
+        for (int g = 0; g < 3; ++g) {
+            double z = mid + half * xg[g];
+            double R[3] = { s[0] + a[0] * (z - s[2]), s[1] + a[1] * (z - s[2]), z };
+            double dn, gr[3];
+            om_sample(m, R, &dn, gr);
+            out[0] += half * wg[g] * gr[0];
+            out[1] += half * wg[g] * gr[1];
+        }
+        ++pieces;
+    }
+    free(zs);
+    return pieces;
 }
 
 /* helpers exposed for tests */

@@ -24,6 +24,16 @@ available; the fields below stand in for it:
 * ``c4``  Tomo-PIV scale: 1e5 particles inside a 100x100x30 mm turbulence
   field (256^3), 1e4 rays each, thick lens f/4 M = 0.2 focused on the volume
   centre, 2048x2048 sensor.
+* ``table1``  the simulated BOS experiment of Sec. 4 with the geometry of
+  Table 1: a 2-D Gaussian random density slice with a k^-5/3 inertial range
+  and a dissipation cutoff at 8 cycles per box (the paper's DNS slice is
+  resolved into its dissipation range), 256^2 nodes over 32x32 mm, mean
+  1.225 kg/m^3, 5 % rms, stacked along z over 10 mm (the paper stacks its
+  slice the same way), K = 0.226e-3 m^3/kg; dots 0.25 m (Z_D) before the
+  volume mid-plane, the lens 0.75 m (Z_A) after it, f = 105 mm, f/11 (M =
+  f / (Z_A + Z_D - f) = 0.117, printed as 0.12); 512x512 sensor of 10 um
+  pixels with 20 random dots per 32x32 pixels (5,120 dots), 1e4 rays each;
+  RK4 step 0.1 mm.
 
 Every generator takes a ``scale`` that shrinks ray and source counts (and the
 grid, where stated) for tests, keeping geometry, spacing and distributions.
@@ -150,6 +160,28 @@ def turbulence_rho(n, seed, mean=1.2, rms_frac=0.05, shape=None) -> np.ndarray:
     field -= field.mean()
     field /= field.std()
     return (mean * (1.0 + rms_frac * field)).astype(np.float32)
+
+
+def turbulence_slice_rho(n, seed, mean=1.225, rms_frac=0.05, k_cut=None) -> np.ndarray:
+    """Periodic 2-D Gaussian random field [n, n] with energy spectrum
+    E(k) ~ k^-5/3, so |rho_hat(k)| ~ |k|^-4/3 in 2-D, times a dissipation
+    cutoff exp(-(k / k_cut)^2) on the energy when k_cut (cycles per box) is
+    given; k = 0 removed; scaled to ``rms_frac`` of ``mean``."""
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal((n, n))
+    spec = np.fft.rfft2(white)
+    ky = np.fft.fftfreq(n) * n
+    kx = np.fft.rfftfreq(n) * n
+    k2 = ky[:, None] ** 2 + kx[None, :] ** 2
+    k2[0, 0] = 1.0
+    amp = k2 ** (-2.0 / 3.0)
+    if k_cut is not None:
+        amp = amp * np.exp(-0.5 * k2 / (k_cut * k_cut))
+    amp[0, 0] = 0.0
+    field = np.fft.irfft2(spec * amp, s=(n, n))
+    field -= field.mean()
+    field /= field.std()
+    return mean * (1.0 + rms_frac * field)
 
 
 def shock_rho(nx, ny, nz, spacing_y, rho1=1.2, ratio=2.5, width=0.5e-3, y_shock=None) -> np.ndarray:
@@ -335,4 +367,33 @@ def c3(scale: float = 1.0, n_frames: int = 64, max_grid: int = 256) -> List[Fram
     return frames
 
 
-WORKLOADS = {"c0": c0, "c1": c1, "c2": c2, "c3": c3, "c4": c4}
+TABLE1 = {"Z_A": 0.75, "Z_D": 0.25, "Lx": 0.032, "Ly": 0.032, "Lz": 0.010, "f": 0.105, "f_number": 11.0,
+          "M_printed": 0.12, "pitch": 10e-6, "dots_per_32x32_px": 20, "K": 0.226e-3, "rho_scale": 1.225}
+
+
+def table1(scale: float = 1.0, grid: Optional[int] = None, rays_per_source: int = 10000,
+           sensor: int = 512) -> List[Frame]:
+    """The BOS experiment of Sec. 4 with the Table 1 geometry (5.12e7 rays at
+    scale 1): a z-stacked 2-D turbulence slice, dots Z_D before the volume
+    mid-plane, an ideal thin lens Z_A after it."""
+    t = TABLE1
+    K = t["K"]
+    n0 = 1.0 + K * t["rho_scale"]
+    N = grid if grid is not None else 256
+    nz = 11
+    rho2 = turbulence_slice_rho(N, seed=5, mean=t["rho_scale"], rms_frac=0.05, k_cut=8.0)
+    rho = np.ascontiguousarray(np.broadcast_to(rho2[None, :, :], (nz, N, N)), dtype=np.float32)
+    z_mid = t["Z_D"]
+    med = Medium(rho, (-t["Lx"] / 2, -t["Ly"] / 2, z_mid - t["Lz"] / 2),
+                 (t["Lx"] / (N - 1), t["Ly"] / (N - 1), t["Lz"] / (nz - 1)), K)
+    # the lens at Z_A + Z_D from the dots, focused on them
+    M = t["f"] / (t["Z_A"] + t["Z_D"] - t["f"])
+    opt = ideal_lens_layout(0.0, M, t["f"], t["f_number"], n0, pitch=t["pitch"], width=sensor, height=sensor)
+    n_dots = max(1, int(round(t["dots_per_32x32_px"] * sensor * sensor / 1024.0 * scale)))
+    half = 0.5 * sensor * t["pitch"] / M
+    src = uniform_points(n_dots, (-half, -half, 0.0), (half, half, 0.0), seed=5)
+    rps = max(1, int(round(rays_per_source * min(1.0, scale * 100))))
+    return [Frame(med, opt, src, rps, seed=5, integrator=RK4, step=0.1e-3)]
+
+
+WORKLOADS = {"c0": c0, "c1": c1, "c2": c2, "c3": c3, "c4": c4, "table1": table1}
