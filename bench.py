@@ -20,6 +20,11 @@ surrogate path's RMS sensor error against the plain tracer (10^6 sampled
 rays) and the oracle (a few thousand rays).  The default run adds the same
 figures, with fewer steps, under the "surrogate" key of its line.
 
+--workload table1 times the simulated BOS experiment of Sec. 4 (Table 1
+geometry): per-dot mean displacements of every ray traced with and without
+the medium, the Eq. 9 theory per dot and the bilinear grid map; the default
+run adds the same figures, with fewer steps, under the "table1" key.
+
 --impl reference times the CPU oracle (the paper's method written plainly in
 FP64 C) on a bounded sample of the same workload on the host cores.
 """
@@ -50,6 +55,10 @@ WORKLOAD_NAMES = {
           "f/4 M=0.2, 2048^2",
     "c3": "64 frames in one persistent graph-replayed launch: 10^U(3,5) sources, grids 64^3-256^3, shock / "
           "gradient / turbulence in rotation, 10^U(3,4) rays/source, RK4 0.2 mm, thick lens f/8 M=0.1, 1024^2",
+    "table1": "BOS experiment of Sec. 4 with the Table 1 geometry: z-stacked 2-D k^-5/3 density slice 256^2 over "
+              "32x32x10 mm, Z_D 0.25 m, Z_A 0.75 m, f 105 mm f/11, 512^2 sensor 10 um, 5,120 dots x 1e4 rays, "
+              "RK4 0.1 mm; per-dot mean displacement (every ray traced with and without the medium), Eq. 9 "
+              "theory and the bilinear 16 px grid map",
 }
 METRIC = "rays/s traced to sensor at 1 GB300 (plain vs surrogate at ≤0.01 px RMS error)"
 
@@ -75,6 +84,8 @@ def _frames(workload, scale=1.0):
         return scenes.c4(scale=scale)
     if workload == "c3":
         return scenes.c3(scale=scale)
+    if workload == "table1":
+        return scenes.table1(scale=scale)
     raise SystemExit("unknown workload %s" % workload)
 
 
@@ -159,6 +170,7 @@ KERNEL_SOURCES = {
     "render": ("render.cu", "trace.cuh", "df64.cuh", "common.cuh"),
     "surrogate": ("surrogate.cu", "surrogate_kernels.cuh", "mlp_tc.cuh", "umma.cuh", "mlp.cuh", "trace.cuh",
                   "df64.cuh", "common.cuh"),
+    "bos": ("bos.cu", "trace.cuh", "df64.cuh", "common.cuh"),
 }
 
 
@@ -398,6 +410,12 @@ def run_gpu(args, rank, world):
             sur = run_surrogate(args, rank, world, steps=max(2, min(args.steps, 3)), warmup=1, embedded=True)
         except Exception as exc:   # reported, never hidden
             sur = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    bos = None
+    if world == 1 and args.workload == "c1" and not args.no_table1:
+        try:
+            bos = run_table1(args, rank, world, steps=3, warmup=1, embedded=True)
+        except Exception as exc:   # reported, never hidden
+            bos = {"error": "%s: %s" % (type(exc).__name__, exc)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, threads, done, t = oracle_sample(frames, seconds_target=12.0)
@@ -419,6 +437,8 @@ def run_gpu(args, rank, world):
         }
         if sur is not None:
             out["surrogate"] = sur
+        if bos is not None:
+            out["table1"] = bos
         print(json.dumps(out), flush=True)
 
 
@@ -606,6 +626,168 @@ def run_surrogate_line(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
+# A ray pair of the BOS experiment: the traced ray without its deposit, the
+# same ray through the uniform medium (generation, optics, sensor), and the
+# fixed-point conversion of its four coordinates plus the warp's segmented
+# reduction (~100 lane operations).
+OPS_PAIR_EXTRA = 710 + 125 + 40 + 100 - 450
+
+
+def run_table1(args, rank, world, steps, warmup, embedded):
+    """The BOS experiment of Sec. 4 (Table 1 geometry): per step, the per-dot
+    displacements of every ray pair, the Eq. 9 theory per dot and the
+    bilinear grid map of the displacements.  Returns the measurement."""
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    fr = _frames("table1", args.scale)[0]
+    fr.seed = fr.seed + 1000003 * rank
+    med = P.Medium(fr.medium, rho=torch.tensor(fr.medium.rho, device=dev))
+    opt = P.Optics(fr.optics)
+    n = len(fr.sources)
+    W = fr.optics.width
+    cell = 16.0
+    G = int(W // cell) + 1
+    dots = torch.tensor(fr.sources, dtype=torch.float64, device=dev)
+    cen = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    disp = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    th = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    grid = torch.empty((G, G, 2), dtype=torch.float64, device=dev)
+    gw = torch.empty((G, G), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        P.pivbos_bos_displacements(med.h, opt.h, dots, n, fr.rays_per_source, fr.seed, fr.frame_index,
+                                   fr.integrator, fr.step, cen, disp, cnt)
+        P.pivbos_bos_theory(med.h, opt.h, dots, n, th)
+        P.pivbos_regrid_bilinear(cen, disp, n, G, G, 0.0, 0.0, cell, 0.05, grid, gw)
+
+    for _ in range(warmup):
+        step()
+    P.pivbos_sync()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    P.pivbos_timing_reset()
+    P.pivbos_timing_enable(True)
+    launches0 = P.pivbos_kernel_launches()
+    ev = []
+    for _ in range(steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    launches = P.pivbos_kernel_launches() - launches0
+    P.pivbos_timing_enable(False)
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    k_ms, k_n = P.pivbos_timing_read("bos_pairs")
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rays = fr.n_rays
+    value = rays * steps * world / (ms * 1e-3)
+    c = cnt.cpu().numpy()
+    d = disp.cpu().numpy()
+    tt = th.cpu().numpy()
+    ok = c > 0.9 * fr.rays_per_source
+    agree = {}
+    for q, name in enumerate(("x", "y")):
+        agree[name] = {"corr": round(float(np.corrcoef(d[ok, q], tt[ok, q])[0, 1]), 4),
+                       "slope": round(float(np.sum(d[ok, q] * tt[ok, q]) / np.sum(tt[ok, q] ** 2)), 4),
+                       "rms_traced_px": round(float(np.sqrt(np.mean(d[ok, q] ** 2))), 4),
+                       "rms_eq9_px": round(float(np.sqrt(np.mean(tt[ok, q] ** 2))), 4)}
+    # roofline of the pair kernel: FP32/INT32 issue, and the L1 gather path
+    ms_steps = mean_steps(P, fr, opt, med, dots)
+    rf = roofline([fr], [ms_steps], k_ms, k_n, clk.get("sm_max_mhz"),
+                  recorded_traffic("bos_table1_traffic", "bos") if args.scale == 1.0 else None)
+    if rf is not None:
+        clk_hz = (clk.get("sm_max_mhz") or 2070.0) * 1e6
+        t_launch = k_ms / k_n * 1e-3
+        ops = (ops_per_ray(fr, ms_steps) + OPS_PAIR_EXTRA + sum(OPS_SURF[sf.type] for sf in fr.optics.surfaces))
+        peak = N_SM * ISSUE_LANES_PER_SM * clk_hz / 1e12
+        rf.update({"achieved": round(ops * rays / t_launch / 1e12, 3), "frac": round(ops * rays / t_launch / 1e12 / peak, 4),
+                   "kernel": "bos_pairs_kernel", "ops_per_ray": round(ops, 1)})
+    e2e = None
+    if not embedded and not args.no_e2e:
+        # dots from pinned host memory in; per-dot results and the grid map out
+        dots_h = torch.tensor(fr.sources, dtype=torch.float64).pin_memory()
+        out_h = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in (cen, disp, cnt, th, grid)]
+
+        def e2e_step():
+            dots.copy_(dots_h, non_blocking=True)
+            step()
+            for h, x in zip(out_h, (cen, disp, cnt, th, grid)):
+                h.copy_(x, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(max(1, steps)):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+        e2e = {"value": rays * max(1, steps) * world / dt, "unit": "rays/s",
+               "h2d_bytes_per_step": int(dots_h.numel() * 8),
+               "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in out_h))}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        om = oracle.Medium.from_scene(fr.medium)
+        oo = oracle.Optics.from_scene(fr.optics)
+        ids = np.arange(0, n, max(1, n // 64))[:64]
+        t0 = time.perf_counter()
+        done = 0
+        for q in ids:
+            oracle.bos_displacements(om, oo, fr.sources, fr.rays_per_source, fr.seed, fr.frame_index,
+                                     fr.integrator, fr.step, dot_ids=[q])
+            done += fr.rays_per_source
+            if time.perf_counter() - t0 > (5.0 if embedded else 12.0):
+                break
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": done / t_cpu, "unit": "rays/s", "cores": oracle.threads(), "kind": "oracle",
+               "sample": "all rays of %d dots (each traced with and without the medium), %.1f s of CPU work"
+                         % (done // fr.rays_per_source, t_cpu)}
+    return {"workload": WORKLOAD_NAMES["table1"], "name": "table1", "rays_per_step": rays, "value": value,
+            "ms_per_step": ms / steps, "kernel_ms_per_step": k_ms / max(k_n, 1), "mean_steps": ms_steps,
+            "dots": n, "dots_with_pairs": int((c > 0).sum()), "eq9_agreement": agree, "roofline": rf,
+            "clocks": clk, "gpu_launches": int(launches), "steps": steps, "warmup": warmup, "e2e": e2e,
+            "cpu_baseline": cpu}
+
+
+def run_table1_line(args, rank, world):
+    """--workload table1: the BOS experiment of Sec. 4 as the line's value."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1812_05902_gb300 import build as libbuild
+    libbuild.build()
+    res = run_table1(args, rank, world, steps=args.steps, warmup=args.warmup, embedded=False)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": res.pop("value"), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (double-float f32 pairs for positions/directions), int64 fixed-point sums",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES["table1"], "name": "table1", "rays_per_step": res["rays_per_step"],
+                       "counting": "a ray is counted once though traced twice (with and without the medium)",
+                       "l2": "flushed between steps",
+                       "parallelism": "replicas (weak)" if world > 1 else "single GPU"},
+            "gpu_launches": res.pop("gpu_launches"), "clocks": res.pop("clocks"), "roofline": res.pop("roofline"),
+            "e2e": res.pop("e2e"), "cpu_baseline": res.pop("cpu_baseline"), "impl": "pivbos", "table1": res,
+        }
+        print(json.dumps(out), flush=True)
+
+
 def run_batch(args, rank, world):
     """C3: all frames in one persistent launch (CUDA graph replay per step)."""
     import torch
@@ -674,6 +856,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the C4 surrogate figures of the default line")
+    ap.add_argument("--no-table1", action="store_true", help="skip the Sec. 4 BOS figures of the default line")
     ap.add_argument("--surrogate", action="store_true",
                     help="the surrogate path as the value (workload c4, the default here, or c2)")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -692,6 +875,8 @@ def main():
             run_surrogate_line(args, rank, world)
         elif args.workload == "c3":
             run_batch(args, rank, world)
+        elif args.workload == "table1":
+            run_table1_line(args, rank, world)
         else:
             run_gpu(args, rank, world)
     finally:

@@ -407,6 +407,60 @@ pivbos_status pivbos_surrogate_sensor(const pivbos_surrogate* sg, const pivbos_f
 pivbos_status pivbos_surrogate_report_get(const pivbos_surrogate* sg, pivbos_surrogate_report* out);
 void pivbos_surrogate_destroy(pivbos_surrogate* sg);
 
+/* ---------------------------------------------------------------------------
+ * The simulated BOS experiment of Sec. 4.
+ *
+ * pivbos_bos_displacements: every ray of every dot (ray k of dot d draws its
+ * lens point exactly as in pivbos_render: counter (k, d, frame, 0)) is traced
+ * through the medium m and, with the same lens point, through the uniform
+ * medium.  Over the rays that reach the sensor both times, per dot:
+ * centroid (device double [n_dots][2]) = mean sensor position without the
+ * medium, pixels; displacement (device double [n_dots][2]) = mean of (with -
+ * without), pixels (Sec. 4: "the ray displacements corresponding to a single
+ * dot are averaged"); n_pairs (device int32 [n_dots]) = the number of such
+ * rays.  Dots without a pair get NaN.  Each of the three outputs may be
+ * NULL.  The sums are taken in fixed point (2^-24 px, rounding error below
+ * 3e-8 px in every mean), so results are bit-identical run to run.
+ * dots: device [n_dots][3] float64.  Limits: rays_per_dot <= 2^22; sensor
+ * at most 65536 pixels per side (else UNSUPPORTED); otherwise as
+ * pivbos_render (m must not be NULL).  Asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_optics* o, const double* dots,
+                                       int64_t n_dots, int32_t rays_per_dot, uint64_t seed, uint32_t frame,
+                                       int integrator, double step, double* centroid, double* displacement,
+                                       int32_t* n_pairs, void* stream);
+
+/* Eq. 9 per dot, in pixels of the sensor frame:
+ *     displacement = (M Z_D / n0) * integral of (dn/dx, dn/dy) dz / pitch,
+ * with M, n0 (= n_object) and the pitch given to pivbos_optics_create, Z_D
+ * from the dot to the mid-plane of the box, and the integral taken along the
+ * dot's chief ray (the line to the centre of the aim disk at z = aim_z),
+ * over its part inside the box, of the trilinearly sampled gradient the
+ * tracer uses (exactly: piece by piece between node-plane crossings).  The
+ * lens inverts the real image, so a ray bent toward +y moves the dot's
+ * image toward +y in the (unflipped) sensor frame.  dots, displacement:
+ * device [n_dots][3] and [n_dots][2] float64.  Asynchronous on `stream`. */
+pivbos_status pivbos_bos_theory(const pivbos_medium* m, const pivbos_optics* o, const double* dots, int64_t n_dots,
+                                double* displacement, void* stream);
+
+/* Sec. 4: scattered values (per-dot displacements at their centroids) onto
+ * a regular grid by bilinear interpolation.  Node (i, j) sits at
+ * (x0 + i cell, y0 + j cell), i < grid_w, j < grid_h (both >= 2).  A point
+ * (xy [n][2]) inside the grid gives the four nodes of its cell its value
+ * (values [n][2]) with the bilinear weights; out[j][i] (device double
+ * [grid_h][grid_w][2]) is the weighted mean at the node, NaN where the
+ * summed weight is 0 or below min_weight; weight (device double
+ * [grid_h][grid_w], may be NULL) receives the summed weight.  Points with a
+ * non-finite coordinate or value, or outside the grid, are skipped.  Sums
+ * are fixed point (weights 2^-40, weighted values 2^-32 px): bit-identical
+ * run to run; the mean at a node that n points reach carries an absolute
+ * error below n 2^-32 (1 + |mean|) / weight.  |value| must be below 256 px
+ * per component (a larger one is skipped and the device status word reads
+ * PIVBOS_ERR_OVERFLOW at the next pivbos_sync).  n <= 2^23.  Asynchronous. */
+pivbos_status pivbos_regrid_bilinear(const double* xy, const double* values, int64_t n, int grid_w, int grid_h,
+                                     double x0, double y0, double cell, double min_weight, double* out,
+                                     double* weight, void* stream);
+
 /* int64 32.32 image -> float32 intensity in rays (value * 2^-32).  Device
  * pointers, n_pixels >= 0. */
 pivbos_status pivbos_image_finalize(const int64_t* image, int64_t n_pixels, float* out, void* stream);

@@ -225,6 +225,8 @@ pivbos_status prepare(const pivbos_medium* m, const pivbos_optics* o, const doub
 
 void set_last_error(const char* msg) { t_err = msg; }
 
+pivbos_status device_status_word(int dev, int** out) { return status_word(dev, out); }
+
 pivbos_status prepare_trace(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
                             int64_t n_sources, int sources_on_device, int32_t rays_per_source, uint64_t seed,
                             uint32_t frame, int integrator, double step, TraceParams* p, int* dev, uint64_t* total)
@@ -455,6 +457,10 @@ pivbos_status pivbos_optics_create(const pivbos_surface* surfaces, int n_surface
     d.inv_pitch = to_dfc(1.0 / pixel_pitch);
     d.half_w = 0.5f * (float)width;
     d.half_h = 0.5f * (float)height;
+    o->aim_z = aim_z;
+    o->magnification = magnification;
+    o->n_object = n_object;
+    o->pixel_pitch = pixel_pitch;
     *out = o;
     return PIVBOS_OK;
 }

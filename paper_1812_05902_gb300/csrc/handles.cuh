@@ -17,6 +17,10 @@ struct pivbos_medium {
 struct pivbos_optics {
     int device;
     pivbos::DevOptics d;
+    double aim_z;          // the creation arguments the BOS theory (Eq. 9) needs, in FP64
+    double magnification;
+    double n_object;
+    double pixel_pitch;
 };
 
 namespace pivbos {
@@ -26,6 +30,8 @@ void set_last_error(const char* msg);
 pivbos_status prepare_trace(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
                             int64_t n_sources, int sources_on_device, int32_t rays_per_source, uint64_t seed,
                             uint32_t frame, int integrator, double step, TraceParams* p, int* dev, uint64_t* total);
+// Device status word of device `dev` (allocated on first use).
+pivbos_status device_status_word(int dev, int** out);
 // Keep kernel timing out of captured streams.
 void timing_suppress(bool on);
 }  // namespace pivbos

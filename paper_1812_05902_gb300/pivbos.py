@@ -125,6 +125,9 @@ def _load():
         "pivbos_surrogate_sensor": ([P, P, P, I64, P, P, P, P], I),
         "pivbos_surrogate_report_get": ([P, P], I),
         "pivbos_surrogate_destroy": ([P], None),
+        "pivbos_bos_displacements": ([P, P, P, I64, I32, U64, U32, I, D, P, P, P, P], I),
+        "pivbos_bos_theory": ([P, P, P, I64, P, P], I),
+        "pivbos_regrid_bilinear": ([P, P, I64, I, I, D, D, D, D, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -141,7 +144,8 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_default_tuning", "pivbos_batch_create", "pivbos_batch_render", "pivbos_batch_destroy",
             "pivbos_autotune", "pivbos_render_range", "pivbos_mlp_forward", "pivbos_mlp_loss_grad",
             "pivbos_surrogate_default_cfg", "pivbos_surrogate_train", "pivbos_surrogate_render",
-            "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy")
+            "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy",
+            "pivbos_bos_displacements", "pivbos_bos_theory", "pivbos_regrid_bilinear")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
@@ -350,6 +354,27 @@ def pivbos_trace_exit_states(m, o, sources, n_sources, rays_per_source, seed, fr
     op, _ = _addr(out)
     _check(_lib.pivbos_trace_exit_states(m, o, sp, n_sources, s_dev, rays_per_source, seed, frame,
                                          integrator, step, rp, n_rays, op, _stream(stream)))
+
+
+def pivbos_bos_displacements(m, o, dots, n_dots, rays_per_dot, seed, frame, integrator, step, centroid=None,
+                             displacement=None, n_pairs=None, stream=None):
+    """Sec. 4: per-dot mean sensor position without the medium, mean
+    displacement (with - without) and pair count; CUDA tensors."""
+    _check(_lib.pivbos_bos_displacements(m, o, _addr(dots)[0], n_dots, rays_per_dot, seed, frame, integrator, step,
+                                         _addr(centroid)[0], _addr(displacement)[0], _addr(n_pairs)[0],
+                                         _stream(stream)))
+
+
+def pivbos_bos_theory(m, o, dots, n_dots, displacement, stream=None):
+    """Eq. 9 per dot (pixels) along the dot's chief ray; CUDA tensors."""
+    _check(_lib.pivbos_bos_theory(m, o, _addr(dots)[0], n_dots, _addr(displacement)[0], _stream(stream)))
+
+
+def pivbos_regrid_bilinear(xy, values, n, grid_w, grid_h, x0, y0, cell, min_weight, out, weight=None,
+                           stream=None):
+    """Scattered values onto a regular grid by bilinear weights; CUDA tensors."""
+    _check(_lib.pivbos_regrid_bilinear(_addr(xy)[0], _addr(values)[0], n, grid_w, grid_h, x0, y0, cell, min_weight,
+                                       _addr(out)[0], _addr(weight)[0], _stream(stream)))
 
 
 def pivbos_image_finalize(image, n_pixels, out, stream=None):

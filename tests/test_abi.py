@@ -153,3 +153,31 @@ def test_argument_errors_without_a_device(P):
     # spot too wide for the window
     assert L.pivbos_optics_create(None, 0, 1.0, 1.0, 0.01, 64.0, 1.0, 5e-7, 0, 2.0, 1e-6, 64, 64,
                                   ctypes.byref(out)) == P.ERR_UNSUPPORTED
+
+
+def test_bos_arguments_without_a_device(P):
+    L = P.lib()
+    fake = ctypes.c_void_p(1)  # never dereferenced: the argument checks fail first
+    assert L.pivbos_bos_displacements(None, fake, fake, 1, 1, 0, 0, 1, 1e-4, None, None, None,
+                                      None) == P.ERR_INVALID_ARG
+    assert L.pivbos_bos_displacements(fake, fake, fake, 1, (1 << 22) + 1, 0, 0, 1, 1e-4, None, None, None,
+                                      None) == P.ERR_UNSUPPORTED
+    assert L.pivbos_bos_displacements(fake, None, fake, 1, 1, 0, 0, 1, 1e-4, None, None, None,
+                                      None) == P.ERR_INVALID_ARG
+    assert L.pivbos_bos_displacements(fake, fake, fake, 1, 1, 0, 0, 7, 1e-4, None, None, None,
+                                      None) == P.ERR_INVALID_ARG
+    assert L.pivbos_bos_theory(None, fake, fake, 1, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_bos_theory(fake, None, fake, 1, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_bos_theory(fake, fake, fake, -1, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_regrid_bilinear(fake, fake, -1, 4, 4, 0.0, 0.0, 1.0, 0.0, fake, None,
+                                    None) == P.ERR_INVALID_ARG
+    assert L.pivbos_regrid_bilinear(fake, fake, (1 << 23) + 1, 4, 4, 0.0, 0.0, 1.0, 0.0, fake, None,
+                                    None) == P.ERR_INVALID_ARG
+    assert L.pivbos_regrid_bilinear(fake, fake, 1, 1, 4, 0.0, 0.0, 1.0, 0.0, fake, None,
+                                    None) == P.ERR_INVALID_ARG
+    assert L.pivbos_regrid_bilinear(fake, fake, 1, 4, 4, 0.0, 0.0, 0.0, 0.0, fake, None,
+                                    None) == P.ERR_INVALID_ARG
+    assert L.pivbos_regrid_bilinear(fake, fake, 1, 4, 4, 0.0, float("nan"), 1.0, 0.0, fake, None,
+                                    None) == P.ERR_INVALID_ARG
+    assert L.pivbos_regrid_bilinear(fake, fake, 1, 4, 4, 0.0, 0.0, 1.0, -1.0, fake, None,
+                                    None) == P.ERR_INVALID_ARG
