@@ -743,7 +743,7 @@ def run_table1(args, rank, world, steps, warmup, embedded):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         om = oracle.Medium.from_scene(fr.medium)
         oo = oracle.Optics.from_scene(fr.optics)
-        ids = np.arange(0, n, max(1, n // 64))[:64]
+        ids = np.arange(0, n, max(1, n // 1024))[:1024]
         t0 = time.perf_counter()
         done = 0
         for q in ids:

@@ -33,77 +33,110 @@ __device__ __forceinline__ long long q24(df x)
     return (long long)(int)ah * (1ll << 20) + (long long)(int)al + (long long)(int)b;
 }
 
-// One thread per ray, rays in (dot, ray) order so that the rays of a dot are
-// consecutive lanes.  A ray counts when it reaches the sensor both through
-// the medium and through the uniform medium.  Each warp reduces runs of
-// equal dot index with a segmented scan, and the last lane of a run adds
-// the run's sums to the dot's accumulators.
+// Work: like the render, the flattened (Morton slot, ray) space is cut into
+// chunks of rays_per_cta consecutive rays, one chunk per CTA, traced in
+// mid-plane Morton order in dense media (order_chunk), so that a warp's field
+// gathers hit few cells.  A ray counts when it reaches the sensor both
+// through the medium and through the uniform medium.  Sums go to per-slot
+// accumulators: a warp reduces its rays slot by slot (the rays of a chunk
+// belong to few slots), the lane holding a slot's sum adds it to the CTA's
+// shared accumulators (the first kBosSharedSlots slots of the chunk) or, past
+// them, to the global ones; the CTA then adds its shared sums to the global
+// accumulators.  All sums are integers, so the order does not matter.
+constexpr int kBosSharedSlots = 32;
+
+struct BosShared {
+    uint32_t order[kMaxOrderRays];
+    unsigned long long acc[kBosSharedSlots * kBosFields];
+};
+
 template <int INTEG>
 __global__ void __launch_bounds__(kBosThreads, 3)
-bos_pairs_kernel(const TraceParams P, unsigned long long* __restrict__ acc, uint64_t total)
+bos_pairs_kernel(const TraceParams P, unsigned long long* __restrict__ acc, uint32_t rays_per_cta, uint64_t total)
 {
-    const uint64_t idx = (uint64_t)blockIdx.x * kBosThreads + threadIdx.x;
-    const bool active = idx < total;
+    __shared__ BosShared sh;
+    const uint64_t first = (uint64_t)blockIdx.x * rays_per_cta;
+    const uint64_t last = min(first + rays_per_cta, total);
+    const uint32_t n_here = (uint32_t)(last - first);
     const uint32_t rps = P.rays_per_source;
-    uint32_t dot = 0xffffffffu;
-    long long v[kBosFields] = {0, 0, 0, 0, 0};
-    if (active) {
-        dot = (uint32_t)(idx / rps);
-        const uint32_t k = (uint32_t)(idx - (uint64_t)dot * rps);
-        const uint32_t sid = dot + P.source_offset;
-        const double* s = P.sources + 3 * (size_t)dot;
-        const df sx = df_from_double(__ldg(s)), sy = df_from_double(__ldg(s + 1)), sz = df_from_double(__ldg(s + 2));
-        // the ray without the medium first (straight to the lens): only its
-        // sensor position stays live across the traced ray
-        df qx, qy;
-        int st0 = PIVBOS_RAY_REACHED;
-        {
-            df dx, dy, dz;
-            ray_start(P, sx, sy, sz, sid, k, dx, dy, dz);
-            df Rx = sx, Ry = sy, Rz = sz;
-            optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, st0, qx, qy);
-        }
-        // the same ray (same lens point) through the medium
-        RayOut r;
-        trace_ray<INTEG, false>(P, sx, sy, sz, sid, k, r, nullptr);
-        if (r.status == PIVBOS_RAY_REACHED && st0 == PIVBOS_RAY_REACHED) {
-            v[0] = 1;
-            v[1] = q24(qx);
-            v[2] = q24(qy);
-            v[3] = q24(df_sub(r.px, qx));
-            v[4] = q24(df_sub(r.py, qy));
-        }
-    }
-    // dot indices never decrease along the lanes of a warp (inactive lanes
-    // carry the largest index), so a run of equal indices is a segment
+    const uint32_t slot0 = (uint32_t)(first / rps);
+    for (int q = threadIdx.x; q < kBosSharedSlots * kBosFields; q += blockDim.x) sh.acc[q] = 0ull;
+    const bool reorder = P.reorder && n_here <= (uint32_t)kMaxOrderRays;
+    if (reorder) order_chunk(P, sh.order, first, n_here);   // ends with a barrier
+    else __syncthreads();
     const int lane = threadIdx.x & 31;
+    const int rounds = (int)((n_here + blockDim.x - 1) / blockDim.x);
+    for (int round = 0; round < rounds; ++round) {
+        const uint32_t e = (uint32_t)round * blockDim.x + threadIdx.x;
+        const bool active = e < n_here;
+        uint32_t slot = 0;
+        long long v[kBosFields] = {0, 0, 0, 0, 0};
+        if (active) {
+            const uint64_t flat = first + (reorder ? (sh.order[e] & 0x7ffu) : e);
+            slot = (uint32_t)(flat / rps);
+            const uint32_t k = (uint32_t)(flat - (uint64_t)slot * rps);
+            const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
+            const float2* sp = P.src_df + 3 * (size_t)slot;
+            const float2 a = __ldg(sp), b = __ldg(sp + 1), c = __ldg(sp + 2);
+            const df sx = df{a.x, a.y}, sy = df{b.x, b.y}, sz = df{c.x, c.y};
+            // the ray without the medium first (straight to the lens): only
+            // its sensor position stays live across the traced ray
+            df qx, qy;
+            int st0 = PIVBOS_RAY_REACHED;
+            {
+                df dx, dy, dz;
+                ray_start(P, sx, sy, sz, sid, k, dx, dy, dz);
+                df Rx = sx, Ry = sy, Rz = sz;
+                optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, st0, qx, qy);
+            }
+            // the same ray (same lens point) through the medium
+            RayOut r;
+            trace_ray<INTEG, false>(P, sx, sy, sz, sid, k, r, nullptr);
+            if (r.status == PIVBOS_RAY_REACHED && st0 == PIVBOS_RAY_REACHED) {
+                v[0] = 1;
+                v[1] = q24(qx);
+                v[2] = q24(qy);
+                v[3] = q24(df_sub(r.px, qx));
+                v[4] = q24(df_sub(r.py, qy));
+            }
+        }
+        // the warp's pairs, one slot at a time
+        const bool has = active && v[0] != 0;
+        unsigned pending = __ballot_sync(0xffffffffu, has);
+        while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const uint32_t s_lead = __shfl_sync(0xffffffffu, slot, leader);
+            const bool mine = has && slot == s_lead;
+            const uint32_t ls = s_lead - slot0;
+            unsigned long long* dst = ls < (uint32_t)kBosSharedSlots ? sh.acc + ls * kBosFields
+                                                                     : acc + (size_t)kBosFields * s_lead;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t d_up = __shfl_up_sync(0xffffffffu, dot, off);
-        long long u[kBosFields];
+            for (int q = 0; q < kBosFields; ++q) {
+                long long w = mine ? v[q] : 0;
 #pragma unroll
-        for (int q = 0; q < kBosFields; ++q) u[q] = __shfl_up_sync(0xffffffffu, v[q], off);
-        if (lane >= off && d_up == dot) {
-#pragma unroll
-            for (int q = 0; q < kBosFields; ++q) v[q] += u[q];
+                for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+                if (lane == leader && w != 0) atomicAdd(dst + q, (unsigned long long)w);
+            }
+            pending &= ~__ballot_sync(0xffffffffu, mine);
         }
     }
-    const uint32_t d_next = __shfl_down_sync(0xffffffffu, dot, 1);
-    const bool last_of_run = lane == 31 || d_next != dot;
-    if (active && last_of_run && v[0] != 0) {
-        unsigned long long* a = acc + (size_t)kBosFields * dot;
-#pragma unroll
-        for (int q = 0; q < kBosFields; ++q)
-            if (v[q] != 0) atomicAdd(a + q, (unsigned long long)v[q]);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kBosSharedSlots * kBosFields; q += blockDim.x) {
+        const unsigned long long x = sh.acc[q];
+        if (x != 0ull) atomicAdd(acc + (size_t)kBosFields * slot0 + q, x);
     }
 }
 
-__global__ void bos_finish_kernel(const unsigned long long* __restrict__ acc, int64_t n, double* __restrict__ centroid,
-                                  double* __restrict__ disp, int32_t* __restrict__ n_pairs)
+// Per-dot results from the per-slot sums (slot = position in Morton order,
+// perm[slot] = the dot).
+__global__ void bos_finish_kernel(const unsigned long long* __restrict__ acc, const uint32_t* __restrict__ perm,
+                                  int64_t n, double* __restrict__ centroid, double* __restrict__ disp,
+                                  int32_t* __restrict__ n_pairs)
 {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    const unsigned long long* a = acc + (size_t)kBosFields * q;
+    const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= n) return;
+    const unsigned long long* a = acc + (size_t)kBosFields * slot;
+    const int64_t q = perm[slot];
     const long long c = (long long)a[0];
     if (n_pairs) n_pairs[q] = (int32_t)c;
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
@@ -366,30 +399,45 @@ pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_opti
     if (displacement && (st = device_ptr(displacement, dev, "displacement"))) return st;
     if (n_pairs && (st = device_ptr(n_pairs, dev, "n_pairs"))) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = (size_t)n_dots * kBosFields * sizeof(unsigned long long);
-    unsigned long long* acc = nullptr;
-    if ((st = bos_cuda(cudaMallocAsync((void**)&acc, bytes, s), "displacement accumulators"))) return st;
-    cudaError_t e = cudaMemsetAsync(acc, 0, bytes, s);
+    // scratch: per-slot sums | Morton keys | permutation | sorted dots (double-float)
+    const uint32_t nd = (uint32_t)n_dots;
+    uint32_t n_pow2 = 2;
+    while (n_pow2 < nd) n_pow2 <<= 1;
+    const size_t acc_bytes = (size_t)nd * kBosFields * sizeof(unsigned long long);
+    const size_t off_keys = acc_bytes;
+    const size_t off_perm = off_keys + (size_t)n_pow2 * 8;
+    const size_t off_sdf = off_perm + (((size_t)nd * 4 + 255) & ~(size_t)255);
+    const size_t bytes = off_sdf + (size_t)nd * 24;
+    char* scratch = nullptr;
+    if ((st = bos_cuda(cudaMallocAsync((void**)&scratch, bytes, s), "displacement scratch"))) return st;
+    unsigned long long* acc = (unsigned long long*)scratch;
+    uint32_t* perm = (uint32_t*)(scratch + off_perm);
+    float2* sdf = (float2*)(scratch + off_sdf);
+    cudaError_t e = cudaMemsetAsync(acc, 0, acc_bytes, s);
+    if (e == cudaSuccess) e = launch_morton_sort(dots, nd, (uint64_t*)(scratch + off_keys), n_pow2, perm, sdf, s);
     if (e == cudaSuccess && total > 0) {
-        const uint64_t blocks = (total + kBosThreads - 1) / kBosThreads;
+        p.perm = perm;
+        p.src_df = sdf;
+        const uint32_t rpc = rays_per_cta_setting(p);
+        const uint64_t blocks = (total + rpc - 1) / rpc;
         timing_begin("bos_pairs", s);
         if (integrator == PIVBOS_RK4)
-            bos_pairs_kernel<PIVBOS_RK4><<<(unsigned)blocks, kBosThreads, 0, s>>>(p, acc, total);
+            bos_pairs_kernel<PIVBOS_RK4><<<(unsigned)blocks, kBosThreads, 0, s>>>(p, acc, rpc, total);
         else
-            bos_pairs_kernel<PIVBOS_EULER><<<(unsigned)blocks, kBosThreads, 0, s>>>(p, acc, total);
+            bos_pairs_kernel<PIVBOS_EULER><<<(unsigned)blocks, kBosThreads, 0, s>>>(p, acc, rpc, total);
         timing_end("bos_pairs", s);
         count_launches(1);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        bos_finish_kernel<<<(unsigned)((n_dots + 255) / 256), 256, 0, s>>>(acc, n_dots, centroid, displacement,
+        bos_finish_kernel<<<(unsigned)((n_dots + 255) / 256), 256, 0, s>>>(acc, perm, n_dots, centroid, displacement,
                                                                           n_pairs);
         count_launches(1);
         e = cudaGetLastError();
     }
-    const cudaError_t ef = cudaFreeAsync(acc, s);
+    const cudaError_t ef = cudaFreeAsync(scratch, s);
     if ((st = bos_cuda(e, "bos_displacements"))) return st;
-    return bos_cuda(ef, "displacement accumulators release");
+    return bos_cuda(ef, "displacement scratch release");
 }
 
 pivbos_status pivbos_bos_theory(const pivbos_medium* m, const pivbos_optics* o, const double* dots, int64_t n_dots,
