@@ -29,7 +29,7 @@ _SO = os.path.join(_BUILD, "libpivbos_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SPHERE, PLANE, IDEAL_THIN, STOP = 0, 1, 2, 3
+SPHERE, PLANE, IDEAL_THIN, STOP, MIRROR, LENS_ARRAY = 0, 1, 2, 3, 4, 5
 EULER, RK4 = 0, 1
 REACHED, KILLED_STOP, KILLED_MISS, KILLED_TIR, KILLED_OFF_SENSOR, KILLED_MAXSTEP = range(6)
 
@@ -94,6 +94,10 @@ def lib():
             L.om_trace_many.argtypes = [P, P, P, ctypes.c_int32, P, I64, U64, U32, I, D, P, I]
             L.om_threads.restype = I
             L.om_line_gradient_integral.argtypes = [P, P, P, P]
+            L.om_optics_tilt_sensor.argtypes = [P, D, D]
+            L.om_reflect.argtypes = [P, P, P]
+            L.om_trace_optics.argtypes = [P, P, P, P]
+            L.om_trace_optics.restype = I
             L.om_line_gradient_integral.restype = I
             _lib = L
     return _lib
@@ -198,8 +202,17 @@ class Optics:
     @classmethod
     def from_scene(cls, o):
         sigma = sigma_eq8(o.f_number, o.magnification, o.wavelength, o.dtau_rule)
-        return cls(o.surface_array(), o.n_object, o.aim_z, o.aim_r, o.sensor_z, o.pitch,
-                   o.width, o.height, sigma)
+        opt = cls(o.surface_array(), o.n_object, o.aim_z, o.aim_r, o.sensor_z, o.pitch,
+                  o.width, o.height, sigma)
+        tx, ty = getattr(o, "sensor_tilt_x", 0.0), getattr(o, "sensor_tilt_y", 0.0)
+        if tx != 0.0 or ty != 0.0:
+            opt.tilt_sensor(tx, ty)
+        return opt
+
+    def tilt_sensor(self, tilt_x, tilt_y):
+        """turn the sensor about its centre: tilt_x about x, then tilt_y about y (radians)"""
+        lib().om_optics_tilt_sensor(self.h, float(tilt_x), float(tilt_y))
+        return self
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -228,6 +241,23 @@ def trace_many(medium, optics, sources, rays_per_source, ray_ids, seed, frame, i
     lib().om_trace_many(_mh(medium), optics.h, _ptr(src), int(rays_per_source), _ptr(ids), len(ids),
                         seed, frame, integrator, step, _ptr(out), threads)
     return out
+
+
+def reflect(d, N):
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    N = np.ascontiguousarray(N, dtype=np.float64)
+    out = np.zeros(3)
+    lib().om_reflect(_ptr(d), _ptr(N), _ptr(out))
+    return out
+
+
+def trace_optics(optics, P, d):
+    """The optics and sensor stages alone from point P, unit direction d."""
+    st = np.zeros(1, dtype=RAY_STATE)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    lib().om_trace_optics(optics.h, _ptr(P), _ptr(d), _ptr(st))
+    return st[0]
 
 
 def deposit(optics, px, py, image=None):

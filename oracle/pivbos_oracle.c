@@ -50,7 +50,8 @@ enum {
     OM_KILLED_MAXSTEP = 5    /* integration step budget exhausted */
 };
 
-enum { OM_SURF_SPHERE = 0, OM_SURF_PLANE = 1, OM_SURF_IDEAL_THIN = 2, OM_SURF_STOP = 3 };
+enum { OM_SURF_SPHERE = 0, OM_SURF_PLANE = 1, OM_SURF_IDEAL_THIN = 2, OM_SURF_STOP = 3,
+       OM_SURF_MIRROR = 4, OM_SURF_LENS_ARRAY = 5 };
 enum { OM_EULER = 0, OM_RK4 = 1 };
 
 /* ------------------------------------------------------------------------ */
@@ -239,7 +240,8 @@ static void om_D(const om_medium *m, const double R[3], double D[3])
 typedef struct {
     int type;
     double z;        /* vertex (or plane) position on the axis */
-    double R;        /* signed radius of curvature, centre at z + R (spheres) */
+    double R;        /* signed radius of curvature, centre at z + R (spheres,
+                      * mirrors); the lenslet pitch of a lens array */
     double f;        /* focal length (ideal thin lens) */
     double n_after;  /* refractive index after the surface */
     double clear_r;  /* clear (or stop) radius */
@@ -253,6 +255,10 @@ typedef struct {
     double sensor_z, pitch;
     int W, H;
     double sigma;           /* Gaussian sigma of the spot, metres (d_tau/4) */
+    /* sensor orientation: pixel axes eu, ev and normal en, the unit vectors
+     * x, y, z turned by tilt_x about x, then by tilt_y about y; the sensor
+     * centre stays at (0, 0, sensor_z) */
+    double eu[3], ev[3], en[3];
 } om_optics;
 
 typedef struct {
@@ -290,7 +296,23 @@ om_optics *om_optics_build(const double *surf /* [ns][6]: type z R f n_after cle
     o->aim_z = aim_z; o->aim_r = aim_r;
     o->sensor_z = sensor_z; o->pitch = pitch; o->W = W; o->H = H;
     o->sigma = sigma;
+    o->eu[0] = 1.0; o->ev[1] = 1.0; o->en[2] = 1.0;
     return o;
+}
+
+/* Fig. 1(d) (perspective) and the Scheimpflug arrangement need a sensor that
+ * is not square to the axis: turn the sensor about its centre, first by
+ * tilt_x (radians) about the x axis, then by tilt_y about the y axis. */
+void om_optics_tilt_sensor(om_optics *o, double tilt_x, double tilt_y)
+{
+    double cx = cos(tilt_x), sx = sin(tilt_x), cy = cos(tilt_y), sy = sin(tilt_y);
+    /* R = Ry(tilt_y) Rx(tilt_x); columns are the turned x, y, z axes */
+    double Rm[3][3] = { { cy, sy * sx, sy * cx }, { 0.0, cx, -sx }, { -sy, cy * sx, cy * cx } };
+    for (int a = 0; a < 3; ++a) {
+        o->eu[a] = Rm[a][0];
+        o->ev[a] = Rm[a][1];
+        o->en[a] = Rm[a][2];
+    }
 }
 
 void om_optics_free(om_optics *o) { free(o); }
@@ -307,6 +329,14 @@ int om_refract(const double d[3], const double N[3], double n_i, double n_f, dou
     double a = eta * ci - sqrt(k);
     for (int q = 0; q < 3; ++q) out[q] = eta * d[q] + a * N[q];
     return 1;
+}
+
+/* Sec. 3.3, item 1: the law of reflection about the unit normal N,
+ * d' = d - 2 (d.N) N. */
+void om_reflect(const double d[3], const double N[3], double out[3])
+{
+    double dn = d[0] * N[0] + d[1] * N[1] + d[2] * N[2];
+    for (int q = 0; q < 3; ++q) out[q] = d[q] - 2.0 * dn * N[q];
 }
 
 /* move the point P along d to the plane z = zp; 0 if the plane is behind */
@@ -364,6 +394,103 @@ int om_max_steps(const om_medium *m, double step)
         diag2 += L * L;
     }
     return (int)ceil(2.0 * sqrt(diag2) / step) + 4;
+}
+
+/* Sec. 3.3 and 3.4: from point R, direction d in object space through the
+ * optical elements in sequence, then onto the sensor.  Mirrors are coaxial
+ * and the system is unfolded at each one: after the reflection the ray and
+ * everything downstream are described in the frame mirrored about the
+ * mirror's vertex plane (z -> 2 z_vertex - z), so light keeps travelling
+ * toward +z and later elements are placed at larger z. */
+static int om_optics_to_sensor(const om_optics *o, double R[3], double d[3], int status, om_ray_state *out)
+{
+    double n_cur = o->n_object;
+    for (int s = 0; s < o->ns && status == OM_REACHED; ++s) {
+        const om_surface *S = &o->s[s];
+        if ((S->type == OM_SURF_SPHERE || S->type == OM_SURF_MIRROR) && S->R != 0.0) {
+            double N[3], dn2[3];
+            if (!om_sphere_hit(R, d, S->z, S->R, N)) { status = OM_KILLED_MISS; break; }
+            if (R[0] * R[0] + R[1] * R[1] > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
+            if (S->type == OM_SURF_MIRROR) {
+                om_reflect(d, N, dn2);
+                /* unfold about the vertex plane */
+                R[2] = 2.0 * S->z - R[2];
+                d[0] = dn2[0]; d[1] = dn2[1]; d[2] = -dn2[2];
+                continue;
+            }
+            if (!om_refract(d, N, n_cur, S->n_after, dn2)) { status = OM_KILLED_TIR; break; }
+            for (int a = 0; a < 3; ++a) d[a] = dn2[a];
+            n_cur = S->n_after;
+        } else {
+            if (!om_to_plane(R, d, S->z)) { status = OM_KILLED_MISS; break; }
+            double r2 = R[0] * R[0] + R[1] * R[1];
+            if (S->type == OM_SURF_STOP) {
+                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_STOP; break; }
+            } else if (S->type == OM_SURF_MIRROR) {
+                /* flat mirror square to the axis: reflection and unfolding
+                 * about its own plane leave the ray as it was */
+                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
+            } else if (S->type == OM_SURF_IDEAL_THIN || S->type == OM_SURF_LENS_ARRAY) {
+                /* reading: an ideal (perfectly stigmatic) thin lens acting on
+                 * the slopes, u' = u - (x - c) / f, c its centre; a lens array
+                 * (Sec. 3.3: "an array of lenses as in a Plenoptic camera") is
+                 * a square grid of such lenslets of pitch p centred at
+                 * (i p, j p), the ray using the lenslet whose cell holds it */
+                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
+                double cx = 0.0, cy = 0.0;
+                if (S->type == OM_SURF_LENS_ARRAY) {
+                    cx = S->R * floor(R[0] / S->R + 0.5);
+                    cy = S->R * floor(R[1] / S->R + 0.5);
+                }
+                double sx = d[0] / d[2] - (R[0] - cx) / S->f;
+                double sy = d[1] / d[2] - (R[1] - cy) / S->f;
+                double nn = sqrt(sx * sx + sy * sy + 1.0);
+                d[0] = sx / nn; d[1] = sy / nn; d[2] = 1.0 / nn;
+            } else { /* flat refracting surface (sphere with R = 0 too) */
+                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
+                double N[3] = { 0.0, 0.0, -1.0 }, dn2[3];
+                if (!om_refract(d, N, n_cur, S->n_after, dn2)) { status = OM_KILLED_TIR; break; }
+                for (int a = 0; a < 3; ++a) d[a] = dn2[a];
+                n_cur = S->n_after;
+            }
+        }
+    }
+
+    /* Sec. 3.4: line-plane intersection with the sensor (through
+     * (0, 0, sensor_z), normal en); pixel (i, j) covers [i, i+1) x [j, j+1)
+     * along the sensor axes eu, ev, with the sensor centre at the array
+     * centre */
+    double px = 0.0, py = 0.0;
+    if (status == OM_REACHED) {
+        double dn = d[0] * o->en[0] + d[1] * o->en[1] + d[2] * o->en[2];
+        double C[3] = { -R[0], -R[1], o->sensor_z - R[2] };   /* sensor centre - R */
+        double t = (C[0] * o->en[0] + C[1] * o->en[1] + C[2] * o->en[2]) / dn;
+        if (!(dn > 0.0) || t < 0.0) status = OM_KILLED_MISS;
+        else {
+            for (int a = 0; a < 3; ++a) R[a] += t * d[a];
+            double X[3] = { R[0], R[1], R[2] - o->sensor_z };  /* hit - sensor centre */
+            px = (X[0] * o->eu[0] + X[1] * o->eu[1] + X[2] * o->eu[2]) / o->pitch + 0.5 * (double)o->W;
+            py = (X[0] * o->ev[0] + X[1] * o->ev[1] + X[2] * o->ev[2]) / o->pitch + 0.5 * (double)o->H;
+            if (!(px >= 0.0 && px < (double)o->W && py >= 0.0 && py < (double)o->H))
+                status = OM_KILLED_OFF_SENSOR;
+        }
+    }
+    if (out) {
+        out->sensor_xy[0] = px; out->sensor_xy[1] = py;
+        for (int a = 0; a < 3; ++a) out->sensor_dir[a] = d[a];
+        out->status = status;
+    }
+    return status;
+}
+
+/* The optics and sensor stages alone, from a given point and unit direction
+ * in object space (for tests). */
+int om_trace_optics(const om_optics *o, const double P[3], const double d_in[3], om_ray_state *out)
+{
+    double R[3] = { P[0], P[1], P[2] }, d[3] = { d_in[0], d_in[1], d_in[2] };
+    for (int a = 0; a < 3; ++a) { out->vol_pos[a] = P[a]; out->vol_dir[a] = d_in[a]; }
+    out->steps = 0;
+    return om_optics_to_sensor(o, R, d, OM_REACHED, out);
 }
 
 int om_trace(const om_medium *m, const om_optics *o, const double src[3],
@@ -465,58 +592,7 @@ int om_trace(const om_medium *m, const om_optics *o, const double src[3],
         out->steps = steps;
     }
 
-    /* Sec. 3.3: the optical elements in sequence */
-    double n_cur = o->n_object;
-    for (int s = 0; s < o->ns && status == OM_REACHED; ++s) {
-        const om_surface *S = &o->s[s];
-        if (S->type == OM_SURF_SPHERE && S->R != 0.0) {
-            double N[3], dn2[3];
-            if (!om_sphere_hit(R, d, S->z, S->R, N)) { status = OM_KILLED_MISS; break; }
-            if (R[0] * R[0] + R[1] * R[1] > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
-            if (!om_refract(d, N, n_cur, S->n_after, dn2)) { status = OM_KILLED_TIR; break; }
-            for (int a = 0; a < 3; ++a) d[a] = dn2[a];
-            n_cur = S->n_after;
-        } else {
-            if (!om_to_plane(R, d, S->z)) { status = OM_KILLED_MISS; break; }
-            double r2 = R[0] * R[0] + R[1] * R[1];
-            if (S->type == OM_SURF_STOP) {
-                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_STOP; break; }
-            } else if (S->type == OM_SURF_IDEAL_THIN) {
-                /* reading: an ideal (perfectly stigmatic) thin lens acting on
-                 * the slopes, u' = u - x / f */
-                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
-                double sx = d[0] / d[2] - R[0] / S->f;
-                double sy = d[1] / d[2] - R[1] / S->f;
-                double nn = sqrt(sx * sx + sy * sy + 1.0);
-                d[0] = sx / nn; d[1] = sy / nn; d[2] = 1.0 / nn;
-            } else { /* flat refracting surface (sphere with R = 0 too) */
-                if (r2 > S->clear_r * S->clear_r) { status = OM_KILLED_MISS; break; }
-                double N[3] = { 0.0, 0.0, -1.0 }, dn2[3];
-                if (!om_refract(d, N, n_cur, S->n_after, dn2)) { status = OM_KILLED_TIR; break; }
-                for (int a = 0; a < 3; ++a) d[a] = dn2[a];
-                n_cur = S->n_after;
-            }
-        }
-    }
-
-    /* Sec. 3.4: line-plane intersection with the sensor; pixel (i, j) covers
-     * [i, i+1) x [j, j+1) with the optical axis at the array centre */
-    double px = 0.0, py = 0.0;
-    if (status == OM_REACHED) {
-        if (!om_to_plane(R, d, o->sensor_z)) status = OM_KILLED_MISS;
-        else {
-            px = R[0] / o->pitch + 0.5 * (double)o->W;
-            py = R[1] / o->pitch + 0.5 * (double)o->H;
-            if (!(px >= 0.0 && px < (double)o->W && py >= 0.0 && py < (double)o->H))
-                status = OM_KILLED_OFF_SENSOR;
-        }
-    }
-    if (out) {
-        out->sensor_xy[0] = px; out->sensor_xy[1] = py;
-        for (int a = 0; a < 3; ++a) out->sensor_dir[a] = d[a];
-        out->status = status;
-    }
-    return status;
+    return om_optics_to_sensor(o, R, d, status, out);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -135,15 +135,26 @@ uint32_t rays_per_cta_setting(const TraceParams& p)
 
 // Gather strategy for a medium: reorder a CTA's rays when a ray makes many
 // field evaluations (the box depth in steps times the stages per step); keep
-// the last cell's corners in registers when, in addition, a step is short
-// against every grid spacing, so that consecutive stages mostly fall in one
-// cell (PIVBOS_CELL_CACHE overrides).
-void choose_gather(const pivbos_medium* m, double step, int integrator, TraceParams& p)
+// the last cell's corners in registers when, in addition, a step moves a ray
+// by less than 0.75 of a grid spacing along every axis, so that consecutive
+// stages mostly fall in one cell (PIVBOS_CELL_CACHE overrides).  Along z a
+// step moves a ray by at most the step; across, by at most the step times
+// the largest lateral slope of a ray that crosses the box toward the aim
+// disk (the whole step when the aim disk is not beyond the box).
+void choose_gather(const pivbos_medium* m, const pivbos_optics* o, double step, int integrator, TraceParams& p)
 {
     const double evals = (double)(m->n[2] - 1) * m->spacing[2] / step * (integrator == PIVBOS_RK4 ? 3.0 : 1.0);
     p.reorder = evals >= 64.0 ? 1 : 0;
-    const double hmin = fmin(m->spacing[0], fmin(m->spacing[1], m->spacing[2]));
-    p.cell_cache = tuning_cell_cache(p.reorder && step < 0.75 * hmin);
+    double slope = 1.0;
+    const double z_hi = m->origin[2] + (double)(m->n[2] - 1) * m->spacing[2];
+    if (o && o->aim_z > z_hi) {
+        double r = 0.0;
+        for (int a = 0; a < 2; ++a)
+            r = fmax(r, fmax(fabs(m->origin[a]), fabs(m->origin[a] + (double)(m->n[a] - 1) * m->spacing[a])));
+        slope = fmin(1.0, (r + o->d.aim_r.hi) / (o->aim_z - z_hi));
+    }
+    const double move = fmax(step / m->spacing[2], fmax(step * slope / m->spacing[0], step * slope / m->spacing[1]));
+    p.cell_cache = tuning_cell_cache(p.reorder && move < 0.75);
 }
 
 namespace {
@@ -202,7 +213,7 @@ pivbos_status prepare(const pivbos_medium* m, const pivbos_optics* o, const doub
         if (ms > 2.0e9) return fail(PIVBOS_ERR_UNSUPPORTED, "step too small for the box (%g steps)", ms);
         p.max_steps = (int)ms;
         p.m.z_key = (float)(m->origin[2] + 0.5 * (double)(m->n[2] - 1) * m->spacing[2]);
-        choose_gather(m, step, integrator, p);
+        choose_gather(m, o, step, integrator, p);
     }
     p.o = o->d;
     p.sources = sources;

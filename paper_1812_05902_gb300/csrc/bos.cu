@@ -50,8 +50,8 @@ struct BosShared {
     unsigned long long acc[kBosSharedSlots * kBosFields];
 };
 
-template <int INTEG>
-__global__ void __launch_bounds__(kBosThreads, 3)
+template <int INTEG, bool CACHE>
+__global__ void __launch_bounds__(kBosThreads, CACHE ? 2 : 3)
 bos_pairs_kernel(const TraceParams P, unsigned long long* __restrict__ acc, uint32_t rays_per_cta, uint64_t total)
 {
     __shared__ BosShared sh;
@@ -91,7 +91,7 @@ bos_pairs_kernel(const TraceParams P, unsigned long long* __restrict__ acc, uint
             }
             // the same ray (same lens point) through the medium
             RayOut r;
-            trace_ray<INTEG, false>(P, sx, sy, sz, sid, k, r, nullptr);
+            trace_ray<INTEG, CACHE>(P, sx, sy, sz, sid, k, r, nullptr);
             if (r.status == PIVBOS_RAY_REACHED && st0 == PIVBOS_RAY_REACHED) {
                 v[0] = 1;
                 v[1] = q24(qx);
@@ -421,10 +421,14 @@ pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_opti
         const uint32_t rpc = rays_per_cta_setting(p);
         const uint64_t blocks = (total + rpc - 1) / rpc;
         timing_begin("bos_pairs", s);
-        if (integrator == PIVBOS_RK4)
-            bos_pairs_kernel<PIVBOS_RK4><<<(unsigned)blocks, kBosThreads, 0, s>>>(p, acc, rpc, total);
-        else
-            bos_pairs_kernel<PIVBOS_EULER><<<(unsigned)blocks, kBosThreads, 0, s>>>(p, acc, rpc, total);
+        const unsigned g = (unsigned)blocks;
+        if (integrator == PIVBOS_RK4) {
+            if (p.cell_cache) bos_pairs_kernel<PIVBOS_RK4, true><<<g, kBosThreads, 0, s>>>(p, acc, rpc, total);
+            else bos_pairs_kernel<PIVBOS_RK4, false><<<g, kBosThreads, 0, s>>>(p, acc, rpc, total);
+        } else {
+            if (p.cell_cache) bos_pairs_kernel<PIVBOS_EULER, true><<<g, kBosThreads, 0, s>>>(p, acc, rpc, total);
+            else bos_pairs_kernel<PIVBOS_EULER, false><<<g, kBosThreads, 0, s>>>(p, acc, rpc, total);
+        }
         timing_end("bos_pairs", s);
         count_launches(1);
         e = cudaGetLastError();

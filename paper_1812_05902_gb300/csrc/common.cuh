@@ -105,7 +105,8 @@ cudaError_t launch_finalize(const int64_t* image, int64_t n, float* out, cudaStr
 // PIVBOS_CELL_CACHE=0/1 overrides the default (on for dense media).
 int tuning_cell_cache(int dense);
 // reorder / cell-cache choice for rendering through a medium (api.cu)
-void choose_gather(const ::pivbos_medium* m, double step, int integrator, TraceParams& p);
+void choose_gather(const ::pivbos_medium* m, const ::pivbos_optics* o, double step, int integrator,
+                   TraceParams& p);
 // rays per CTA of a render (api.cu)
 uint32_t rays_per_cta_setting(const TraceParams& p);
 

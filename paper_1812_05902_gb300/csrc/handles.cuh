@@ -17,7 +17,7 @@ struct pivbos_medium {
 struct pivbos_optics {
     int device;
     pivbos::DevOptics d;
-    double aim_z;          // the creation arguments the BOS theory (Eq. 9) needs, in FP64
+    double aim_z;          // creation arguments kept in FP64 (Eq. 9 theory, gather choice)
     double magnification;
     double n_object;
     double pixel_pitch;

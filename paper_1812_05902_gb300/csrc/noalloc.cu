@@ -148,7 +148,7 @@ extern "C" pivbos_status pivbos_render_noalloc(const pivbos_medium* m, const piv
         if (ms > 2.0e9) return err(PIVBOS_ERR_UNSUPPORTED, "step too small for the box (%g steps)", ms);
         p.max_steps = (int)ms;
         p.m.z_key = (float)(m->origin[2] + 0.5 * (double)(m->n[2] - 1) * m->spacing[2]);
-        pivbos::choose_gather(m, step, integrator, p);
+        pivbos::choose_gather(m, o, step, integrator, p);
     }
     p.o = o->d;
     p.sources = sources;

@@ -46,7 +46,7 @@ from typing import List, Optional
 
 import numpy as np
 
-SPHERE, PLANE, IDEAL_THIN, STOP = 0, 1, 2, 3
+SPHERE, PLANE, IDEAL_THIN, STOP, MIRROR, LENS_ARRAY = 0, 1, 2, 3, 4, 5
 EULER, RK4 = 0, 1
 
 K_AIR = 0.225e-3          # m^3/kg, the Gladstone-Dale constant the workloads use
@@ -58,7 +58,7 @@ LAMBDA_GREEN = 532e-9     # m, effective wavelength for white light (Sec. 3.4)
 class Surface:
     type: int
     z: float
-    R: float = 0.0
+    R: float = 0.0          # signed radius (spheres, mirrors); lenslet pitch (lens arrays)
     f: float = 0.0
     n_after: float = 1.0
     clear_r: float = 1.0
@@ -81,6 +81,8 @@ class Optics:
     magnification: float
     wavelength: float = LAMBDA_GREEN
     dtau_rule: int = 0     # 0: Eq. 8 as printed (2.44 pi ...), 1: textbook 2.44
+    sensor_tilt_x: float = 0.0   # radians about x, then
+    sensor_tilt_y: float = 0.0   # radians about y (the sensor turns about its centre)
 
     def surface_array(self) -> np.ndarray:
         return np.array([s.as_row() for s in self.surfaces], dtype=np.float64).reshape(-1, 6)
