@@ -167,7 +167,7 @@ N_SM = 152
 
 # the sources each profiled kernel is compiled from
 KERNEL_SOURCES = {
-    "render": ("render.cu", "trace.cuh", "df64.cuh", "common.cuh"),
+    "render": ("render.cu", "render_chunk.cuh", "trace.cuh", "df64.cuh", "common.cuh"),
     "surrogate": ("surrogate.cu", "surrogate_kernels.cuh", "mlp_tc.cuh", "umma.cuh", "mlp.cuh", "trace.cuh",
                   "df64.cuh", "common.cuh"),
     "bos": ("bos.cu", "trace.cuh", "df64.cuh", "common.cuh"),

@@ -55,12 +55,22 @@ enum {
     PIVBOS_RAY_NSTATUS = 6
 };
 
-/* Optical element kinds (Sec. 3.3). */
+/* Optical element kinds (Sec. 3.3).  Elements are sequential along +z.  A
+ * mirror reflects by the law of reflection (Sec. 3.3, item 1) and the system
+ * is unfolded there: the reflected ray and every later element (and the
+ * sensor) are described in the frame mirrored about the mirror's vertex
+ * plane, z -> 2 z_vertex - z, so later elements sit at larger z.  Mirrors
+ * are coaxial; the index the ray travels in does not change at a mirror. */
 enum {
     PIVBOS_SURF_SPHERE = 0,     /* refracting sphere: vertex z, signed radius (centre at z + R) */
     PIVBOS_SURF_PLANE = 1,      /* flat refracting surface at z */
     PIVBOS_SURF_IDEAL_THIN = 2, /* ideal thin lens of focal length f at z (slopes u' = u - x/f) */
-    PIVBOS_SURF_STOP = 3        /* aperture: rays outside clear_radius at z are blocked */
+    PIVBOS_SURF_STOP = 3,       /* aperture: rays outside clear_radius at z are blocked */
+    PIVBOS_SURF_MIRROR = 4,     /* mirror: vertex z, signed radius (0 = flat, square to the axis) */
+    PIVBOS_SURF_LENS_ARRAY = 5  /* square array of ideal thin lenslets at z (Sec. 3.3: plenoptic camera):
+                                   focal length f, lenslet pitch in `radius`, lenslet centres at
+                                   (i pitch, j pitch); a ray uses the lenslet whose cell holds it:
+                                   u' = u - (x - centre) / f */
 };
 
 /* Integrators of the ray equation (Sec. 3.2). */
@@ -78,8 +88,8 @@ typedef struct {
     int32_t type;          /* PIVBOS_SURF_* */
     int32_t reserved;      /* must be 0 */
     double z_vertex;       /* m, position of the vertex (or plane) on the axis */
-    double radius;         /* m, signed radius of curvature (spheres only) */
-    double focal;          /* m, focal length (ideal thin lens only) */
+    double radius;         /* m, signed radius of curvature (spheres, mirrors); lenslet pitch (lens arrays) */
+    double focal;          /* m, focal length (ideal thin lens, lens array) */
     double n_after;        /* refractive index after the surface */
     double clear_radius;   /* m, clear (or stop) radius */
 } pivbos_surface;
@@ -142,6 +152,16 @@ pivbos_status pivbos_optics_create(const pivbos_surface* surfaces, int n_surface
                                    double f_number, double magnification, double wavelength,
                                    int dtau_rule, double sensor_z, double pixel_pitch,
                                    int width, int height, pivbos_optics** out);
+
+/* A copy of `o` whose sensor is turned about its centre (0, 0, sensor_z):
+ * first by tilt_x radians about the x axis, then by tilt_y about the y axis
+ * (Fig. 1(d): perspective; the Scheimpflug arrangement).  Pixel (i, j) then
+ * covers [i, i+1) x [j, j+1) along the turned x and y axes of the sensor,
+ * the sensor centre at the array centre; a ray meets the sensor plane where
+ * the line crosses it (a ray travelling away from the sensor's front, or
+ * with the plane behind it, is a MISS).  The spot keeps its size in pixels.
+ * Errors: INVALID_ARG (NULL, non-finite angles), OOM. */
+pivbos_status pivbos_optics_tilt_sensor(const pivbos_optics* o, double tilt_x, double tilt_y, pivbos_optics** out);
 
 void pivbos_optics_destroy(pivbos_optics* o);
 

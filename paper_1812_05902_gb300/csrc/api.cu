@@ -413,10 +413,12 @@ pivbos_status pivbos_optics_create(const pivbos_surface* surfaces, int n_surface
         return fail(PIVBOS_ERR_INVALID_ARG, "sensor %d x %d", width, height);
     for (int i = 0; i < n_surfaces; ++i) {
         const pivbos_surface& s = surfaces[i];
-        if (s.type < PIVBOS_SURF_SPHERE || s.type > PIVBOS_SURF_STOP || s.reserved != 0 || !isfinite(s.z_vertex) ||
-            !isfinite(s.radius) || !(isfinite(s.clear_radius) && s.clear_radius >= 0.0) ||
+        if (s.type < PIVBOS_SURF_SPHERE || s.type > PIVBOS_SURF_LENS_ARRAY || s.reserved != 0 ||
+            !isfinite(s.z_vertex) || !isfinite(s.radius) || !(isfinite(s.clear_radius) && s.clear_radius >= 0.0) ||
             ((s.type == PIVBOS_SURF_SPHERE || s.type == PIVBOS_SURF_PLANE) && !finite_pos(s.n_after)) ||
-            (s.type == PIVBOS_SURF_IDEAL_THIN && !(isfinite(s.focal) && s.focal != 0.0)))
+            ((s.type == PIVBOS_SURF_IDEAL_THIN || s.type == PIVBOS_SURF_LENS_ARRAY) &&
+             !(isfinite(s.focal) && s.focal != 0.0)) ||
+            (s.type == PIVBOS_SURF_LENS_ARRAY && !(s.radius > 0.0)))
             return fail(PIVBOS_ERR_INVALID_ARG, "surface %d is malformed", i);
     }
     {
@@ -446,7 +448,8 @@ pivbos_status pivbos_optics_create(const pivbos_surface* surfaces, int n_surface
         D.z = to_dfc(s.z_vertex);
         D.R = to_dfc(s.radius);
         D.invR = to_dfc(s.radius != 0.0 ? 1.0 / s.radius : 0.0);
-        D.inv_f = to_dfc(s.type == PIVBOS_SURF_IDEAL_THIN ? 1.0 / s.focal : 0.0);
+        D.inv_f = to_dfc((s.type == PIVBOS_SURF_IDEAL_THIN || s.type == PIVBOS_SURF_LENS_ARRAY) ? 1.0 / s.focal
+                                                                                               : 0.0);
         if (D.type == PIVBOS_SURF_SPHERE || D.type == PIVBOS_SURF_PLANE) {
             const double eta = n_cur / s.n_after;
             D.eta = to_dfc(eta);
@@ -473,6 +476,30 @@ pivbos_status pivbos_optics_create(const pivbos_surface* surfaces, int n_surface
     o->n_object = n_object;
     o->pixel_pitch = pixel_pitch;
     *out = o;
+    return PIVBOS_OK;
+}
+
+pivbos_status pivbos_optics_tilt_sensor(const pivbos_optics* o, double tilt_x, double tilt_y, pivbos_optics** out)
+{
+    t_err.clear();
+    if (!o || !out) return fail(PIVBOS_ERR_INVALID_ARG, "optics or out is NULL");
+    *out = nullptr;
+    if (!isfinite(tilt_x) || !isfinite(tilt_y)) return fail(PIVBOS_ERR_INVALID_ARG, "tilt angles must be finite");
+    pivbos_optics* c = new (std::nothrow) pivbos_optics(*o);
+    if (!c) return fail(PIVBOS_ERR_OOM, "host allocation");
+    // the sensor's axes: x, y, z turned by tilt_x about x, then by tilt_y about y
+    const double cx = cos(tilt_x), sx = sin(tilt_x), cy = cos(tilt_y), sy = sin(tilt_y);
+    const double eu[3] = {cy, 0.0, -sy};
+    const double ev[3] = {sy * sx, cx, cy * sx};
+    const double en[3] = {sy * cx, -sx, cy * cx};
+    DevOptics& d = c->d;
+    d.tilted = 1;
+    for (int a = 0; a < 3; ++a) {
+        d.eu[a] = to_dfc(eu[a]);
+        d.ev[a] = to_dfc(ev[a]);
+        d.en[a] = to_dfc(en[a]);
+    }
+    *out = c;
     return PIVBOS_OK;
 }
 

@@ -93,8 +93,10 @@ pivbos_status enqueue(pivbos_batch* b, cudaStream_t s)
                                        const_cast<uint32_t*>(F.p.perm), const_cast<float2*>(F.p.src_df), s);
         if (e != cudaSuccess) return cerr(e, "batch source ordering");
     }
+    bool ext = false;
+    for (int f = 0; f < b->n_frames; ++f) ext = ext || pivbos::optics_ext(b->frames[f].p.o);
     e = pivbos::launch_batch(b->d_frames, b->d_item_start, b->n_frames, b->total_items, b->d_counter, b->integrator,
-                             b->tuning.cell_cache != 0, b->tuning.ctas_per_sm, s);
+                             b->tuning.cell_cache != 0, ext, b->tuning.ctas_per_sm, s);
     if (e != cudaSuccess) return cerr(e, "batch kernel");
     return PIVBOS_OK;
 }

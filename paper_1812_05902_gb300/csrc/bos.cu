@@ -50,7 +50,7 @@ struct BosShared {
     unsigned long long acc[kBosSharedSlots * kBosFields];
 };
 
-template <int INTEG, bool CACHE>
+template <int INTEG, bool CACHE, bool EXT>
 __global__ void __launch_bounds__(kBosThreads, CACHE ? 2 : 3)
 bos_pairs_kernel(const TraceParams P, unsigned long long* __restrict__ acc, uint32_t rays_per_cta, uint64_t total)
 {
@@ -87,11 +87,11 @@ bos_pairs_kernel(const TraceParams P, unsigned long long* __restrict__ acc, uint
                 df dx, dy, dz;
                 ray_start(P, sx, sy, sz, sid, k, dx, dy, dz);
                 df Rx = sx, Ry = sy, Rz = sz;
-                optics_to_sensor(P.o, Rx, Ry, Rz, dx, dy, dz, st0, qx, qy);
+                optics_to_sensor<DfOps, EXT>(P.o, Rx, Ry, Rz, dx, dy, dz, st0, qx, qy);
             }
             // the same ray (same lens point) through the medium
             RayOut r;
-            trace_ray<INTEG, CACHE>(P, sx, sy, sz, sid, k, r, nullptr);
+            trace_ray<INTEG, CACHE, EXT>(P, sx, sy, sz, sid, k, r, nullptr);
             if (r.status == PIVBOS_RAY_REACHED && st0 == PIVBOS_RAY_REACHED) {
                 v[0] = 1;
                 v[1] = q24(qx);
@@ -422,13 +422,10 @@ pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_opti
         const uint64_t blocks = (total + rpc - 1) / rpc;
         timing_begin("bos_pairs", s);
         const unsigned g = (unsigned)blocks;
-        if (integrator == PIVBOS_RK4) {
-            if (p.cell_cache) bos_pairs_kernel<PIVBOS_RK4, true><<<g, kBosThreads, 0, s>>>(p, acc, rpc, total);
-            else bos_pairs_kernel<PIVBOS_RK4, false><<<g, kBosThreads, 0, s>>>(p, acc, rpc, total);
-        } else {
-            if (p.cell_cache) bos_pairs_kernel<PIVBOS_EULER, true><<<g, kBosThreads, 0, s>>>(p, acc, rpc, total);
-            else bos_pairs_kernel<PIVBOS_EULER, false><<<g, kBosThreads, 0, s>>>(p, acc, rpc, total);
-        }
+        const bool ext = optics_ext(p.o);
+#define PV_BOS(I, C, E) bos_pairs_kernel<I, C, E><<<g, kBosThreads, 0, s>>>(p, acc, rpc, total)
+        PV_DISPATCH(integrator, p.cell_cache != 0, ext, PV_BOS);
+#undef PV_BOS
         timing_end("bos_pairs", s);
         count_launches(1);
         e = cudaGetLastError();

@@ -33,7 +33,7 @@ struct DevSurface {
     float R_f;         // signed radius (FP32, for sign tests)
     float clear_r2;    // clear radius squared (FP32, for the aperture tests)
     float pad;
-    dfc z, R, invR;    // vertex position, radius, 1/R
+    dfc z, R, invR;    // vertex position, radius, 1/R (lens array: pitch, 1/pitch)
     dfc eta, eta2;     // n_before / n_after and its square (refracting surfaces)
     dfc inv_f;         // 1 / focal length (ideal thin lens)
 };
@@ -48,7 +48,19 @@ struct DevOptics {
     float half_w, half_h;  // W/2, H/2
     float inv_sqrt2_sigma; // 1 / (sqrt(2) sigma_px)
     float sigma_px;
+    int tilted;            // 0: sensor square to the axis; 1: axes eu, ev and normal en below
+    dfc eu[3], ev[3], en[3];
 };
+
+// Whether optics hold a mirror, a lens array or a turned sensor: the kernels
+// compiled with the extended optics stage are launched only then.
+inline bool optics_ext(const DevOptics& o)
+{
+    if (o.tilted) return true;
+    for (int s = 0; s < o.ns; ++s)
+        if (o.s[s].type == PIVBOS_SURF_MIRROR || o.s[s].type == PIVBOS_SURF_LENS_ARRAY) return true;
+    return false;
+}
 
 struct TraceParams {
     DevMedium m;
@@ -98,7 +110,21 @@ cudaError_t launch_list(const TraceParams& p, int integrator, const unsigned lon
                         int64_t* image, int64_t* stats, uint32_t rays_per_cta, unsigned long long* counter,
                         cudaStream_t s);
 cudaError_t launch_batch(const BatchFrame* frames, const uint64_t* item_start, int n_frames, uint64_t total_items,
-                         unsigned long long* counter, int integrator, bool cache, int ctas_per_sm, cudaStream_t s);
+                         unsigned long long* counter, int integrator, bool cache, bool ext, int ctas_per_sm,
+                         cudaStream_t s);
+
+// Launch KERNEL_CALL(INTEG, CACHE, EXT) with the template arguments chosen
+// at run time (integrator, cell cache, extended optics).
+#define PV_DISPATCH(integrator, cache, ext, KERNEL_CALL)                                        \
+    do {                                                                                       \
+        if ((integrator) == PIVBOS_RK4) {                                                      \
+            if (cache) { if (ext) KERNEL_CALL(PIVBOS_RK4, true, true); else KERNEL_CALL(PIVBOS_RK4, true, false); } \
+            else { if (ext) KERNEL_CALL(PIVBOS_RK4, false, true); else KERNEL_CALL(PIVBOS_RK4, false, false); }   \
+        } else {                                                                               \
+            if (cache) { if (ext) KERNEL_CALL(PIVBOS_EULER, true, true); else KERNEL_CALL(PIVBOS_EULER, true, false); } \
+            else { if (ext) KERNEL_CALL(PIVBOS_EULER, false, true); else KERNEL_CALL(PIVBOS_EULER, false, false); }   \
+        }                                                                                      \
+    } while (0)
 cudaError_t launch_finalize(const int64_t* image, int64_t n, float* out, cudaStream_t s);
 
 // Tuning knob (api.cu): keep cell corners in registers during integration;

@@ -678,8 +678,12 @@ pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_f
                     pivbos::timing_end("surrogate_net", s);
                 }
                 pivbos::timing_begin("surrogate_finish", s);
-                pivbos::surr_finish_kernel<<<sms * 4, 256, 0, s>>>(P, sg->S, sv, sg->S.use_net ? sv.R : sv.B,
-                                                                    frame->image, frame->stats, sv.count + 1);
+                if (pivbos::optics_ext(P.o))
+                    pivbos::surr_finish_kernel<true><<<sms * 4, 256, 0, s>>>(
+                        P, sg->S, sv, sg->S.use_net ? sv.R : sv.B, frame->image, frame->stats, sv.count + 1);
+                else
+                    pivbos::surr_finish_kernel<false><<<sms * 4, 256, 0, s>>>(
+                        P, sg->S, sv, sg->S.use_net ? sv.R : sv.B, frame->image, frame->stats, sv.count + 1);
                 pivbos::timing_end("surrogate_finish", s);
                 pivbos::count_launches(sg->S.use_net ? 3 : 2);
                 e = cudaGetLastError();

@@ -262,6 +262,7 @@ __device__ __forceinline__ void surr_residual(const SurrParams& S, const float* 
 // lens and reaches the sensor in FP32 (the surrogate's own error, ~1e-3 px,
 // is far above their rounding; the plain path keeps double-float optics for
 // its 1e-5 px parity).  status: PIVBOS_RAY_REACHED on entry.
+template <bool EXT = true>
 __device__ __forceinline__ void surr_sensor(const DevOptics& o, const SurrParams& S, float xs, float ys, float ux,
                                             float uy, const float* r, int& status, df& px, df& py)
 {
@@ -270,7 +271,7 @@ __device__ __forceinline__ void surr_sensor(const DevOptics& o, const SurrParams
     const float inn = rsqrtf(fmaf(vx, vx, fmaf(vy, vy, 1.0f)));
     float dx = vx * inn, dy = vy * inn, dz = inn;
     float fx, fy;
-    optics_to_sensor<F32Ops>(o, x, y, z, dx, dy, dz, status, fx, fy);
+    optics_to_sensor<F32Ops, EXT>(o, x, y, z, dx, dy, dz, status, fx, fy);
     px = dfv(fx);
     py = dfv(fy);
 }
@@ -731,6 +732,7 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
 // Finish: the served list in chunks of 256 consecutive entries (one round of
 // the prep kernel's rays: a few neighbouring sources), each chunk deposited
 // into a shared tile anchored at its first hit.
+template <bool EXT>
 __global__ void __launch_bounds__(256, 3)
 surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const float4* __restrict__ resid,
                    int64_t* __restrict__ image, int64_t* __restrict__ stats, unsigned long long* __restrict__ counter)
@@ -765,7 +767,7 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
                 res[0] = rv.x; res[1] = rv.y; res[2] = rv.z; res[3] = rv.w;
             }
             r.status = PIVBOS_RAY_REACHED;
-            surr_sensor(P.o, S, l.x, l.y, l.z, l.w, res, r.status, r.px, r.py);
+            surr_sensor<EXT>(P.o, S, l.x, l.y, l.z, l.w, res, r.status, r.px, r.py);
             cnt[r.status]++;
             if (r.status == PIVBOS_RAY_REACHED) atomicMin(&anchor_tid, tid);
         }

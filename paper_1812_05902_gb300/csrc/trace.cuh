@@ -288,6 +288,7 @@ struct DfOps {
     static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
     static __device__ __forceinline__ T add_f(T a, float b) { return df_add_f(a, b); }
     static __device__ __forceinline__ bool lt(T a, T b) { return df_lt(a, b); }
+    static __device__ __forceinline__ int floor_i(T a) { float f; return df_floor(a, f); }
 };
 struct F32Ops {
     using T = float;
@@ -306,9 +307,15 @@ struct F32Ops {
     static __device__ __forceinline__ T neg(T a) { return -a; }
     static __device__ __forceinline__ T add_f(T a, float b) { return a + b; }
     static __device__ __forceinline__ bool lt(T a, T b) { return a < b; }
+    static __device__ __forceinline__ int floor_i(T a) { return (int)floorf(a); }
 };
 
-template <class N = DfOps>
+// EXT = false compiles the plain elements only (spheres, planes, ideal thin
+// lenses, stops) and a sensor square to the axis; EXT = true adds mirrors,
+// lens arrays and a turned sensor.  Launchers pick EXT = false unless the
+// optics hold one of those, so the plain path's code stays as compact as
+// before they existed.
+template <class N = DfOps, bool EXT = true>
 __device__ __forceinline__ void optics_to_sensor(const DevOptics& o, typename N::T& Rx, typename N::T& Ry,
                                                  typename N::T& Rz, typename N::T& dx, typename N::T& dy,
                                                  typename N::T& dz, int& status, typename N::T& px,
@@ -320,7 +327,7 @@ __device__ __forceinline__ void optics_to_sensor(const DevOptics& o, typename N:
         if (!(N::hi(dz) > 0.0f)) { status = PIVBOS_RAY_MISS; break; }
         const T inv_dz = N::rcp(dz);
         const T t0 = N::mul(N::sub(N::k(S.z), Rz), inv_dz);
-        if (S.type == PIVBOS_SURF_SPHERE && S.R_f != 0.0f) {
+        if ((S.type == PIVBOS_SURF_SPHERE || (EXT && S.type == PIVBOS_SURF_MIRROR)) && S.R_f != 0.0f) {
             // vertex-relative quadratic t^2 + 2 b t + c = 0 from the point Q
             // on the vertex plane; the vertex-side root has the smaller
             // magnitude: t = c / (-b - sign(b) sqrt(b^2 - c))
@@ -343,6 +350,18 @@ __device__ __forceinline__ void optics_to_sensor(const DevOptics& o, typename N:
             if (N::hi(Nx) * N::hi(dx) + N::hi(Ny) * N::hi(dy) + N::hi(Nz) * N::hi(dz) > 0.0f) {
                 Nx = N::neg(Nx); Ny = N::neg(Ny); Nz = N::neg(Nz);
             }
+            if (EXT && S.type == PIVBOS_SURF_MIRROR) {
+                // Sec. 3.3, item 1: d' = d - 2 (d.N) N; then unfold about the
+                // vertex plane (z - z_v -> z_v - z, d_z -> -d_z)
+                const T dn2 = N::mul(N::v(2.0f), N::add(N::add(N::mul(Nx, dx), N::mul(Ny, dy)), N::mul(Nz, dz)));
+                dx = N::sub(dx, N::mul(dn2, Nx));
+                dy = N::sub(dy, N::mul(dn2, Ny));
+                dz = N::neg(N::sub(dz, N::mul(dn2, Nz)));
+                Rx = Hx;
+                Ry = Hy;
+                Rz = N::sub(N::k(S.z), Hz);
+                continue;
+            }
             // Eq. 7, vector form
             const T eta = N::k(S.eta);
             const T ci = N::neg(N::add(N::add(N::mul(Nx, dx), N::mul(Ny, dy)), N::mul(Nz, dz)));
@@ -363,11 +382,25 @@ __device__ __forceinline__ void optics_to_sensor(const DevOptics& o, typename N:
             const float r2 = N::hi(Rx) * N::hi(Rx) + N::hi(Ry) * N::hi(Ry);
             if (S.type == PIVBOS_SURF_STOP) {
                 if (r2 > S.clear_r2) { status = PIVBOS_RAY_STOP; break; }
-            } else if (S.type == PIVBOS_SURF_IDEAL_THIN) {
+            } else if (EXT && S.type == PIVBOS_SURF_MIRROR) {
+                // flat mirror square to the axis: reflection and unfolding
+                // about its own plane leave the ray as it was
+                if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
+            } else if (S.type == PIVBOS_SURF_IDEAL_THIN || (EXT && S.type == PIVBOS_SURF_LENS_ARRAY)) {
                 if (r2 > S.clear_r2) { status = PIVBOS_RAY_MISS; break; }
                 const T invf = N::k(S.inv_f);
-                const T ux = N::sub(N::mul(dx, inv_dz), N::mul(Rx, invf));
-                const T uy = N::sub(N::mul(dy, inv_dz), N::mul(Ry, invf));
+                // position relative to the lens centre: the lenslet of the
+                // ray's cell for an array (centres at multiples of the pitch)
+                T xr = Rx, yr = Ry;
+                if (EXT && S.type == PIVBOS_SURF_LENS_ARRAY) {
+                    const T p = N::k(S.R), ip = N::k(S.invR);
+                    const float ci = (float)N::floor_i(N::add_f(N::mul(Rx, ip), 0.5f));
+                    const float cj = (float)N::floor_i(N::add_f(N::mul(Ry, ip), 0.5f));
+                    xr = N::sub(Rx, N::mul(p, N::v(ci)));
+                    yr = N::sub(Ry, N::mul(p, N::v(cj)));
+                }
+                const T ux = N::sub(N::mul(dx, inv_dz), N::mul(xr, invf));
+                const T uy = N::sub(N::mul(dy, inv_dz), N::mul(yr, invf));
                 const T inn = N::rsqrt(N::add_f(N::add(N::sqr(ux), N::sqr(uy)), 1.0f));
                 dx = N::mul(ux, inn);
                 dy = N::mul(uy, inn);
@@ -389,7 +422,29 @@ __device__ __forceinline__ void optics_to_sensor(const DevOptics& o, typename N:
     // ---- Sec. 3.4: sensor plane -------------------------------------------
     px = N::v(0.0f);
     py = N::v(0.0f);
-    if (status == PIVBOS_RAY_REACHED) {
+    bool turned = false;
+    if constexpr (EXT) turned = o.tilted != 0;
+    if (EXT && turned && status == PIVBOS_RAY_REACHED) {
+        // a turned sensor: the plane through (0, 0, sensor_z) with normal en,
+        // pixel axes eu, ev
+        const T enx = N::k(o.en[0]), eny = N::k(o.en[1]), enz = N::k(o.en[2]);
+        const T dn = N::add(N::add(N::mul(dx, enx), N::mul(dy, eny)), N::mul(dz, enz));
+        const T cz = N::sub(N::k(o.sensor_z), Rz);
+        const T t = N::div(N::sub(N::mul(cz, enz), N::add(N::mul(Rx, enx), N::mul(Ry, eny))), dn);
+        if (!(N::hi(dn) > 0.0f) || N::hi(t) < 0.0f) {
+            status = PIVBOS_RAY_MISS;
+        } else {
+            const T Xx = N::fma(t, dx, Rx), Xy = N::fma(t, dy, Ry), Xz = N::sub(N::mul(t, dz), cz);
+            const T ipitch = N::k(o.inv_pitch);
+            const T u = N::add(N::add(N::mul(Xx, N::k(o.eu[0])), N::mul(Xy, N::k(o.eu[1]))), N::mul(Xz, N::k(o.eu[2])));
+            const T w = N::add(N::add(N::mul(Xx, N::k(o.ev[0])), N::mul(Xy, N::k(o.ev[1]))), N::mul(Xz, N::k(o.ev[2])));
+            px = N::add_f(N::mul(u, ipitch), o.half_w);
+            py = N::add_f(N::mul(w, ipitch), o.half_h);
+            const bool inx = !N::lt(px, N::v(0.0f)) && N::lt(px, N::v((float)o.W));
+            const bool iny = !N::lt(py, N::v(0.0f)) && N::lt(py, N::v((float)o.H));
+            if (!(inx && iny)) status = PIVBOS_RAY_OFF_SENSOR;
+        }
+    } else if (status == PIVBOS_RAY_REACHED) {
         if (!(N::hi(dz) > 0.0f)) {
             status = PIVBOS_RAY_MISS;
         } else {
@@ -412,7 +467,7 @@ __device__ __forceinline__ void optics_to_sensor(const DevOptics& o, typename N:
 // One ray through all stages.  INTEG: PIVBOS_EULER or PIVBOS_RK4.  If st is
 // not null the full exit state is written (parity path).
 // ---------------------------------------------------------------------------
-template <int INTEG, bool CACHE>
+template <int INTEG, bool CACHE, bool EXT = true>
 __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df sz, uint32_t sid, uint32_t rid,
                                           RayOut& out, pivbos_ray_state* st)
 {
@@ -531,7 +586,7 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
 
     // ---- Sec. 3.3-3.4: optical elements and the sensor plane --------------
     df px, py;
-    optics_to_sensor(o, Rx, Ry, Rz, dx, dy, dz, status, px, py);
+    optics_to_sensor<DfOps, EXT>(o, Rx, Ry, Rz, dx, dy, dz, status, px, py);
     if (st) {
         st->sensor_xy[0] = df_to_double(px);
         st->sensor_xy[1] = df_to_double(py);

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libpivbos.so")
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_OVERFLOW, ERR_UNSUPPORTED = range(7)
 RAY_REACHED, RAY_STOP, RAY_MISS, RAY_TIR, RAY_OFF_SENSOR, RAY_MAXSTEP = range(6)
 RAY_NSTATUS = 6
-SURF_SPHERE, SURF_PLANE, SURF_IDEAL_THIN, SURF_STOP = range(4)
+SURF_SPHERE, SURF_PLANE, SURF_IDEAL_THIN, SURF_STOP, SURF_MIRROR, SURF_LENS_ARRAY = range(6)
 EULER, RK4 = 0, 1
 MAX_SURFACES = 16
 MAX_WINDOW = 12
@@ -100,6 +100,7 @@ def _load():
         "pivbos_medium_destroy": ([P], None),
         "pivbos_optics_create": ([P, I, D, D, D, D, D, D, I, D, D, I, I, P], I),
         "pivbos_optics_destroy": ([P], None),
+        "pivbos_optics_tilt_sensor": ([P, D, D, P], I),
         "pivbos_render": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
         "pivbos_trace_exit_states": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I64, P, P], I),
         "pivbos_image_finalize": ([P, I64, P, P], I),
@@ -145,7 +146,7 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_autotune", "pivbos_render_range", "pivbos_mlp_forward", "pivbos_mlp_loss_grad",
             "pivbos_surrogate_default_cfg", "pivbos_surrogate_train", "pivbos_surrogate_render",
             "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy",
-            "pivbos_bos_displacements", "pivbos_bos_theory", "pivbos_regrid_bilinear")
+            "pivbos_bos_displacements", "pivbos_bos_theory", "pivbos_regrid_bilinear", "pivbos_optics_tilt_sensor")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
@@ -216,6 +217,13 @@ def pivbos_optics_create(surfaces, n_object, aim_z, aim_radius, f_number, magnif
     _check(_lib.pivbos_optics_create(arr if n else None, n, n_object, aim_z, aim_radius, f_number, magnification,
                                      wavelength, dtau_rule, sensor_z, pixel_pitch, width, height,
                                      ctypes.byref(out)))
+    return out
+
+
+def pivbos_optics_tilt_sensor(o, tilt_x, tilt_y):
+    """A new optics handle: `o` with its sensor turned about its centre."""
+    out = ctypes.c_void_p()
+    _check(_lib.pivbos_optics_tilt_sensor(o, tilt_x, tilt_y, ctypes.byref(out)))
     return out
 
 
@@ -443,6 +451,11 @@ class Optics:
         self.h = pivbos_optics_create([s.as_row() for s in so.surfaces], so.n_object, so.aim_z, so.aim_r,
                                       so.f_number, so.magnification, so.wavelength, so.dtau_rule,
                                       so.sensor_z, so.pitch, so.width, so.height)
+        tx, ty = getattr(so, "sensor_tilt_x", 0.0), getattr(so, "sensor_tilt_y", 0.0)
+        if tx != 0.0 or ty != 0.0:
+            flat = self.h
+            self.h = pivbos_optics_tilt_sensor(flat, tx, ty)
+            pivbos_optics_destroy(flat)
 
     def close(self):
         if getattr(self, "h", None):

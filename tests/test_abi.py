@@ -181,3 +181,18 @@ def test_bos_arguments_without_a_device(P):
                                     None) == P.ERR_INVALID_ARG
     assert L.pivbos_regrid_bilinear(fake, fake, 1, 4, 4, 0.0, 0.0, 1.0, -1.0, fake, None,
                                     None) == P.ERR_INVALID_ARG
+
+
+def test_optics_extension_arguments_without_a_device(P):
+    L = P.lib()
+    out = ctypes.c_void_p()
+    fake = ctypes.c_void_p(1)
+    assert L.pivbos_optics_tilt_sensor(None, 0.1, 0.0, ctypes.byref(out)) == P.ERR_INVALID_ARG
+    assert L.pivbos_optics_tilt_sensor(fake, float("inf"), 0.0, ctypes.byref(out)) == P.ERR_INVALID_ARG
+    assert L.pivbos_optics_tilt_sensor(fake, 0.1, 0.0, None) == P.ERR_INVALID_ARG
+    # a lens array needs a positive pitch and a focal length; type 6 does not exist
+    for row in ((P.SURF_LENS_ARRAY, 0, 1.0, 0.0, 0.01, 1.0, 0.05), (P.SURF_LENS_ARRAY, 0, 1.0, 1e-3, 0.0, 1.0, 0.05),
+                (6, 0, 1.0, 0.0, 0.0, 1.0, 0.05)):
+        bad = (P.pivbos_surface * 1)(P.pivbos_surface(*row))
+        assert L.pivbos_optics_create(bad, 1, 1.0, 1.0, 0.01, 8.0, 0.1, 5e-7, 0, 2.0, 1e-5, 64, 64,
+                                      ctypes.byref(out)) == P.ERR_INVALID_ARG
