@@ -98,6 +98,11 @@ def lib():
             L.om_reflect.argtypes = [P, P, P]
             L.om_trace_optics.argtypes = [P, P, P, P]
             L.om_trace_optics.restype = I
+            L.om_mie.argtypes = [D, D, D, I, P, P]
+            L.om_mie.restype = I
+            L.om_optics_radiance.argtypes = [P, P, I, P, P]
+            L.om_ray_weight.argtypes = [P, P, U64, U32, U32, U32]
+            L.om_ray_weight.restype = D
             L.om_line_gradient_integral.restype = I
             _lib = L
     return _lib
@@ -207,7 +212,22 @@ class Optics:
         tx, ty = getattr(o, "sensor_tilt_x", 0.0), getattr(o, "sensor_tilt_y", 0.0)
         if tx != 0.0 or ty != 0.0:
             opt.tilt_sensor(tx, ty)
+        mie_cfg = getattr(o, "mie", None)
+        if mie_cfg is not None:
+            s12, _ = mie(mie_size_parameter(mie_cfg.diameter, mie_cfg.wavelength, mie_cfg.n_medium),
+                         mie_cfg.m_re, mie_cfg.m_im, mie_cfg.n_angles)
+            opt.radiance(s12, mie_cfg.laser_dir, mie_cfg.polarisation)
         return opt
+
+    def radiance(self, s12, laser_dir, polarisation=None):
+        """Mie radiance per ray (Sec. 3.1): table s12 [n, 2] of |S1|^2, |S2|^2 at
+        angles 0..pi, laser direction, polarisation (None = unpolarised)"""
+        self._rad = np.ascontiguousarray(s12, dtype=np.float64).reshape(-1, 2)
+        L = np.ascontiguousarray(laser_dir, dtype=np.float64)
+        pol = None if polarisation is None else np.ascontiguousarray(polarisation, dtype=np.float64)
+        lib().om_optics_radiance(self.h, _ptr(self._rad), len(self._rad), _ptr(L),
+                                 None if pol is None else _ptr(pol))
+        return self
 
     def tilt_sensor(self, tilt_x, tilt_y):
         """turn the sensor about its centre: tilt_x about x, then tilt_y about y (radians)"""
@@ -241,6 +261,26 @@ def trace_many(medium, optics, sources, rays_per_source, ray_ids, seed, frame, i
     lib().om_trace_many(_mh(medium), optics.h, _ptr(src), int(rays_per_source), _ptr(ids), len(ids),
                         seed, frame, integrator, step, _ptr(out), threads)
     return out
+
+
+def mie_size_parameter(diameter, wavelength, n_medium):
+    """x = pi d n_medium / lambda (lambda in vacuum)"""
+    return np.pi * diameter * n_medium / wavelength
+
+
+def mie(x, m_re, m_im=0.0, n_angles=181):
+    """Mie scattering by a homogeneous sphere (``om_mie``): returns (s12 [n, 2] =
+    |S1|^2, |S2|^2 at theta = 0..pi, {q_ext, q_sca, re_s0, terms})."""
+    s12 = np.zeros((n_angles, 2))
+    q = np.zeros(4)
+    if not lib().om_mie(float(x), float(m_re), float(m_im), int(n_angles), _ptr(s12), _ptr(q)):
+        raise ValueError("bad Mie input")
+    return s12, {"q_ext": q[0], "q_sca": q[1], "re_s0": q[2], "terms": int(q[3])}
+
+
+def ray_weight(optics, src, seed, source_id, ray_id, frame):
+    s = np.ascontiguousarray(src, dtype=np.float64)
+    return lib().om_ray_weight(optics.h, _ptr(s), seed, source_id, ray_id, frame)
 
 
 def reflect(d, N):

@@ -18,6 +18,7 @@
  *   om_trace (optics part) .............. Sec. 3.3, Eq. 7 (Snell), apertures
  *   om_trace (sensor) / om_deposit ...... Sec. 3.4, Eq. 8 (diffraction spot)
  *   om_line_gradient_integral ........... Sec. 4, Eq. 9 (BOS theory deflection)
+ *   om_mie / om_ray_weight .............. Sec. 3.1 (Mie radiance of a ray)
  *
  * Readings where the paper is silent (box faces, final step, windows,
  * quantisation, ideal lens) are documented at each function.
@@ -29,6 +30,7 @@
  * Build: gcc -O2 -std=c11 -fopenmp -ffp-contract=off -shared -fPIC
  * (-ffp-contract=off so that x86 and Arm give the same FP64 results.)
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -259,6 +261,12 @@ typedef struct {
      * x, y, z turned by tilt_x about x, then by tilt_y about y; the sensor
      * centre stays at (0, 0, sensor_z) */
     double eu[3], ev[3], en[3];
+    /* Mie radiance (Sec. 3.1): 0 = none (every ray weighs 1), 1 = unpolarised
+     * laser, 2 = linearly polarised along pol; table of |S1|^2, |S2|^2 at
+     * n_rad angles from 0 to pi; laser along L */
+    int rad_mode, n_rad;
+    double *rad;
+    double L[3], pol[3], rad_max;
 } om_optics;
 
 typedef struct {
@@ -315,7 +323,11 @@ void om_optics_tilt_sensor(om_optics *o, double tilt_x, double tilt_y)
     }
 }
 
-void om_optics_free(om_optics *o) { free(o); }
+void om_optics_free(om_optics *o)
+{
+    if (o) free(o->rad);
+    free(o);
+}
 
 /* Eq. 7 in vector form.  N is the unit surface normal facing the incoming
  * ray (N.d < 0).  Returns 0 on total internal reflection (the ray is then
@@ -596,6 +608,140 @@ int om_trace(const om_medium *m, const om_optics *o, const double src[3],
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 3.1: the radiance of a ray from a PIV particle follows Mie          */
+/* scattering (the paper computes it with Bohren & Huffman's method).  The  */
+/* series solution for a homogeneous sphere of size parameter x = pi d /   */
+/* lambda (wavelength in the medium) and relative index m:                  */
+/*   a_n, b_n from the Riccati-Bessel functions psi_n(x) = x j_n(x),        */
+/*   xi_n(x) = x h_n(x) = psi_n - i chi_n (upward recurrences from n = -1,  */
+/*   0) and the logarithmic derivative D_n(mx) = psi_n'(mx) / psi_n(mx)     */
+/*   (downward recurrence, started well above the last order);             */
+/*   S1 = sum (2n+1)/(n(n+1)) (a_n pi_n + b_n tau_n),                       */
+/*   S2 = sum (2n+1)/(n(n+1)) (a_n tau_n + b_n pi_n), with the angular      */
+/*   functions pi_n, tau_n of mu = cos(theta) by their recurrences;         */
+/*   Q_ext = (2/x^2) sum (2n+1) Re(a_n + b_n),                              */
+/*   Q_sca = (2/x^2) sum (2n+1) (|a_n|^2 + |b_n|^2);                        */
+/*   the series stops after x + 4 x^(1/3) + 2 terms.                        */
+/* s12[2i], s12[2i+1] = |S1|^2, |S2|^2 at theta_i = pi i / (n_angles - 1);  */
+/* q = {Q_ext, Q_sca, Re S(0), n_terms}.  Returns the number of terms, 0 on */
+/* bad input.                                                               */
+/* ------------------------------------------------------------------------ */
+int om_mie(double x, double m_re, double m_im, int n_angles, double *s12, double *q)
+{
+    if (!(x > 0.0) || !(m_re > 0.0) || n_angles < 2) return 0;
+    double complex m = m_re + I * m_im;
+    int nstop = (int)(x + 4.0 * cbrt(x) + 2.0);
+    double mx = cabs(m * x);
+    int nmx = (int)fmax((double)nstop, mx) + 16;
+    double complex *D = (double complex *)calloc((size_t)nmx + 1, sizeof(double complex));
+    double complex *a = (double complex *)calloc((size_t)nstop + 1, sizeof(double complex));
+    double complex *b = (double complex *)calloc((size_t)nstop + 1, sizeof(double complex));
+    double complex z = m * x;
+    D[nmx] = 0.0;
+    for (int n = nmx; n >= 1; --n) D[n - 1] = (double)n / z - 1.0 / (D[n] + (double)n / z);
+    double psi_m1 = cos(x), psi_0 = sin(x);      /* psi_{-1}, psi_0 */
+    double chi_m1 = -sin(x), chi_0 = cos(x);     /* chi_{-1}, chi_0 */
+    double qe = 0.0, qs = 0.0;
+    for (int n = 1; n <= nstop; ++n) {
+        double psi_n = (2.0 * n - 1.0) / x * psi_0 - psi_m1;
+        double chi_n = (2.0 * n - 1.0) / x * chi_0 - chi_m1;
+        double complex xi_n = psi_n - I * chi_n, xi_p = psi_0 - I * chi_0;
+        double complex ta = D[n] / m + (double)n / x;
+        double complex tb = m * D[n] + (double)n / x;
+        a[n] = (ta * psi_n - psi_0) / (ta * xi_n - xi_p);
+        b[n] = (tb * psi_n - psi_0) / (tb * xi_n - xi_p);
+        qe += (2.0 * n + 1.0) * creal(a[n] + b[n]);
+        qs += (2.0 * n + 1.0) * (creal(a[n]) * creal(a[n]) + cimag(a[n]) * cimag(a[n]) +
+                                 creal(b[n]) * creal(b[n]) + cimag(b[n]) * cimag(b[n]));
+        psi_m1 = psi_0; psi_0 = psi_n;
+        chi_m1 = chi_0; chi_0 = chi_n;
+    }
+    double complex s_fwd = 0.0;
+    for (int i = 0; i < n_angles; ++i) {
+        double th = M_PI * (double)i / (double)(n_angles - 1);
+        double mu = cos(th);
+        double pi_prev = 0.0, pi_n = 1.0;   /* pi_0, pi_1 */
+        double complex S1 = 0.0, S2 = 0.0;
+        for (int n = 1; n <= nstop; ++n) {
+            double tau_n = n * mu * pi_n - (n + 1.0) * pi_prev;
+            double f = (2.0 * n + 1.0) / ((double)n * (n + 1.0));
+            S1 += f * (a[n] * pi_n + b[n] * tau_n);
+            S2 += f * (a[n] * tau_n + b[n] * pi_n);
+            double pi_next = ((2.0 * n + 1.0) / n) * mu * pi_n - ((n + 1.0) / n) * pi_prev;
+            pi_prev = pi_n;
+            pi_n = pi_next;
+        }
+        if (i == 0) s_fwd = S1;
+        s12[2 * i] = creal(S1) * creal(S1) + cimag(S1) * cimag(S1);
+        s12[2 * i + 1] = creal(S2) * creal(S2) + cimag(S2) * cimag(S2);
+    }
+    if (q) {
+        q[0] = 2.0 / (x * x) * qe;
+        q[1] = 2.0 / (x * x) * qs;
+        q[2] = creal(s_fwd);
+        q[3] = nstop;
+    }
+    free(D); free(a); free(b);
+    return nstop;
+}
+
+/* Give the optics a Mie radiance: the table of |S1|^2, |S2|^2 over n
+ * angles (om_mie), the laser direction L (unit) and, for a linearly
+ * polarised laser, its polarisation pol (unit, normal to L; NULL =
+ * unpolarised).  A ray leaving its source along d0 scatters by theta =
+ * acos(d0.L); |S1|^2 and |S2|^2 are interpolated linearly in theta; its
+ * radiance is |S2|^2 cos^2(phi) + |S1|^2 sin^2(phi) (phi between pol and
+ * the scattering plane; unpolarised: the mean of the two) divided by the
+ * largest entry of the table, so that weights lie in [0, 1]. */
+void om_optics_radiance(om_optics *o, const double *s12, int n, const double L[3], const double *pol)
+{
+    free(o->rad);
+    o->rad = (double *)malloc((size_t)n * 2 * sizeof(double));
+    memcpy(o->rad, s12, (size_t)n * 2 * sizeof(double));
+    o->n_rad = n;
+    o->rad_mode = pol ? 2 : 1;
+    o->rad_max = 0.0;
+    for (int i = 0; i < 2 * n; ++i) if (s12[i] > o->rad_max) o->rad_max = s12[i];
+    for (int a = 0; a < 3; ++a) { o->L[a] = L[a]; o->pol[a] = pol ? pol[a] : 0.0; }
+}
+
+double om_radiance(const om_optics *o, const double d0[3])
+{
+    if (!o->rad_mode) return 1.0;
+    double c = d0[0] * o->L[0] + d0[1] * o->L[1] + d0[2] * o->L[2];
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    double t = acos(c) / M_PI * (double)(o->n_rad - 1);
+    int i = (int)floor(t);
+    if (i > o->n_rad - 2) i = o->n_rad - 2;
+    double f = t - (double)i;
+    double s1 = (1.0 - f) * o->rad[2 * i] + f * o->rad[2 * i + 2];
+    double s2 = (1.0 - f) * o->rad[2 * i + 1] + f * o->rad[2 * i + 3];
+    double I_ = 0.5 * (s1 + s2);
+    if (o->rad_mode == 2) {
+        /* the scattering plane holds L and d0; the incident field's
+         * component in it is along e = d0 - (d0.L) L */
+        double e[3], e2 = 0.0, pe = 0.0;
+        for (int a = 0; a < 3; ++a) { e[a] = d0[a] - c * o->L[a]; e2 += e[a] * e[a]; pe += o->pol[a] * e[a]; }
+        double c2 = e2 > 0.0 ? pe * pe / e2 : 0.5;
+        I_ = s2 * c2 + s1 * (1.0 - c2);
+    }
+    return I_ / o->rad_max;
+}
+
+/* the radiance weight of ray ray_id of a source (for tests) */
+double om_ray_weight(const om_optics *o, const double src[3], uint64_t seed, uint32_t source_id, uint32_t ray_id,
+                     uint32_t frame)
+{
+    double p[3], d[3], L2 = 0.0;
+    om_lens_point(seed, source_id, ray_id, frame, o->aim_r, o->aim_z, p);
+    for (int a = 0; a < 3; ++a) { d[a] = p[a] - src[a]; L2 += d[a] * d[a]; }
+    double L = sqrt(L2);
+    for (int a = 0; a < 3; ++a) d[a] /= L;
+    return om_radiance(o, d);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 3.4 deposit: Gaussian spot of standard deviation sigma centred on the */
 /* hit, integrated over each pixel with erf, over the pixels within 3 sigma  */
 /* (clipped to the sensor), renormalised over that window and quantised to   */
@@ -620,14 +766,24 @@ static void om_axis_weights(double p, double sp, int N, int *lo, int *hi, double
 }
 
 /* returns the number of pixels touched; adds into image (row-major, y = row) */
+/* A ray of radiance weight w (Sec. 3.1; 1 without Mie radiance) deposits
+ * round(w 2^32) in all: each pixel's share w_i w_j w 2^32 rounded, the
+ * remainder on the largest. */
+int om_deposit_weighted(const om_optics *o, double px, double py, double w, int64_t *image, int atomic);
+
 int om_deposit(const om_optics *o, double px, double py, int64_t *image, int atomic)
+{
+    return om_deposit_weighted(o, px, py, 1.0, image, atomic);
+}
+
+int om_deposit_weighted(const om_optics *o, double px, double py, double w, int64_t *image, int atomic)
 {
     double sp = o->sigma / o->pitch;
     int xlo, xhi, ylo, yhi;
     double wx[4096], wy[4096];
     om_axis_weights(px, sp, o->W, &xlo, &xhi, wx);
     om_axis_weights(py, sp, o->H, &ylo, &yhi, wy);
-    const double two32 = 4294967296.0;
+    const double two32 = 4294967296.0 * w;
     int64_t sum = 0, qmax = -1;
     int imax = 0, jmax = 0;
     for (int j = ylo; j <= yhi; ++j)
@@ -636,7 +792,7 @@ int om_deposit(const om_optics *o, double px, double py, int64_t *image, int ato
             sum += q;
             if (q > qmax) { qmax = q; imax = i; jmax = j; }
         }
-    int64_t rem = (int64_t)4294967296LL - sum;
+    int64_t rem = (int64_t)llrint(w * 4294967296.0) - sum;
     for (int j = ylo; j <= yhi; ++j)
         for (int i = xlo; i <= xhi; ++i) {
             int64_t q = (int64_t)llrint(wx[i - xlo] * wy[j - ylo] * two32);
@@ -680,7 +836,10 @@ void om_render(const om_medium *m, const om_optics *o, const double *sources, in
             uint32_t k = (uint32_t)(r % rays_per_source);
             om_ray_state st;
             int status = om_trace(m, o, &sources[3 * s], seed, (uint32_t)s, k, frame, integrator, step, &st);
-            if (status == OM_REACHED) om_deposit(o, st.sensor_xy[0], st.sensor_xy[1], image, 1);
+            if (status == OM_REACHED) {
+                double w = o->rad_mode ? om_ray_weight(o, &sources[3 * s], seed, (uint32_t)s, k, frame) : 1.0;
+                om_deposit_weighted(o, st.sensor_xy[0], st.sensor_xy[1], w, image, 1);
+            }
             lc[status] += 1;
         }
 #pragma omp critical

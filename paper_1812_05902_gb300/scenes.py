@@ -68,6 +68,22 @@ class Surface:
 
 
 @dataclasses.dataclass
+class Mie:
+    """Mie radiance of the rays of PIV particles (Sec. 3.1): sphere diameter,
+    laser wavelength (vacuum), index of the medium, the particle's index
+    relative to it, laser direction and polarisation (None = unpolarised),
+    and the angle table size."""
+    diameter: float = 1e-6
+    wavelength: float = 532e-9
+    n_medium: float = 1.000277
+    m_re: float = 1.45 / 1.000277
+    m_im: float = 0.0
+    laser_dir: tuple = (1.0, 0.0, 0.0)
+    polarisation: Optional[tuple] = (0.0, 1.0, 0.0)
+    n_angles: int = 1801
+
+
+@dataclasses.dataclass
 class Optics:
     surfaces: List[Surface]
     n_object: float
@@ -83,6 +99,7 @@ class Optics:
     dtau_rule: int = 0     # 0: Eq. 8 as printed (2.44 pi ...), 1: textbook 2.44
     sensor_tilt_x: float = 0.0   # radians about x, then
     sensor_tilt_y: float = 0.0   # radians about y (the sensor turns about its centre)
+    mie: Optional["Mie"] = None  # Mie radiance of the rays (None: every ray weighs 1)
 
     def surface_array(self) -> np.ndarray:
         return np.array([s.as_row() for s in self.surfaces], dtype=np.float64).reshape(-1, 6)
