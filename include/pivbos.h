@@ -163,6 +163,36 @@ pivbos_status pivbos_optics_create(const pivbos_surface* surfaces, int n_surface
  * Errors: INVALID_ARG (NULL, non-finite angles), OOM. */
 pivbos_status pivbos_optics_tilt_sensor(const pivbos_optics* o, double tilt_x, double tilt_y, pivbos_optics** out);
 
+/* Sec. 3.1: the radiance of a ray from a PIV particle follows Mie
+ * scattering (the paper uses the method of Bohren & Huffman).  pivbos_mie
+ * evaluates the series solution for a homogeneous sphere of `diameter` in a
+ * medium of index n_medium lit at vacuum `wavelength`, with relative index
+ * m = m_re + i m_im (m_im >= 0 absorbs): s12 (host double [n_angles][2])
+ * receives |S1|^2 and |S2|^2 at theta_i = pi i / (n_angles - 1) from the
+ * laser's direction; q (host double [4], may be NULL) receives Q_ext,
+ * Q_sca, Re S(0) and the number of terms (x + 4 x^(1/3) + 2, size parameter
+ * x = pi diameter n_medium / wavelength).  Runs on the current device,
+ * synchronously (allocates its own scratch).  Errors: INVALID_ARG;
+ * UNSUPPORTED for x > 20000; OOM; CUDA. */
+pivbos_status pivbos_mie(double diameter, double wavelength, double n_medium, double m_re, double m_im,
+                         int n_angles, double* s12, double* q);
+
+/* A copy of `o` whose rays carry Mie radiance: a ray leaving its source
+ * along d0 has theta = acos(d0 . laser_dir); |S1|^2 and |S2|^2 are
+ * interpolated linearly in theta from the table s12 (host, as pivbos_mie
+ * writes it, n_angles >= 2 covering 0..pi); its radiance is
+ * |S2|^2 cos^2(phi) + |S1|^2 sin^2(phi) for a laser polarised along
+ * `polarisation` (host double[3], normal to laser_dir; phi is its angle to
+ * the scattering plane, which holds laser_dir and d0), or the mean of the
+ * two for unpolarised light (polarisation NULL); divided by the largest
+ * table entry, so weights lie in [0, 1].  A ray of weight w adds
+ * round(w 2^32) to the image in all, spread like any spot.  The table is
+ * held in FP32 on the device by the new handle.  Renders, batches and the
+ * surrogate path use the weights; the BOS displacement means and the
+ * per-ray exit states ignore them.  Errors: INVALID_ARG, OOM, CUDA. */
+pivbos_status pivbos_optics_radiance(const pivbos_optics* o, const double laser_dir[3], const double* polarisation,
+                                     const double* s12, int n_angles, pivbos_optics** out);
+
 void pivbos_optics_destroy(pivbos_optics* o);
 
 /* ---------------------------------------------------------------------------

@@ -487,6 +487,21 @@ pivbos_status pivbos_optics_tilt_sensor(const pivbos_optics* o, double tilt_x, d
     if (!isfinite(tilt_x) || !isfinite(tilt_y)) return fail(PIVBOS_ERR_INVALID_ARG, "tilt angles must be finite");
     pivbos_optics* c = new (std::nothrow) pivbos_optics(*o);
     if (!c) return fail(PIVBOS_ERR_OOM, "host allocation");
+    c->rad_owned = nullptr;
+    if (o->rad_owned) {
+        // the copy owns a copy of the radiance table
+        float2* t = nullptr;
+        cudaError_t e = cudaMalloc((void**)&t, (size_t)o->d.rad_n * sizeof(float2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(t, o->rad_owned, (size_t)o->d.rad_n * sizeof(float2), cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) {
+            if (t) cudaFree(t);
+            delete c;
+            return cuda_fail(e, "radiance table copy");
+        }
+        c->rad_owned = t;
+        c->d.rad = t;
+    }
     // the sensor's axes: x, y, z turned by tilt_x about x, then by tilt_y about y
     const double cx = cos(tilt_x), sx = sin(tilt_x), cy = cos(tilt_y), sy = sin(tilt_y);
     const double eu[3] = {cy, 0.0, -sy};
@@ -503,7 +518,13 @@ pivbos_status pivbos_optics_tilt_sensor(const pivbos_optics* o, double tilt_x, d
     return PIVBOS_OK;
 }
 
-void pivbos_optics_destroy(pivbos_optics* o) { delete o; }
+void pivbos_optics_destroy(pivbos_optics* o)
+{
+    if (!o) return;
+    // cudaFree waits for work on the device that may still read the table
+    if (o->rad_owned) cudaFree(o->rad_owned);
+    delete o;
+}
 
 // ---------------------------------------------------------------------------
 // render

@@ -50,13 +50,18 @@ struct DevOptics {
     float sigma_px;
     int tilted;            // 0: sensor square to the axis; 1: axes eu, ev and normal en below
     dfc eu[3], ev[3], en[3];
+    // Mie radiance of the rays (Sec. 3.1): 0 none, 1 unpolarised, 2 polarised
+    int rad_mode, rad_n;
+    const float2* rad;     // |S1|^2, |S2|^2 over the table's maximum at rad_n angles 0..pi
+    float rad_L[3];        // laser direction (unit)
+    float rad_pol[3];      // polarisation (unit, normal to rad_L; mode 2)
 };
 
-// Whether optics hold a mirror, a lens array or a turned sensor: the kernels
+// Whether optics hold a mirror, a lens array, a turned sensor or a radiance: the kernels
 // compiled with the extended optics stage are launched only then.
 inline bool optics_ext(const DevOptics& o)
 {
-    if (o.tilted) return true;
+    if (o.tilted || o.rad_mode) return true;
     for (int s = 0; s < o.ns; ++s)
         if (o.s[s].type == PIVBOS_SURF_MIRROR || o.s[s].type == PIVBOS_SURF_LENS_ARRAY) return true;
     return false;

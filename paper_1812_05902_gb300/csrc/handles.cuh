@@ -21,6 +21,7 @@ struct pivbos_optics {
     double magnification;
     double n_object;
     double pixel_pitch;
+    float2* rad_owned = nullptr;  // device radiance table this handle frees (d.rad), or NULL
 };
 
 namespace pivbos {

@@ -81,7 +81,10 @@ __device__ __forceinline__ void render_chunk(const TraceParams& P, ChunkShared& 
             ax = sh.ax;
             ay = sh.ay;
         }
-        if (active && r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, sh.tile, ax, ay, image);
+        if (active && r.status == PIVBOS_RAY_REACHED) {
+            if constexpr (EXT) deposit_ray<true>(P.o, r.px, r.py, sh.tile, ax, ay, image, r.w);
+            else deposit_ray(P.o, r.px, r.py, sh.tile, ax, ay, image);
+        }
     }
     if (stats) {
 #pragma unroll

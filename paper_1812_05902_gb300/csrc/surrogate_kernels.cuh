@@ -768,6 +768,15 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
             }
             r.status = PIVBOS_RAY_REACHED;
             surr_sensor<EXT>(P.o, S, l.x, l.y, l.z, l.w, res, r.status, r.px, r.py);
+            r.w = 1.0f;
+            if constexpr (EXT) {
+                // the ray's radiance from its direction at the source: the
+                // straight line's slopes
+                if (P.o.rad_mode) {
+                    const float inn = rsqrtf(fmaf(l.z, l.z, fmaf(l.w, l.w, 1.0f)));
+                    r.w = ray_radiance(P.o, l.z * inn, l.w * inn, inn);
+                }
+            }
             cnt[r.status]++;
             if (r.status == PIVBOS_RAY_REACHED) atomicMin(&anchor_tid, tid);
         }
@@ -780,7 +789,7 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
         __syncthreads();
         const int ax = anchor_tid == 0x7fffffff ? -(1 << 28) : sax;
         const int ay = anchor_tid == 0x7fffffff ? -(1 << 28) : say;
-        if (active && r.status == PIVBOS_RAY_REACHED) deposit_ray(P.o, r.px, r.py, tile, ax, ay, image);
+        if (active && r.status == PIVBOS_RAY_REACHED) deposit_ray<EXT>(P.o, r.px, r.py, tile, ax, ay, image, r.w);
         __syncthreads();
         for (int q = tid; q < kTileW * kTileH; q += blockDim.x) {
             const unsigned long long v = tile[q];

@@ -189,7 +189,30 @@ struct RayOut {
     df px, py;     // sensor pixel coordinates
     int status;
     int steps;
+    float w;       // radiance weight (Sec. 3.1; 1 without a Mie radiance)
 };
+
+// Sec. 3.1: the radiance of a ray leaving its source along d0 (unit), from
+// the optics' Mie table: theta = acos(d0.L) from the laser direction L,
+// |S1|^2 and |S2|^2 interpolated linearly in theta (the table is already
+// divided by its maximum); unpolarised light takes their mean, a laser
+// polarised along p takes |S2|^2 cos^2(phi) + |S1|^2 sin^2(phi), phi the
+// angle between p and the scattering plane (which holds L and d0).
+__device__ __forceinline__ float ray_radiance(const DevOptics& o, float dx, float dy, float dz)
+{
+    const float c = fminf(fmaxf(fmaf(dx, o.rad_L[0], fmaf(dy, o.rad_L[1], dz * o.rad_L[2])), -1.0f), 1.0f);
+    const float t = acosf(c) * (0.31830988618379067f * (float)(o.rad_n - 1));
+    const int i = min((int)t, o.rad_n - 2);
+    const float f = t - (float)i;
+    const float2 a = __ldg(o.rad + i), b = __ldg(o.rad + i + 1);
+    const float s1 = fmaf(f, b.x - a.x, a.x), s2 = fmaf(f, b.y - a.y, a.y);
+    if (o.rad_mode != 2) return 0.5f * (s1 + s2);
+    const float ex = fmaf(-c, o.rad_L[0], dx), ey = fmaf(-c, o.rad_L[1], dy), ez = fmaf(-c, o.rad_L[2], dz);
+    const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    const float pe = fmaf(o.rad_pol[0], ex, fmaf(o.rad_pol[1], ey, o.rad_pol[2] * ez));
+    const float c2 = e2 > 0.0f ? pe * pe / e2 : 0.5f;
+    return fmaf(s2 - s1, c2, s1);
+}
 
 __device__ __forceinline__ void put3(double* dst, df x, df y, df z)
 {
@@ -480,6 +503,10 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
     ray_start(P, sx, sy, sz, sid, rid, dx, dy, dz);
     int status = PIVBOS_RAY_REACHED;
     int steps = 0;
+    out.w = 1.0f;
+    if constexpr (EXT) {
+        if (o.rad_mode) out.w = ray_radiance(o, dx.hi, dy.hi, dz.hi);
+    }
 
     // ---- Sec. 3.2: through the density box ------------------------------
     if (m.present) {
@@ -671,11 +698,20 @@ __device__ __forceinline__ long long round_pos_to_ll(float x)
 }
 
 // Quantise the spot of one ray and add it (tile if inside, image otherwise).
+// WEIGHTED: the ray carries the radiance weight w in [0, 1] and adds
+// round(w 2^32) in all; otherwise exactly 2^32.
+template <bool WEIGHTED = false>
 __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
-                                            unsigned long long* tile, int ax, int ay, int64_t* image)
+                                            unsigned long long* tile, int ax, int ay, int64_t* image,
+                                            float w = 1.0f)
 {
     SpotWindow sw;
     spot_window(o, px, py, sw);
+    long long total = 4294967296LL;
+    if constexpr (WEIGHTED) {
+        sw.scale *= w;
+        total = round_pos_to_ll(w * 4294967296.0f);
+    }
     long long sum = 0, qmax = -1;
     int imax = 0, jmax = 0;
 #pragma unroll 1
@@ -688,7 +724,7 @@ __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
             if (q > qmax) { qmax = q; imax = i; jmax = j; }
         }
     }
-    const long long rem = 4294967296LL - sum;
+    const long long rem = total - sum;
 #pragma unroll 1
     for (int j = 0; j < sw.ny; ++j) {
         const float wyj = sw.wy[j] * sw.scale;

@@ -101,6 +101,8 @@ def _load():
         "pivbos_optics_create": ([P, I, D, D, D, D, D, D, I, D, D, I, I, P], I),
         "pivbos_optics_destroy": ([P], None),
         "pivbos_optics_tilt_sensor": ([P, D, D, P], I),
+        "pivbos_mie": ([D, D, D, D, D, I, P, P], I),
+        "pivbos_optics_radiance": ([P, P, P, P, I, P], I),
         "pivbos_render": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
         "pivbos_trace_exit_states": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I64, P, P], I),
         "pivbos_image_finalize": ([P, I64, P, P], I),
@@ -146,7 +148,8 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_autotune", "pivbos_render_range", "pivbos_mlp_forward", "pivbos_mlp_loss_grad",
             "pivbos_surrogate_default_cfg", "pivbos_surrogate_train", "pivbos_surrogate_render",
             "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy",
-            "pivbos_bos_displacements", "pivbos_bos_theory", "pivbos_regrid_bilinear", "pivbos_optics_tilt_sensor")
+            "pivbos_bos_displacements", "pivbos_bos_theory", "pivbos_regrid_bilinear", "pivbos_optics_tilt_sensor",
+            "pivbos_mie", "pivbos_optics_radiance")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
@@ -224,6 +227,25 @@ def pivbos_optics_tilt_sensor(o, tilt_x, tilt_y):
     """A new optics handle: `o` with its sensor turned about its centre."""
     out = ctypes.c_void_p()
     _check(_lib.pivbos_optics_tilt_sensor(o, tilt_x, tilt_y, ctypes.byref(out)))
+    return out
+
+
+def pivbos_mie(diameter, wavelength, n_medium, m_re, m_im=0.0, n_angles=1801):
+    """Mie scattering of a sphere on the GPU: (s12 [n, 2] of |S1|^2, |S2|^2,
+    {q_ext, q_sca, re_s0, terms})."""
+    s12 = np.zeros((n_angles, 2))
+    q = np.zeros(4)
+    _check(_lib.pivbos_mie(diameter, wavelength, n_medium, m_re, m_im, n_angles, s12.ctypes.data, q.ctypes.data))
+    return s12, {"q_ext": q[0], "q_sca": q[1], "re_s0": q[2], "terms": int(q[3])}
+
+
+def pivbos_optics_radiance(o, laser_dir, polarisation, s12):
+    """A new optics handle: `o` with Mie radiance weights per ray."""
+    s12 = np.ascontiguousarray(s12, dtype=np.float64).reshape(-1, 2)
+    L = (ctypes.c_double * 3)(*laser_dir)
+    pol = (ctypes.c_double * 3)(*polarisation) if polarisation is not None else None
+    out = ctypes.c_void_p()
+    _check(_lib.pivbos_optics_radiance(o, L, pol, s12.ctypes.data, len(s12), ctypes.byref(out)))
     return out
 
 
@@ -456,6 +478,12 @@ class Optics:
             flat = self.h
             self.h = pivbos_optics_tilt_sensor(flat, tx, ty)
             pivbos_optics_destroy(flat)
+        mie = getattr(so, "mie", None)
+        if mie is not None:
+            s12, _ = pivbos_mie(mie.diameter, mie.wavelength, mie.n_medium, mie.m_re, mie.m_im, mie.n_angles)
+            plain = self.h
+            self.h = pivbos_optics_radiance(plain, mie.laser_dir, mie.polarisation, s12)
+            pivbos_optics_destroy(plain)
 
     def close(self):
         if getattr(self, "h", None):
