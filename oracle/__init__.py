@@ -103,6 +103,8 @@ def lib():
             L.om_optics_radiance.argtypes = [P, P, I, P, P]
             L.om_ray_weight.argtypes = [P, P, U64, U32, U32, U32]
             L.om_ray_weight.restype = D
+            L.om_advect.argtypes = [P, I64, P, I, I, I, P, P, D, P]
+            L.om_image_u16.argtypes = [P, I64, D, P]
             L.om_line_gradient_integral.restype = I
             _lib = L
     return _lib
@@ -281,6 +283,27 @@ def mie(x, m_re, m_im=0.0, n_angles=181):
 def ray_weight(optics, src, seed, source_id, ray_id, frame):
     s = np.ascontiguousarray(src, dtype=np.float64)
     return lib().om_ray_weight(optics.h, _ptr(s), seed, source_id, ray_id, frame)
+
+
+def advect(sources, vel, origin, spacing, dt):
+    """Second frame of an image pair: particles moved over dt by the velocity
+    field vel [nz, ny, nx, 3] (explicit midpoint rule, trilinear samples)."""
+    src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(vel, dtype=np.float32)
+    nz, ny, nx, _ = v.shape
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    h = np.ascontiguousarray(spacing, dtype=np.float64)
+    out = np.zeros_like(src)
+    lib().om_advect(_ptr(src), len(src), _ptr(v), nx, ny, nz, _ptr(o), _ptr(h), float(dt), _ptr(out))
+    return out
+
+
+def image_u16(image, full_scale):
+    """16-bit image: full_scale rays read 65535 (rounded, clipped)."""
+    img = np.ascontiguousarray(image, dtype=np.int64)
+    out = np.zeros(img.shape, dtype=np.uint16)
+    lib().om_image_u16(_ptr(img), img.size, float(full_scale), _ptr(out))
+    return out
 
 
 def reflect(d, N):

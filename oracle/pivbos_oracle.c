@@ -19,6 +19,8 @@
  *   om_trace (sensor) / om_deposit ...... Sec. 3.4, Eq. 8 (diffraction spot)
  *   om_line_gradient_integral ........... Sec. 4, Eq. 9 (BOS theory deflection)
  *   om_mie / om_ray_weight .............. Sec. 3.1 (Mie radiance of a ray)
+ *   om_advect / om_image_u16 ............ image pairs and 16-bit images
+ *                                         (Sec. 3.4's dynamic range)
  *
  * Readings where the paper is silent (box faces, final step, windows,
  * quantisation, ideal lens) are documented at each function.
@@ -943,6 +945,64 @@ int om_line_gradient_integral(const om_medium *m, const double s[3], const doubl
     }
     free(zs);
     return pieces;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Image pairs for displacement analysis: the second frame's particles are  */
+/* the first frame's moved by a velocity field u (3 components per node on  */
+/* a grid like the density's, trilinear, clamped to the grid) over dt with   */
+/* the explicit midpoint rule: k = u(x), x' = x + dt u(x + dt k / 2).        */
+/* vel: [nz][ny][nx][3] float32.                                             */
+/* ------------------------------------------------------------------------ */
+static void om_vel_sample(const float *vel, const int n[3], const double o[3], const double h[3],
+                          const double x[3], double u[3])
+{
+    int i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double g = (x[a] - o[a]) / h[a];
+        if (g < 0.0) g = 0.0;
+        if (g > (double)(n[a] - 1)) g = (double)(n[a] - 1);
+        int i = (int)floor(g);
+        if (i > n[a] - 2) i = n[a] - 2;
+        i0[a] = i;
+        f[a] = g - (double)i;
+    }
+    u[0] = u[1] = u[2] = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+        double w = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) * (dk ? f[2] : 1.0 - f[2]);
+        size_t p = (((size_t)(i0[2] + dk) * (size_t)n[1] + (size_t)(i0[1] + dj)) * (size_t)n[0] + (size_t)(i0[0] + di));
+        for (int a = 0; a < 3; ++a) u[a] += w * (double)vel[3 * p + a];
+    }
+}
+
+void om_advect(const double *src, int64_t n_src, const float *vel, int nx, int ny, int nz, const double origin[3],
+               const double spacing[3], double dt, double *out)
+{
+    const int n[3] = { nx, ny, nz };
+    for (int64_t q = 0; q < n_src; ++q) {
+        const double *x = &src[3 * q];
+        double k[3], xm[3], u[3];
+        om_vel_sample(vel, n, origin, spacing, x, k);
+        for (int a = 0; a < 3; ++a) xm[a] = x[a] + 0.5 * dt * k[a];
+        om_vel_sample(vel, n, origin, spacing, xm, u);
+        for (int a = 0; a < 3; ++a) out[3 * q + a] = x[a] + dt * u[a];
+    }
+}
+
+/* 16-bit image (Sec. 3.4: about 1e4 rays per particle give a 16-bit
+ * dynamic range): intensity in rays, image * 2^-32, scaled so that
+ * full_scale rays read 65535, rounded to nearest even, clipped to
+ * [0, 65535]. */
+void om_image_u16(const int64_t *image, int64_t n, double full_scale, uint16_t *out)
+{
+    for (int64_t q = 0; q < n; ++q) {
+        double v = rint((double)image[q] * 0x1p-32 / full_scale * 65535.0);
+        if (v < 0.0) v = 0.0;
+        if (v > 65535.0) v = 65535.0;
+        out[q] = (uint16_t)v;
+    }
 }
 
 /* helpers exposed for tests */
