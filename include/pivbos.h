@@ -511,6 +511,28 @@ pivbos_status pivbos_regrid_bilinear(const double* xy, const double* values, int
                                      double x0, double y0, double cell, double min_weight, double* out,
                                      double* weight, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Image pairs for displacement analysis and 16-bit images.
+ *
+ * pivbos_advect_sources: the particles of the second frame of a pair, the
+ * first frame's sources (device double [n][3]) moved over dt by a velocity
+ * field (device float [nz][ny][nx][3], m/s, nodes at origin + (i, j, k) *
+ * spacing like a medium's; sampled trilinearly, the point clamped into the
+ * grid) with the explicit midpoint rule: k = u(x), x' = x + dt u(x + dt k/2).
+ * out: device double [n][3] (may not alias sources).  FP64.  Asynchronous.
+ *
+ * pivbos_image_u16: the 16 bits a camera writes (Sec. 3.4: about 1e4 rays per
+ * particle give a 16-bit dynamic range): counts = rint(image 2^-32 /
+ * full_scale * 65535) clipped to [0, 65535] (full_scale rays read 65535).
+ * image (device int64) and out (device uint16) 16-byte aligned.
+ * Asynchronous.  Errors (both): INVALID_ARG, CUDA.
+ * ------------------------------------------------------------------------- */
+pivbos_status pivbos_advect_sources(const double* sources, int64_t n_sources, const float* velocity, int nx, int ny,
+                                    int nz, const double origin[3], const double spacing[3], double dt,
+                                    double* out, void* stream);
+pivbos_status pivbos_image_u16(const int64_t* image, int64_t n_pixels, double full_scale, uint16_t* out,
+                               void* stream);
+
 /* int64 32.32 image -> float32 intensity in rays (value * 2^-32).  Device
  * pointers, n_pixels >= 0. */
 pivbos_status pivbos_image_finalize(const int64_t* image, int64_t n_pixels, float* out, void* stream);

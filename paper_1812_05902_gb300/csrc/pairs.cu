@@ -1,0 +1,195 @@
+// Image pairs for displacement analysis and 16-bit images: the second
+// frame's particles moved by a velocity field, and the 32.32 image converted
+// to the 16 bits a camera writes (Sec. 3.4: ~1e4 rays per particle give a
+// 16-bit dynamic range).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "handles.cuh"
+
+namespace pivbos {
+
+struct VelGrid {
+    const float* v;   // [nz][ny][nx][3]
+    int n[3];
+    double origin[3], h[3];
+};
+
+// trilinear sample of the velocity, the point clamped into the grid (FP64)
+__device__ __forceinline__ void vel_sample(const VelGrid& G, const double x[3], double u[3])
+{
+    int c[3];
+    double f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double g = fmin(fmax((x[a] - G.origin[a]) / G.h[a], 0.0), (double)(G.n[a] - 1));
+        c[a] = min((int)g, G.n[a] - 2);
+        f[a] = g - (double)c[a];
+    }
+    u[0] = u[1] = u[2] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int di = q & 1, dj = (q >> 1) & 1, dk = q >> 2;
+        const double w = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) * (dk ? f[2] : 1.0 - f[2]);
+        const float* p = G.v + 3 * (((size_t)(c[2] + dk) * G.n[1] + (c[1] + dj)) * G.n[0] + (c[0] + di));
+        u[0] += w * (double)__ldg(p);
+        u[1] += w * (double)__ldg(p + 1);
+        u[2] += w * (double)__ldg(p + 2);
+    }
+}
+
+// explicit midpoint rule: k = u(x), x' = x + dt u(x + dt k / 2); one thread per particle
+__global__ void advect_kernel(const VelGrid G, const double* __restrict__ src, int64_t n, double dt,
+                              double* __restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const double x[3] = {src[3 * q], src[3 * q + 1], src[3 * q + 2]};
+    double k[3], u[3];
+    vel_sample(G, x, k);
+    const double xm[3] = {x[0] + 0.5 * dt * k[0], x[1] + 0.5 * dt * k[1], x[2] + 0.5 * dt * k[2]};
+    vel_sample(G, xm, u);
+    out[3 * q] = x[0] + dt * u[0];
+    out[3 * q + 1] = x[1] + dt * u[1];
+    out[3 * q + 2] = x[2] + dt * u[2];
+}
+
+// counts = rint(image 2^-32 / full_scale * 65535), clipped to [0, 65535]
+__device__ __forceinline__ uint16_t to_u16(long long v, double fs)
+{
+    const double c = rint(__dmul_rn(__ddiv_rn((double)v * 0x1p-32, fs), 65535.0));
+    return (uint16_t)fmin(fmax(c, 0.0), 65535.0);
+}
+
+// 8 pixels per thread and step: 64 B read as four 16-byte loads, 16 B written
+// as one; grid-stride over the image (the host sizes the grid to the SMs).
+__global__ void image_u16_kernel(const int64_t* __restrict__ img, int64_t n, double full_scale,
+                                 uint16_t* __restrict__ out)
+{
+    const int64_t n8 = n / 8;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const longlong2* in2 = reinterpret_cast<const longlong2*>(img);
+    uint4* out8 = reinterpret_cast<uint4*>(out);
+    for (int64_t t = t0; t < n8; t += stride) {
+        const longlong2 a = __ldcs(in2 + 4 * t), b = __ldcs(in2 + 4 * t + 1);
+        const longlong2 c = __ldcs(in2 + 4 * t + 2), d = __ldcs(in2 + 4 * t + 3);
+        uint4 o;
+        o.x = (uint32_t)to_u16(a.x, full_scale) | ((uint32_t)to_u16(a.y, full_scale) << 16);
+        o.y = (uint32_t)to_u16(b.x, full_scale) | ((uint32_t)to_u16(b.y, full_scale) << 16);
+        o.z = (uint32_t)to_u16(c.x, full_scale) | ((uint32_t)to_u16(c.y, full_scale) << 16);
+        o.w = (uint32_t)to_u16(d.x, full_scale) | ((uint32_t)to_u16(d.y, full_scale) << 16);
+        __stcs(out8 + t, o);
+    }
+    for (int64_t q = 8 * n8 + t0; q < n; q += stride) out[q] = to_u16(img[q], full_scale);
+}
+
+}  // namespace pivbos
+
+namespace {
+
+pivbos_status pairs_fail(pivbos_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    pivbos::set_last_error(buf);
+    return st;
+}
+
+pivbos_status on_device(const void* p, int dev, const char* what)
+{
+    if (!p) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "%s is NULL", what);
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "%s is not a CUDA pointer", what);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "%s is not device memory", what);
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "%s belongs to device %d, current is %d", what, a.device, dev);
+    return PIVBOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pivbos_status pivbos_advect_sources(const double* sources, int64_t n_sources, const float* velocity, int nx, int ny,
+                                    int nz, const double origin[3], const double spacing[3], double dt,
+                                    double* out, void* stream)
+{
+    using namespace pivbos;
+    set_last_error("");
+    if (n_sources < 0 || n_sources > (1ll << 31)) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "n_sources");
+    if (nx < 2 || ny < 2 || nz < 2 || !origin || !spacing || !isfinite(dt))
+        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "grid or dt");
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(origin[a]) || !(spacing[a] > 0.0) || !isfinite(spacing[a]))
+            return pairs_fail(PIVBOS_ERR_INVALID_ARG, "origin or spacing");
+    if (n_sources == 0) return PIVBOS_OK;
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return pairs_fail(PIVBOS_ERR_CUDA, "cudaGetDevice");
+    }
+    pivbos_status st;
+    if ((st = on_device(sources, dev, "sources")) || (st = on_device(velocity, dev, "velocity")) ||
+        (st = on_device(out, dev, "out")))
+        return st;
+    VelGrid G;
+    G.v = velocity;
+    G.n[0] = nx;
+    G.n[1] = ny;
+    G.n[2] = nz;
+    for (int a = 0; a < 3; ++a) {
+        G.origin[a] = origin[a];
+        G.h[a] = spacing[a];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    timing_begin("advect", s);
+    advect_kernel<<<(unsigned)((n_sources + 255) / 256), 256, 0, s>>>(G, sources, n_sources, dt, out);
+    timing_end("advect", s);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pairs_fail(PIVBOS_ERR_CUDA, "advect: %s", cudaGetErrorString(e));
+    return PIVBOS_OK;
+}
+
+pivbos_status pivbos_image_u16(const int64_t* image, int64_t n_pixels, double full_scale, uint16_t* out,
+                               void* stream)
+{
+    using namespace pivbos;
+    set_last_error("");
+    if (n_pixels < 0) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "n_pixels < 0");
+    if (!(full_scale > 0.0) || !isfinite(full_scale)) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "full_scale");
+    if (n_pixels == 0) return PIVBOS_OK;
+    if ((reinterpret_cast<uintptr_t>(image) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "image and out must be 16-byte aligned");
+    int dev, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return pairs_fail(PIVBOS_ERR_CUDA, "cudaGetDevice");
+    }
+    pivbos_status st;
+    if ((st = on_device(image, dev, "image")) || (st = on_device(out, dev, "out"))) return st;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = (n_pixels / 8 + 255) / 256 + 1;
+    const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)(sms > 0 ? sms : 152) * 8);
+    cudaStream_t s = (cudaStream_t)stream;
+    timing_begin("image_u16", s);
+    image_u16_kernel<<<grid, 256, 0, s>>>(image, n_pixels, full_scale, out);
+    timing_end("image_u16", s);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pairs_fail(PIVBOS_ERR_CUDA, "image_u16: %s", cudaGetErrorString(e));
+    return PIVBOS_OK;
+}
+
+}  // extern "C"

@@ -103,6 +103,8 @@ def _load():
         "pivbos_optics_tilt_sensor": ([P, D, D, P], I),
         "pivbos_mie": ([D, D, D, D, D, I, P, P], I),
         "pivbos_optics_radiance": ([P, P, P, P, I, P], I),
+        "pivbos_advect_sources": ([P, I64, P, I, I, I, P, P, D, P, P], I),
+        "pivbos_image_u16": ([P, I64, D, P, P], I),
         "pivbos_render": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
         "pivbos_trace_exit_states": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I64, P, P], I),
         "pivbos_image_finalize": ([P, I64, P, P], I),
@@ -149,7 +151,7 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_surrogate_default_cfg", "pivbos_surrogate_train", "pivbos_surrogate_render",
             "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy",
             "pivbos_bos_displacements", "pivbos_bos_theory", "pivbos_regrid_bilinear", "pivbos_optics_tilt_sensor",
-            "pivbos_mie", "pivbos_optics_radiance")
+            "pivbos_mie", "pivbos_optics_radiance", "pivbos_advect_sources", "pivbos_image_u16")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
@@ -405,6 +407,21 @@ def pivbos_regrid_bilinear(xy, values, n, grid_w, grid_h, x0, y0, cell, min_weig
     """Scattered values onto a regular grid by bilinear weights; CUDA tensors."""
     _check(_lib.pivbos_regrid_bilinear(_addr(xy)[0], _addr(values)[0], n, grid_w, grid_h, x0, y0, cell, min_weight,
                                        _addr(out)[0], _addr(weight)[0], _stream(stream)))
+
+
+def pivbos_advect_sources(sources, n_sources, velocity, origin, spacing, dt, out, stream=None):
+    """Second frame of an image pair: sources moved by the velocity field
+    (CUDA tensor [nz, ny, nx, 3]) over dt; CUDA tensors."""
+    nz, ny, nx = (int(v) for v in velocity.shape[:3])
+    o = (ctypes.c_double * 3)(*origin)
+    h = (ctypes.c_double * 3)(*spacing)
+    _check(_lib.pivbos_advect_sources(_addr(sources)[0], n_sources, _addr(velocity)[0], nx, ny, nz, o, h, dt,
+                                      _addr(out)[0], _stream(stream)))
+
+
+def pivbos_image_u16(image, n_pixels, full_scale, out, stream=None):
+    """16-bit image (full_scale rays read 65535); CUDA tensors (out uint16)."""
+    _check(_lib.pivbos_image_u16(_addr(image)[0], n_pixels, full_scale, _addr(out)[0], _stream(stream)))
 
 
 def pivbos_image_finalize(image, n_pixels, out, stream=None):

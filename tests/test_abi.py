@@ -196,3 +196,27 @@ def test_optics_extension_arguments_without_a_device(P):
         bad = (P.pivbos_surface * 1)(P.pivbos_surface(*row))
         assert L.pivbos_optics_create(bad, 1, 1.0, 1.0, 0.01, 8.0, 0.1, 5e-7, 0, 2.0, 1e-5, 64, 64,
                                       ctypes.byref(out)) == P.ERR_INVALID_ARG
+
+
+def test_pairs_arguments_without_a_device(P):
+    L = P.lib()
+    fake = ctypes.c_void_p(1)
+    o3 = (ctypes.c_double * 3)(0, 0, 0)
+    h3 = (ctypes.c_double * 3)(1e-3, 1e-3, 1e-3)
+    bad = (ctypes.c_double * 3)(1e-3, 0.0, 1e-3)
+    assert L.pivbos_advect_sources(fake, -1, fake, 4, 4, 4, o3, h3, 1e-3, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_advect_sources(fake, 1, fake, 1, 4, 4, o3, h3, 1e-3, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_advect_sources(fake, 1, fake, 4, 4, 4, o3, bad, 1e-3, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_advect_sources(fake, 1, fake, 4, 4, 4, o3, h3, float("nan"), fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_advect_sources(fake, 0, fake, 4, 4, 4, o3, h3, 1e-3, fake, None) == P.OK
+    assert L.pivbos_image_u16(fake, -1, 1.0, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_image_u16(fake, 4, 0.0, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_image_u16(fake, 4, 1.0, fake, None) == P.ERR_INVALID_ARG     # misaligned
+    assert L.pivbos_image_u16(fake, 0, 1.0, fake, None) == P.OK
+    assert L.pivbos_mie(-1.0, 5e-7, 1.0, 1.5, 0.0, 10, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_mie(1e-6, 5e-7, 1.0, 1.5, 0.0, 1, fake, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_mie(1e-6, 5e-7, 1.0, 1.5, -0.1, 10, fake, None) == P.ERR_INVALID_ARG
+    out = ctypes.c_void_p()
+    L3 = (ctypes.c_double * 3)(1, 0, 0)
+    assert L.pivbos_optics_radiance(None, L3, None, fake, 10, ctypes.byref(out)) == P.ERR_INVALID_ARG
+    assert L.pivbos_optics_radiance(fake, L3, None, fake, 1, ctypes.byref(out)) == P.ERR_INVALID_ARG
