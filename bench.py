@@ -160,7 +160,14 @@ class Clocks:
 #   sensor plane 125, spot deposit 450, bookkeeping 40
 OPS_RAY_BASE = 710 + 470 + 125 + 450 + 40
 OPS_STEP = {scenes.RK4: 430.0, scenes.EULER: 160.0}
-OPS_SURF = {scenes.SPHERE: 530.0, scenes.PLANE: 80.0, scenes.IDEAL_THIN: 80.0, scenes.STOP: 80.0}
+OPS_SURF = {scenes.SPHERE: 530.0, scenes.PLANE: 80.0, scenes.IDEAL_THIN: 80.0, scenes.STOP: 80.0,
+            scenes.MIRROR: 530.0, scenes.LENS_ARRAY: 120.0}
+# extended optics: a flat mirror is a clear-radius test; a turned sensor's
+# general plane intersection costs ~150 more than the square sensor; a Mie
+# radiance weight (acos, table lookup, scattering-plane projection) ~70
+OPS_FLAT_MIRROR = 80.0
+OPS_TILT = 150.0
+OPS_MIE = 70.0
 ISSUE_LANES_PER_SM = 128
 N_SM = 152
 
@@ -197,8 +204,65 @@ def recorded_traffic(record, kind="render"):
 
 
 def ops_per_ray(frame, mean_steps):
-    surf = sum(OPS_SURF[s.type] for s in frame.optics.surfaces)
-    return OPS_RAY_BASE + surf + OPS_STEP[frame.integrator] * mean_steps
+    o = frame.optics
+    surf = sum(OPS_FLAT_MIRROR if (s.type == scenes.MIRROR and s.R == 0.0) else OPS_SURF[s.type]
+               for s in o.surfaces)
+    extra = (OPS_TILT if (o.sensor_tilt_x or o.sensor_tilt_y) else 0.0) + (OPS_MIE if o.mie is not None else 0.0)
+    return OPS_RAY_BASE + surf + extra + OPS_STEP[frame.integrator] * mean_steps
+
+
+OPTICS_VARIANTS = ("plain", "mie", "plenoptic", "tilted", "mirror")
+
+
+def apply_optics_variant(frames, variant):
+    """The workload's camera with an optical extension of Sec. 3.3-3.4 (a copy
+    per frame): Mie radiance of a polarised laser, a lenslet array 0.5 mm
+    before the sensor (plenoptic), a sensor turned by 0.05 / -0.03 rad, or a
+    flat fold mirror before the stop."""
+    import dataclasses
+    if variant == "plain":
+        return
+    for fr in frames:
+        o = fr.optics
+        if variant == "mie":
+            fr.optics = dataclasses.replace(o, mie=scenes.Mie())
+        elif variant == "plenoptic":
+            fr.optics = dataclasses.replace(o, surfaces=list(o.surfaces) + [
+                scenes.Surface(scenes.LENS_ARRAY, o.sensor_z - 5e-4, R=1e-4, f=5e-4, clear_r=0.05)])
+        elif variant == "tilted":
+            fr.optics = dataclasses.replace(o, sensor_tilt_x=0.05, sensor_tilt_y=-0.03)
+        elif variant == "mirror":
+            fr.optics = dataclasses.replace(o, surfaces=[scenes.Surface(scenes.MIRROR, o.aim_z - 0.05, R=0.0,
+                                                                        clear_r=0.2)] + list(o.surfaces))
+        else:
+            raise SystemExit("unknown optics variant %s" % variant)
+
+
+def measure_image_u16(P, dev, n=16384 * 16384, reps=5):
+    """HBM roofline of the 16-bit conversion on a 16384^2 image (2 GiB of
+    int64 in, 0.5 GiB out): CUDA events over `reps` launches."""
+    import torch
+    img = torch.randint(0, 1 << 40, (n,), dtype=torch.int64, device=dev)
+    out = torch.empty(n, dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        P.pivbos_image_u16(img, n, 100.0, out)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        P.pivbos_image_u16(img, n, 100.0, out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / reps * 1e-3
+    peaks, src_kind = _peaks()
+    gbs = n * 10 / t / 1e9
+    del img, out
+    return {"kernel": "image_u16_kernel", "pixels": n, "ms_per_launch": round(t * 1e3, 3), "bound": "hbm",
+            "achieved": round(gbs, 1), "unit": "GB/s", "peak": peaks.get("hbm_gbs", 6800.0),
+            "frac": round(gbs / peaks.get("hbm_gbs", 6800.0), 4), "bytes_per_pixel": 10,
+            "peak_source": "%s hbm_gbs" % src_kind}
 
 
 # field gathers: 8 corners x 16 B per evaluation of D; RK4 evaluates 3 times per step
@@ -307,6 +371,7 @@ def run_gpu(args, rank, world):
     from paper_1812_05902_gb300 import pivbos as P
 
     frames = _frames(args.workload, args.scale)
+    apply_optics_variant(frames, args.optics)
     # weak scaling: every rank renders its own images (seed offset by rank)
     for fr in frames:
         fr.seed = fr.seed + 1000003 * rank
@@ -403,15 +468,22 @@ def run_gpu(args, rank, world):
 
     msteps = [mean_steps(P, fr, opt, meds[i], src_d[i]) for i, fr in enumerate(frames)]
     rf = roofline(frames, msteps, render_ms, render_n, clk.get("sm_max_mhz"),
-                  recorded_traffic("render_%s_traffic" % args.workload) if args.scale == 1.0 else None)
+                  recorded_traffic("render_%s_traffic" % args.workload)
+                  if args.scale == 1.0 and args.optics == "plain" else None)
+    u16 = None
+    if world == 1 and args.workload == "c1" and args.optics == "plain" and not args.no_table1:
+        try:
+            u16 = measure_image_u16(P, dev)
+        except Exception as exc:   # reported, never hidden
+            u16 = {"error": "%s: %s" % (type(exc).__name__, exc)}
     sur = None
-    if world == 1 and args.workload == "c1" and not args.no_surrogate:
+    if world == 1 and args.workload == "c1" and args.optics == "plain" and not args.no_surrogate:
         try:
             sur = run_surrogate(args, rank, world, steps=max(2, min(args.steps, 3)), warmup=1, embedded=True)
         except Exception as exc:   # reported, never hidden
             sur = {"error": "%s: %s" % (type(exc).__name__, exc)}
     bos = None
-    if world == 1 and args.workload == "c1" and not args.no_table1:
+    if world == 1 and args.workload == "c1" and args.optics == "plain" and not args.no_table1:
         try:
             bos = run_table1(args, rank, world, steps=3, warmup=1, embedded=True)
         except Exception as exc:   # reported, never hidden
@@ -429,7 +501,7 @@ def run_gpu(args, rank, world):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAMES[args.workload] + ("" if args.scale == 1.0 else
                                                                      " (scaled by %g)" % args.scale),
-                       "name": args.workload,
+                       "name": args.workload, "optics": args.optics,
                        "rays_per_step": rays_step, "images_per_step": len(frames), "l2": "flushed between steps",
                        "parallelism": "replicas (weak)" if world > 1 else "single GPU"},
             "gpu_launches": int(launches), "clocks": clk, "roofline": rf, "e2e": e2e, "cpu_baseline": cpu,
@@ -439,6 +511,8 @@ def run_gpu(args, rank, world):
             out["surrogate"] = sur
         if bos is not None:
             out["table1"] = bos
+        if u16 is not None:
+            out["image_u16"] = u16
         print(json.dumps(out), flush=True)
 
 
@@ -856,7 +930,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the C4 surrogate figures of the default line")
-    ap.add_argument("--no-table1", action="store_true", help="skip the Sec. 4 BOS figures of the default line")
+    ap.add_argument("--no-table1", action="store_true",
+                    help="skip the Sec. 4 BOS and 16-bit conversion figures of the default line")
+    ap.add_argument("--optics", default="plain", choices=OPTICS_VARIANTS,
+                    help="the workload's camera with an optical extension (plain render workloads only)")
     ap.add_argument("--surrogate", action="store_true",
                     help="the surrogate path as the value (workload c4, the default here, or c2)")
     ap.add_argument("--scale", type=float, default=1.0,

@@ -522,9 +522,11 @@ pivbos_status pivbos_regrid_bilinear(const double* xy, const double* values, int
  * out: device double [n][3] (may not alias sources).  FP64.  Asynchronous.
  *
  * pivbos_image_u16: the 16 bits a camera writes (Sec. 3.4: about 1e4 rays per
- * particle give a 16-bit dynamic range): counts = rint(image 2^-32 /
- * full_scale * 65535) clipped to [0, 65535] (full_scale rays read 65535).
- * image (device int64) and out (device uint16) 16-byte aligned.
+ * particle give a 16-bit dynamic range): one count is d = llround(full_scale
+ * 2^32 / 65535) units of the 32.32 image (full_scale rays read 65535);
+ * counts = (image + floor(d/2)) / d in integers (rounded half up), clipped
+ * to [0, 65535].  full_scale <= 2^14 * 65535 rays.  image (device int64) and
+ * out (device uint16) 16-byte aligned.
  * Asynchronous.  Errors (both): INVALID_ARG, CUDA.
  * ------------------------------------------------------------------------- */
 pivbos_status pivbos_advect_sources(const double* sources, int64_t n_sources, const float* velocity, int nx, int ny,

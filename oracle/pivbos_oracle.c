@@ -992,16 +992,19 @@ void om_advect(const double *src, int64_t n_src, const float *vel, int nx, int n
 }
 
 /* 16-bit image (Sec. 3.4: about 1e4 rays per particle give a 16-bit
- * dynamic range): intensity in rays, image * 2^-32, scaled so that
- * full_scale rays read 65535, rounded to nearest even, clipped to
- * [0, 65535]. */
+ * dynamic range): one count is d = llround(full_scale 2^32 / 65535) units of
+ * the 32.32 image (full_scale rays read 65535); counts = the image divided
+ * by d, rounded half up, clipped to [0, 65535] -- integer arithmetic once d
+ * is fixed. */
 void om_image_u16(const int64_t *image, int64_t n, double full_scale, uint16_t *out)
 {
+    int64_t d = (int64_t)llround(full_scale * 4294967296.0 / 65535.0);
+    if (d < 1) d = 1;
     for (int64_t q = 0; q < n; ++q) {
-        double v = rint((double)image[q] * 0x1p-32 / full_scale * 65535.0);
-        if (v < 0.0) v = 0.0;
-        if (v > 65535.0) v = 65535.0;
-        out[q] = (uint16_t)v;
+        int64_t v = image[q] < 0 ? 0 : image[q];
+        /* (v + floor(d/2)) / d, computed without overflow */
+        int64_t c = v / d + ((v % d) >= d - d / 2 ? 1 : 0);
+        out[q] = (uint16_t)(c > 65535 ? 65535 : c);
     }
 }
 

@@ -57,16 +57,32 @@ __global__ void advect_kernel(const VelGrid G, const double* __restrict__ src, i
     out[3 * q + 2] = x[2] + dt * u[2];
 }
 
-// counts = rint(image 2^-32 / full_scale * 65535), clipped to [0, 65535]
-__device__ __forceinline__ uint16_t to_u16(long long v, double fs)
+// counts = (image + floor(d/2)) / d (integer division), clipped to
+// [0, 65535]; d = llround(full_scale 2^32 / 65535) >= 1, thr = 65535 d -
+// floor(d/2) (counts reach 65535 from there).  The quotient is at most 65535:
+// an FP32 estimate from the reciprocal of d is within one of it, and one
+// exact 64-bit multiply-subtract corrects it, so no FP64 or 64-bit division
+// runs per pixel.
+struct U16Scale {
+    long long d, h, thr;
+    float inv_d;
+};
+
+__device__ __forceinline__ uint32_t to_u16(long long v, const U16Scale& S)
 {
-    const double c = rint(__dmul_rn(__ddiv_rn((double)v * 0x1p-32, fs), 65535.0));
-    return (uint16_t)fmin(fmax(c, 0.0), 65535.0);
+    if (v <= 0) return 0u;
+    if (v >= S.thr) return 65535u;
+    const unsigned long long x = (unsigned long long)(v + S.h);
+    const float xf = fmaf((float)(uint32_t)(x >> 32), 4294967296.0f, (float)(uint32_t)x);
+    long long q = (int)(xf * S.inv_d);   // below 65536: a 32-bit conversion
+    const long long r = (long long)x - q * S.d;
+    q += (r >= S.d) - (r < 0);
+    return (uint32_t)q;
 }
 
 // 8 pixels per thread and step: 64 B read as four 16-byte loads, 16 B written
 // as one; grid-stride over the image (the host sizes the grid to the SMs).
-__global__ void image_u16_kernel(const int64_t* __restrict__ img, int64_t n, double full_scale,
+__global__ void image_u16_kernel(const int64_t* __restrict__ img, int64_t n, const U16Scale S,
                                  uint16_t* __restrict__ out)
 {
     const int64_t n8 = n / 8;
@@ -78,13 +94,13 @@ __global__ void image_u16_kernel(const int64_t* __restrict__ img, int64_t n, dou
         const longlong2 a = __ldcs(in2 + 4 * t), b = __ldcs(in2 + 4 * t + 1);
         const longlong2 c = __ldcs(in2 + 4 * t + 2), d = __ldcs(in2 + 4 * t + 3);
         uint4 o;
-        o.x = (uint32_t)to_u16(a.x, full_scale) | ((uint32_t)to_u16(a.y, full_scale) << 16);
-        o.y = (uint32_t)to_u16(b.x, full_scale) | ((uint32_t)to_u16(b.y, full_scale) << 16);
-        o.z = (uint32_t)to_u16(c.x, full_scale) | ((uint32_t)to_u16(c.y, full_scale) << 16);
-        o.w = (uint32_t)to_u16(d.x, full_scale) | ((uint32_t)to_u16(d.y, full_scale) << 16);
+        o.x = to_u16(a.x, S) | (to_u16(a.y, S) << 16);
+        o.y = to_u16(b.x, S) | (to_u16(b.y, S) << 16);
+        o.z = to_u16(c.x, S) | (to_u16(c.y, S) << 16);
+        o.w = to_u16(d.x, S) | (to_u16(d.y, S) << 16);
         __stcs(out8 + t, o);
     }
-    for (int64_t q = 8 * n8 + t0; q < n; q += stride) out[q] = to_u16(img[q], full_scale);
+    for (int64_t q = 8 * n8 + t0; q < n; q += stride) out[q] = (uint16_t)to_u16(img[q], S);
 }
 
 }  // namespace pivbos
@@ -182,9 +198,15 @@ pivbos_status pivbos_image_u16(const int64_t* image, int64_t n_pixels, double fu
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t need = (n_pixels / 8 + 255) / 256 + 1;
     const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)(sms > 0 ? sms : 152) * 8);
+    U16Scale S;
+    S.d = std::max<long long>(1, llround(full_scale * 4294967296.0 / 65535.0));
+    if (S.d > (1ll << 46)) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "full_scale above 2^46 / 2^32 * 65535 rays");
+    S.h = S.d / 2;
+    S.thr = 65535ll * S.d - S.h;
+    S.inv_d = (float)(1.0 / (double)S.d);
     cudaStream_t s = (cudaStream_t)stream;
     timing_begin("image_u16", s);
-    image_u16_kernel<<<grid, 256, 0, s>>>(image, n_pixels, full_scale, out);
+    image_u16_kernel<<<grid, 256, 0, s>>>(image, n_pixels, S, out);
     timing_end("image_u16", s);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();

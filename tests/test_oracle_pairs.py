@@ -3,7 +3,7 @@ moved by a velocity field (explicit midpoint rule over trilinear samples),
 and the 16-bit image (Sec. 3.4: ~1e4 rays per particle give a 16-bit
 dynamic range).  Against closed forms: translation, the midpoint rule's
 exact map for linear fields, its order on a rotation, clamping, and exact
-integer conversions."""
+integer counts (one or two counts per ray, half-up rounding, clipping)."""
 import numpy as np
 import pytest
 
@@ -86,10 +86,16 @@ def test_second_order_on_a_rotation():
 
 def test_u16_conversion_exact():
     two32 = 1 << 32
-    img = np.array([0, 1 * two32, 50 * two32, 100 * two32, 250 * two32, -5 * two32], dtype=np.int64)
-    out = oracle.image_u16(img, 100.0)
-    exp = [0, round(65535 / 100), round(50 * 65535 / 100), 65535, 65535, 0]
-    assert out.tolist() == exp
-    # ties go to even: 2.5 -> 2, 3.5 -> 4 (full scale 65535 rays = 1 count per ray)
-    half = np.array([5 * two32 // 2, 7 * two32 // 2], dtype=np.int64)
-    assert oracle.image_u16(half, 65535.0).tolist() == [2, 4]
+    # full scale 65535 rays: one count per ray (d = 2^32 exactly)
+    k = np.array([0, 1, 7, 1000, 65535, 65536, 200000], dtype=np.int64)
+    assert oracle.image_u16(k * two32, 65535.0).tolist() == [0, 1, 7, 1000, 65535, 65535, 65535]
+    # half the full scale: two counts per ray (d = 2^31)
+    assert oracle.image_u16(k[:4] * two32, 65535.0 / 2).tolist() == [0, 2, 14, 2000]
+    # rounding half up at the count boundaries, negatives clip to 0
+    d = two32
+    v = np.array([3 * d + d // 2 - 1, 3 * d + d // 2, 3 * d + d // 2 + 1, -5 * d], dtype=np.int64)
+    assert oracle.image_u16(v, 65535.0).tolist() == [3, 4, 4, 0]
+    # a full scale of 100 rays: counts = k * 655.35 rounded
+    k = np.arange(0, 101, dtype=np.int64)
+    assert np.array_equal(oracle.image_u16(k * two32, 100.0).astype(np.int64),
+                          np.floor(k * 655.35 + 0.5).astype(np.int64))
