@@ -238,6 +238,24 @@ void set_last_error(const char* msg) { t_err = msg; }
 
 pivbos_status device_status_word(int dev, int** out) { return status_word(dev, out); }
 
+pivbos_status failf(pivbos_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+pivbos_status cuda_status(cudaError_t e, const char* what)
+{
+    return e == cudaSuccess ? PIVBOS_OK : cuda_fail(e, what);
+}
+
+pivbos_status device_pointer(const void* p, int dev, const char* what) { return check_device_ptr(p, dev, what); }
+
 pivbos_status prepare_trace(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
                             int64_t n_sources, int sources_on_device, int32_t rays_per_source, uint64_t seed,
                             uint32_t frame, int integrator, double step, TraceParams* p, int* dev, uint64_t* total)

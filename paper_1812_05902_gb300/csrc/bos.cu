@@ -337,42 +337,6 @@ __global__ void regrid_finish_kernel(const unsigned long long* __restrict__ acc,
 // ---------------------------------------------------------------------------
 // entry points
 // ---------------------------------------------------------------------------
-namespace {
-
-pivbos_status bos_fail(pivbos_status st, const char* fmt, ...)
-{
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    pivbos::set_last_error(buf);
-    return st;
-}
-
-pivbos_status bos_cuda(cudaError_t e, const char* what)
-{
-    if (e == cudaSuccess) return PIVBOS_OK;
-    return bos_fail(e == cudaErrorMemoryAllocation ? PIVBOS_ERR_OOM : PIVBOS_ERR_CUDA, "%s: %s", what,
-                    cudaGetErrorString(e));
-}
-
-pivbos_status device_ptr(const void* p, int dev, const char* what)
-{
-    if (!p) return bos_fail(PIVBOS_ERR_INVALID_ARG, "%s is NULL", what);
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return bos_fail(PIVBOS_ERR_INVALID_ARG, "%s is not a CUDA pointer", what);
-    }
-    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
-        return bos_fail(PIVBOS_ERR_INVALID_ARG, "%s is not device memory", what);
-    if (a.type == cudaMemoryTypeDevice && a.device != dev)
-        return bos_fail(PIVBOS_ERR_INVALID_ARG, "%s belongs to device %d, current is %d", what, a.device, dev);
-    return PIVBOS_OK;
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -383,8 +347,8 @@ pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_opti
 {
     using namespace pivbos;
     set_last_error("");
-    if (!m) return bos_fail(PIVBOS_ERR_INVALID_ARG, "medium handle is NULL");
-    if (rays_per_dot > (1 << 22)) return bos_fail(PIVBOS_ERR_UNSUPPORTED, "more than 2^22 rays per dot");
+    if (!m) return failf(PIVBOS_ERR_INVALID_ARG, "medium handle is NULL");
+    if (rays_per_dot > (1 << 22)) return failf(PIVBOS_ERR_UNSUPPORTED, "more than 2^22 rays per dot");
     TraceParams p;
     int dev;
     uint64_t total;
@@ -392,12 +356,12 @@ pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_opti
                                      &total);
     if (st) return st;
     if (o->d.W > 65536 || o->d.H > 65536)
-        return bos_fail(PIVBOS_ERR_UNSUPPORTED, "sensor wider than 65536 pixels");
+        return failf(PIVBOS_ERR_UNSUPPORTED, "sensor wider than 65536 pixels");
     if (n_dots == 0) return PIVBOS_OK;
     if (!centroid && !displacement && !n_pairs) return PIVBOS_OK;
-    if (centroid && (st = device_ptr(centroid, dev, "centroid"))) return st;
-    if (displacement && (st = device_ptr(displacement, dev, "displacement"))) return st;
-    if (n_pairs && (st = device_ptr(n_pairs, dev, "n_pairs"))) return st;
+    if (centroid && (st = device_pointer(centroid, dev, "centroid"))) return st;
+    if (displacement && (st = device_pointer(displacement, dev, "displacement"))) return st;
+    if (n_pairs && (st = device_pointer(n_pairs, dev, "n_pairs"))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     // scratch: per-slot sums | Morton keys | permutation | sorted dots (double-float)
     const uint32_t nd = (uint32_t)n_dots;
@@ -409,7 +373,7 @@ pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_opti
     const size_t off_sdf = off_perm + (((size_t)nd * 4 + 255) & ~(size_t)255);
     const size_t bytes = off_sdf + (size_t)nd * 24;
     char* scratch = nullptr;
-    if ((st = bos_cuda(cudaMallocAsync((void**)&scratch, bytes, s), "displacement scratch"))) return st;
+    if ((st = cuda_status(cudaMallocAsync((void**)&scratch, bytes, s), "displacement scratch"))) return st;
     unsigned long long* acc = (unsigned long long*)scratch;
     uint32_t* perm = (uint32_t*)(scratch + off_perm);
     float2* sdf = (float2*)(scratch + off_sdf);
@@ -437,8 +401,8 @@ pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_opti
         e = cudaGetLastError();
     }
     const cudaError_t ef = cudaFreeAsync(scratch, s);
-    if ((st = bos_cuda(e, "bos_displacements"))) return st;
-    return bos_cuda(ef, "displacement scratch release");
+    if ((st = cuda_status(e, "bos_displacements"))) return st;
+    return cuda_status(ef, "displacement scratch release");
 }
 
 pivbos_status pivbos_bos_theory(const pivbos_medium* m, const pivbos_optics* o, const double* dots, int64_t n_dots,
@@ -446,16 +410,16 @@ pivbos_status pivbos_bos_theory(const pivbos_medium* m, const pivbos_optics* o, 
 {
     using namespace pivbos;
     set_last_error("");
-    if (!m || !o) return bos_fail(PIVBOS_ERR_INVALID_ARG, "medium or optics handle is NULL");
-    if (n_dots < 0 || n_dots > (1ll << 31)) return bos_fail(PIVBOS_ERR_INVALID_ARG, "n_dots %lld", (long long)n_dots);
+    if (!m || !o) return failf(PIVBOS_ERR_INVALID_ARG, "medium or optics handle is NULL");
+    if (n_dots < 0 || n_dots > (1ll << 31)) return failf(PIVBOS_ERR_INVALID_ARG, "n_dots %lld", (long long)n_dots);
     int dev;
-    if (cudaGetDevice(&dev) != cudaSuccess) return bos_cuda(cudaGetLastError(), "cudaGetDevice");
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status(cudaGetLastError(), "cudaGetDevice");
     if (m->device != dev || o->device != dev)
-        return bos_fail(PIVBOS_ERR_INVALID_ARG, "handles belong to another device");
+        return failf(PIVBOS_ERR_INVALID_ARG, "handles belong to another device");
     if (n_dots == 0) return PIVBOS_OK;
     pivbos_status st;
-    if ((st = device_ptr(dots, dev, "dots"))) return st;
-    if ((st = device_ptr(displacement, dev, "displacement"))) return st;
+    if ((st = device_pointer(dots, dev, "dots"))) return st;
+    if ((st = device_pointer(displacement, dev, "displacement"))) return st;
     Eq9Geom G;
     G.field = m->field;
     for (int a = 0; a < 3; ++a) {
@@ -471,7 +435,7 @@ pivbos_status pivbos_bos_theory(const pivbos_medium* m, const pivbos_optics* o, 
     bos_theory_kernel<<<(unsigned)((n_dots + 127) / 128), 128, 0, s>>>(G, dots, n_dots, displacement);
     timing_end("bos_theory", s);
     count_launches(1);
-    return bos_cuda(cudaGetLastError(), "bos_theory");
+    return cuda_status(cudaGetLastError(), "bos_theory");
 }
 
 pivbos_status pivbos_regrid_bilinear(const double* xy, const double* values, int64_t n, int grid_w, int grid_h,
@@ -480,19 +444,19 @@ pivbos_status pivbos_regrid_bilinear(const double* xy, const double* values, int
 {
     using namespace pivbos;
     set_last_error("");
-    if (n < 0 || n > (1ll << 23)) return bos_fail(PIVBOS_ERR_INVALID_ARG, "n %lld outside [0, 2^23]", (long long)n);
+    if (n < 0 || n > (1ll << 23)) return failf(PIVBOS_ERR_INVALID_ARG, "n %lld outside [0, 2^23]", (long long)n);
     if (grid_w < 2 || grid_h < 2 || (int64_t)grid_w * grid_h > (1ll << 28))
-        return bos_fail(PIVBOS_ERR_INVALID_ARG, "grid %d x %d", grid_w, grid_h);
+        return failf(PIVBOS_ERR_INVALID_ARG, "grid %d x %d", grid_w, grid_h);
     if (!(isfinite(x0) && isfinite(y0) && isfinite(cell) && cell > 0.0) || !(min_weight >= 0.0))
-        return bos_fail(PIVBOS_ERR_INVALID_ARG, "grid origin, cell or min_weight");
+        return failf(PIVBOS_ERR_INVALID_ARG, "grid origin, cell or min_weight");
     int dev;
-    if (cudaGetDevice(&dev) != cudaSuccess) return bos_cuda(cudaGetLastError(), "cudaGetDevice");
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status(cudaGetLastError(), "cudaGetDevice");
     pivbos_status st;
-    if ((st = device_ptr(out, dev, "out"))) return st;
-    if (weight && (st = device_ptr(weight, dev, "weight"))) return st;
+    if ((st = device_pointer(out, dev, "out"))) return st;
+    if (weight && (st = device_pointer(weight, dev, "weight"))) return st;
     if (n > 0) {
-        if ((st = device_ptr(xy, dev, "xy"))) return st;
-        if ((st = device_ptr(values, dev, "values"))) return st;
+        if ((st = device_pointer(xy, dev, "xy"))) return st;
+        if ((st = device_pointer(values, dev, "values"))) return st;
     }
     int* sw = nullptr;
     if ((st = device_status_word(dev, &sw))) return st;
@@ -500,7 +464,7 @@ pivbos_status pivbos_regrid_bilinear(const double* xy, const double* values, int
     const int64_t nodes = (int64_t)grid_w * grid_h;
     const size_t bytes = (size_t)nodes * 3 * sizeof(unsigned long long);
     unsigned long long* acc = nullptr;
-    if ((st = bos_cuda(cudaMallocAsync((void**)&acc, bytes, s), "regrid accumulators"))) return st;
+    if ((st = cuda_status(cudaMallocAsync((void**)&acc, bytes, s), "regrid accumulators"))) return st;
     cudaError_t e = cudaMemsetAsync(acc, 0, bytes, s);
     if (e == cudaSuccess && n > 0) {
         timing_begin("regrid", s);
@@ -516,8 +480,8 @@ pivbos_status pivbos_regrid_bilinear(const double* xy, const double* values, int
         e = cudaGetLastError();
     }
     const cudaError_t ef = cudaFreeAsync(acc, s);
-    if ((st = bos_cuda(e, "regrid_bilinear"))) return st;
-    return bos_cuda(ef, "regrid accumulators release");
+    if ((st = cuda_status(e, "regrid_bilinear"))) return st;
+    return cuda_status(ef, "regrid accumulators release");
 }
 
 }  // extern "C"

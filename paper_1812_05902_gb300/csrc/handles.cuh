@@ -33,6 +33,12 @@ pivbos_status prepare_trace(const pivbos_medium* m, const pivbos_optics* o, cons
                             uint32_t frame, int integrator, double step, TraceParams* p, int* dev, uint64_t* total);
 // Device status word of device `dev` (allocated on first use).
 pivbos_status device_status_word(int dev, int** out);
+// Record a formatted message for pivbos_last_error() and return st.
+pivbos_status failf(pivbos_status st, const char* fmt, ...);
+// PIVBOS_OK for cudaSuccess; otherwise OOM or CUDA with a message naming `what`.
+pivbos_status cuda_status(cudaError_t e, const char* what);
+// A pointer declared as device memory must be device (or managed) memory of device `dev`.
+pivbos_status device_pointer(const void* p, int dev, const char* what);
 // Keep kernel timing out of captured streams.
 void timing_suppress(bool on);
 }  // namespace pivbos

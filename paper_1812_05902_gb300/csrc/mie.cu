@@ -103,27 +103,6 @@ __global__ void mie_angles_kernel(int nstop, const cplx* __restrict__ a, const c
 
 }  // namespace pivbos
 
-namespace {
-
-pivbos_status mie_fail(pivbos_status st, const char* fmt, ...)
-{
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    pivbos::set_last_error(buf);
-    return st;
-}
-
-pivbos_status mie_cuda(cudaError_t e, const char* what)
-{
-    if (e == cudaSuccess) return PIVBOS_OK;
-    return mie_fail(e == cudaErrorMemoryAllocation ? PIVBOS_ERR_OOM : PIVBOS_ERR_CUDA, "%s: %s", what,
-                    cudaGetErrorString(e));
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -134,16 +113,16 @@ pivbos_status pivbos_mie(double diameter, double wavelength, double n_medium, do
     set_last_error("");
     if (!(diameter > 0.0 && wavelength > 0.0 && n_medium > 0.0 && m_re > 0.0 && m_im >= 0.0) ||
         !isfinite(diameter) || !isfinite(wavelength) || !isfinite(n_medium) || !isfinite(m_re) || !isfinite(m_im))
-        return mie_fail(PIVBOS_ERR_INVALID_ARG, "diameter, wavelength, indices");
-    if (n_angles < 2 || n_angles > (1 << 20) || !s12) return mie_fail(PIVBOS_ERR_INVALID_ARG, "n_angles or s12");
+        return failf(PIVBOS_ERR_INVALID_ARG, "diameter, wavelength, indices");
+    if (n_angles < 2 || n_angles > (1 << 20) || !s12) return failf(PIVBOS_ERR_INVALID_ARG, "n_angles or s12");
     const double x = M_PI * diameter * n_medium / wavelength;
-    if (x > 20000.0) return mie_fail(PIVBOS_ERR_UNSUPPORTED, "size parameter %.4g above 20000", x);
+    if (x > 20000.0) return failf(PIVBOS_ERR_UNSUPPORTED, "size parameter %.4g above 20000", x);
     const int nstop = (int)(x + 4.0 * cbrt(x) + 2.0);
     const int nmx = (int)fmax((double)nstop, x * hypot(m_re, m_im)) + 16;
     const size_t coef = (size_t)(nstop + 1) * sizeof(cplx);
     const size_t bytes = (size_t)(nmx + 1) * sizeof(cplx) + 2 * coef + (size_t)n_angles * 2 * sizeof(double) + 64;
     char* buf = nullptr;
-    pivbos_status st = mie_cuda(cudaMalloc((void**)&buf, bytes), "Mie scratch");
+    pivbos_status st = cuda_status(cudaMalloc((void**)&buf, bytes), "Mie scratch");
     if (st) return st;
     cplx* D = (cplx*)buf;
     cplx* a = (cplx*)(buf + (size_t)(nmx + 1) * sizeof(cplx));
@@ -158,7 +137,7 @@ pivbos_status pivbos_mie(double diameter, double wavelength, double n_medium, do
     if (e == cudaSuccess) e = cudaMemcpy(s12, ds12, (size_t)n_angles * 2 * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(hq, dq, sizeof hq, cudaMemcpyDeviceToHost);
     cudaFree(buf);
-    if ((st = mie_cuda(e, "Mie kernels"))) return st;
+    if ((st = cuda_status(e, "Mie kernels"))) return st;
     if (q) {
         q[0] = hq[0];
         q[1] = hq[1];
@@ -173,32 +152,32 @@ pivbos_status pivbos_optics_radiance(const pivbos_optics* o, const double laser_
 {
     using namespace pivbos;
     set_last_error("");
-    if (!o || !out || !laser_dir || !s12) return mie_fail(PIVBOS_ERR_INVALID_ARG, "NULL argument");
+    if (!o || !out || !laser_dir || !s12) return failf(PIVBOS_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
-    if (n_angles < 2 || n_angles > (1 << 20)) return mie_fail(PIVBOS_ERR_INVALID_ARG, "n_angles %d", n_angles);
+    if (n_angles < 2 || n_angles > (1 << 20)) return failf(PIVBOS_ERR_INVALID_ARG, "n_angles %d", n_angles);
     const double ll = sqrt(laser_dir[0] * laser_dir[0] + laser_dir[1] * laser_dir[1] + laser_dir[2] * laser_dir[2]);
-    if (!(ll > 0.0) || !isfinite(ll)) return mie_fail(PIVBOS_ERR_INVALID_ARG, "laser direction");
+    if (!(ll > 0.0) || !isfinite(ll)) return failf(PIVBOS_ERR_INVALID_ARG, "laser direction");
     double L[3], P[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < 3; ++k) L[k] = laser_dir[k] / ll;
     if (polarisation) {
         const double pl = sqrt(polarisation[0] * polarisation[0] + polarisation[1] * polarisation[1] +
                                polarisation[2] * polarisation[2]);
-        if (!(pl > 0.0) || !isfinite(pl)) return mie_fail(PIVBOS_ERR_INVALID_ARG, "polarisation");
+        if (!(pl > 0.0) || !isfinite(pl)) return failf(PIVBOS_ERR_INVALID_ARG, "polarisation");
         for (int k = 0; k < 3; ++k) P[k] = polarisation[k] / pl;
         if (fabs(P[0] * L[0] + P[1] * L[1] + P[2] * L[2]) > 1e-6)
-            return mie_fail(PIVBOS_ERR_INVALID_ARG, "polarisation must be normal to the laser direction");
+            return failf(PIVBOS_ERR_INVALID_ARG, "polarisation must be normal to the laser direction");
     }
     double mx = 0.0;
     for (int i = 0; i < 2 * n_angles; ++i) {
-        if (!(s12[i] >= 0.0) || !isfinite(s12[i])) return mie_fail(PIVBOS_ERR_INVALID_ARG, "table entry %d", i);
+        if (!(s12[i] >= 0.0) || !isfinite(s12[i])) return failf(PIVBOS_ERR_INVALID_ARG, "table entry %d", i);
         mx = fmax(mx, s12[i]);
     }
-    if (!(mx > 0.0)) return mie_fail(PIVBOS_ERR_INVALID_ARG, "the table is zero");
+    if (!(mx > 0.0)) return failf(PIVBOS_ERR_INVALID_ARG, "the table is zero");
     int dev;
-    if (cudaGetDevice(&dev) != cudaSuccess) return mie_cuda(cudaGetLastError(), "cudaGetDevice");
-    if (o->device != dev) return mie_fail(PIVBOS_ERR_INVALID_ARG, "optics handle belongs to device %d", o->device);
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status(cudaGetLastError(), "cudaGetDevice");
+    if (o->device != dev) return failf(PIVBOS_ERR_INVALID_ARG, "optics handle belongs to device %d", o->device);
     float2* h = new (std::nothrow) float2[n_angles];
-    if (!h) return mie_fail(PIVBOS_ERR_OOM, "host allocation");
+    if (!h) return failf(PIVBOS_ERR_OOM, "host allocation");
     for (int i = 0; i < n_angles; ++i) h[i] = make_float2((float)(s12[2 * i] / mx), (float)(s12[2 * i + 1] / mx));
     float2* d = nullptr;
     cudaError_t e = cudaMalloc((void**)&d, (size_t)n_angles * sizeof(float2));
@@ -206,12 +185,12 @@ pivbos_status pivbos_optics_radiance(const pivbos_optics* o, const double laser_
     delete[] h;
     if (e != cudaSuccess) {
         if (d) cudaFree(d);
-        return mie_cuda(e, "radiance table");
+        return cuda_status(e, "radiance table");
     }
     pivbos_optics* c = new (std::nothrow) pivbos_optics(*o);
     if (!c) {
         cudaFree(d);
-        return mie_fail(PIVBOS_ERR_OOM, "host allocation");
+        return failf(PIVBOS_ERR_OOM, "host allocation");
     }
     c->d.rad = d;
     c->d.rad_n = n_angles;

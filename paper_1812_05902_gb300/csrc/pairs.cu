@@ -105,35 +105,6 @@ __global__ void image_u16_kernel(const int64_t* __restrict__ img, int64_t n, con
 
 }  // namespace pivbos
 
-namespace {
-
-pivbos_status pairs_fail(pivbos_status st, const char* fmt, ...)
-{
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    pivbos::set_last_error(buf);
-    return st;
-}
-
-pivbos_status on_device(const void* p, int dev, const char* what)
-{
-    if (!p) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "%s is NULL", what);
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "%s is not a CUDA pointer", what);
-    }
-    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
-        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "%s is not device memory", what);
-    if (a.type == cudaMemoryTypeDevice && a.device != dev)
-        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "%s belongs to device %d, current is %d", what, a.device, dev);
-    return PIVBOS_OK;
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -143,21 +114,21 @@ pivbos_status pivbos_advect_sources(const double* sources, int64_t n_sources, co
 {
     using namespace pivbos;
     set_last_error("");
-    if (n_sources < 0 || n_sources > (1ll << 31)) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "n_sources");
+    if (n_sources < 0 || n_sources > (1ll << 31)) return failf(PIVBOS_ERR_INVALID_ARG, "n_sources");
     if (nx < 2 || ny < 2 || nz < 2 || !origin || !spacing || !isfinite(dt))
-        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "grid or dt");
+        return failf(PIVBOS_ERR_INVALID_ARG, "grid or dt");
     for (int a = 0; a < 3; ++a)
         if (!isfinite(origin[a]) || !(spacing[a] > 0.0) || !isfinite(spacing[a]))
-            return pairs_fail(PIVBOS_ERR_INVALID_ARG, "origin or spacing");
+            return failf(PIVBOS_ERR_INVALID_ARG, "origin or spacing");
     if (n_sources == 0) return PIVBOS_OK;
     int dev;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
-        return pairs_fail(PIVBOS_ERR_CUDA, "cudaGetDevice");
+        return failf(PIVBOS_ERR_CUDA, "cudaGetDevice");
     }
     pivbos_status st;
-    if ((st = on_device(sources, dev, "sources")) || (st = on_device(velocity, dev, "velocity")) ||
-        (st = on_device(out, dev, "out")))
+    if ((st = device_pointer(sources, dev, "sources")) || (st = device_pointer(velocity, dev, "velocity")) ||
+        (st = device_pointer(out, dev, "out")))
         return st;
     VelGrid G;
     G.v = velocity;
@@ -174,7 +145,7 @@ pivbos_status pivbos_advect_sources(const double* sources, int64_t n_sources, co
     timing_end("advect", s);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return pairs_fail(PIVBOS_ERR_CUDA, "advect: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return failf(PIVBOS_ERR_CUDA, "advect: %s", cudaGetErrorString(e));
     return PIVBOS_OK;
 }
 
@@ -183,24 +154,24 @@ pivbos_status pivbos_image_u16(const int64_t* image, int64_t n_pixels, double fu
 {
     using namespace pivbos;
     set_last_error("");
-    if (n_pixels < 0) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "n_pixels < 0");
-    if (!(full_scale > 0.0) || !isfinite(full_scale)) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "full_scale");
+    if (n_pixels < 0) return failf(PIVBOS_ERR_INVALID_ARG, "n_pixels < 0");
+    if (!(full_scale > 0.0) || !isfinite(full_scale)) return failf(PIVBOS_ERR_INVALID_ARG, "full_scale");
     if (n_pixels == 0) return PIVBOS_OK;
     if ((reinterpret_cast<uintptr_t>(image) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
-        return pairs_fail(PIVBOS_ERR_INVALID_ARG, "image and out must be 16-byte aligned");
+        return failf(PIVBOS_ERR_INVALID_ARG, "image and out must be 16-byte aligned");
     int dev, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
-        return pairs_fail(PIVBOS_ERR_CUDA, "cudaGetDevice");
+        return failf(PIVBOS_ERR_CUDA, "cudaGetDevice");
     }
     pivbos_status st;
-    if ((st = on_device(image, dev, "image")) || (st = on_device(out, dev, "out"))) return st;
+    if ((st = device_pointer(image, dev, "image")) || (st = device_pointer(out, dev, "out"))) return st;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t need = (n_pixels / 8 + 255) / 256 + 1;
     const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)(sms > 0 ? sms : 152) * 8);
     U16Scale S;
     S.d = std::max<long long>(1, llround(full_scale * 4294967296.0 / 65535.0));
-    if (S.d > (1ll << 46)) return pairs_fail(PIVBOS_ERR_INVALID_ARG, "full_scale above 2^46 / 2^32 * 65535 rays");
+    if (S.d > (1ll << 46)) return failf(PIVBOS_ERR_INVALID_ARG, "full_scale above 2^46 / 2^32 * 65535 rays");
     S.h = S.d / 2;
     S.thr = 65535ll * S.d - S.h;
     S.inv_d = (float)(1.0 / (double)S.d);
@@ -210,7 +181,7 @@ pivbos_status pivbos_image_u16(const int64_t* image, int64_t n_pixels, double fu
     timing_end("image_u16", s);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return pairs_fail(PIVBOS_ERR_CUDA, "image_u16: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return failf(PIVBOS_ERR_CUDA, "image_u16: %s", cudaGetErrorString(e));
     return PIVBOS_OK;
 }
 
