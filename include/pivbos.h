@@ -480,6 +480,16 @@ pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_opti
                                        int integrator, double step, double* centroid, double* displacement,
                                        int32_t* n_pairs, void* stream);
 
+/* The same for dots [first_dot, first_dot + n_dots) of a larger dot set:
+ * `dots` points at that range and ray k of local dot d draws its lens point
+ * with counter (k, first_dot + d, frame, 0), so ranges computed separately
+ * (on one GPU or several) give, dot for dot and bit for bit, the results of
+ * the whole set.  first_dot + n_dots <= 2^32. */
+pivbos_status pivbos_bos_displacements_range(const pivbos_medium* m, const pivbos_optics* o, const double* dots,
+                                             int64_t n_dots, int64_t first_dot, int32_t rays_per_dot, uint64_t seed,
+                                             uint32_t frame, int integrator, double step, double* centroid,
+                                             double* displacement, int32_t* n_pairs, void* stream);
+
 /* Eq. 9 per dot, in pixels of the sensor frame:
  *     displacement = (M Z_D / n0) * integral of (dn/dx, dn/dy) dz / pitch,
  * with M, n0 (= n_object) and the pitch given to pivbos_optics_create, Z_D

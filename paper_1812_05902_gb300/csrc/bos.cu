@@ -340,14 +340,30 @@ __global__ void regrid_finish_kernel(const unsigned long long* __restrict__ acc,
 
 extern "C" {
 
+pivbos_status pivbos_bos_displacements_range(const pivbos_medium* m, const pivbos_optics* o, const double* dots,
+                                             int64_t n_dots, int64_t first_dot, int32_t rays_per_dot, uint64_t seed,
+                                             uint32_t frame, int integrator, double step, double* centroid,
+                                             double* displacement, int32_t* n_pairs, void* stream);
+
 pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_optics* o, const double* dots,
                                        int64_t n_dots, int32_t rays_per_dot, uint64_t seed, uint32_t frame,
                                        int integrator, double step, double* centroid, double* displacement,
                                        int32_t* n_pairs, void* stream)
 {
+    return pivbos_bos_displacements_range(m, o, dots, n_dots, 0, rays_per_dot, seed, frame, integrator, step,
+                                          centroid, displacement, n_pairs, stream);
+}
+
+pivbos_status pivbos_bos_displacements_range(const pivbos_medium* m, const pivbos_optics* o, const double* dots,
+                                             int64_t n_dots, int64_t first_dot, int32_t rays_per_dot, uint64_t seed,
+                                             uint32_t frame, int integrator, double step, double* centroid,
+                                             double* displacement, int32_t* n_pairs, void* stream)
+{
     using namespace pivbos;
     set_last_error("");
     if (!m) return failf(PIVBOS_ERR_INVALID_ARG, "medium handle is NULL");
+    if (first_dot < 0 || first_dot + n_dots > 0xffffffffll)
+        return failf(PIVBOS_ERR_INVALID_ARG, "first_dot %lld outside [0, 2^32 - n_dots]", (long long)first_dot);
     if (rays_per_dot > (1 << 22)) return failf(PIVBOS_ERR_UNSUPPORTED, "more than 2^22 rays per dot");
     TraceParams p;
     int dev;
@@ -382,6 +398,7 @@ pivbos_status pivbos_bos_displacements(const pivbos_medium* m, const pivbos_opti
     if (e == cudaSuccess && total > 0) {
         p.perm = perm;
         p.src_df = sdf;
+        p.source_offset = (uint32_t)first_dot;
         const uint32_t rpc = rays_per_cta_setting(p);
         const uint64_t blocks = (total + rpc - 1) / rpc;
         timing_begin("bos_pairs", s);

@@ -131,6 +131,7 @@ def _load():
         "pivbos_surrogate_report_get": ([P, P], I),
         "pivbos_surrogate_destroy": ([P], None),
         "pivbos_bos_displacements": ([P, P, P, I64, I32, U64, U32, I, D, P, P, P, P], I),
+        "pivbos_bos_displacements_range": ([P, P, P, I64, I64, I32, U64, U32, I, D, P, P, P, P], I),
         "pivbos_bos_theory": ([P, P, P, I64, P, P], I),
         "pivbos_regrid_bilinear": ([P, P, I64, I, I, D, D, D, D, P, P, P], I),
     }
@@ -150,7 +151,7 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_autotune", "pivbos_render_range", "pivbos_mlp_forward", "pivbos_mlp_loss_grad",
             "pivbos_surrogate_default_cfg", "pivbos_surrogate_train", "pivbos_surrogate_render",
             "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy",
-            "pivbos_bos_displacements", "pivbos_bos_theory", "pivbos_regrid_bilinear", "pivbos_optics_tilt_sensor",
+            "pivbos_bos_displacements", "pivbos_bos_displacements_range", "pivbos_bos_theory", "pivbos_regrid_bilinear", "pivbos_optics_tilt_sensor",
             "pivbos_mie", "pivbos_optics_radiance", "pivbos_advect_sources", "pivbos_image_u16")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
@@ -395,6 +396,14 @@ def pivbos_bos_displacements(m, o, dots, n_dots, rays_per_dot, seed, frame, inte
     _check(_lib.pivbos_bos_displacements(m, o, _addr(dots)[0], n_dots, rays_per_dot, seed, frame, integrator, step,
                                          _addr(centroid)[0], _addr(displacement)[0], _addr(n_pairs)[0],
                                          _stream(stream)))
+
+
+def pivbos_bos_displacements_range(m, o, dots, n_dots, first_dot, rays_per_dot, seed, frame, integrator, step,
+                                   centroid=None, displacement=None, n_pairs=None, stream=None):
+    """pivbos_bos_displacements for dots [first_dot, first_dot + n_dots) of a larger set."""
+    _check(_lib.pivbos_bos_displacements_range(m, o, _addr(dots)[0], n_dots, first_dot, rays_per_dot, seed, frame,
+                                               integrator, step, _addr(centroid)[0], _addr(displacement)[0],
+                                               _addr(n_pairs)[0], _stream(stream)))
 
 
 def pivbos_bos_theory(m, o, dots, n_dots, displacement, stream=None):

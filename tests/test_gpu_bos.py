@@ -105,6 +105,29 @@ def test_displacements_are_bit_reproducible_and_edge_cases():
     assert (cnt.cpu().numpy() == 0).all()
 
 
+def test_dot_ranges_reproduce_the_whole_set():
+    """Dots split into ranges with global indices (one range per rank of a
+    sharded run) give the whole set's results bit for bit."""
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    fr = scenes.table1(scale=0.004, grid=64, rays_per_source=97)[0]
+    h = gpu_handles(fr)
+    whole = _gpu_bos(fr, h)
+    n = len(fr.sources)
+    parts = []
+    for first, count in ((0, 7), (7, n - 7)):
+        d = torch.tensor(fr.sources[first:first + count], dtype=torch.float64, device="cuda")
+        cen = torch.empty((count, 2), dtype=torch.float64, device="cuda")
+        disp = torch.empty((count, 2), dtype=torch.float64, device="cuda")
+        cnt = torch.empty(count, dtype=torch.int32, device="cuda")
+        P.pivbos_bos_displacements_range(h[0].h, h[1].h, d, count, first, fr.rays_per_source, fr.seed,
+                                         fr.frame_index, fr.integrator, fr.step, cen, disp, cnt)
+        P.pivbos_sync()
+        parts.append((cen.cpu().numpy(), disp.cpu().numpy(), cnt.cpu().numpy()))
+    for k in range(3):
+        assert np.array_equal(np.concatenate([p[k] for p in parts]), whole[k], equal_nan=True)
+
+
 def test_full_size_table1_sampled_dots():
     """The bench's Table 1 workload at full size (5,120 dots x 1e4 rays, 256^2
     slice): sampled dots against the oracle, and Eq. 9 against the traced

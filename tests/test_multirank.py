@@ -1,7 +1,9 @@
 """Sharding across ranks without a GPU: two gloo ranks each render a disjoint
 contiguous source range (global source indices), all-reduce the int64
 fixed-point images, and must reproduce the single-process image bit for
-bit.  The oracle renders the partial images here (CPU ranks)."""
+bit; the same ranks split the dots of the Sec. 4 BOS experiment and gather
+the per-dot displacements.  The oracle computes the partial results here
+(CPU ranks)."""
 import os
 import socket
 
@@ -67,3 +69,44 @@ def test_two_gloo_ranks_sum_to_the_single_render(tmp_path):
     n = img.size
     assert np.array_equal(got[:n].reshape(img.shape), img)
     assert np.array_equal(got[n:], st)
+
+
+def _bos_rank_main(rank, world, port, out_path):
+    import torch
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    fr = scenes.c0(scale=0.01, rays_per_source=20)[0]
+    med, opt = oracle.Medium.from_scene(fr.medium), oracle.Optics.from_scene(fr.optics)
+    first, count = source_range(len(fr.sources), world, rank)
+    _, disp, cnt = oracle.bos_displacements(med, opt, fr.sources, fr.rays_per_source, fr.seed, 0, fr.integrator,
+                                            fr.step, threads=1, dot_ids=np.arange(first, first + count))
+    # ranks' dot counts differ by at most one: pad to the largest, then gather
+    m = source_range(len(fr.sources), world, 0)[1]
+    pad = np.full((m, 3), np.nan)
+    pad[:count, :2] = disp
+    pad[:count, 2] = cnt
+    parts = [torch.zeros((m, 3), dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(parts, torch.from_numpy(pad))
+    if rank == 0:
+        rows = [p.numpy()[:source_range(len(fr.sources), world, r)[1]] for r, p in enumerate(parts)]
+        np.save(out_path, np.concatenate(rows))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_the_bos_dots(tmp_path):
+    import torch.multiprocessing as mp
+    import oracle
+    oracle.build()
+    out = str(tmp_path / "bos.npy")
+    mp.spawn(_bos_rank_main, args=(2, _free_port(), out), nprocs=2, join=True)
+    got = np.load(out)
+    fr = scenes.c0(scale=0.01, rays_per_source=20)[0]
+    med, opt = oracle.Medium.from_scene(fr.medium), oracle.Optics.from_scene(fr.optics)
+    _, disp, cnt = oracle.bos_displacements(med, opt, fr.sources, fr.rays_per_source, fr.seed, 0, fr.integrator,
+                                            fr.step)
+    assert np.array_equal(got[:, :2], disp, equal_nan=True)
+    assert np.array_equal(got[:, 2].astype(np.int32), cnt)
