@@ -105,6 +105,29 @@ def test_displacements_are_bit_reproducible_and_edge_cases():
     assert (cnt.cpu().numpy() == 0).all()
 
 
+def test_theory_and_grid_edge_cases():
+    """Eq. 9 is zero for a chief ray that misses the box or runs parallel to
+    the sensor; an empty grid map is all NaN with zero weight."""
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    fr = scenes.c0(scale=0.01, rays_per_source=8)[0]
+    med, opt = gpu_handles(fr)
+    dots = torch.tensor([[0.2, 0.2, 0.0],                       # chief ray misses the box
+                         [0.0, 0.0, fr.optics.aim_z],           # at the lens plane: no chief ray
+                         [1e-3, 2e-3, 0.0]], dtype=torch.float64, device="cuda")
+    th = torch.full((3, 2), 7.0, dtype=torch.float64, device="cuda")
+    P.pivbos_bos_theory(med.h, opt.h, dots, 3, th)
+    P.pivbos_sync()
+    t = th.cpu().numpy()
+    assert (t[:2] == 0.0).all() and abs(t[2, 1]) > 0.0
+    out = torch.full((4, 5, 2), 3.0, dtype=torch.float64, device="cuda")
+    w = torch.full((4, 5), 3.0, dtype=torch.float64, device="cuda")
+    empty = torch.empty((0, 2), dtype=torch.float64, device="cuda")
+    P.pivbos_regrid_bilinear(empty, empty, 0, 5, 4, 0.0, 0.0, 1.0, 0.0, out, w)
+    P.pivbos_sync()
+    assert torch.isnan(out).all() and (w == 0.0).all()
+
+
 def test_dot_ranges_reproduce_the_whole_set():
     """Dots split into ranges with global indices (one range per rank of a
     sharded run) give the whole set's results bit for bit."""
