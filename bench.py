@@ -271,7 +271,21 @@ EVALS_PER_STEP = {scenes.RK4: 3, scenes.EULER: 1}
 L1_BYTES_PER_CLK_PER_SM = 128
 
 
-def roofline(frames, mean_steps, render_ms, render_launches, sm_max_mhz, traffic=None):
+_L1_PEAK = {}
+
+
+def measured_l1_gbs(P):
+    """The L1 data path's measured bandwidth for 16-byte loads (GB/s), from
+    the library's probe; taken once per process, outside any timed region."""
+    if "v" not in _L1_PEAK:
+        try:
+            _L1_PEAK["v"] = P.pivbos_probe_l1_bandwidth() / 1e9
+        except Exception:
+            _L1_PEAK["v"] = None
+    return _L1_PEAK["v"]
+
+
+def roofline(frames, mean_steps, render_ms, render_launches, sm_max_mhz, traffic=None, l1_gbs=None):
     if render_launches == 0:
         return None
     t = render_ms / render_launches * 1e-3
@@ -294,6 +308,11 @@ def roofline(frames, mean_steps, render_ms, render_launches, sm_max_mhz, traffic
                          "unit": "GB/s", "frac": round(gbytes / t / 1e9 / gpeak, 4),
                          "bytes_per_ray": round(gbytes / rays, 1),
                          "peak_source": "152 SMs x 128 B/clk L1 data path x max SM clock"}
+        if l1_gbs:
+            out["gather"].update({"peak_measured": round(l1_gbs, 1),
+                                  "frac_measured": round(gbytes / t / 1e9 / l1_gbs, 4),
+                                  "peak_measured_source": "pivbos_probe_l1_bandwidth: coalesced 16-byte loads "
+                                                          "from an L1-resident 48 KB buffer on every SM"})
     return out
 
 
@@ -469,7 +488,8 @@ def run_gpu(args, rank, world):
     msteps = [mean_steps(P, fr, opt, meds[i], src_d[i]) for i, fr in enumerate(frames)]
     rf = roofline(frames, msteps, render_ms, render_n, clk.get("sm_max_mhz"),
                   recorded_traffic("render_%s_traffic" % args.workload)
-                  if args.scale == 1.0 and args.optics == "plain" else None)
+                  if args.scale == 1.0 and args.optics == "plain" else None,
+                  l1_gbs=measured_l1_gbs(P) if all(f.medium is not None for f in frames) else None)
     u16 = None
     if world == 1 and args.workload == "c1" and args.optics == "plain" and not args.no_table1:
         try:
@@ -783,7 +803,8 @@ def run_table1(args, rank, world, steps, warmup, embedded):
     # roofline of the pair kernel: FP32/INT32 issue, and the L1 gather path
     ms_steps = mean_steps(P, fr, opt, med, dots)
     rf = roofline([fr], [ms_steps], k_ms, k_n, clk.get("sm_max_mhz"),
-                  recorded_traffic("bos_table1_traffic", "bos") if args.scale == 1.0 else None)
+                  recorded_traffic("bos_table1_traffic", "bos") if args.scale == 1.0 else None,
+                  l1_gbs=measured_l1_gbs(P))
     if rf is not None:
         clk_hz = (clk.get("sm_max_mhz") or 2070.0) * 1e6
         t_launch = k_ms / k_n * 1e-3

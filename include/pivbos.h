@@ -545,6 +545,13 @@ pivbos_status pivbos_advect_sources(const double* sources, int64_t n_sources, co
 pivbos_status pivbos_image_u16(const int64_t* image, int64_t n_pixels, double full_scale, uint16_t* out,
                                void* stream);
 
+/* Measurement facility (no counterpart in the paper): the bandwidth of the
+ * current device's L1 data path for coalesced 16-byte loads from an
+ * L1-resident buffer (every SM streams 48 KB), in bytes per second -- the
+ * denominator of the field-gather rooflines.  Synchronous; allocates a small
+ * scratch.  Errors: INVALID_ARG, OOM, CUDA. */
+pivbos_status pivbos_probe_l1_bandwidth(double* bytes_per_second);
+
 /* int64 32.32 image -> float32 intensity in rays (value * 2^-32).  Device
  * pointers, n_pixels >= 0. */
 pivbos_status pivbos_image_finalize(const int64_t* image, int64_t n_pixels, float* out, void* stream);

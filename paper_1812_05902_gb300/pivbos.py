@@ -105,6 +105,7 @@ def _load():
         "pivbos_optics_radiance": ([P, P, P, P, I, P], I),
         "pivbos_advect_sources": ([P, I64, P, I, I, I, P, P, D, P, P], I),
         "pivbos_image_u16": ([P, I64, D, P, P], I),
+        "pivbos_probe_l1_bandwidth": ([ctypes.POINTER(D)], I),
         "pivbos_render": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
         "pivbos_trace_exit_states": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I64, P, P], I),
         "pivbos_image_finalize": ([P, I64, P, P], I),
@@ -152,7 +153,8 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_surrogate_default_cfg", "pivbos_surrogate_train", "pivbos_surrogate_render",
             "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy",
             "pivbos_bos_displacements", "pivbos_bos_displacements_range", "pivbos_bos_theory", "pivbos_regrid_bilinear", "pivbos_optics_tilt_sensor",
-            "pivbos_mie", "pivbos_optics_radiance", "pivbos_advect_sources", "pivbos_image_u16")
+            "pivbos_mie", "pivbos_optics_radiance", "pivbos_advect_sources", "pivbos_image_u16",
+            "pivbos_probe_l1_bandwidth")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
@@ -431,6 +433,13 @@ def pivbos_advect_sources(sources, n_sources, velocity, origin, spacing, dt, out
 def pivbos_image_u16(image, n_pixels, full_scale, out, stream=None):
     """16-bit image (full_scale rays read 65535); CUDA tensors (out uint16)."""
     _check(_lib.pivbos_image_u16(_addr(image)[0], n_pixels, full_scale, _addr(out)[0], _stream(stream)))
+
+
+def pivbos_probe_l1_bandwidth():
+    """Measured L1 bandwidth for coalesced 16-byte loads (bytes/s)."""
+    v = ctypes.c_double()
+    _check(_lib.pivbos_probe_l1_bandwidth(ctypes.byref(v)))
+    return v.value
 
 
 def pivbos_image_finalize(image, n_pixels, out, stream=None):
