@@ -6,7 +6,7 @@
 namespace pivbos {
 
 template <int INTEG, bool CACHE, bool EXT>
-__global__ void __launch_bounds__(kRenderThreads, CACHE ? 2 : kRenderMinBlocks)
+__global__ void __launch_bounds__(kRenderThreads, CACHE ? 3 : kRenderMinBlocks)
 render_kernel(const TraceParams P, int64_t* __restrict__ image, int64_t* __restrict__ stats,
               uint32_t rays_per_cta, uint64_t total_rays)
 {
