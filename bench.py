@@ -152,7 +152,7 @@ class Clocks:
 # (no FP64 left on the path, no tensor-core work, DRAM and L2 lightly used),
 # so its roofline is the SM issue rate: 152 SMs x 128 lanes x clock.  The
 # algorithmic work of one ray is a static count of FP32/INT32 lane operations
-# of the double-float and FP32 formulation, per stage (see DESIGN.md):
+# of the double-float and FP32 formulation, per stage:
 #   ray generation (Philox4x64-10, lens point, direction)  710
 #   volume entry + exit to the optics                       470
 #   each integration step: RK4 430, first-order 160
