@@ -552,6 +552,14 @@ pivbos_status pivbos_image_u16(const int64_t* image, int64_t n_pixels, double fu
  * scratch.  Errors: INVALID_ARG, OOM, CUDA. */
 pivbos_status pivbos_probe_l1_bandwidth(double* bytes_per_second);
 
+/* Self-test of the failure detection (no counterpart in the paper): a
+ * kernel waits, with the bounded wait the tensor-core kernels use, on an
+ * mbarrier nothing arrives at; after `polls` polls (1..2^20) it gives up and
+ * latches PIVBOS_ERR_DEVICE_TIMEOUT in the device status word, which the next
+ * pivbos_sync returns (and clears).  The context stays usable.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+pivbos_status pivbos_selftest_wait_timeout(uint32_t polls, void* stream);
+
 /* int64 32.32 image -> float32 intensity in rays (value * 2^-32).  Device
  * pointers, n_pixels >= 0. */
 pivbos_status pivbos_image_finalize(const int64_t* image, int64_t n_pixels, float* out, void* stream);

@@ -106,6 +106,7 @@ def _load():
         "pivbos_advect_sources": ([P, I64, P, I, I, I, P, P, D, P, P], I),
         "pivbos_image_u16": ([P, I64, D, P, P], I),
         "pivbos_probe_l1_bandwidth": ([ctypes.POINTER(D)], I),
+        "pivbos_selftest_wait_timeout": ([U32, P], I),
         "pivbos_render": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
         "pivbos_trace_exit_states": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I64, P, P], I),
         "pivbos_image_finalize": ([P, I64, P, P], I),
@@ -154,7 +155,7 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy",
             "pivbos_bos_displacements", "pivbos_bos_displacements_range", "pivbos_bos_theory", "pivbos_regrid_bilinear", "pivbos_optics_tilt_sensor",
             "pivbos_mie", "pivbos_optics_radiance", "pivbos_advect_sources", "pivbos_image_u16",
-            "pivbos_probe_l1_bandwidth")
+            "pivbos_probe_l1_bandwidth", "pivbos_selftest_wait_timeout")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
@@ -440,6 +441,11 @@ def pivbos_probe_l1_bandwidth():
     v = ctypes.c_double()
     _check(_lib.pivbos_probe_l1_bandwidth(ctypes.byref(v)))
     return v.value
+
+
+def pivbos_selftest_wait_timeout(polls, stream=None):
+    """Enqueue the bounded-wait self-test (the next pivbos_sync reports the timeout)."""
+    _check(_lib.pivbos_selftest_wait_timeout(polls, _stream(stream)))
 
 
 def pivbos_image_finalize(image, n_pixels, out, stream=None):

@@ -220,3 +220,9 @@ def test_pairs_arguments_without_a_device(P):
     L3 = (ctypes.c_double * 3)(1, 0, 0)
     assert L.pivbos_optics_radiance(None, L3, None, fake, 10, ctypes.byref(out)) == P.ERR_INVALID_ARG
     assert L.pivbos_optics_radiance(fake, L3, None, fake, 1, ctypes.byref(out)) == P.ERR_INVALID_ARG
+
+
+def test_selftest_arguments_without_a_device(P):
+    L = P.lib()
+    assert L.pivbos_selftest_wait_timeout(0, None) == P.ERR_INVALID_ARG
+    assert L.pivbos_selftest_wait_timeout((1 << 20) + 1, None) == P.ERR_INVALID_ARG
