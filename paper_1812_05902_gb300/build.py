@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpivbos.so")
-SOURCES = ["api.cu", "medium.cu", "sort.cu", "render.cu", "render_batch.cu", "render_list.cu", "noalloc.cu", "batch.cu", "mlp.cu", "surrogate.cu", "bos.cu", "mie.cu", "pairs.cu"]
+SOURCES = ["api.cu", "medium.cu", "sort.cu", "render.cu", "render_batch.cu", "render_list.cu", "noalloc.cu", "batch.cu", "mlp.cu", "surrogate.cu", "bos.cu", "mie.cu", "pairs.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -765,38 +765,3 @@ void pivbos_surrogate_destroy(pivbos_surrogate* sg)
 }
 
 }  // extern "C"
-
-namespace pivbos {
-
-// The bounded mbarrier wait of the tensor-core kernels on a barrier nothing
-// arrives at: the wait gives up after `polls` polls and reports a device
-// timeout instead of hanging.
-__global__ void wait_timeout_kernel(uint32_t polls, int* __restrict__ status)
-{
-    __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x == 0) umma::mbar_init(&bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0 && !umma::mbar_wait(&bar, 0u, polls))
-        atomicCAS(status, 0, (int)PIVBOS_ERR_DEVICE_TIMEOUT);
-}
-
-}  // namespace pivbos
-
-extern "C" pivbos_status pivbos_selftest_wait_timeout(uint32_t polls, void* stream)
-{
-    pivbos::set_last_error("");
-    if (polls == 0 || polls > (1u << 20)) return serr(PIVBOS_ERR_INVALID_ARG, "polls outside [1, 2^20]");
-    int dev;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return serr(PIVBOS_ERR_CUDA, "cudaGetDevice");
-    }
-    int* sw = nullptr;
-    pivbos_status st = pivbos::device_status_word(dev, &sw);
-    if (st) return st;
-    pivbos::wait_timeout_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(polls, sw);
-    pivbos::count_launches(1);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return serr(PIVBOS_ERR_CUDA, "self-test launch: %s", cudaGetErrorString(e));
-    return PIVBOS_OK;
-}
