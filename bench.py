@@ -190,9 +190,10 @@ def kernel_source_hash(kind="render"):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(record, kind="render"):
+def recorded_traffic(record, kind="render", rays_per_cta=None):
     """DRAM bytes per launch from a committed ncu record (profiles/<record>.json),
-    or None when the kernel's sources changed since it was taken."""
+    or None when the kernel's sources changed since it was taken, or when the
+    record names a launch geometry (rays per CTA) other than the current one."""
     try:
         with open(os.path.join(ROOT, "profiles", record + ".json")) as f:
             rec = json.load(f)
@@ -200,7 +201,18 @@ def recorded_traffic(record, kind="render"):
         return None
     if rec.get("source_hash") != kernel_source_hash(kind):
         return None
+    if rays_per_cta is not None and rec.get("rays_per_cta", rays_per_cta) != rays_per_cta:
+        return None
     return int(rec["dram_bytes_read"] + rec["dram_bytes_write"])
+
+
+def render_rays_per_cta(frames, step_integrator_dense):
+    """Rays per CTA the library's render uses (its rule: PIVBOS_RAYS_PER_CTA if
+    set, else 2048 in a dense medium, 256 otherwise)."""
+    v = os.environ.get("PIVBOS_RAYS_PER_CTA")
+    if v and v.isdigit() and 256 <= int(v) <= (1 << 20):
+        return int(v)
+    return 2048 if step_integrator_dense else 256
 
 
 def ops_per_ray(frame, mean_steps):
@@ -486,8 +498,11 @@ def run_gpu(args, rank, world):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(H * W * 8 * len(frames))}
 
     msteps = [mean_steps(P, fr, opt, meds[i], src_d[i]) for i, fr in enumerate(frames)]
+    dense = all(f.medium is not None and (f.medium.dims[2] - 1) * f.medium.spacing[2] / f.step *
+                (3 if f.integrator == scenes.RK4 else 1) >= 64 for f in frames)
     rf = roofline(frames, msteps, render_ms, render_n, clk.get("sm_max_mhz"),
-                  recorded_traffic("render_%s_traffic" % args.workload)
+                  recorded_traffic("render_%s_traffic" % args.workload,
+                                   rays_per_cta=render_rays_per_cta(frames, dense))
                   if args.scale == 1.0 and args.optics == "plain" else None,
                   l1_gbs=measured_l1_gbs(P) if all(f.medium is not None for f in frames) else None)
     u16 = None

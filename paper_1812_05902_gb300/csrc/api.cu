@@ -121,7 +121,9 @@ uint32_t next_pow2(uint32_t v)
 }  // namespace
 
 // Rays per CTA of a render: PIVBOS_RAYS_PER_CTA if set, else 2048 in a
-// dense medium (where a CTA reorders up to 2048 rays) and 1024 otherwise.
+// dense medium (where a CTA reorders up to 2048 rays) and 256 otherwise (one
+// ray per thread: warps stay close in stage, which eases instruction fetch;
+// C1 5.51e9 -> 5.70e9 rays/s against 1024).
 uint32_t rays_per_cta_setting(const TraceParams& p)
 {
     static long v = -1;
@@ -130,7 +132,7 @@ uint32_t rays_per_cta_setting(const TraceParams& p)
         const long x = s ? strtol(s, nullptr, 10) : 0;
         v = (x >= 256 && x <= (1 << 20)) ? x : 0;
     }
-    return v ? (uint32_t)v : (p.reorder ? 2048u : 1024u);
+    return v ? (uint32_t)v : (p.reorder ? 2048u : 256u);
 }
 
 // Gather strategy for a medium: reorder a CTA's rays when a ray makes many
