@@ -226,3 +226,26 @@ def test_selftest_arguments_without_a_device(P):
     L = P.lib()
     assert L.pivbos_selftest_wait_timeout(0, None) == P.ERR_INVALID_ARG
     assert L.pivbos_selftest_wait_timeout((1 << 20) + 1, None) == P.ERR_INVALID_ARG
+
+
+def _declared_arity():
+    """Parameter count of every function the header declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(pivbos_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header(P):
+    """The ctypes argument lists of the binding have as many parameters as
+    the header's declarations (an ABI drift would misplace arguments)."""
+    arity = _declared_arity()
+    assert len(arity) >= 40
+    L = P.lib()
+    for name, n in arity.items():
+        f = getattr(L, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
