@@ -46,6 +46,12 @@ pivbos_status cuda_fail(cudaError_t e, const char* what)
     } while (0)
 
 // ---- per-device status word ---------------------------------------------
+// A file-scope device array: every device that loads the library holds its
+// own copy, zero at load, so looking the word up never allocates (the render
+// without allocation shares it).  Its host-side name is not a device
+// address: the address is looked up once per device with that device current.
+__device__ __align__(64) int g_status_word[16];
+
 std::mutex g_dev_mu;
 int* g_status[64] = {nullptr};
 
@@ -54,12 +60,10 @@ pivbos_status status_word(int dev, int** out)
     if (dev < 0 || dev >= 64) return fail(PIVBOS_ERR_UNSUPPORTED, "device ordinal %d", dev);
     std::lock_guard<std::mutex> lk(g_dev_mu);
     if (!g_status[dev]) {
-        int* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, 64);
-        if (e != cudaSuccess) return cuda_fail(e, "status word allocation");
-        e = cudaMemset(p, 0, 64);
-        if (e != cudaSuccess) return cuda_fail(e, "status word clear");
-        g_status[dev] = p;
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_status_word);
+        if (e != cudaSuccess) return cuda_fail(e, "status word lookup");
+        g_status[dev] = (int*)p;
     }
     *out = g_status[dev];
     return PIVBOS_OK;
@@ -126,12 +130,12 @@ uint32_t next_pow2(uint32_t v)
 // C1 5.51e9 -> 5.70e9 rays/s against 1024).
 uint32_t rays_per_cta_setting(const TraceParams& p)
 {
-    static long v = -1;
-    if (v < 0) {
+    // read once; a function-local static is initialised thread-safely
+    static const long v = [] {
         const char* s = getenv("PIVBOS_RAYS_PER_CTA");
         const long x = s ? strtol(s, nullptr, 10) : 0;
-        v = (x >= 256 && x <= (1 << 20)) ? x : 0;
-    }
+        return (x >= 256 && x <= (1 << 20)) ? x : 0L;
+    }();
     return v ? (uint32_t)v : (p.reorder ? 2048u : 256u);
 }
 
@@ -277,11 +281,10 @@ void timing_suppress(bool on) { g_timing_suppressed = on; }
 
 int tuning_cell_cache(int dense)
 {
-    static int v = -2;
-    if (v == -2) {
+    static const int v = [] {
         const char* s = getenv("PIVBOS_CELL_CACHE");
-        v = s ? (atoi(s) != 0 ? 1 : 0) : -1;
-    }
+        return s ? (atoi(s) != 0 ? 1 : 0) : -1;
+    }();
     return v >= 0 ? v : dense;
 }
 

@@ -31,7 +31,7 @@ void set_last_error(const char* msg);
 pivbos_status prepare_trace(const pivbos_medium* m, const pivbos_optics* o, const double* sources,
                             int64_t n_sources, int sources_on_device, int32_t rays_per_source, uint64_t seed,
                             uint32_t frame, int integrator, double step, TraceParams* p, int* dev, uint64_t* total);
-// Device status word of device `dev` (allocated on first use).
+// Device status word of device `dev` (a fixed device array; looked up once per device, never allocated).
 pivbos_status device_status_word(int dev, int** out);
 // Record a formatted message for pivbos_last_error() and return st.
 pivbos_status failf(pivbos_status st, const char* fmt, ...);
