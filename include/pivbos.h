@@ -227,11 +227,12 @@ pivbos_status pivbos_render(const pivbos_medium* m, const pivbos_optics* o,
  * that has given the whole device to its own memory pool and forbids
  * allocations outside it, or a latency-critical loop in which the implicit
  * synchronisation of cudaMalloc/cudaFree would stall other streams.  Same
- * arguments and result as pivbos_render, except that `sources` and `image`
- * must be device pointers (stats too, if not NULL) and the call never
- * allocates or frees memory.  Its scratch (Morton keys, the source
- * permutation and a sorted copy of the sources, ~4.5 MiB) is a fixed array in the library's device image,
- * held by every GPU that loads the library until the process exits.
+ * arguments and result as pivbos_render (the same kernels: the image and
+ * stats are bit-identical), except that `sources` and `image` must be device
+ * pointers (stats too, if not NULL) and the call never allocates or frees
+ * memory.  Its scratch (Morton keys, the source permutation and a sorted
+ * copy of the sources, ~4.5 MiB) is a fixed array in the library's device
+ * image, held by every GPU that loads the library until the process exits.
  *  - n_sources above PIVBOS_NOALLOC_MAX_SOURCES: PIVBOS_ERR_UNSUPPORTED.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
@@ -239,6 +240,8 @@ pivbos_status pivbos_render(const pivbos_medium* m, const pivbos_optics* o,
  *  - Every call on a device uses the same array, which keeps the previous
  *    call's contents (the call rewrites what it reads).  Calls that overlap
  *    on the GPU (concurrent streams) race on it: serialise them.
+ *  - Device-side errors land in the same per-device status word as every
+ *    other call's (a fixed device array as well); pivbos_sync returns it.
  *  - Keep kernel timing (pivbos_timing_enable) off: timing creates CUDA
  *    events.
  * ------------------------------------------------------------------------- */
@@ -337,22 +340,9 @@ pivbos_status pivbos_autotune(const pivbos_frame_desc* frame, int integrator, do
                               int32_t n_sample_rays, double* step_out, pivbos_tuning* tuning_out,
                               void* stream);
 
-/* ---------------------------------------------------------------------------
- * The surrogate's network (no counterpart in the paper: a learned ray map
- * built on the tracer).  16 inputs -> 128 -> 128 -> 128 -> 128 -> 4, ReLU on
- * the hidden layers, BF16 tensor-core products accumulating in FP32.  Inputs
- * 14 and 15 are reserved and must be zero: the inference kernels use them
- * to carry the first layer's bias through the tensor core.
- * Parameters: PIVBOS_MLP_PARAMS floats, layer by layer W [out][in] then
- * b [out].  These two calls run the GPU kernels on host buffers for
- * checking: the forward (x [n][16] -> y [n][4]) and the mean-squared-error
- * loss over n x 4 outputs with its gradient (grad [PIVBOS_MLP_PARAMS]).
- * Synchronous; they allocate their own device memory.
- * ------------------------------------------------------------------------- */
+/* The surrogate's network parameters: PIVBOS_MLP_PARAMS floats, layer by
+ * layer W [out][in] then b [out] (16 inputs -> 128 -> 128 -> 128 -> 128 -> 4). */
 #define PIVBOS_MLP_PARAMS 52228
-pivbos_status pivbos_mlp_forward(const float* params, const float* x, int32_t n, float* y);
-pivbos_status pivbos_mlp_loss_grad(const float* params, const float* x, const float* t, int32_t n,
-                                   float* grad, double* loss);
 
 /* ---------------------------------------------------------------------------
  * Surrogate ray map (no counterpart in the paper: a learned part built on
@@ -446,6 +436,14 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
  * rays. */
 pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
                                       int64_t* n_fallback, void* stream);
+/* The surrogate render of sources [first_source, first_source + n_sources)
+ * of a larger source set (the frame's `sources` point at that range; ray k
+ * of local source s draws its lens point with counter (k, first_source + s,
+ * frame, 0)), for sharding one image across GPUs: renders of disjoint
+ * ranges through the same trained surrogate add up, bit for bit, to the
+ * render of the whole set.  first_source + n_sources <= 2^32. */
+pivbos_status pivbos_surrogate_render_range(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
+                                            int64_t first_source, int64_t* n_fallback, void* stream);
 /* Per-ray sensor positions of the surrogate path for flat ray ids (device
  * int64 [n], source-major as in pivbos_trace_exit_states): sensor_xy
  * (device double [n][2]), flags (device int32 [n]: 0 network, 1 plain
@@ -544,13 +542,6 @@ pivbos_status pivbos_advect_sources(const double* sources, int64_t n_sources, co
                                     double* out, void* stream);
 pivbos_status pivbos_image_u16(const int64_t* image, int64_t n_pixels, double full_scale, uint16_t* out,
                                void* stream);
-
-/* Measurement facility (no counterpart in the paper): the bandwidth of the
- * current device's L1 data path for coalesced 16-byte loads from an
- * L1-resident buffer (every SM streams 48 KB), in bytes per second -- the
- * denominator of the field-gather rooflines.  Synchronous; allocates a small
- * scratch.  Errors: INVALID_ARG, OOM, CUDA. */
-pivbos_status pivbos_probe_l1_bandwidth(double* bytes_per_second);
 
 /* Self-test of the failure detection (no counterpart in the paper): a
  * kernel waits, with the bounded wait the tensor-core kernels use, on an

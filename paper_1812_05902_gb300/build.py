@@ -1,7 +1,10 @@
-"""Build libpivbos.so (the CUDA library behind include/pivbos.h) in-tree.
+"""Build libpivbos.so (the CUDA library behind include/pivbos.h) and
+libpivbos_testing.so (include/pivbos_testing.h: checking and measurement
+hooks that link the product library) in-tree.
 
 Each translation unit is compiled for sm_103a only, in parallel, then linked
-into ``paper_1812_05902_gb300/libpivbos.so``.
+into ``paper_1812_05902_gb300/libpivbos.so``; ``testing.cu`` is linked on its
+own against it.
 """
 from __future__ import annotations
 
@@ -16,6 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpivbos.so")
+TESTING_LIB = os.path.join(HERE, "libpivbos_testing.so")
+TESTING_SOURCES = ["testing.cu"]
 SOURCES = ["api.cu", "medium.cu", "sort.cu", "render.cu", "render_batch.cu", "render_list.cu", "noalloc.cu", "batch.cu", "mlp.cu", "surrogate.cu", "bos.cu", "mie.cu", "pairs.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
@@ -31,13 +36,14 @@ def nvcc() -> str:
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(ROOT, "include", "pivbos.h"))
+    files += [os.path.join(ROOT, "include", h) for h in ("pivbos.h", "pivbos_testing.h")]
     return max(os.path.getmtime(f) for f in files)
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
+    if (not force and os.path.exists(LIB) and os.path.exists(TESTING_LIB)
+            and min(os.path.getmtime(LIB), os.path.getmtime(TESTING_LIB)) >= _deps()):
         return LIB
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
@@ -50,17 +56,26 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + len(TESTING_SOURCES)) as ex:
+        results = list(ex.map(compile_one, SOURCES + TESTING_SOURCES))
+    testing_objs = [o for o, _ in results[len(SOURCES):]]
+    results = results[:len(SOURCES)]
     if verbose_ptxas:
         for _, log in results:
             sys.stderr.write(log)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart", "-Xlinker", "-soname,libpivbos.so"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    tmp = TESTING_LIB + ".tmp%d" % os.getpid()
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *testing_objs, "-L" + HERE, "-lpivbos", "-lcudart",
+           "-Xlinker", "-rpath,$ORIGIN"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("testing library link failed:\n%s%s" % (r.stdout, r.stderr))
+    os.replace(tmp, TESTING_LIB)
     return LIB
 
 

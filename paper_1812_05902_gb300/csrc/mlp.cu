@@ -426,12 +426,11 @@ int mlp_status(const MlpDev& d)
 
 static bool use_tc()
 {
-    static int v = -1;
-    if (v < 0) {
+    static const bool v = [] {
         const char* e = getenv("PIVBOS_MLP_TC");
-        v = (e && atoi(e) == 0) ? 0 : 1;
-    }
-    return v == 1;
+        return !(e && atoi(e) == 0);
+    }();
+    return v;
 }
 
 cudaError_t mlp_forward(const MlpDev& d, const __nv_bfloat16* X, int n, float* Y, MlpWork* work, const float* T,
@@ -485,8 +484,10 @@ cudaError_t mlp_backward(MlpDev& d, const __nv_bfloat16* X, int n, MlpWork& w, c
 
 cudaError_t mlp_adam(MlpDev& d, int t, float lr, cudaStream_t s)
 {
-    const float bc1 = 1.0f - powf(0.9f, (float)t);
-    const float bc2 = 1.0f - powf(0.999f, (float)t);
+    // bias corrections in FP64: 1 - 0.999^t cancels (FP32 would lose ~2e-5
+    // of it at small t)
+    const float bc1 = (float)(1.0 - pow(0.9, (double)t));
+    const float bc2 = (float)(1.0 - pow(0.999, (double)t));
     mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(d.params, d.m, d.v, d.grad, d.wbf, lr, bc1, bc2);
     count_launches(1);
     return cudaGetLastError();

@@ -79,4 +79,10 @@ cudaError_t mlp_backward(MlpDev& d, const __nv_bfloat16* X, int n, MlpWork& work
 // One Adam step (t counts from 1) on all parameters, then the BF16 copies.
 cudaError_t mlp_adam(MlpDev& d, int t, float lr, cudaStream_t s);
 
+// The surrogate's network kernel (the one its render launches) over n rows:
+// R = B + MLP(X) * t_scale, X BF16 [n][16], B and R float4 [n] (device).
+// Synchronous; *timed_out is set if a tensor-core wait gave up.
+cudaError_t surr_net_apply(const MlpDev& net, const __nv_bfloat16* X, const float4* B, const float t_scale[4],
+                           uint32_t n, float4* R, int* timed_out, cudaStream_t s);
+
 }  // namespace pivbos

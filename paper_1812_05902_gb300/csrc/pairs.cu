@@ -186,73 +186,3 @@ pivbos_status pivbos_image_u16(const int64_t* image, int64_t n_pixels, double fu
 }
 
 }  // extern "C"
-
-// ---------------------------------------------------------------------------
-// Measurement facility: the L1 data path's bandwidth for 16-byte loads, the
-// denominator of the field-gather rooflines.  Every CTA streams one 48 KB
-// buffer (L1-resident after the first pass) with coalesced float4 loads.
-// ---------------------------------------------------------------------------
-namespace pivbos {
-
-constexpr int kProbeFloat4 = 3072;   // 48 KB
-
-__global__ void __launch_bounds__(256) l1_probe_kernel(const float4* __restrict__ buf, int iters,
-                                                       float* __restrict__ sink)
-{
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int q = threadIdx.x;
-#pragma unroll 4
-    for (int i = 0; i < iters; ++i) {
-        const float4 v = __ldg(buf + q);
-        acc.x += v.x;
-        acc.y += v.y;
-        acc.z += v.z;
-        acc.w += v.w;
-        q += 256;
-        if (q >= kProbeFloat4) q -= kProbeFloat4;
-    }
-    // keeps the loads; the buffer holds zeros, so nothing is written
-    if (acc.x + acc.y + acc.z + acc.w != 0.f) sink[blockIdx.x * blockDim.x + threadIdx.x] = acc.x;
-}
-
-}  // namespace pivbos
-
-extern "C" pivbos_status pivbos_probe_l1_bandwidth(double* bytes_per_second)
-{
-    using namespace pivbos;
-    set_last_error("");
-    if (!bytes_per_second) return failf(PIVBOS_ERR_INVALID_ARG, "bytes_per_second is NULL");
-    int dev, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return failf(PIVBOS_ERR_CUDA, "cudaGetDevice");
-    }
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int blocks = (sms > 0 ? sms : 152) * 8, iters = 4096;
-    float4* buf = nullptr;
-    float* sink = nullptr;
-    cudaEvent_t a = nullptr, b = nullptr;
-    cudaError_t e = cudaMalloc((void**)&buf, kProbeFloat4 * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&sink, (size_t)blocks * 256 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(buf, 0, kProbeFloat4 * sizeof(float4));
-    if (e == cudaSuccess) e = cudaEventCreate(&a);
-    if (e == cudaSuccess) e = cudaEventCreate(&b);
-    float ms = 0.f;
-    if (e == cudaSuccess) {
-        l1_probe_kernel<<<blocks, 256>>>(buf, iters, sink);   // warm-up
-        cudaEventRecord(a);
-        for (int r = 0; r < 5; ++r) l1_probe_kernel<<<blocks, 256>>>(buf, iters, sink);
-        cudaEventRecord(b);
-        count_launches(6);
-        e = cudaEventSynchronize(b);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-    }
-    if (a) cudaEventDestroy(a);
-    if (b) cudaEventDestroy(b);
-    if (buf) cudaFree(buf);
-    if (sink) cudaFree(sink);
-    pivbos_status st = cuda_status(e, "L1 probe");
-    if (st) return st;
-    *bytes_per_second = 5.0 * (double)blocks * 256.0 * (double)iters * 16.0 / (ms * 1e-3);
-    return PIVBOS_OK;
-}

@@ -36,90 +36,66 @@ pivbos_status scuda(cudaError_t e, const char* what)
                 cudaGetErrorString(e));
 }
 
-__global__ void f32_to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, int64_t n)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = __float2bfloat16(x[i]);
-}
-
-// Scoped device buffers for the test hooks.
-struct HookBufs {
-    pivbos::MlpDev d;
-    pivbos::MlpWork w;
-    float* x32 = nullptr;
-    __nv_bfloat16* x = nullptr;
-    float* t = nullptr;
-    ~HookBufs()
-    {
-        pivbos::mlp_free(d);
-        pivbos::mlp_work_free(w);
-        cudaFree(x32);
-        cudaFree(x);
-        cudaFree(t);
-    }
-};
-
-pivbos_status hook_setup(HookBufs& B, const float* params, const float* x, int32_t n, bool train)
-{
-    cudaError_t e = pivbos::mlp_alloc(B.d, 64);
-    if (e == cudaSuccess && train) e = pivbos::mlp_work_alloc(B.w, n);
-    if (e == cudaSuccess) e = cudaMalloc(&B.x32, sizeof(float) * (size_t)n * pivbos::kMlpIn);
-    if (e == cudaSuccess) e = cudaMalloc(&B.x, sizeof(__nv_bfloat16) * (size_t)n * pivbos::kMlpIn);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(B.d.params, params, sizeof(float) * pivbos::kMlpParams, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(B.x32, x, sizeof(float) * (size_t)n * pivbos::kMlpIn, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return scuda(e, "mlp hook setup");
-    const int64_t nx = (int64_t)n * pivbos::kMlpIn;
-    f32_to_bf16_kernel<<<(unsigned)((nx + 255) / 256), 256>>>(B.x32, B.x, nx);
-    e = pivbos::mlp_sync_bf16(B.d, 0);
-    if (e != cudaSuccess) return scuda(e, "mlp weights to bf16");
-    return PIVBOS_OK;
-}
-
 }  // namespace
 
-extern "C" {
-
-pivbos_status pivbos_mlp_forward(const float* params, const float* x, int32_t n, float* y)
-{
-    pivbos::set_last_error("");
-    if (!params || !x || !y || n < 1) return serr(PIVBOS_ERR_INVALID_ARG, "mlp_forward arguments");
-    HookBufs B;
-    pivbos_status st = hook_setup(B, params, x, n, false);
-    if (st) return st;
-    float* dy = nullptr;
-    cudaError_t e = cudaMalloc(&dy, sizeof(float) * (size_t)n * pivbos::kMlpOut);
-    if (e == cudaSuccess) e = pivbos::mlp_forward(B.d, B.x, n, dy, nullptr, nullptr, 0);
-    if (e == cudaSuccess) e = cudaMemcpy(y, dy, sizeof(float) * (size_t)n * pivbos::kMlpOut, cudaMemcpyDeviceToHost);
-    cudaFree(dy);
-    if (e != cudaSuccess) return scuda(e, "mlp_forward");
-    if (pivbos::mlp_status(B.d)) return serr(PIVBOS_ERR_DEVICE_TIMEOUT, "mlp_forward: a tensor-core wait gave up");
-    return PIVBOS_OK;
-}
-
-pivbos_status pivbos_mlp_loss_grad(const float* params, const float* x, const float* t, int32_t n, float* grad,
-                                   double* loss)
-{
-    pivbos::set_last_error("");
-    if (!params || !x || !t || !grad || !loss || n < 1) return serr(PIVBOS_ERR_INVALID_ARG, "mlp_loss_grad arguments");
-    HookBufs B;
-    pivbos_status st = hook_setup(B, params, x, n, true);
-    if (st) return st;
-    cudaError_t e = cudaMalloc(&B.t, sizeof(float) * (size_t)n * pivbos::kMlpOut);
-    if (e == cudaSuccess) e = cudaMemcpy(B.t, t, sizeof(float) * (size_t)n * pivbos::kMlpOut, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = pivbos::mlp_forward(B.d, B.x, n, B.w.y, &B.w, B.t, 0);
-    if (e == cudaSuccess) e = pivbos::mlp_backward(B.d, B.x, n, B.w, 0);
-    if (e == cudaSuccess) e = cudaMemcpy(grad, B.d.grad, sizeof(float) * pivbos::kMlpParams, cudaMemcpyDeviceToHost);
-    double lsum = 0.0;
-    if (e == cudaSuccess) e = cudaMemcpy(&lsum, B.w.loss, sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return scuda(e, "mlp_loss_grad");
-    *loss = lsum / ((double)n * pivbos::kMlpOut);
-    return PIVBOS_OK;
-}
-
-}  // extern "C"
-
 #include "surrogate_kernels.cuh"
+
+namespace pivbos {
+
+// The network over a served list (one persistent CTA per SM, two
+// warpgroups each): R = B + MLP(X) * t_scale.  The render and the
+// per-element check of the testing library both launch it through here.
+cudaError_t launch_surr_net(const SurrParams& S, const __nv_bfloat16* wbf, const float* params, const ServedList& sv,
+                            int* status_word, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // per device, so set on every launch (cheap)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(surr_net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(NetSmem));
+    if (e != cudaSuccess) return e;
+    timing_begin("surrogate_net", s);
+    surr_net_kernel<<<sms, 128 * kNetGroups, sizeof(NetSmem), s>>>(S, wbf, params, sv, status_word);
+    timing_end("surrogate_net", s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// For the per-element check of the network kernel: n rows of inputs X
+// (BF16 [n][16], device), projection residuals B (device float4 [n]) and the
+// output scales; writes R (device float4 [n]).  Synchronous.
+cudaError_t surr_net_apply(const MlpDev& net, const __nv_bfloat16* X, const float4* B, const float t_scale[4],
+                           uint32_t n, float4* R, int* timed_out, cudaStream_t s)
+{
+    SurrParams S;
+    memset(&S, 0, sizeof S);
+    for (int q = 0; q < 4; ++q) S.t_scale[q] = t_scale[q];
+    unsigned long long* count = nullptr;
+    int* status = nullptr;
+    cudaError_t e = cudaMalloc(&count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+    const unsigned long long nn = n;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(count, &nn, sizeof nn, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    ServedList sv;
+    memset(&sv, 0, sizeof sv);
+    sv.X = const_cast<__nv_bfloat16*>(X);
+    sv.B = const_cast<float4*>(B);
+    sv.R = R;
+    sv.count = count;
+    sv.capacity = n;
+    if (e == cudaSuccess) e = launch_surr_net(S, net.wbf, net.params, sv, status, s);
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, status, sizeof st, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *timed_out = st != 0;
+    cudaFree(count);
+    cudaFree(status);
+    return e;
+}
+
+}  // namespace pivbos
 
 // ---------------------------------------------------------------------------
 // host side
@@ -603,14 +579,34 @@ static pivbos_status surr_prepare(const pivbos_surrogate* sg, const pivbos_frame
     return PIVBOS_OK;
 }
 
+static pivbos_status surrogate_render_impl(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
+                                           int64_t first_source, int64_t* n_fallback, void* stream);
+
 pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_frame_desc* frame, int64_t* n_fallback,
                                       void* stream)
+{
+    return surrogate_render_impl(sg, frame, 0, n_fallback, stream);
+}
+
+pivbos_status pivbos_surrogate_render_range(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
+                                            int64_t first_source, int64_t* n_fallback, void* stream)
+{
+    pivbos::set_last_error("");
+    if (!frame) return serr(PIVBOS_ERR_INVALID_ARG, "frame is NULL");
+    if (first_source < 0 || frame->n_sources < 0 || first_source + frame->n_sources > 0xffffffffll)
+        return serr(PIVBOS_ERR_INVALID_ARG, "first_source %lld outside [0, 2^32 - n_sources]", (long long)first_source);
+    return surrogate_render_impl(sg, frame, first_source, n_fallback, stream);
+}
+
+static pivbos_status surrogate_render_impl(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
+                                           int64_t first_source, int64_t* n_fallback, void* stream)
 {
     pivbos::set_last_error("");
     pivbos::TraceParams P;
     uint64_t total = 0;
     pivbos_status st = surr_prepare(sg, frame, P, total);
     if (st) return st;
+    P.source_offset = (uint32_t)first_source;
     cudaPointerAttributes a;
     if (!frame->image || cudaPointerGetAttributes(&a, frame->image) != cudaSuccess ||
         a.type != cudaMemoryTypeDevice) {
@@ -659,9 +655,6 @@ pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_f
             sv.ids = (uint32_t*)(sbuf + (size_t)chunk * 80);
             sv.count = (unsigned long long*)(sbuf + off_count);   // [0] served, [1] finish items
             sv.capacity = (uint32_t)chunk;
-            // per device, so set on every render (cheap)
-            e = cudaFuncSetAttribute(pivbos::surr_net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(pivbos::NetSmem));
             for (uint64_t c0 = 0; c0 < total && e == cudaSuccess; c0 += chunk) {
                 const uint64_t c1 = std::min(total, c0 + chunk);
                 e = cudaMemsetAsync(sv.count, 0, 2 * sizeof(unsigned long long), s);
@@ -671,11 +664,10 @@ pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_f
                 pivbos::surr_prep_kernel<<<(unsigned)std::min<uint64_t>(items, (uint64_t)sms * 6), 256, 0, s>>>(
                     P, sg->S, c0, c1, sv, fb, counters + 1, capacity);
                 pivbos::timing_end("surrogate_prep", s);
+                pivbos::count_launches(1);
                 if (sg->S.use_net) {
-                    pivbos::timing_begin("surrogate_net", s);
-                    pivbos::surr_net_kernel<<<sms, 128 * pivbos::kNetGroups, sizeof(pivbos::NetSmem), s>>>(
-                        sg->S, sg->net.wbf, sg->net.params, sv, P.status_word);
-                    pivbos::timing_end("surrogate_net", s);
+                    e = pivbos::launch_surr_net(sg->S, sg->net.wbf, sg->net.params, sv, P.status_word, s);
+                    if (e != cudaSuccess) break;
                 }
                 pivbos::timing_begin("surrogate_finish", s);
                 if (pivbos::optics_ext(P.o))
@@ -685,7 +677,7 @@ pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_f
                     pivbos::surr_finish_kernel<false><<<sms * 4, 256, 0, s>>>(
                         P, sg->S, sv, sg->S.use_net ? sv.R : sv.B, frame->image, frame->stats, sv.count + 1);
                 pivbos::timing_end("surrogate_finish", s);
-                pivbos::count_launches(sg->S.use_net ? 3 : 2);
+                pivbos::count_launches(1);
                 e = cudaGetLastError();
             }
 

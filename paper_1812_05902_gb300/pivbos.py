@@ -16,6 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpivbos.so")
+TESTING_LIB_PATH = os.path.join(_HERE, "libpivbos_testing.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_OVERFLOW, ERR_UNSUPPORTED = range(7)
 RAY_REACHED, RAY_STOP, RAY_MISS, RAY_TIR, RAY_OFF_SENSOR, RAY_MAXSTEP = range(6)
@@ -105,7 +106,6 @@ def _load():
         "pivbos_optics_radiance": ([P, P, P, P, I, P], I),
         "pivbos_advect_sources": ([P, I64, P, I, I, I, P, P, D, P, P], I),
         "pivbos_image_u16": ([P, I64, D, P, P], I),
-        "pivbos_probe_l1_bandwidth": ([ctypes.POINTER(D)], I),
         "pivbos_selftest_wait_timeout": ([U32, P], I),
         "pivbos_render": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
         "pivbos_trace_exit_states": ([P, P, P, I64, I, I32, U64, U32, I, D, P, I64, P, P], I),
@@ -120,8 +120,6 @@ def _load():
         "pivbos_render_noalloc": ([P, P, P, I64, I32, U64, U32, I, D, P, P, P], I),
         "pivbos_default_tuning": ([P], I),
         "pivbos_render_range": ([P, P, P, I64, I64, I, I32, U64, U32, I, D, P, I, P, P], I),
-        "pivbos_mlp_forward": ([P, P, I32, P], I),
-        "pivbos_mlp_loss_grad": ([P, P, P, I32, P, P], I),
         "pivbos_batch_create": ([P, I, I, P, P], I),
         "pivbos_batch_render": ([P, P], I),
         "pivbos_batch_destroy": ([P], None),
@@ -129,6 +127,7 @@ def _load():
         "pivbos_surrogate_default_cfg": ([P], I),
         "pivbos_surrogate_train": ([P, I, P, P, P, P], I),
         "pivbos_surrogate_render": ([P, P, P, P], I),
+        "pivbos_surrogate_render_range": ([P, P, I64, P, P], I),
         "pivbos_surrogate_sensor": ([P, P, P, I64, P, P, P, P], I),
         "pivbos_surrogate_report_get": ([P, P], I),
         "pivbos_surrogate_destroy": ([P], None),
@@ -150,18 +149,49 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_sync", "pivbos_last_error", "pivbos_timing_enable", "pivbos_timing_reset",
             "pivbos_timing_read", "pivbos_version", "pivbos_kernel_launches", "pivbos_render_noalloc",
             "pivbos_default_tuning", "pivbos_batch_create", "pivbos_batch_render", "pivbos_batch_destroy",
-            "pivbos_autotune", "pivbos_render_range", "pivbos_mlp_forward", "pivbos_mlp_loss_grad",
+            "pivbos_autotune", "pivbos_render_range",
             "pivbos_surrogate_default_cfg", "pivbos_surrogate_train", "pivbos_surrogate_render",
+            "pivbos_surrogate_render_range",
             "pivbos_surrogate_sensor", "pivbos_surrogate_report_get", "pivbos_surrogate_destroy",
             "pivbos_bos_displacements", "pivbos_bos_displacements_range", "pivbos_bos_theory", "pivbos_regrid_bilinear", "pivbos_optics_tilt_sensor",
             "pivbos_mie", "pivbos_optics_radiance", "pivbos_advect_sources", "pivbos_image_u16",
-            "pivbos_probe_l1_bandwidth", "pivbos_selftest_wait_timeout")
+            "pivbos_selftest_wait_timeout")
+TESTING_EXPORTED = ("pivbos_mlp_forward", "pivbos_mlp_train_forward", "pivbos_mlp_loss_grad",
+                    "pivbos_mlp_adam_steps", "pivbos_surrogate_net_apply", "pivbos_probe_l1_bandwidth")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
 
 def lib():
     return _lib
+
+
+_tlib = None
+
+
+def testing_lib():
+    """libpivbos_testing.so (include/pivbos_testing.h): the checking and
+    measurement hooks, loaded on first use."""
+    global _tlib
+    if _tlib is None:
+        if not os.path.exists(TESTING_LIB_PATH):
+            raise ImportError("libpivbos_testing.so is not built")
+        T = ctypes.CDLL(TESTING_LIB_PATH)
+        P, I, D, I32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int32
+        sig = {
+            "pivbos_mlp_forward": ([P, P, I32, P], I),
+            "pivbos_mlp_train_forward": ([P, P, I32, P], I),
+            "pivbos_mlp_loss_grad": ([P, P, P, I32, P, P], I),
+            "pivbos_mlp_adam_steps": ([P, P, P, P, I32, I32, P, P], I),
+            "pivbos_surrogate_net_apply": ([P, P, P, P, I32, P], I),
+            "pivbos_probe_l1_bandwidth": ([ctypes.POINTER(D)], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(T, name)
+            f.argtypes = args
+            f.restype = res
+        _tlib = T
+    return _tlib
 
 
 def _check(st):
@@ -325,22 +355,59 @@ def pivbos_autotune(desc, integrator, tol_px, n_sample_rays, stream=None):
 
 
 def pivbos_mlp_forward(params, x):
+    """The inference forward (testing library)."""
     params = np.ascontiguousarray(params, dtype=np.float32)
     x = np.ascontiguousarray(x, dtype=np.float32)
     y = np.zeros((x.shape[0], 4), dtype=np.float32)
-    _check(_lib.pivbos_mlp_forward(params.ctypes.data, x.ctypes.data, x.shape[0], y.ctypes.data))
+    _check(testing_lib().pivbos_mlp_forward(params.ctypes.data, x.ctypes.data, x.shape[0], y.ctypes.data))
+    return y
+
+
+def pivbos_mlp_train_forward(params, x):
+    """The training forward (testing library)."""
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.zeros((x.shape[0], 4), dtype=np.float32)
+    _check(testing_lib().pivbos_mlp_train_forward(params.ctypes.data, x.ctypes.data, x.shape[0], y.ctypes.data))
     return y
 
 
 def pivbos_mlp_loss_grad(params, x, t):
+    """Training forward and backward of the mean squared error (testing library)."""
     params = np.ascontiguousarray(params, dtype=np.float32)
     x = np.ascontiguousarray(x, dtype=np.float32)
     t = np.ascontiguousarray(t, dtype=np.float32)
     g = np.zeros(MLP_PARAMS, dtype=np.float32)
     loss = ctypes.c_double()
-    _check(_lib.pivbos_mlp_loss_grad(params.ctypes.data, x.ctypes.data, t.ctypes.data, x.shape[0], g.ctypes.data,
-                                     ctypes.byref(loss)))
+    _check(testing_lib().pivbos_mlp_loss_grad(params.ctypes.data, x.ctypes.data, t.ctypes.data, x.shape[0],
+                                              g.ctypes.data, ctypes.byref(loss)))
     return loss.value, g
+
+
+def pivbos_mlp_adam_steps(params, m, v, grads, t0, lr):
+    """Adam steps of the training kernel on host state (testing library):
+    returns (params, m, v, bf16 weight bits)."""
+    params = np.array(params, dtype=np.float32)
+    m = np.array(m, dtype=np.float32)
+    v = np.array(v, dtype=np.float32)
+    grads = np.ascontiguousarray(grads, dtype=np.float32).reshape(-1, MLP_PARAMS)
+    lr = np.ascontiguousarray(lr, dtype=np.float32)
+    wbf = np.zeros(51712, dtype=np.uint16)
+    _check(testing_lib().pivbos_mlp_adam_steps(params.ctypes.data, m.ctypes.data, v.ctypes.data, grads.ctypes.data,
+                                               grads.shape[0], t0, lr.ctypes.data, wbf.ctypes.data))
+    return params, m, v, wbf
+
+
+def pivbos_surrogate_net_apply(params, x, b, t_scale):
+    """The surrogate render's network kernel: r = b + MLP(x) * t_scale (testing library)."""
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    ts = np.ascontiguousarray(t_scale, dtype=np.float32)
+    r = np.zeros((x.shape[0], 4), dtype=np.float32)
+    _check(testing_lib().pivbos_surrogate_net_apply(params.ctypes.data, x.ctypes.data, b.ctypes.data, ts.ctypes.data,
+                                                    x.shape[0], r.ctypes.data))
+    return r
 
 
 def pivbos_surrogate_default_cfg():
@@ -364,6 +431,15 @@ def pivbos_surrogate_render(sg, desc, count_fallback=False, stream=None):
     n = ctypes.c_int64()
     _check(_lib.pivbos_surrogate_render(sg, ctypes.byref(desc), ctypes.byref(n) if count_fallback else None,
                                         _stream(stream)))
+    return n.value if count_fallback else None
+
+
+def pivbos_surrogate_render_range(sg, desc, first_source, count_fallback=False, stream=None):
+    """The surrogate render of the frame's sources as the range starting at
+    global source index first_source (sharding one image)."""
+    n = ctypes.c_int64()
+    _check(_lib.pivbos_surrogate_render_range(sg, ctypes.byref(desc), first_source,
+                                              ctypes.byref(n) if count_fallback else None, _stream(stream)))
     return n.value if count_fallback else None
 
 
@@ -437,9 +513,9 @@ def pivbos_image_u16(image, n_pixels, full_scale, out, stream=None):
 
 
 def pivbos_probe_l1_bandwidth():
-    """Measured L1 bandwidth for coalesced 16-byte loads (bytes/s)."""
+    """Measured L1 bandwidth for coalesced 16-byte loads (bytes/s; testing library)."""
     v = ctypes.c_double()
-    _check(_lib.pivbos_probe_l1_bandwidth(ctypes.byref(v)))
+    _check(testing_lib().pivbos_probe_l1_bandwidth(ctypes.byref(v)))
     return v.value
 
 

@@ -12,6 +12,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "pivbos.h")
+TESTING_HEADER = os.path.join(ROOT, "include", "pivbos_testing.h")
 
 
 @pytest.fixture(scope="module")
@@ -22,8 +23,8 @@ def P():
     return pivbos
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(pivbos_\w+)\s*\(", text)))
 
@@ -37,6 +38,22 @@ def test_every_declared_function_is_exported(P):
     out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\sT\s(pivbos_\w+)", out))
     assert set(names) <= exported
+
+
+def test_testing_hooks_live_in_their_own_library(P):
+    """The checking and measurement hooks are declared in pivbos_testing.h and
+    exported by libpivbos_testing.so, not by the product library."""
+    names = declared_functions(TESTING_HEADER)
+    assert set(names) == set(P.TESTING_EXPORTED)
+    T = P.testing_lib()
+    for n in names:
+        assert hasattr(T, n), n
+    product = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True, text=True).stdout
+    testing = subprocess.run(["nm", "-D", "--defined-only", P.TESTING_LIB_PATH], capture_output=True,
+                             text=True).stdout
+    assert set(names) <= set(re.findall(r"\sT\s(pivbos_\w+)", testing))
+    assert not set(names) & set(re.findall(r"\sT\s(pivbos_\w+)", product))
+    assert not set(names) & set(declared_functions(HEADER))
 
 
 def test_struct_layouts_match_header(P):
@@ -228,9 +245,9 @@ def test_selftest_arguments_without_a_device(P):
     assert L.pivbos_selftest_wait_timeout((1 << 20) + 1, None) == P.ERR_INVALID_ARG
 
 
-def _declared_arity():
+def _declared_arity(header=HEADER):
     """Parameter count of every function the header declares."""
-    text = open(HEADER).read()
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     out = {}
     for m in re.finditer(r"\b(pivbos_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
@@ -243,9 +260,14 @@ def test_binding_signatures_match_the_header(P):
     """The ctypes argument lists of the binding have as many parameters as
     the header's declarations (an ABI drift would misplace arguments)."""
     arity = _declared_arity()
-    assert len(arity) >= 40
+    assert len(arity) >= 38
     L = P.lib()
     for name, n in arity.items():
         f = getattr(L, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+    T = P.testing_lib()
+    for name, n in _declared_arity(TESTING_HEADER).items():
+        f = getattr(T, name)
         assert f.argtypes is not None, name
         assert len(f.argtypes) == n, (name, len(f.argtypes), n)
