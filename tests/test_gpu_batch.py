@@ -1,10 +1,12 @@
 """Batched rendering (one persistent launch over frames of uneven size,
-CUDA-graph replay) against per-frame pivbos_render, and the autotuner."""
+CUDA-graph replay) against the oracle's render of every frame and against
+per-frame pivbos_render, and the autotuner."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1812_05902_gb300 import scenes
-from gpu_helpers import gpu_handles
+from gpu_helpers import compare_images, gpu_handles
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +53,27 @@ def test_batch_matches_single_renders_and_graph_replay():
                 assert torch.equal(im, 2 * r)
         finally:
             P.pivbos_batch_destroy(b)
+
+
+@pytest.mark.parametrize("tuning", [None, (1024, 1, 2, 1), (512, 0, 3, 0)])
+def test_batch_images_against_the_oracle(tuning):
+    """Frames of uneven size (shock, gradient and turbulence fields, grids
+    from 64^3) in one persistent launch: every frame's image and status
+    counts against the oracle's render of that frame."""
+    from paper_1812_05902_gb300 import pivbos as P
+    frames = scenes.c3(scale=0.002, n_frames=5, max_grid=96)
+    hs, src, imgs, stats, descs = _setup(frames)
+    b = P.pivbos_batch_create(descs, scenes.RK4, P.pivbos_tuning(*tuning) if tuning else None)
+    try:
+        P.pivbos_batch_render(b)
+        P.pivbos_sync()
+    finally:
+        P.pivbos_batch_destroy(b)
+    for i, f in enumerate(frames):
+        img_o, st_o = oracle.render_frame(f)
+        st_g = stats[i].cpu().numpy()
+        compare_images(imgs[i].cpu().numpy(), img_o, st_g, st_o, f, label="batch frame %d" % i)
+        assert np.abs(st_g - st_o).sum() <= 2, (st_g, st_o)
 
 
 def test_batch_rejects_host_buffers_and_bad_tuning():

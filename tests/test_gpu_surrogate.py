@@ -111,14 +111,15 @@ def test_surrogate_error_against_plain_tracer_and_oracle(trained):
     # fallback rays are the plain tracer's own result
     fb = flags[both] == 1
     assert np.max(np.abs(d[fb])) < 1e-9
-    # against the oracle on a sample the CPU traces in seconds
-    sub = ids[:4000]
-    o = oracle_states(frame, sub)
-    ok = (status[:4000] == 0) & (o["status"] == 0)
-    do = xy[:4000][ok] - o["sensor_xy"][ok]
+    # against the oracle on 1e5 of the rays (the metric's judge)
+    n_or = 100_000
+    o = oracle_states(frame, ids[:n_or])
+    ok = (status[:n_or] == 0) & (o["status"] == 0)
+    assert ok.sum() > 0.99 * n_or
+    do = xy[:n_or][ok] - o["sensor_xy"][ok]
     rms_o = np.sqrt((do ** 2).sum(1).mean())
     print("rms vs oracle %.5f px over %d rays" % (rms_o, ok.sum()))
-    assert rms_o <= 1.5 * BUDGET_PX    # a 4,000-ray sample of a <= 0.8-budget estimate
+    assert rms_o <= BUDGET_PX
 
 
 def test_surrogate_render_image(trained):
