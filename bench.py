@@ -1,29 +1,38 @@
 """Benchmark: rays/s traced to the sensor on one GB300 (and N by torchrun).
 
-Default workload (config C1): PIV uniform medium n = 1.000277, 10,000
-particles uniform in a 50x50x1 mm sheet, 10,000 rays each, thick biconvex
-lens (R = +-0.1 m, 10 mm, n = 1.5) at f/4 and M = 0.2, the sheet 2 mm before
-and 2 mm behind focus (two images per step), 1024x1024 sensor, 17 um pitch.
+Default workload (config C4, Tomo-PIV scale): 1e5 particles inside a
+100x100x30 mm k^-5/3 turbulence field on a 256^3 grid, 1e4 rays each (1e9
+rays per image), RK4 with 0.2 mm steps, the thick biconvex lens at f/4 and
+M = 0.2 focused on the volume centre, 2048x2048 sensor.  The metric compares
+the plain tracer with the surrogate path (learned ray map + plain fallback)
+at <= 0.01 px RMS sensor error against the oracle, so the line times three
+arms on the same image:
+  * plain       -- Morton sort, the fused trace/optics/deposit kernel,
+                   finalisation;
+  * surrogate   -- the trained ray map (first-order projection plus the
+                   tcgen05 network's correction) for rays in served bins,
+                   the plain tracer for the rest (the line's value);
+  * projection  -- the same without the network (what the learned part is
+                   measured against).
+A step is one image of an arm.  The medium (Eq. 1 and the node gradients)
+is built once per density field and the surrogate trained once per field:
+both are outside the timed steps and reported with the images per field at
+which the surrogate breaks even.  Inputs are resident on the GPU when the
+timed region starts; L2 is flushed between timed steps.  The e2e figures run
+the same steps with host buffers (sources in, image out).  The line also
+reports the RMS sensor error of both surrogate arms against the plain tracer
+(1e6 rays) and against the oracle (2e5 rays), and carries the C1 (PIV
+uniform medium), Table 1 (Sec. 4 BOS experiment) and 16-bit conversion
+figures as sub-objects.
 
-A step is one pass of the whole path over both images: medium build from
-the density grid (Eq. 1 and the node gradients), Morton ordering of the
-sources, the fused trace/optics/deposit kernel and the fixed-point -> float
-finalisation.  Inputs are resident on the GPU when the timed region starts;
-L2 is flushed between timed steps.  The e2e figure runs the same step through
-the C ABI with host buffers (host density and sources in, host image out).
+With N ranks (torchrun) the image's sources are split into N contiguous
+ranges; every rank renders its range (global ray indices, so the sum is the
+single-GPU image bit for bit) and one NCCL all-reduce sums the int64 images:
+strong scaling of one image.
 
---surrogate (workload C4, Tomo-PIV scale, 10^9 rays per image) trains the
-surrogate ray map on the image (outside the timed region), then times the
-plain render and the surrogate render (projection + network for served
-rays, plain tracer for the rest) of the same image, and measures the
-surrogate path's RMS sensor error against the plain tracer (10^6 sampled
-rays) and the oracle (a few thousand rays).  The default run adds the same
-figures, with fewer steps, under the "surrogate" key of its line.
-
---workload table1 times the simulated BOS experiment of Sec. 4 (Table 1
-geometry): per-dot mean displacements of every ray traced with and without
-the medium, the Eq. 9 theory per dot and the bilinear grid map; the default
-run adds the same figures, with fewer steps, under the "table1" key.
+--workload c0/c1/c2 time the plain tracer alone on that config, c3 the
+64-frame batch, table1 the Sec. 4 experiment; --surrogate --workload c2 the
+surrogate on the C2 BOS field.
 
 --impl reference times the CPU oracle (the paper's method written plainly in
 FP64 C) on a bounded sample of the same workload on the host cores.
@@ -190,10 +199,14 @@ def kernel_source_hash(kind="render"):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(record, kind="render", rays_per_cta=None):
+def recorded_traffic(record, kind="render", rays_per_cta=None, scale_to_rays=None):
     """DRAM bytes per launch from a committed ncu record (profiles/<record>.json),
     or None when the kernel's sources changed since it was taken, or when the
-    record names a launch geometry (rays per CTA) other than the current one."""
+    record names a launch geometry (rays per CTA) other than the current one.
+    A record taken on a smaller launch (its rays_per_launch) is scaled to
+    scale_to_rays rays in proportion (the field and image parts of the
+    traffic do not grow with the rays, so the scaled figure is an upper
+    bound)."""
     try:
         with open(os.path.join(ROOT, "profiles", record + ".json")) as f:
             rec = json.load(f)
@@ -203,7 +216,10 @@ def recorded_traffic(record, kind="render", rays_per_cta=None):
         return None
     if rays_per_cta is not None and rec.get("rays_per_cta", rays_per_cta) != rays_per_cta:
         return None
-    return int(rec["dram_bytes_read"] + rec["dram_bytes_write"])
+    b = float(rec["dram_bytes_read"] + rec["dram_bytes_write"])
+    if scale_to_rays and rec.get("rays_per_launch"):
+        b *= scale_to_rays / float(rec["rays_per_launch"])
+    return int(b)
 
 
 def render_rays_per_cta(frames, step_integrator_dense):
@@ -297,12 +313,14 @@ def measured_l1_gbs(P):
     return _L1_PEAK["v"]
 
 
-def roofline(frames, mean_steps, render_ms, render_launches, sm_max_mhz, traffic=None, l1_gbs=None):
+def roofline(frames, mean_steps, render_ms, render_launches, sm_max_mhz, traffic=None, l1_gbs=None, ray_frac=1.0):
+    """Issue and gather rooflines of a render launch (ray_frac: the share of
+    a frame's rays one launch traces, for sharded images)."""
     if render_launches == 0:
         return None
     t = render_ms / render_launches * 1e-3
-    rays = sum(f.n_rays for f in frames) / len(frames)
-    ops = sum(ops_per_ray(f, ms) * f.n_rays for f, ms in zip(frames, mean_steps)) / len(frames)
+    rays = ray_frac * sum(f.n_rays for f in frames) / len(frames)
+    ops = ray_frac * sum(ops_per_ray(f, ms) * f.n_rays for f, ms in zip(frames, mean_steps)) / len(frames)
     achieved = ops / t / 1e12
     clk = (sm_max_mhz or 2070.0) * 1e6
     peak = N_SM * ISSUE_LANES_PER_SM * clk / 1e12
@@ -313,8 +331,8 @@ def roofline(frames, mean_steps, render_ms, render_launches, sm_max_mhz, traffic
            "ops_per_ray": round(ops / rays, 1), "launch_ms": round(t * 1e3, 4), "rays_per_launch": int(rays)}
     if all(f.medium is not None for f in frames):
         # the same launch against the L1 data path, for the field gathers
-        gbytes = sum(GATHER_BYTES_PER_EVAL * EVALS_PER_STEP[f.integrator] * ms * f.n_rays
-                     for f, ms in zip(frames, mean_steps)) / len(frames)
+        gbytes = ray_frac * sum(GATHER_BYTES_PER_EVAL * EVALS_PER_STEP[f.integrator] * ms * f.n_rays
+                                for f, ms in zip(frames, mean_steps)) / len(frames)
         gpeak = N_SM * L1_BYTES_PER_CLK_PER_SM * clk / 1e9
         out["gather"] = {"bound": "l1", "achieved": round(gbytes / t / 1e9, 1), "peak": round(gpeak, 1),
                          "unit": "GB/s", "frac": round(gbytes / t / 1e9 / gpeak, 4),
@@ -365,45 +383,137 @@ def oracle_sample(frames, seconds_target=12.0, max_rays=None):
     return done / t_total, threads, done, t_total
 
 
+def c4_subset(fr, n_sources=10000, rays=100):
+    """The fixed subset of an image the oracle baselines use: rays 0..rays-1
+    of its first n_sources sources (the same Philox counters as in the full
+    image, whatever its rays per source)."""
+    import copy
+    sub = copy.copy(fr)
+    sub.sources = fr.sources[:n_sources]
+    sub.rays_per_source = min(rays, fr.rays_per_source)
+    return sub
+
+
+def oracle_subset_rate(fr, seconds_cap=30.0):
+    """The oracle's rays/s on the fixed 1e6-ray subset of the image (first
+    1e4 sources x 100 rays), all host cores; fewer sources if a first chunk
+    says the whole subset would exceed seconds_cap."""
+    import oracle
+    sub = c4_subset(fr)
+    med = oracle.Medium.from_scene(sub.medium) if sub.medium is not None else None
+    opt = oracle.Optics.from_scene(sub.optics)
+    img = np.zeros((sub.optics.height, sub.optics.width), dtype=np.int64)
+    t0 = time.perf_counter()
+    first = 50000
+    oracle.render(med, opt, sub.sources, sub.rays_per_source, sub.seed, sub.frame_index, sub.integrator, sub.step,
+                  image=img, first_ray=0, ray_count=first)
+    t_first = time.perf_counter() - t0
+    budget = int(max(first, min(sub.n_rays, first * seconds_cap / max(t_first, 1e-9))))
+    done = first
+    if budget > first:
+        oracle.render(med, opt, sub.sources, sub.rays_per_source, sub.seed, sub.frame_index, sub.integrator,
+                      sub.step, image=img, first_ray=first, ray_count=budget - first)
+        done = budget
+    t = time.perf_counter() - t0
+    return {"value": done / t, "unit": "rays/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "rays 0-%d of the first %d sources (%d rays, the fixed image subset), %.1f s of CPU work"
+                      % (sub.rays_per_source - 1, min(len(sub.sources), (done + sub.rays_per_source - 1)
+                                                      // sub.rays_per_source), done, t)}
+
+
+def config_for(args):
+    """The line's config object (both arms print the same one)."""
+    wl = args.workload
+    if wl == "c4" and not args.surrogate:
+        cfg = {"workload": WORKLOAD_NAMES["c4"] + ("" if args.scale == 1.0 else " (scaled by %g)" % args.scale),
+               "name": "c4", "arms": "plain tracer vs surrogate (projection + tcgen05 network, plain fallback) "
+                                     "vs projection alone",
+               "budget_px_rms": 0.01, "rays_per_step": 0, "l2": "flushed between steps (inputs also > L2)"}
+    elif args.surrogate:
+        cfg = {"workload": WORKLOAD_NAMES[wl] + " - surrogate path", "name": wl + "-surrogate",
+               "rays_per_step": 0, "l2": "flushed between steps"}
+    else:
+        cfg = {"workload": WORKLOAD_NAMES[wl] + ("" if args.scale == 1.0 else " (scaled by %g)" % args.scale),
+               "name": wl, "optics": args.optics, "rays_per_step": 0, "l2": "flushed between steps"}
+    frames = _frames(wl, args.scale)
+    cfg["rays_per_step"] = sum(f.n_rays for f in frames) if not (wl == "c4" or args.surrogate) else frames[0].n_rays
+    cfg["parallelism"] = ("single GPU" if args.gpus <= 1 else
+                          ("one image sharded by source ranges + NCCL int64 all-reduce" if wl == "c4"
+                           else "replicas (weak)"))
+    return cfg
+
+
 # ----------------------------------------------------------------------------
 def run_reference(args, rank, world):
+    """The oracle on the host cores, on this workload's config: every step
+    traces a bounded sample of the image's rays (the fixed subset: rays 0..99
+    of the first 1e4 sources, continued cyclically); ms_per_step is the wall
+    time those rays took, value the rays traced per second."""
     if rank != 0:
         return
-    frames = _frames(args.workload)
-    vals = []
+    import oracle
+    frames = _frames(args.workload, args.scale)
+    fr = frames[0]
+    sub = c4_subset(fr) if fr.rays_per_source > 100 else fr
+    med = oracle.Medium.from_scene(sub.medium) if sub.medium is not None else None
+    opt = oracle.Optics.from_scene(sub.optics)
+    img = np.zeros((sub.optics.height, sub.optics.width), dtype=np.int64)
+    # size a step to ~2.5 s of CPU work from a short probe (whole run: a minute or two)
+    t0 = time.perf_counter()
+    oracle.render(med, opt, sub.sources, sub.rays_per_source, sub.seed, sub.frame_index, sub.integrator, sub.step,
+                  image=img, first_ray=0, ray_count=20000)
+    rate0 = 20000 / max(time.perf_counter() - t0, 1e-9)
+    per_step = int(min(sub.n_rays, max(20000, rate0 * min(2.5, 150.0 / max(args.steps + args.warmup, 1)))))
+    pos = 0
+
+    def step():
+        nonlocal pos
+        done = 0
+        while done < per_step:
+            n = min(per_step - done, sub.n_rays - pos)
+            oracle.render(med, opt, sub.sources, sub.rays_per_source, sub.seed, sub.frame_index, sub.integrator,
+                          sub.step, image=img, first_ray=pos, ray_count=n)
+            done += n
+            pos = (pos + n) % sub.n_rays
+        return done
+
     for _ in range(args.warmup):
-        oracle_sample(frames, seconds_target=1.0)
-    sample_s = max(2.0, min(20.0, 150.0 / max(args.steps, 1)))
+        step()
+    traced, secs = 0, 0.0
     for _ in range(args.steps):
-        v, threads, done, t = oracle_sample(frames, seconds_target=sample_s)
-        vals.append(v)
-    value = statistics.median(vals)
+        t0 = time.perf_counter()
+        traced += step()
+        secs += time.perf_counter() - t0
+    value = traced / secs
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(f.n_rays for f in frames) / value,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAMES[args.workload], "name": args.workload},
-        "cpu_baseline": {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle",
-                         "sample": "first %d rays (source order) of image 1 per step, ~%.0f s each" % (done, sample_s)},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "strong" if (args.workload == "c4" and args.gpus > 1) else "weak",
+        "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": config_for(args),
+        "cpu_baseline": {"value": value, "unit": "rays/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": "%d rays per step from the image's fixed subset (rays 0..%d of the first %d "
+                                   "sources), %.2f s per step; the plain method (the oracle has no surrogate)"
+                                   % (per_step, sub.rays_per_source - 1, len(sub.sources), secs / args.steps)},
         "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "rays_per_step_traced": per_step,
     }
     print(json.dumps(out), flush=True)
 
 
-def run_gpu(args, rank, world):
+def measure_plain(args, workload, rank, world, steps, warmup, with_e2e=True, with_cpu=True):
+    """A plain-tracer workload (C0, C1, C2): per step the medium build, the
+    Morton ordering, the render kernel and the finalisation of every image
+    (weak scaling across ranks: every rank renders its own images).  Returns
+    the measurement as a dict."""
     import torch
     import torch.distributed as dist
-
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1812_05902_gb300 import build as libbuild
-    libbuild.build()
     from paper_1812_05902_gb300 import pivbos as P
 
-    frames = _frames(args.workload, args.scale)
+    frames = _frames(workload, args.scale)
     apply_optics_variant(frames, args.optics)
-    # weak scaling: every rank renders its own images (seed offset by rank)
     for fr in frames:
         fr.seed = fr.seed + 1000003 * rank
     opt = P.Optics(frames[0].optics)
@@ -415,7 +525,6 @@ def run_gpu(args, rank, world):
     fimg = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in frames]
     stats = torch.zeros(P.RAY_NSTATUS, dtype=torch.int64, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
 
     def step():
         for i, fr in enumerate(frames):
@@ -425,10 +534,9 @@ def run_gpu(args, rank, world):
                             fr.frame_index, fr.integrator, fr.step, img, stats)
             P.pivbos_image_finalize(img, H * W, fimg[i])
 
-    for _ in range(args.warmup):
-        step()
+    step()
     P.pivbos_sync()
-    # exact-total check of the last warm-up image (outside the timed region)
+    # exact-total check of an image (outside the timed region)
     stats.zero_()
     step()
     P.pivbos_sync()
@@ -436,56 +544,39 @@ def run_gpu(args, rank, world):
     assert int(st.sum()) == sum(fr.n_rays for fr in frames)
 
     clocks = Clocks(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    P.pivbos_timing_reset()
-    P.pivbos_timing_enable(True)
-    launches0 = P.pivbos_kernel_launches()
-    times = []
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        times.append((e0, e1))
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    launches = P.pivbos_kernel_launches() - launches0
-    P.pivbos_timing_enable(False)
-    render_ms, render_n = P.pivbos_timing_read("render")
+    timer = ArmTimer(P, torch, flush, world)
+    ms, launches, kt = timer(step, steps, warmup, ("render", "medium", "sort", "finalize"))
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in times)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     rays_step = sum(fr.n_rays for fr in frames)
-    value = rays_step * args.steps * world / (ms * 1e-3)
+    value = rays_step * steps * world / (ms * 1e-3)
 
-    # e2e: same step through the C ABI with host buffers (pinned)
+    # e2e: the same step through the C ABI with host buffers: host density,
+    # host sources in; the host image out (the render call copies)
     e2e = None
-    if not args.no_e2e:
+    if with_e2e and not args.no_e2e:
         rho_h = [torch.tensor(fr.medium.rho).pin_memory() for fr in frames]
         src_h = [torch.tensor(fr.sources, dtype=torch.float64).pin_memory() for fr in frames]
         img_h = torch.zeros((H, W), dtype=torch.int64).pin_memory()
+        fimg_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
 
         def step_host():
             for i, fr in enumerate(frames):
                 P.pivbos_medium_refill(meds[i].h, rho_h[i])
                 img_h.zero_()
                 P.pivbos_render(meds[i].h, opt.h, src_h[i], len(fr.sources), fr.rays_per_source, fr.seed,
-                                fr.frame_index, fr.integrator, fr.step, img_h, None)
+                                fr.frame_index, fr.integrator, fr.step, img_h, stats)
+                # the same finalisation as the device-timed step
+                img.copy_(img_h, non_blocking=True)
+                P.pivbos_image_finalize(img, H * W, fimg[i])
+                fimg_h.copy_(fimg[i], non_blocking=True)
 
         step_host()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, steps)):
+            flush.fill_(1)
             step_host()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -493,65 +584,384 @@ def run_gpu(args, rank, world):
             t = torch.tensor([dt], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
-        h2d = sum(r.numel() * 4 + s.numel() * 8 + H * W * 8 for r, s in zip(rho_h, src_h))
-        e2e = {"value": rays_step * max(1, args.steps) * world / dt, "unit": "rays/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(H * W * 8 * len(frames))}
+        h2d = sum(r.numel() * 4 + s.numel() * 8 + H * W * 8 * 2 for r, s in zip(rho_h, src_h))
+        e2e = {"value": rays_step * max(1, steps) * world / dt, "unit": "rays/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int((H * W * 8 + H * W * 4) * len(frames)),
+               "note": "wall clock including the L2 flush of every step"}
 
     msteps = [mean_steps(P, fr, opt, meds[i], src_d[i]) for i, fr in enumerate(frames)]
     dense = all(f.medium is not None and (f.medium.dims[2] - 1) * f.medium.spacing[2] / f.step *
                 (3 if f.integrator == scenes.RK4 else 1) >= 64 for f in frames)
-    rf = roofline(frames, msteps, render_ms, render_n, clk.get("sm_max_mhz"),
-                  recorded_traffic("render_%s_traffic" % args.workload,
-                                   rays_per_cta=render_rays_per_cta(frames, dense))
+    rk = kt["render"]
+    rf = roofline(frames, msteps, rk["ms_per_launch"] or 0.0, 1 if rk["ms_per_launch"] else 0,
+                  clk.get("sm_max_mhz"),
+                  recorded_traffic("render_%s_traffic" % workload, rays_per_cta=render_rays_per_cta(frames, dense),
+                                   scale_to_rays=sum(f.n_rays for f in frames) / len(frames))
                   if args.scale == 1.0 and args.optics == "plain" else None,
                   l1_gbs=measured_l1_gbs(P) if all(f.medium is not None for f in frames) else None)
-    u16 = None
-    if world == 1 and args.workload == "c1" and args.optics == "plain" and not args.no_table1:
-        try:
-            u16 = measure_image_u16(P, dev)
-        except Exception as exc:   # reported, never hidden
-            u16 = {"error": "%s: %s" % (type(exc).__name__, exc)}
-    sur = None
-    if world == 1 and args.workload == "c1" and args.optics == "plain" and not args.no_surrogate:
-        try:
-            sur = run_surrogate(args, rank, world, steps=max(2, min(args.steps, 3)), warmup=1, embedded=True)
-        except Exception as exc:   # reported, never hidden
-            sur = {"error": "%s: %s" % (type(exc).__name__, exc)}
-    bos = None
-    if world == 1 and args.workload == "c1" and args.optics == "plain" and not args.no_table1:
-        try:
-            bos = run_table1(args, rank, world, steps=3, warmup=1, embedded=True)
-        except Exception as exc:   # reported, never hidden
-            bos = {"error": "%s: %s" % (type(exc).__name__, exc)}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if with_cpu and rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, threads, done, t = oracle_sample(frames, seconds_target=12.0)
         cpu = {"value": v, "unit": "rays/s", "cores": threads, "kind": "oracle",
                "sample": "first %d rays (source order) of image 1, %.1f s of CPU work" % (done, t)}
+    return {"workload": WORKLOAD_NAMES[workload], "name": workload, "value": value, "unit": "rays/s",
+            "ms_per_step": ms / steps, "steps": steps, "warmup": warmup, "rays_per_step": rays_step,
+            "images_per_step": len(frames), "gpu_launches": launches, "clocks": clk, "kernels": kt,
+            "mean_steps_per_ray": msteps, "roofline": rf, "e2e": e2e, "cpu_baseline": cpu}
+
+
+def run_gpu_sub(args, workload):
+    """A plain workload's figures as a sub-object of the default line."""
+    return measure_plain(args, workload, 0, 1, steps=3, warmup=2, with_e2e=True, with_cpu=True)
+
+
+def run_gpu(args, rank, world):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1812_05902_gb300 import build as libbuild
+    libbuild.build()
+    res = measure_plain(args, args.workload, rank, world, args.steps, args.warmup)
     if rank == 0:
         out = {
-            "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": res["value"], "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (double-float f32 pairs for positions/directions)",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAMES[args.workload] + ("" if args.scale == 1.0 else
-                                                                     " (scaled by %g)" % args.scale),
-                       "name": args.workload, "optics": args.optics,
-                       "rays_per_step": rays_step, "images_per_step": len(frames), "l2": "flushed between steps",
-                       "parallelism": "replicas (weak)" if world > 1 else "single GPU"},
-            "gpu_launches": int(launches), "clocks": clk, "roofline": rf, "e2e": e2e, "cpu_baseline": cpu,
-            "impl": "pivbos",
+            "data": "synthetic", "config": config_for(args), "gpu_launches": res["gpu_launches"],
+            "clocks": res["clocks"], "roofline": res["roofline"], "e2e": res["e2e"],
+            "cpu_baseline": res["cpu_baseline"], "impl": "pivbos", "plain": res,
         }
-        if sur is not None:
-            out["surrogate"] = sur
-        if bos is not None:
-            out["table1"] = bos
-        if u16 is not None:
-            out["image_u16"] = u16
         print(json.dumps(out), flush=True)
 
 
 MLP_FLOP_PER_RAY = 2 * (16 * 128 + 3 * 128 * 128 + 128 * 4)   # one forward of the surrogate network
+
+
+def shard_range(n, rank, world):
+    """Contiguous source range [lo, hi) of rank `rank` among `world`."""
+    return n * rank // world, n * (rank + 1) // world
+
+
+class ArmTimer:
+    """Times K steps of one arm (CUDA events on the launching stream, L2
+    flushed before each step outside the events, max over ranks) and reads
+    the library's per-kernel timings of those steps."""
+
+    def __init__(self, P, torch, flush, world):
+        self.P, self.torch, self.flush, self.world = P, torch, flush, world
+
+    def __call__(self, fn, steps, warmup, kernels=()):
+        P, torch = self.P, self.torch
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        stream = torch.cuda.current_stream()
+        P.pivbos_timing_reset()
+        P.pivbos_timing_enable(True)
+        l0 = P.pivbos_kernel_launches()
+        ev = []
+        for _ in range(steps):
+            self.flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        launches = P.pivbos_kernel_launches() - l0
+        P.pivbos_timing_enable(False)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        if self.world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        kt = {}
+        for k in kernels:
+            kms, kn = P.pivbos_timing_read(k)
+            kt[k] = {"ms_per_step": kms / steps, "launches_per_step": kn / steps,
+                     "ms_per_launch": kms / kn if kn else None}
+        return ms, int(launches), kt
+
+
+def surrogate_error(P, torch, oracle, fr, med, opt, src, sg, desc, n_plain=1_000_000, n_oracle=200_000, seed=777):
+    """RMS sensor error (px) of a trained surrogate's path on seeded random
+    rays of the image: against the plain tracer (n_plain rays) and against
+    the oracle (the first n_oracle of them); rays whose status differs
+    (a ray grazing a stop) are counted, not averaged in.  Also the plain
+    tracer's own worst error against the oracle on the same rays."""
+    dev = src.device
+    ids = np.random.default_rng(seed).choice(fr.n_rays, n_plain, replace=False).astype(np.int64)
+    ids_t = torch.tensor(ids, device=dev)
+    xy = torch.empty((len(ids), 2), dtype=torch.float64, device=dev)
+    flags = torch.empty(len(ids), dtype=torch.int32, device=dev)
+    sst = torch.empty(len(ids), dtype=torch.int32, device=dev)
+    P.pivbos_surrogate_sensor(sg, desc, ids_t, xy, flags, sst)
+    out = torch.empty(len(ids) * P.RAY_STATE.itemsize, dtype=torch.uint8, device=dev)
+    P.pivbos_trace_exit_states(med.h, opt.h, src, len(fr.sources), fr.rays_per_source, fr.seed, fr.frame_index,
+                               fr.integrator, fr.step, ids_t, len(ids), out)
+    P.pivbos_sync()
+    plain = np.frombuffer(out.cpu().numpy().tobytes(), dtype=P.RAY_STATE)
+    xy, flags, sst = xy.cpu().numpy(), flags.cpu().numpy(), sst.cpu().numpy()
+    ok = (sst == 0) & (plain["status"] == 0)
+    d = xy[ok] - plain["sensor_xy"][ok]
+    res = {"rms_px_vs_plain": float(np.sqrt((d ** 2).sum(1).mean())), "rays_vs_plain": int(ok.sum()),
+           "status_differs_vs_plain": int(((sst == 0) != (plain["status"] == 0)).sum()),
+           "served_frac_sample": float((flags[ok] == 0).mean())}
+    om = oracle.Medium.from_scene(fr.medium)
+    oo = oracle.Optics.from_scene(fr.optics)
+    t0 = time.perf_counter()
+    ost = oracle.trace_many(om, oo, fr.sources, fr.rays_per_source, ids[:n_oracle], fr.seed, fr.frame_index,
+                            fr.integrator, fr.step)
+    t_or = time.perf_counter() - t0
+    ok_o = (sst[:n_oracle] == 0) & (ost["status"] == 0)
+    do = xy[:n_oracle][ok_o] - ost["sensor_xy"][ok_o]
+    both = (plain["status"][:n_oracle] == ost["status"]) & (ost["status"] == 0)
+    res.update({"rms_px_vs_oracle": float(np.sqrt((do ** 2).sum(1).mean())), "rays_vs_oracle": int(ok_o.sum()),
+                "status_differs_vs_oracle": int(((sst[:n_oracle] == 0) != (ost["status"] == 0)).sum()),
+                "plain_max_err_px_vs_oracle": float(np.max(np.abs(plain["sensor_xy"][:n_oracle][both] -
+                                                                  ost["sensor_xy"][both]))),
+                "plain_status_mismatch_vs_oracle": int((plain["status"][:n_oracle] != ost["status"]).sum()),
+                "oracle_seconds": round(t_or, 2)})
+    return res
+
+
+def run_c4(args, rank, world):
+    """The default line: C4, plain vs surrogate vs projection alone."""
+    import torch
+    import oracle
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1812_05902_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1812_05902_gb300 import pivbos as P
+    if world > 1:
+        import torch.distributed as dist
+    fr = _frames("c4", args.scale)[0]
+    n_src = len(fr.sources)
+    lo, hi = shard_range(n_src, rank, world)
+    W, H = fr.optics.width, fr.optics.height
+    rho_d = torch.tensor(fr.medium.rho, device=dev)
+    opt = P.Optics(fr.optics)
+    src_all = torch.tensor(fr.sources, dtype=torch.float64, device=dev)
+    src = src_all[lo:hi].contiguous()
+    img = torch.zeros((H, W), dtype=torch.int64, device=dev)
+    fimg = torch.empty((H, W), dtype=torch.float32, device=dev)
+    stats = torch.zeros(P.RAY_NSTATUS, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    timer = ArmTimer(P, torch, flush, world)
+    # A1 once per density field: the medium build, timed on its own
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    med = P.Medium(fr.medium, rho=rho_d)
+    torch.cuda.synchronize()
+    a.record(stream)
+    med.refill(rho_d)
+    b.record(stream)
+    torch.cuda.synchronize()
+    medium_ms = a.elapsed_time(b)
+    desc_all = P.frame_desc(med.h, opt.h, src_all, n_src, fr.rays_per_source, fr.frame_index, fr.seed, fr.step,
+                            img, stats)
+    desc = P.frame_desc(med.h, opt.h, src, hi - lo, fr.rays_per_source, fr.frame_index, fr.seed, fr.step, img, stats)
+    # training, once per density field (every rank trains the same surrogate)
+    t0 = time.perf_counter()
+    sg, rep = P.pivbos_surrogate_train(desc_all, fr.integrator, P.pivbos_surrogate_default_cfg())
+    train_s = time.perf_counter() - t0
+    cfg_p = P.pivbos_surrogate_default_cfg()
+    cfg_p.use_network = 0
+    t0 = time.perf_counter()
+    sgp, repp = P.pivbos_surrogate_train(desc_all, fr.integrator, cfg_p)
+    train_p_s = time.perf_counter() - t0
+
+    def reduce():
+        if world > 1:
+            dist.all_reduce(img, op=dist.ReduceOp.SUM)
+
+    def plain_step():
+        img.zero_()
+        P.pivbos_render_range(med.h, opt.h, src, hi - lo, lo, fr.rays_per_source, fr.seed, fr.frame_index,
+                              fr.integrator, fr.step, img, stats)
+        reduce()
+        P.pivbos_image_finalize(img, H * W, fimg)
+
+    def sur_step(g):
+        def f():
+            img.zero_()
+            P.pivbos_surrogate_render_range(g, desc, lo)
+            reduce()
+            P.pivbos_image_finalize(img, H * W, fimg)
+        return f
+
+    sur_kernels = ("surrogate_prep", "surrogate_net", "surrogate_finish", "surrogate_fallback", "render", "sort")
+    try:
+        clocks = Clocks(local)
+        clocks.start()
+        time.sleep(0.3)
+        ms_plain, l_plain, k_plain = timer(plain_step, args.steps, args.warmup, ("render", "sort"))
+        img_plain = img.clone() if world > 1 and rank == 0 else None
+        ms_proj, l_proj, k_proj = timer(sur_step(sgp), args.steps, args.warmup, sur_kernels)
+        ms_sur, l_sur, k_sur = timer(sur_step(sg), args.steps, args.warmup, sur_kernels)
+        clk = clocks.stop()
+        n_fb = P.pivbos_surrogate_render(sg, desc_all, count_fallback=True)
+        n_fb_p = P.pivbos_surrogate_render(sgp, desc_all, count_fallback=True)
+        if world > 1 and rank == 0:
+            # the sharded image is the single-GPU image, bit for bit
+            ref = torch.zeros_like(img)
+            P.pivbos_render(med.h, opt.h, src_all, n_src, fr.rays_per_source, fr.seed, fr.frame_index,
+                            fr.integrator, fr.step, ref)
+            P.pivbos_sync()
+            assert torch.equal(ref, img_plain), "sharded image differs from the single-GPU image"
+        # e2e through the C ABI with host buffers: sources in, image out, every step
+        e2e_plain = e2e_sur = None
+        if not args.no_e2e:
+            src_h = torch.tensor(fr.sources[lo:hi], dtype=torch.float64).pin_memory()
+            img_h = torch.zeros((H, W), dtype=torch.int64).pin_memory()
+            fimg_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+
+            def e2e_plain_step():
+                # the C ABI copies host sources in and the host image out itself
+                img_h.zero_()
+                P.pivbos_render_range(med.h, opt.h, src_h, hi - lo, lo, fr.rays_per_source, fr.seed,
+                                      fr.frame_index, fr.integrator, fr.step, img_h)
+                if world > 1:
+                    img.copy_(img_h, non_blocking=True)
+                    reduce()
+                    P.pivbos_image_finalize(img, H * W, fimg)
+                    fimg_h.copy_(fimg, non_blocking=True)
+
+            def e2e_sur_step():
+                src.copy_(src_h, non_blocking=True)
+                sur_step(sg)()
+                fimg_h.copy_(fimg, non_blocking=True)
+
+            def wall(fn):
+                fn()
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                for _ in range(max(1, args.steps)):
+                    fn()
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t1
+                if world > 1:
+                    t = torch.tensor([dt], dtype=torch.float64, device=dev)
+                    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                    dt = float(t.item())
+                return fr.n_rays * max(1, args.steps) / dt
+
+            e2e_plain = {"value": wall(e2e_plain_step), "unit": "rays/s",
+                         "h2d_bytes_per_step": int(src_h.numel() * 8 + H * W * 8),
+                         "d2h_bytes_per_step": int(H * W * 8 + (H * W * 4 if world > 1 else 0)),
+                         "path": "pivbos_render_range with host sources and a host image (the call copies)"}
+            e2e_sur = {"value": wall(e2e_sur_step), "unit": "rays/s", "h2d_bytes_per_step": int(src_h.numel() * 8),
+                       "d2h_bytes_per_step": int(H * W * 4),
+                       "path": "pinned host sources -> device, pivbos_surrogate_render_range, "
+                               "pivbos_image_finalize, float image -> pinned host"}
+        err = err_p = None
+        if rank == 0:
+            err = surrogate_error(P, torch, oracle, fr, med, opt, src_all, sg, desc_all)
+            err_p = surrogate_error(P, torch, oracle, fr, med, opt, src_all, sgp, desc_all)
+    finally:
+        P.pivbos_surrogate_destroy(sg)
+        P.pivbos_surrogate_destroy(sgp)
+    rays = fr.n_rays
+    v_plain = rays * args.steps / (ms_plain * 1e-3)
+    v_proj = rays * args.steps / (ms_proj * 1e-3)
+    v_sur = rays * args.steps / (ms_sur * 1e-3)
+    peaks, src_kind = _peaks()
+    peak_tf = peaks.get("bf16_tflops", 1900.0)
+    # roofline of the surrogate step's dominant kernel, the network: the
+    # forward's FLOPs for the rays it served, per launch
+    net = k_sur["surrogate_net"]
+    served = rays - n_fb
+    rf = None
+    if net["ms_per_launch"]:
+        per_launch_rays = served / net["launches_per_step"]
+        achieved = per_launch_rays * MLP_FLOP_PER_RAY / (net["ms_per_launch"] * 1e-3) / 1e12
+        rf = {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak_tf, "unit": "TFLOP/s",
+              "frac": round(achieved / peak_tf, 4),
+              "traffic": (recorded_traffic("surrogate_c4_traffic", "surrogate", scale_to_rays=per_launch_rays)
+                          if args.scale == 1.0 and world == 1 else None),
+              "kernel": "surr_net_kernel", "op": "BF16 MLP forward on tcgen05, %d FLOP per served ray"
+                                                  % MLP_FLOP_PER_RAY,
+              "peak_source": "%s bf16_tflops (burst)" % src_kind, "launch_ms": round(net["ms_per_launch"], 3),
+              "rays_per_launch": int(per_launch_rays)}
+    # the plain arm's render kernel: the gather roofline (128 B per field
+    # evaluation through L1) and the issue roofline
+    msteps = mean_steps(P, fr, opt, med, src_all)
+    rk = k_plain["render"]
+    rf_plain = None
+    if rk["ms_per_launch"]:
+        per_launch = rays / world
+        rf_plain = roofline([fr], [msteps], rk["ms_per_launch"], 1, clk.get("sm_max_mhz"),
+                            recorded_traffic("render_c4_traffic", "render", rays_per_cta=2048,
+                                             scale_to_rays=per_launch)
+                            if args.scale == 1.0 and world == 1 else None,
+                            l1_gbs=measured_l1_gbs(P), ray_frac=1.0 / world)
+    # once per density field: medium build + table + data + training
+    t_plain, t_sur = ms_plain * 1e-3 / args.steps, ms_sur * 1e-3 / args.steps
+    t_proj = ms_proj * 1e-3 / args.steps
+    amort = {"medium_build_ms": round(medium_ms, 2), "surrogate_train_seconds": round(train_s, 3),
+             "projection_build_seconds": round(train_p_s, 3),
+             "break_even_images_surrogate": (train_s / (t_plain - t_sur)) if t_plain > t_sur else None,
+             "break_even_images_projection": (train_p_s / (t_plain - t_proj)) if t_plain > t_proj else None,
+             "rays_per_s_one_image_incl_training": rays / (train_s + t_sur),
+             "rays_per_s_ten_images_incl_training": 10 * rays / (train_s + 10 * t_sur),
+             "plain_rays_per_s_one_image_incl_medium": rays / (medium_ms * 1e-3 + t_plain),
+             "note": "the medium build is needed by every arm; the surrogate (table, data, training) is built "
+                     "once per density field and serves every image rendered through that field"}
+    c1 = t1 = u16 = None
+    if world == 1 and not args.no_table1:
+        try:
+            c1 = run_gpu_sub(args, "c1")
+        except Exception as exc:   # reported, never hidden
+            c1 = {"error": "%s: %s" % (type(exc).__name__, exc)}
+        try:
+            t1 = run_table1(args, rank, world, steps=3, warmup=1, embedded=True)
+        except Exception as exc:
+            t1 = {"error": "%s: %s" % (type(exc).__name__, exc)}
+        try:
+            u16 = measure_image_u16(P, dev)
+        except Exception as exc:
+            u16 = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_subset_rate(fr)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": v_sur, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_sur / args.steps, "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+            "dtype": "bf16 network (f32 accumulation) / f32 projection, optics and integration (double-float pairs "
+                     "for plain-path positions and directions) / int64 image",
+            "data": "synthetic", "config": config_for(args),
+            "gpu_launches": l_sur, "clocks": clk, "roofline": rf, "e2e": e2e_sur, "cpu_baseline": cpu,
+            "impl": "pivbos",
+            "plain_rays_per_s": v_plain, "surrogate_rays_per_s": v_sur, "projection_rays_per_s": v_proj,
+            "speedup_vs_plain": v_sur / v_plain,
+            "surrogate": {"rays_per_s": v_sur, "ms_per_step": ms_sur / args.steps, "gpu_launches": l_sur,
+                          "served_frac": served / rays, "fallback_rays": int(n_fb), "kernels": k_sur,
+                          "error": err, "report": rep.as_dict(), "e2e": e2e_sur},
+            "projection": {"rays_per_s": v_proj, "ms_per_step": ms_proj / args.steps, "gpu_launches": l_proj,
+                           "served_frac": (rays - n_fb_p) / rays, "fallback_rays": int(n_fb_p), "kernels": k_proj,
+                           "error": err_p, "report": repp.as_dict()},
+            "plain": {"rays_per_s": v_plain, "ms_per_step": ms_plain / args.steps, "gpu_launches": l_plain,
+                      "kernels": k_plain, "mean_steps_per_ray": msteps, "roofline": rf_plain, "e2e": e2e_plain},
+            "per_density_field": amort,
+        }
+        if c1 is not None:
+            out["c1"] = c1
+        if t1 is not None:
+            out["table1"] = t1
+        if u16 is not None:
+            out["image_u16"] = u16
+        print(json.dumps(out), flush=True)
 
 
 def run_surrogate(args, rank, world, steps, warmup, embedded, workload="c4"):
@@ -962,16 +1372,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pivbos", choices=["pivbos", "reference"])
-    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOAD_NAMES))
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOAD_NAMES))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-surrogate", action="store_true", help="skip the C4 surrogate figures of the default line")
     ap.add_argument("--no-table1", action="store_true",
-                    help="skip the Sec. 4 BOS and 16-bit conversion figures of the default line")
+                    help="skip the C1, Sec. 4 BOS and 16-bit conversion sub-objects of the default line")
     ap.add_argument("--optics", default="plain", choices=OPTICS_VARIANTS,
                     help="the workload's camera with an optical extension (plain render workloads only)")
     ap.add_argument("--surrogate", action="store_true",
-                    help="the surrogate path as the value (workload c4, the default here, or c2)")
+                    help="the surrogate path alone as the value (workload c2; c4's default line has all arms)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (profiling captures only; the JSON line says so)")
     args = ap.parse_args()
@@ -986,6 +1395,8 @@ def main():
     try:
         if args.surrogate:
             run_surrogate_line(args, rank, world)
+        elif args.workload == "c4":
+            run_c4(args, rank, world)
         elif args.workload == "c3":
             run_batch(args, rank, world)
         elif args.workload == "table1":

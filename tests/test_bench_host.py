@@ -71,3 +71,56 @@ def test_traffic_record_dropped_when_sources_change(tmp_path, monkeypatch):
     (csrc / "trace.cuh").write_text("// changed\n")
     assert bench.recorded_traffic("t") is None
     assert bench.recorded_traffic("missing") is None
+
+
+def test_shard_ranges_cover_the_sources_once():
+    for n in (1, 7, 100000):
+        for world in (1, 2, 3, 8):
+            ranges = [bench.shard_range(n, r, world) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+            assert max(h - l for l, h in ranges) - min(h - l for l, h in ranges) <= 1
+
+
+def test_oracle_subset_keeps_the_image_rays():
+    fr = scenes.c4(scale=0.2, grid=16)[0]
+    sub = bench.c4_subset(fr)
+    assert len(sub.sources) == 10000 and sub.rays_per_source == 100
+    assert sub.sources is not fr.sources or len(fr.sources) == 10000
+    assert fr.rays_per_source == 10000                  # the frame itself is untouched
+    assert (sub.sources == fr.sources[:10000]).all()
+
+
+def test_both_arms_print_the_same_config():
+    import argparse
+    for wl, sur in (("c4", False), ("c1", False), ("c2", True)):
+        a = argparse.Namespace(workload=wl, scale=0.01, optics="plain", surrogate=sur, gpus=1)
+        assert bench.config_for(a) == bench.config_for(argparse.Namespace(**vars(a)))
+        assert bench.config_for(a)["rays_per_step"] > 0
+    a = argparse.Namespace(workload="c4", scale=0.01, optics="plain", surrogate=False, gpus=4)
+    assert "all-reduce" in bench.config_for(a)["parallelism"]
+
+
+def test_traffic_record_scaled_to_the_launch(tmp_path, monkeypatch):
+    rec = {"source_hash": bench.kernel_source_hash("render"), "dram_bytes_read": 300, "dram_bytes_write": 100,
+           "rays_per_launch": 1000, "rays_per_cta": 2048}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "t.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc = tmp_path / "paper_1812_05902_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in bench.KERNEL_SOURCES["render"]:
+        (csrc / name).write_bytes(open(os.path.join(os.path.dirname(bench.__file__), "paper_1812_05902_gb300",
+                                                    "csrc", name), "rb").read())
+    assert bench.recorded_traffic("t", rays_per_cta=2048, scale_to_rays=5000) == 2000
+    assert bench.recorded_traffic("t", rays_per_cta=256, scale_to_rays=5000) is None
+    assert bench.recorded_traffic("t") == 400
+
+
+def test_roofline_of_a_sharded_launch():
+    fr = scenes.c2(scale=0.1, grid=32)[0]
+    whole = bench.roofline([fr], [100.0], 10.0, 1, 2000.0, l1_gbs=30000.0)
+    half = bench.roofline([fr], [100.0], 5.0, 1, 2000.0, l1_gbs=30000.0, ray_frac=0.5)
+    assert half["achieved"] == pytest.approx(whole["achieved"], rel=1e-3)
+    assert half["rays_per_launch"] == whole["rays_per_launch"] // 2
