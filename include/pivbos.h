@@ -362,12 +362,14 @@ pivbos_status pivbos_autotune(const pivbos_frame_desc* frame, int integrator, do
  * the GPU (tensor cores, Adam, cosine learning rate), the loss weighting
  * each output by its measured effect on the sensor.
  *
- * Confidence: on held-out rays the plain tracer judges the predictor at the
+ * Confidence: on held-out rays the plain tracer judges the predictors at the
  * sensor, per entry-space bin (16 x 16 x 16 positions x 4 x 4 slopes).
- * Bins are served in order of plain-path steps saved per unit of squared
- * sensor error while the summed error keeps the RMS over all rays reaching
- * the sensor within budget_margin * err_budget_px; the other rays are traced
- * by the plain path at render time.  The report gives the same figures for
+ * With one predictor, bins are served in order of plain-path steps saved
+ * per unit of squared sensor error while the summed error keeps the RMS over
+ * all rays reaching the sensor within budget_margin * err_budget_px; with
+ * the automatic choice each bin takes the least costly of the projection,
+ * the corrected projection and the plain path under the same budget.  Rays
+ * of bins not served are traced by the plain path at render time.  The report gives the same figures for
  * the projection alone and for the straight ray.  The surrogate is tied to
  * the frame's medium and optics (they must outlive it; a refill of the
  * medium makes later surrogate calls fail with INVALID_ARG) and needs the
@@ -387,7 +389,12 @@ typedef struct {
     int32_t born_segments;  /* 0..64; 0 = no projection (the network alone); -1 = the smallest of
                                1, 2, 4, ..., 32 whose projection alone keeps the pilot rays' RMS
                                sensor error within 0.8 * budget_margin * err_budget_px */
-    int32_t use_network;    /* 1, or 0 = the projection alone */
+    int32_t use_network;    /* -1 (default) = automatic: the network is trained only if the projection
+                               alone, served within the budget, would leave more than 1 % of the plain
+                               path's integration steps to the fallback; then each bin is served by the
+                               projection alone, the projection with the network's correction or the plain
+                               path, whichever costs least under the budget.  1 = the network's
+                               correction in every served bin; 0 = the projection alone */
     int32_t table_columns_per_cell;  /* projection-table columns per grid spacing across the box, 1..8, at
                                         most 2048 per axis; 0 = the densest of 4, 2, 1 whose table fits
                                         in 16 GiB */
@@ -418,6 +425,8 @@ typedef struct {
     double target_rms[4];              /* RMS residuals: x, y (m) on the reference plane, slope x, y */
     double correction_rms[4];          /* RMS of residual minus projection */
     double sensor_px_per_unit[4];      /* RMS sensor shift per unit of each residual (loss weights) */
+    double network_trained;            /* 1 if the network was trained (use_network 1, or -1 when needed) */
+    double val_served_frac_net;        /* held-out box rays served with the network's correction */
 } pivbos_surrogate_report;
 
 typedef struct pivbos_surrogate pivbos_surrogate;
@@ -446,9 +455,9 @@ pivbos_status pivbos_surrogate_render_range(const pivbos_surrogate* sg, const pi
                                             int64_t first_source, int64_t* n_fallback, void* stream);
 /* Per-ray sensor positions of the surrogate path for flat ray ids (device
  * int64 [n], source-major as in pivbos_trace_exit_states): sensor_xy
- * (device double [n][2]), flags (device int32 [n]: 0 network, 1 plain
- * fallback, 2 never enters the box) and status (device int32 [n]).
- * Synchronous. */
+ * (device double [n][2]), flags (device int32 [n]: 0 the projection with the
+ * network's correction, 3 the projection alone, 1 plain fallback, 2 never
+ * enters the box) and status (device int32 [n]).  Synchronous. */
 pivbos_status pivbos_surrogate_sensor(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
                                       const int64_t* ray_ids, int64_t n, double* sensor_xy, int32_t* flags,
                                       int32_t* status, void* stream);

@@ -111,6 +111,7 @@ struct pivbos_surrogate {
     pivbos::MlpDev net;
     pivbos::SurrParams S;
     uint32_t* bin_ok = nullptr;
+    uint32_t* bin_net = nullptr;
     float4* table = nullptr;
     pivbos_surrogate_report rep;
 };
@@ -185,6 +186,111 @@ Served choose_bins(const std::vector<double>& err2, const std::vector<double>& s
     return sv;
 }
 
+// Automatic mode trains the network when the projection alone, served
+// within the budget, saves less than this share of the plain path's steps.
+constexpr double kAutoTrainBelow = 0.99;
+
+// Render cost of a held-out ray by how it is served, in units of one plain
+// integration step of one ray, measured on GB300 (C4: a plain step 18 ps; a
+// ray served by the projection alone 120 ps with 1 segment, 219 ps with 8,
+// 530 ps with 32 -- prep and finish; the network's forward 95 ps more; a
+// plain fallback ray its steps plus ~120 ps of generation, optics and
+// deposit).
+inline double cost_projection(int segments) { return 6.0 + 0.72 * segments; }
+constexpr double kCostNetworkExtra = 5.3;
+constexpr double kCostFallbackRay = 7.0;
+
+struct Mixed {
+    double err2 = 0.0, steps = 0.0, rays = 0.0, net_rays = 0.0, cost = 0.0;
+};
+
+// Per-bin choice among the projection alone (err2p), the projection with the
+// network's correction (err2n) and the plain fallback (no error): for a
+// multiplier lam, every bin takes the option of least cost + lam * err2;
+// lam is the smallest (bisected) whose summed error meets budget2, which
+// minimises the render cost under the budget up to the bins' granularity.
+// Bins with fewer than min_count held-out rays fall back.
+Mixed choose_mixed(const std::vector<double>& err2n, const std::vector<double>& err2p,
+                   const std::vector<double>& steps, const std::vector<unsigned>& cnt, int min_count, double budget2,
+                   int segments, std::vector<uint32_t>* ok, std::vector<uint32_t>* net)
+{
+    const int nb = (int)cnt.size();
+    const double kCostProjection = cost_projection(segments), kCostNetwork = kCostProjection + kCostNetworkExtra;
+    auto pick = [&](double lam, bool write) {
+        Mixed m;
+        for (int b = 0; b < nb; ++b) {
+            const double n = cnt[b];
+            if (cnt[b] == 0) continue;
+            const double fb = steps[b] + kCostFallbackRay * n;
+            int choice = 0;   // 0 fallback, 1 projection, 2 network
+            double best = fb;
+            if ((int)cnt[b] >= min_count) {
+                const double cp = kCostProjection * n + lam * err2p[b];
+                const double cn = kCostNetwork * n + lam * err2n[b];
+                if (cp < best) { best = cp; choice = 1; }
+                if (cn < best) { best = cn; choice = 2; }
+            }
+            if (choice == 0) {
+                m.cost += fb;
+                continue;
+            }
+            m.err2 += choice == 2 ? err2n[b] : err2p[b];
+            m.cost += (choice == 2 ? kCostNetwork : kCostProjection) * n;
+            m.steps += steps[b];
+            m.rays += n;
+            if (choice == 2) m.net_rays += n;
+            if (write) {
+                (*ok)[b >> 5] |= 1u << (b & 31);
+                if (choice == 2) (*net)[b >> 5] |= 1u << (b & 31);
+            }
+        }
+        return m;
+    };
+    double lam = 0.0;
+    if (pick(0.0, false).err2 > budget2) {
+        double lo = 0.0, hi = 1.0;
+        while (pick(hi, false).err2 > budget2 && hi < 1e300) hi *= 16.0;
+        for (int it = 0; it < 200; ++it) {
+            const double mid = lo > 0.0 ? sqrt(lo * hi) : hi / 16.0;
+            if (pick(mid, false).err2 > budget2) lo = mid;
+            else hi = mid;
+            if (lo > 0.0 && hi / lo < 1.0 + 1e-12) break;
+        }
+        lam = hi;
+    }
+    Mixed m = pick(lam, true);
+    // The bins are coarse, so one multiplier can leave part of the budget
+    // unused: serve further fallback bins, in order of cost saved per unit of
+    // squared error, with whichever predictor saves the most and still fits.
+    struct Up { double ratio, save, e2; int b, choice; };
+    std::vector<Up> ups;
+    for (int b = 0; b < nb; ++b) {
+        if ((int)cnt[b] < min_count || (((*ok)[b >> 5] >> (b & 31)) & 1u)) continue;
+        const double n = cnt[b], fb = steps[b] + kCostFallbackRay * n;
+        const double sp = fb - kCostProjection * n, sn = fb - kCostNetwork * n;
+        if (sp > 0.0) ups.push_back({sp / fmax(err2p[b], 1e-300), sp, err2p[b], b, 1});
+        if (sn > 0.0) ups.push_back({sn / fmax(err2n[b], 1e-300), sn, err2n[b], b, 2});
+    }
+    std::sort(ups.begin(), ups.end(), [](const Up& x, const Up& y) {
+        return x.ratio != y.ratio ? x.ratio > y.ratio : (x.b != y.b ? x.b < y.b : x.choice < y.choice);
+    });
+    for (const Up& u : ups) {
+        if (((*ok)[u.b >> 5] >> (u.b & 31)) & 1u) continue;   // served by an earlier candidate
+        if (m.err2 + u.e2 > budget2) continue;
+        const double n = cnt[u.b];
+        m.err2 += u.e2;
+        m.cost -= u.save;
+        m.steps += steps[u.b];
+        m.rays += n;
+        (*ok)[u.b >> 5] |= 1u << (u.b & 31);
+        if (u.choice == 2) {
+            m.net_rays += n;
+            (*net)[u.b >> 5] |= 1u << (u.b & 31);
+        }
+    }
+    return m;
+}
+
 }  // namespace
 
 extern "C" {
@@ -203,7 +309,7 @@ pivbos_status pivbos_surrogate_default_cfg(pivbos_surrogate_cfg* c)
     c->seed = 7;
     c->ref_plane_z = NAN;
     c->born_segments = -1;
-    c->use_network = 1;
+    c->use_network = -1;
     c->table_columns_per_cell = 0;
     c->table_levels_per_cell = 1;
     return PIVBOS_OK;
@@ -223,7 +329,7 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
         c.batch < 256 || c.batch > 65536 || !(c.lr > 0.f) || !(c.err_budget_px > 0.f) ||
         !(c.budget_margin > 0.f && c.budget_margin <= 1.f) || c.min_bin_count < 1 ||
         (!std::isnan(c.ref_plane_z) && !std::isfinite(c.ref_plane_z)) ||
-        c.born_segments < -1 || c.born_segments > 64 || (c.use_network != 0 && c.use_network != 1) ||
+        c.born_segments < -1 || c.born_segments > 64 || (c.use_network < -1 || c.use_network > 1) ||
         c.table_columns_per_cell < 0 || c.table_columns_per_cell > 8 || c.table_levels_per_cell < 1 ||
         c.table_levels_per_cell > 4)
         return serr(PIVBOS_ERR_INVALID_ARG, "surrogate configuration out of range");
@@ -276,13 +382,14 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
     S.nby = 16;
     S.nbz = 16;
     S.nbu = 4;
-    S.use_net = c.use_network;
+    S.use_net = c.use_network == 1 ? 1 : 0;
     // -1: chosen below from the pilot rays; until then the table is built
     // and the pilot runs with a nonzero count
     S.born_k = c.born_segments < 0 ? 8 : c.born_segments;
     const int nbins = pivbos::kSurrBins;
     cudaError_t e = pivbos::mlp_alloc(sg->net, 128);
     if (e == cudaSuccess) e = cudaMalloc(&sg->bin_ok, sizeof(uint32_t) * (nbins / 32));
+    if (e == cudaSuccess) e = cudaMalloc(&sg->bin_net, sizeof(uint32_t) * (nbins / 32));
     if (e != cudaSuccess) {
         pivbos_surrogate_destroy(sg);
         return scuda(e, "surrogate allocation");
@@ -352,9 +459,8 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
     DevBuf<double> refpx, pilot, accd;
     DevBuf<int> refst;
     DevBuf<unsigned int> bincnt;
-    e = Xt.alloc((size_t)c.n_train * pivbos::kMlpIn);
-    if (e == cudaSuccess) e = Tt.alloc((size_t)c.n_train * 4);
-    if (e == cudaSuccess) e = Xv.alloc((size_t)c.n_val * pivbos::kMlpIn);
+    // the training set is allocated when the network is trained
+    e = Xv.alloc((size_t)c.n_val * pivbos::kMlpIn);
     if (e == cudaSuccess) e = Yv.alloc((size_t)c.n_val * 4);
     if (e == cudaSuccess) e = idv.alloc((size_t)c.n_val);
     if (e == cudaSuccess) e = refpx.alloc((size_t)c.n_val * 2);
@@ -457,106 +563,169 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
             pivbos::surr_data_kernel<PIVBOS_EULER><<<blocks, 128, 0, s>>>(P, S, total, n, streamid, c.seed, X, T, ids, rp, rs);
         pivbos::count_launches(1);
     };
-    if (c.use_network) data(c.n_train, 0, Xt.p, Tt.p, nullptr, nullptr, nullptr);
     data(c.n_val, 1, Xv.p, nullptr, idv.p, refpx.p, refst.p);
     e = cudaStreamSynchronize(s);
     R.seconds_data = now_s() - t0;
-    // ---- S2: training on the GPU
-    const double t1 = now_s();
-    if (c.use_network) {
+    // ---- S2: training on the GPU (its data first: plain-traced rays)
+    auto train = [&]() -> cudaError_t {
+        const double td = now_s();
+        cudaError_t et = Xt.alloc((size_t)c.n_train * pivbos::kMlpIn);
+        if (et == cudaSuccess) et = Tt.alloc((size_t)c.n_train * 4);
+        if (et != cudaSuccess) return et;
+        data(c.n_train, 0, Xt.p, Tt.p, nullptr, nullptr, nullptr);
+        et = cudaStreamSynchronize(s);
+        R.seconds_data += now_s() - td;
+        if (et != cudaSuccess) return et;
+        const double t1 = now_s();
         std::vector<float> p0;
         init_params(p0, c.seed);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(sg->net.params, p0.data(), sizeof(float) * p0.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = pivbos::mlp_sync_bf16(sg->net, s);
+        et = cudaMemcpy(sg->net.params, p0.data(), sizeof(float) * p0.size(), cudaMemcpyHostToDevice);
+        if (et == cudaSuccess) et = pivbos::mlp_sync_bf16(sg->net, s);
         pivbos::MlpWork w;
-        if (e == cudaSuccess) e = pivbos::mlp_work_alloc(w, c.batch);
+        if (et == cudaSuccess) et = pivbos::mlp_work_alloc(w, c.batch);
         const int64_t per_epoch = (c.n_train + c.batch - 1) / c.batch;
         const int64_t steps = per_epoch * c.epochs;
         double last_loss = 0.0;
-        for (int64_t t = 0; t < steps && e == cudaSuccess; ++t) {
+        for (int64_t t = 0; t < steps && et == cudaSuccess; ++t) {
             const int64_t off = (t % per_epoch) * c.batch;
             const int rows = (int)std::min<int64_t>(c.batch, c.n_train - off);
             const float lr = (float)(c.lr * (0.01 + 0.99 * 0.5 * (1.0 + cos(M_PI * (double)t / (double)steps))));
-            e = pivbos::mlp_forward(sg->net, Xt.p + off * pivbos::kMlpIn, rows, w.y, &w, Tt.p + off * 4, s);
-            if (e == cudaSuccess) e = pivbos::mlp_backward(sg->net, Xt.p + off * pivbos::kMlpIn, rows, w, s);
-            if (e == cudaSuccess) e = pivbos::mlp_adam(sg->net, (int)(t + 1), lr, s);
-            if (e == cudaSuccess && t == steps - 1) {
+            et = pivbos::mlp_forward(sg->net, Xt.p + off * pivbos::kMlpIn, rows, w.y, &w, Tt.p + off * 4, s);
+            if (et == cudaSuccess) et = pivbos::mlp_backward(sg->net, Xt.p + off * pivbos::kMlpIn, rows, w, s);
+            if (et == cudaSuccess) et = pivbos::mlp_adam(sg->net, (int)(t + 1), lr, s);
+            if (et == cudaSuccess && t == steps - 1) {
                 double l = 0.0;
-                e = cudaMemcpyAsync(&l, w.loss, sizeof l, cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                et = cudaMemcpyAsync(&l, w.loss, sizeof l, cudaMemcpyDeviceToHost, s);
+                if (et == cudaSuccess) et = cudaStreamSynchronize(s);
                 last_loss = l / ((double)rows * pivbos::kMlpOut);
             }
         }
         pivbos::mlp_work_free(w);
         R.train_loss = last_loss;
         R.train_steps = (double)steps;
-    }
-    R.seconds_train = now_s() - t1;
-    // ---- confidence map: the plain tracer judges the predictors on held-out rays
-    const double t2 = now_s();
-    if (e == cudaSuccess) {
-        if (c.use_network) e = pivbos::mlp_forward(sg->net, Xv.p, (int)c.n_val, Yv.p, nullptr, nullptr, s);
-        else e = cudaMemsetAsync(Yv.p, 0, sizeof(float) * 4 * (size_t)c.n_val, s);
-    }
+        R.network_trained = 1.0;
+        R.seconds_train += now_s() - t1;
+        return et;
+    };
+    // ---- confidence map: the plain tracer judges the predictors on the
+    // held-out rays, per bin (with_net: the network's outputs, else zero)
     const size_t nacc = (size_t)4 * nbins + 5;
-    if (e == cudaSuccess) e = cudaMemsetAsync(accd.p, 0, sizeof(double) * nacc, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bincnt.p, 0, sizeof(unsigned int) * nbins, s);
-    if (e == cudaSuccess) {
-        pivbos::BinAcc acc{{accd.p, accd.p + nbins, accd.p + 2 * (size_t)nbins}, accd.p + 3 * (size_t)nbins,
-                           bincnt.p, accd.p + 4 * (size_t)nbins};
-        pivbos::surr_eval_kernel<<<(unsigned)((c.n_val + 127) / 128), 128, 0, s>>>(P, S, idv.p, Yv.p, refpx.p,
-                                                                                   refst.p, c.n_val, acc);
-        pivbos::count_launches(1);
-    }
     std::vector<double> hd(nacc);
     std::vector<unsigned int> hc(nbins);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), accd.p, sizeof(double) * nacc, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), bincnt.p, sizeof(unsigned) * nbins, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    auto evaluate = [&](bool with_net) -> cudaError_t {
+        const double t2 = now_s();
+        cudaError_t ev = with_net ? pivbos::mlp_forward(sg->net, Xv.p, (int)c.n_val, Yv.p, nullptr, nullptr, s)
+                                  : cudaMemsetAsync(Yv.p, 0, sizeof(float) * 4 * (size_t)c.n_val, s);
+        if (ev == cudaSuccess) ev = cudaMemsetAsync(accd.p, 0, sizeof(double) * nacc, s);
+        if (ev == cudaSuccess) ev = cudaMemsetAsync(bincnt.p, 0, sizeof(unsigned int) * nbins, s);
+        if (ev == cudaSuccess) {
+            pivbos::BinAcc acc{{accd.p, accd.p + nbins, accd.p + 2 * (size_t)nbins}, accd.p + 3 * (size_t)nbins,
+                               bincnt.p, accd.p + 4 * (size_t)nbins};
+            pivbos::surr_eval_kernel<<<(unsigned)((c.n_val + 127) / 128), 128, 0, s>>>(P, S, idv.p, Yv.p, refpx.p,
+                                                                                       refst.p, c.n_val, acc);
+            pivbos::count_launches(1);
+        }
+        if (ev == cudaSuccess)
+            ev = cudaMemcpyAsync(hd.data(), accd.p, sizeof(double) * nacc, cudaMemcpyDeviceToHost, s);
+        if (ev == cudaSuccess)
+            ev = cudaMemcpyAsync(hc.data(), bincnt.p, sizeof(unsigned) * nbins, cudaMemcpyDeviceToHost, s);
+        if (ev == cudaSuccess) ev = cudaStreamSynchronize(s);
+        R.seconds_validate += now_s() - t2;
+        return ev;
+    };
+    if (e == cudaSuccess) e = c.use_network == 1 ? train() : cudaSuccess;
+    if (e == cudaSuccess) e = evaluate(c.use_network == 1);
     if (e != cudaSuccess) {
         pivbos_surrogate_destroy(sg);
         return scuda(e, "surrogate training");
     }
-    std::vector<double> err2[3];
-    for (int v = 0; v < 3; ++v) err2[v].assign(hd.begin() + (size_t)v * nbins, hd.begin() + (size_t)(v + 1) * nbins);
-    const std::vector<double> stp(hd.begin() + 3 * (size_t)nbins, hd.begin() + 4 * (size_t)nbins);
-    const double* tot = hd.data() + 4 * (size_t)nbins;
-    const double n_reached = tot[0], n_box = tot[1];
-    double all_err[3] = {0, 0, 0}, all_steps = 0.0;
-    for (int b = 0; b < nbins; ++b) {
-        for (int v = 0; v < 3; ++v) all_err[v] += err2[v][b];
-        all_steps += stp[b];
-    }
+    auto sums = [&](std::vector<double>* err2, std::vector<double>& stp, double* tot, double* all_err,
+                    double& all_steps) {
+        for (int v = 0; v < 3; ++v)
+            err2[v].assign(hd.begin() + (size_t)v * nbins, hd.begin() + (size_t)(v + 1) * nbins);
+        stp.assign(hd.begin() + 3 * (size_t)nbins, hd.begin() + 4 * (size_t)nbins);
+        for (int q = 0; q < 5; ++q) tot[q] = hd[4 * (size_t)nbins + q];
+        all_steps = 0.0;
+        for (int v = 0; v < 3; ++v) all_err[v] = 0.0;
+        for (int b = 0; b < nbins; ++b) {
+            for (int v = 0; v < 3; ++v) all_err[v] += err2[v][b];
+            all_steps += stp[b];
+        }
+    };
+    std::vector<double> err2[3], stp;
+    double tot[5], all_err[3], all_steps = 0.0;
+    sums(err2, stp, tot, all_err, all_steps);
     const double margin = c.budget_margin;
-    const double budget2 = margin * margin * (double)c.err_budget_px * c.err_budget_px * n_reached;
-    std::vector<uint32_t> ok(nbins / 32, 0u);
-    // the served predictor: the network's (projection + correction), or
-    // the projection alone without a network
-    const int vs = c.use_network ? 0 : 1;
+    const double budget2 = margin * margin * (double)c.err_budget_px * c.err_budget_px * tot[0];
+    const double n_reached = tot[0], n_box = tot[1];
+    // Automatic mode: the network is trained only when the projection alone,
+    // served within the budget, would leave more than 1 % of the plain
+    // path's integration work to the fallback; the projection alone then
+    // serves and no network runs.
+    bool mixed = false;
+    if (c.use_network == -1) {
+        const Served pv = choose_bins(err2[1], stp, hc, c.min_bin_count, budget2, nullptr);
+        if (all_steps > 0 && pv.steps < kAutoTrainBelow * all_steps) {
+            e = train();
+            if (e == cudaSuccess) e = evaluate(true);
+            if (e != cudaSuccess) {
+                pivbos_surrogate_destroy(sg);
+                return scuda(e, "surrogate training");
+            }
+            sums(err2, stp, tot, all_err, all_steps);
+            mixed = true;
+        }
+    }
+    std::vector<uint32_t> ok(nbins / 32, 0u), netb(nbins / 32, 0u);
+    auto rms = [&](double e2, double flips) { return n_box > flips ? sqrt(e2 / (n_box - flips)) : 0.0; };
     Served sv[3];
-    for (int v = 0; v < 3; ++v) sv[v] = choose_bins(err2[v], stp, hc, c.min_bin_count, budget2, v == vs ? &ok : nullptr);
-    auto rms = [&](int v) { return n_box > tot[2 + v] ? sqrt(all_err[v] / (n_box - tot[2 + v])) : 0.0; };
-    R.val_rms_px = rms(vs);
-    R.val_rms_px_born = rms(1);
-    R.val_rms_px_straight = rms(2);
-    R.val_rms_px_served = n_reached > 0 ? sqrt(sv[vs].err2 / n_reached) : 0.0;
-    R.val_served_frac = n_box > 0 ? sv[vs].rays / n_box : 0.0;
+    if (mixed) {
+        // per bin: the projection alone, the projection with the network's
+        // correction, or the plain fallback, whichever costs least under the
+        // error budget
+        const Mixed mx = choose_mixed(err2[0], err2[1], stp, hc, c.min_bin_count, budget2, S.born_k, &ok, &netb);
+        sv[0] = choose_bins(err2[0], stp, hc, c.min_bin_count, budget2, nullptr);
+        sv[1] = choose_bins(err2[1], stp, hc, c.min_bin_count, budget2, nullptr);
+        sv[2] = choose_bins(err2[2], stp, hc, c.min_bin_count, budget2, nullptr);
+        double e_pred = 0.0;
+        for (int b = 0; b < nbins; ++b) e_pred += ((netb[b >> 5] >> (b & 31)) & 1u) ? err2[0][b] : err2[1][b];
+        S.use_net = mx.net_rays > 0 ? 2 : 0;
+        R.val_rms_px = rms(e_pred, tot[3]);
+        R.val_rms_px_served = n_reached > 0 ? sqrt(mx.err2 / n_reached) : 0.0;
+        R.val_served_frac = n_box > 0 ? mx.rays / n_box : 0.0;
+        R.val_served_frac_net = n_box > 0 ? mx.net_rays / n_box : 0.0;
+        R.steps_saved_frac = all_steps > 0 ? mx.steps / all_steps : 0.0;
+        R.val_status_flip_frac = n_box > 0 ? tot[3] / n_box : 0.0;
+    } else {
+        // one predictor for every served bin: the network's (forced), or the
+        // projection alone
+        const int vs = c.use_network == 1 ? 0 : 1;
+        for (int v = 0; v < 3; ++v)
+            sv[v] = choose_bins(err2[v], stp, hc, c.min_bin_count, budget2, v == vs ? &ok : nullptr);
+        S.use_net = c.use_network == 1 ? 1 : 0;
+        R.val_rms_px = rms(all_err[vs], tot[2 + vs]);
+        R.val_rms_px_served = n_reached > 0 ? sqrt(sv[vs].err2 / n_reached) : 0.0;
+        R.val_served_frac = n_box > 0 ? sv[vs].rays / n_box : 0.0;
+        R.val_served_frac_net = vs == 0 ? R.val_served_frac : 0.0;
+        R.steps_saved_frac = all_steps > 0 ? sv[vs].steps / all_steps : 0.0;
+        R.val_status_flip_frac = n_box > 0 ? tot[2 + vs] / n_box : 0.0;
+    }
+    R.val_rms_px_born = rms(all_err[1], tot[3]);
+    R.val_rms_px_straight = rms(all_err[2], tot[4]);
     R.val_served_frac_born = n_box > 0 ? sv[1].rays / n_box : 0.0;
     R.val_served_frac_straight = n_box > 0 ? sv[2].rays / n_box : 0.0;
-    R.steps_saved_frac = all_steps > 0 ? sv[vs].steps / all_steps : 0.0;
     R.steps_saved_frac_born = all_steps > 0 ? sv[1].steps / all_steps : 0.0;
     R.steps_saved_frac_straight = all_steps > 0 ? sv[2].steps / all_steps : 0.0;
-    R.val_status_flip_frac = n_box > 0 ? tot[2 + vs] / n_box : 0.0;
     R.n_val_reached = n_reached;
     R.n_val_box = n_box;
     e = cudaMemcpy(sg->bin_ok, ok.data(), sizeof(uint32_t) * ok.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(sg->bin_net, netb.data(), sizeof(uint32_t) * netb.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         pivbos_surrogate_destroy(sg);
         return scuda(e, "surrogate bins");
     }
     S.bin_ok = sg->bin_ok;
-    R.seconds_validate = now_s() - t2;
+    S.bin_net = sg->bin_net;
     if (report) *report = R;
     *out = sg;
     return PIVBOS_OK;
@@ -642,9 +811,13 @@ static pivbos_status surrogate_render_impl(const pivbos_surrogate* sg, const piv
     if (e == cudaSuccess) {
         // three kernels per chunk of up to 2^26 rays: prep -> network -> finish
         const uint64_t chunk = std::min<uint64_t>(total, 1ull << 26);
+        const int use_net = sg->S.use_net;
         pivbos::ServedList sv;
+        memset(&sv, 0, sizeof sv);
         char* sbuf = nullptr;
-        const size_t off_count = ((size_t)chunk * 84 + 255) & ~(size_t)255;
+        // per entry: network input 32 B, projection residual 16 B, full
+        // residual 16 B, straight line 16 B, ray id 4 B, network slot 4 B
+        const size_t off_count = ((size_t)chunk * 88 + 255) & ~(size_t)255;
         const size_t sbytes = off_count + 256;
         e = cudaMallocAsync((void**)&sbuf, sbytes, s);
         if (e == cudaSuccess) {
@@ -653,11 +826,16 @@ static pivbos_status surrogate_render_impl(const pivbos_surrogate* sg, const piv
             sv.R = (float4*)(sbuf + (size_t)chunk * 48);
             sv.L = (float4*)(sbuf + (size_t)chunk * 64);
             sv.ids = (uint32_t*)(sbuf + (size_t)chunk * 80);
-            sv.count = (unsigned long long*)(sbuf + off_count);   // [0] served, [1] finish items
+            // [0] served, [1] finish items, [2] network rays
+            sv.count = (unsigned long long*)(sbuf + off_count);
             sv.capacity = (uint32_t)chunk;
+            if (use_net == 2) {
+                sv.net_idx = (uint32_t*)(sbuf + (size_t)chunk * 84);
+                sv.net_count = sv.count + 2;
+            }
             for (uint64_t c0 = 0; c0 < total && e == cudaSuccess; c0 += chunk) {
                 const uint64_t c1 = std::min(total, c0 + chunk);
-                e = cudaMemsetAsync(sv.count, 0, 2 * sizeof(unsigned long long), s);
+                e = cudaMemsetAsync(sv.count, 0, 3 * sizeof(unsigned long long), s);
                 if (e != cudaSuccess) break;
                 const uint64_t items = (c1 - c0 + pivbos::kMaxOrderRays - 1) / pivbos::kMaxOrderRays;
                 pivbos::timing_begin("surrogate_prep", s);
@@ -665,17 +843,17 @@ static pivbos_status surrogate_render_impl(const pivbos_surrogate* sg, const piv
                     P, sg->S, c0, c1, sv, fb, counters + 1, capacity);
                 pivbos::timing_end("surrogate_prep", s);
                 pivbos::count_launches(1);
-                if (sg->S.use_net) {
+                if (use_net) {
                     e = pivbos::launch_surr_net(sg->S, sg->net.wbf, sg->net.params, sv, P.status_word, s);
                     if (e != cudaSuccess) break;
                 }
                 pivbos::timing_begin("surrogate_finish", s);
                 if (pivbos::optics_ext(P.o))
                     pivbos::surr_finish_kernel<true><<<sms * 4, 256, 0, s>>>(
-                        P, sg->S, sv, sg->S.use_net ? sv.R : sv.B, frame->image, frame->stats, sv.count + 1);
+                        P, sg->S, sv, use_net ? sv.R : sv.B, frame->image, frame->stats, sv.count + 1);
                 else
                     pivbos::surr_finish_kernel<false><<<sms * 4, 256, 0, s>>>(
-                        P, sg->S, sv, sg->S.use_net ? sv.R : sv.B, frame->image, frame->stats, sv.count + 1);
+                        P, sg->S, sv, use_net ? sv.R : sv.B, frame->image, frame->stats, sv.count + 1);
                 pivbos::timing_end("surrogate_finish", s);
                 pivbos::count_launches(1);
                 e = cudaGetLastError();
@@ -724,8 +902,13 @@ pivbos_status pivbos_surrogate_sensor(const pivbos_surrogate* sg, const pivbos_f
     if (e == cudaSuccess) e = Y.alloc((size_t)n * 4);
     if (e != cudaSuccess) return scuda(e, "surrogate sensor scratch");
     const unsigned blocks = (unsigned)((n + 127) / 128);
-    pivbos::surr_features_kernel<<<blocks, 128, 0, s>>>(P, sg->S, ray_ids, n, X.p);
-    e = pivbos::mlp_forward(sg->net, X.p, (int)n, Y.p, nullptr, nullptr, s);
+    if (sg->S.use_net) {
+        pivbos::surr_features_kernel<<<blocks, 128, 0, s>>>(P, sg->S, ray_ids, n, X.p);
+        pivbos::count_launches(1);
+        e = pivbos::mlp_forward(sg->net, X.p, (int)n, Y.p, nullptr, nullptr, s);
+    } else {
+        e = cudaMemsetAsync(Y.p, 0, sizeof(float) * 4 * (size_t)n, s);
+    }
     if (e == cudaSuccess) {
         if (sg->integrator == PIVBOS_RK4)
             pivbos::surr_sensor_kernel<PIVBOS_RK4><<<blocks, 128, 0, s>>>(P, sg->S, Y.p, ray_ids, n, sensor_xy, flags,
@@ -733,7 +916,7 @@ pivbos_status pivbos_surrogate_sensor(const pivbos_surrogate* sg, const pivbos_f
         else
             pivbos::surr_sensor_kernel<PIVBOS_EULER><<<blocks, 128, 0, s>>>(P, sg->S, Y.p, ray_ids, n, sensor_xy,
                                                                            flags, status);
-        pivbos::count_launches(2);
+        pivbos::count_launches(1);
         e = cudaStreamSynchronize(s);
     }
     if (e != cudaSuccess) return scuda(e, "surrogate sensor");
@@ -752,6 +935,7 @@ void pivbos_surrogate_destroy(pivbos_surrogate* sg)
     if (!sg) return;
     pivbos::mlp_free(sg->net);
     cudaFree(sg->bin_ok);
+    cudaFree(sg->bin_net);
     cudaFree(sg->table);
     delete sg;
 }

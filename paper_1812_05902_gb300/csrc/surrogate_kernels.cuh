@@ -22,8 +22,10 @@ struct SurrParams {
     float t_scale[4];               // network output scales: dx, dy (m) at z_ref, dux, duy
     float b_scale[4];               // scales of the projection (Born) residual as network input
     int nbx, nby, nbz, nbu;         // confidence bins
-    const uint32_t* bin_ok;         // bit b set: bin b is served by the network
-    int use_net;                    // 0: the projection residual alone
+    const uint32_t* bin_ok;         // bit b set: bin b is served (not traced by the plain path)
+    const uint32_t* bin_net;        // bit b set: bin b is served with the network's correction (use_net 2)
+    int use_net;                    // 0: the projection residual alone; 1: with the network's correction in
+                                    // every served bin; 2: in the bins of bin_net only
     // projection table: suffix integrals of grad n along lines through the
     // pupil centre (0, 0, aim_z), columns indexed by where they cross z_hi
     const float4* table;            // G plane [level][row][col] {Gx, Gy, Gz, 0}, then the H plane
@@ -250,11 +252,19 @@ __device__ __forceinline__ void surr_exit(const SurrParams& S, const Entry& e, c
     dz = inn;
 }
 
-// Full residual: projection plus the network's correction (y scaled).
-__device__ __forceinline__ void surr_residual(const SurrParams& S, const float* born, const float* y, float* r)
+// Whether served rays of bin b take the network's correction.
+__device__ __forceinline__ bool net_bin(const SurrParams& S, int b)
+{
+    if (S.use_net == 2) return (__ldg(S.bin_net + (b >> 5)) >> (b & 31)) & 1u;
+    return S.use_net == 1;
+}
+
+// Full residual: projection plus (with net) the network's correction (y scaled).
+__device__ __forceinline__ void surr_residual(const SurrParams& S, const float* born, const float* y, bool net,
+                                              float* r)
 {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) r[c] = born[c] + (S.use_net ? y[c] * S.t_scale[c] : 0.0f);
+    for (int c = 0; c < 4; ++c) r[c] = born[c] + (net ? y[c] * S.t_scale[c] : 0.0f);
 }
 
 // Sensor position of a surrogate ray: its straight line (xs, ys at z_ref,
@@ -516,12 +526,18 @@ __global__ void surr_eval_kernel(const TraceParams P, const SurrParams S, const 
 // ---------------------------------------------------------------------------
 struct ServedList {
     uint32_t* ids;              // flat ray index; top bit: never enters the box (straight)
-    __nv_bfloat16* X;           // [capacity][16] network input
-    float4* B;                  // [capacity] projection residual
-    float4* R;                  // [capacity] full residual (projection + correction)
+    __nv_bfloat16* X;           // [capacity][16] network input (by network slot)
+    float4* B;                  // [capacity] projection residual (by network slot with use_net 1 and 2,
+                                // by served slot with use_net 0)
+    float4* R;                  // [capacity] full residual (projection + correction), by served slot
     float4* L;                  // [capacity] straight line: x, y at z_ref and slopes x, y
     unsigned long long* count;  // rays appended
     uint32_t capacity;
+    // use_net 2: the rays that take the network's correction, a sub-list of
+    // the served list (network slot -> served slot); nullptr: every served
+    // ray, network slot = served slot
+    uint32_t* net_idx;
+    unsigned long long* net_count;
 };
 
 constexpr uint32_t kStraightBit = 0x80000000u;
@@ -567,6 +583,8 @@ surr_prep_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t 
 {
     __shared__ int warp_off[2][8];
     __shared__ unsigned long long base[2];
+    __shared__ int warp_off_n[2][8];
+    __shared__ unsigned long long base_n[2];
     __shared__ uint32_t order[kMaxOrderRays];
     const uint32_t rps = P.rays_per_source;
     // items of kMaxOrderRays rays; with many projection segments per ray an
@@ -583,6 +601,7 @@ surr_prep_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t 
             const bool active = pos < n_here;
             const uint64_t idx = first + (reorder && active ? (order[pos] & 0x7ffu) : pos);
             int mode = 3;
+            bool net = false;
             Entry e;
             e.enters = false;
             e.f[0] = e.f[1] = e.f[2] = e.f[3] = e.f[4] = 0.0f;
@@ -596,23 +615,39 @@ surr_prep_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t 
                 surr_entry_f(P, S, a.x + a.y, b.x + b.y, c.x + c.y, sid, k, e);
                 if (!e.enters) mode = 2;
                 else mode = ((__ldg(S.bin_ok + (e.bin >> 5)) >> (e.bin & 31)) & 1u) ? 0 : 1;
-                if (mode == 0) born_residual(S, e, born);
+                if (mode == 0) {
+                    born_residual(S, e, born);
+                    net = net_bin(S, e.bin);
+                }
+                // use_net 1 runs the network over the whole served list
+                // (a straight ray's result is not read)
+                if (mode == 2 && S.use_net == 1) net = true;
             }
             // served and straight rays to the served list, the rest to the
             // fallback list
             const unsigned long long ps = block_append2(mode == 0 || mode == 2, mode == 1, sv.count, fb_count,
                                                         warp_off, base);
+            // use_net 2: the served rays that take the network's correction
+            // to the network's sub-list as well
+            unsigned long long pn = ps;
+            if (S.use_net == 2) pn = block_append2(net, false, sv.net_count, sv.net_count, warp_off_n, base_n);
             if (mode == 0 || mode == 2) {
-                if (ps < sv.capacity) {
+                if (ps < sv.capacity && (!net || pn < sv.capacity)) {
                     // streaming stores: the lists pass through HBM once,
                     // leaving L2 to the projection table
                     __stcs(sv.ids + ps, (uint32_t)idx | (mode == 2 ? kStraightBit : 0u));
-                    __align__(16) __nv_bfloat16 x[kMlpIn];
-                    encode_features(S, e.f, born, x);
-                    uint4* xr = reinterpret_cast<uint4*>(sv.X + ps * kMlpIn);
-                    __stcs(xr, *reinterpret_cast<const uint4*>(&x[0]));
-                    __stcs(xr + 1, *reinterpret_cast<const uint4*>(&x[8]));
-                    __stcs(sv.B + ps, make_float4(born[0], born[1], born[2], born[3]));
+                    const float4 b4 = make_float4(born[0], born[1], born[2], born[3]);
+                    if (net) {
+                        __align__(16) __nv_bfloat16 x[kMlpIn];
+                        encode_features(S, e.f, born, x);
+                        uint4* xr = reinterpret_cast<uint4*>(sv.X + pn * kMlpIn);
+                        __stcs(xr, *reinterpret_cast<const uint4*>(&x[0]));
+                        __stcs(xr + 1, *reinterpret_cast<const uint4*>(&x[8]));
+                        __stcs(sv.B + pn, b4);
+                        if (S.use_net == 2) __stcs(sv.net_idx + pn, (uint32_t)ps);
+                    }
+                    if (S.use_net == 0) __stcs(sv.B + ps, b4);
+                    else if (!net) __stcs(sv.R + ps, b4);   // the projection alone (or a straight ray)
                     __stcs(sv.L + ps, make_float4(e.xs, e.ys, e.ux, e.uy));
                 } else {
                     atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_OVERFLOW);   // cannot happen: capacity = chunk
@@ -654,7 +689,7 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
     const uint32_t d_tmem = sh.tmem_base + (uint32_t)grp * mlptc::kTileCols, a_tmem = d_tmem + mlptc::kACol;
     const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
     mlptc::store_constants(a_tmem + lane);
-    const uint64_t n = min(*sv.count, (unsigned long long)sv.capacity);
+    const uint64_t n = min(*(sv.net_idx ? sv.net_count : sv.count), (unsigned long long)sv.capacity);
     const uint64_t tiles = (n + mlptc::kRows - 1) / mlptc::kRows;
     uint32_t parity = 0;
     const uint64_t stride = (uint64_t)gridDim.x * kNetGroups;
@@ -708,9 +743,11 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
             } else {
                 float y[kMlpOut];
                 mlptc::epilogue_out(d_tmem + lane, y);
-                if (r < n)
-                    __stcs(sv.R + r, make_float4(b.x + y[0] * S.t_scale[0], b.y + y[1] * S.t_scale[1],
-                                                 b.z + y[2] * S.t_scale[2], b.w + y[3] * S.t_scale[3]));
+                if (r < n) {
+                    const uint64_t dst = sv.net_idx ? (uint64_t)__ldcs(sv.net_idx + r) : r;
+                    __stcs(sv.R + dst, make_float4(b.x + y[0] * S.t_scale[0], b.y + y[1] * S.t_scale[1],
+                                                   b.z + y[2] * S.t_scale[2], b.w + y[3] * S.t_scale[3]));
+                }
             }
         }
         if (bad) break;
@@ -789,7 +826,9 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
         __syncthreads();
         const int ax = anchor_tid == 0x7fffffff ? -(1 << 28) : sax;
         const int ay = anchor_tid == 0x7fffffff ? -(1 << 28) : say;
-        if (active && r.status == PIVBOS_RAY_REACHED) deposit_ray<EXT>(P.o, r.px, r.py, tile, ax, ay, image, r.w);
+        const unsigned dep = __ballot_sync(0xffffffffu, active && r.status == PIVBOS_RAY_REACHED);
+        if (active && r.status == PIVBOS_RAY_REACHED)
+            deposit_ray<EXT>(P.o, r.px, r.py, tile, ax, ay, image, r.w, dep);
         __syncthreads();
         for (int q = tid; q < kTileW * kTileH; q += blockDim.x) {
             const unsigned long long v = tile[q];
@@ -820,7 +859,10 @@ __global__ void surr_sensor_kernel(const TraceParams P, const SurrParams S, cons
     df sx, sy, sz;
     Entry e;
     surr_ray_by_id(P, S, (uint64_t)ids[q], sid, k, sx, sy, sz, e);
-    const int flag = !e.enters ? 2 : (((S.bin_ok[e.bin >> 5] >> (e.bin & 31)) & 1u) ? 0 : 1);
+    // 0: the network's corrected projection, 3: the projection alone, 1: the
+    // plain fallback, 2: never enters the box
+    int flag = !e.enters ? 2 : (((S.bin_ok[e.bin >> 5] >> (e.bin & 31)) & 1u) ? 0 : 1);
+    if (flag == 0 && !net_bin(S, e.bin)) flag = 3;
     int status = PIVBOS_RAY_REACHED;
     df px = dfv(0.f), py = dfv(0.f);
     if (flag == 1) {
@@ -833,10 +875,10 @@ __global__ void surr_sensor_kernel(const TraceParams P, const SurrParams S, cons
         // the straight line (a ray that never enters the box) or the
         // surrogate's exit line, as the render's finish kernel takes them
         float res[4] = {0.f, 0.f, 0.f, 0.f};
-        if (flag == 0) {
+        if (flag == 0 || flag == 3) {
             float born[4];
             born_residual(S, e, born);
-            surr_residual(S, born, Y + q * 4, res);
+            surr_residual(S, born, Y + q * 4, flag == 0, res);
         }
         surr_sensor(P.o, S, e.xs, e.ys, e.ux, e.uy, res, status, px, py);
     }

@@ -69,14 +69,16 @@ _REPORT_SCALARS = ("train_loss", "train_steps", "val_rms_px", "val_rms_px_born",
                    "table_columns_per_cell")
 _REPORT_VECTORS = (("pilot_rms_px_born_k", 6), ("target_rms", 4), ("correction_rms", 4),
                    ("sensor_px_per_unit", 4))
+_REPORT_TAIL = ("network_trained", "val_served_frac_net")
 
 
 class pivbos_surrogate_report(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_double) for n in _REPORT_SCALARS] +
-                [(n, ctypes.c_double * k) for n, k in _REPORT_VECTORS])
+                [(n, ctypes.c_double * k) for n, k in _REPORT_VECTORS] +
+                [(n, ctypes.c_double) for n in _REPORT_TAIL])
 
     def as_dict(self):
-        d = {n: getattr(self, n) for n in _REPORT_SCALARS}
+        d = {n: getattr(self, n) for n in _REPORT_SCALARS + _REPORT_TAIL}
         for n, _ in _REPORT_VECTORS:
             d[n] = list(getattr(self, n))
         return d

@@ -94,7 +94,7 @@ def test_surrogate_arguments_without_a_device(P):
     assert L.pivbos_surrogate_default_cfg(None) == P.ERR_INVALID_ARG
     cfg = P.pivbos_surrogate_default_cfg()
     assert cfg.n_train == 20_000_000 and cfg.batch == 16384 and np.isnan(cfg.ref_plane_z)
-    assert cfg.born_segments == -1 and cfg.use_network == 1
+    assert cfg.born_segments == -1 and cfg.use_network == -1
     assert abs(cfg.err_budget_px - 0.01) < 1e-9
     out = ctypes.c_void_p()
     rep = P.pivbos_surrogate_report()
@@ -107,7 +107,7 @@ def test_surrogate_arguments_without_a_device(P):
     for field, value in (("batch", 100), ("batch", 1 << 17), ("n_train", 10), ("epochs", 0), ("lr", 0.0),
                          ("err_budget_px", -1.0), ("budget_margin", 1.5), ("min_bin_count", 0),
                          ("ref_plane_z", float("inf")), ("born_segments", -2), ("born_segments", 65),
-                         ("use_network", 2), ("table_columns_per_cell", -1), ("table_columns_per_cell", 9),
+                         ("use_network", 2), ("use_network", -2), ("table_columns_per_cell", -1), ("table_columns_per_cell", 9),
                          ("table_levels_per_cell", 5)):
         bad = P.pivbos_surrogate_default_cfg()
         setattr(bad, field, value)
