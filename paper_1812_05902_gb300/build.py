@@ -47,6 +47,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return LIB
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    # measurement builds only (e.g. -DPIVBOS_DEPOSIT_AGG=0 for the unaggregated deposit)
+    extra += os.environ.get("PIVBOS_NVCC_EXTRA", "").split()
 
     def compile_one(src):
         obj = os.path.join(OBJ, src.replace(".cu", ".o"))

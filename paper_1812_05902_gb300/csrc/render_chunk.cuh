@@ -81,9 +81,11 @@ __device__ __forceinline__ void render_chunk(const TraceParams& P, ChunkShared& 
             ax = sh.ax;
             ay = sh.ay;
         }
+        // every lane of the warp reaches this ballot (the loop is uniform)
+        const unsigned dep = __ballot_sync(0xffffffffu, active && r.status == PIVBOS_RAY_REACHED);
         if (active && r.status == PIVBOS_RAY_REACHED) {
-            if constexpr (EXT) deposit_ray<true>(P.o, r.px, r.py, sh.tile, ax, ay, image, r.w);
-            else deposit_ray(P.o, r.px, r.py, sh.tile, ax, ay, image);
+            if constexpr (EXT) deposit_ray<true>(P.o, r.px, r.py, sh.tile, ax, ay, image, r.w, dep);
+            else deposit_ray(P.o, r.px, r.py, sh.tile, ax, ay, image, 1.0f, dep);
         }
     }
     if (stats) {
