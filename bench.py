@@ -638,8 +638,11 @@ MLP_FLOP_PER_RAY = 2 * (16 * 128 + 3 * 128 * 128 + 128 * 4)   # one forward of t
 
 
 def shard_range(n, rank, world):
-    """Contiguous source range [lo, hi) of rank `rank` among `world`."""
-    return n * rank // world, n * (rank + 1) // world
+    """Contiguous source range [lo, hi) of rank `rank` among `world` (the
+    library's sharding rule, shard.source_range)."""
+    from paper_1812_05902_gb300.shard import source_range
+    first, count = source_range(n, world, rank)
+    return first, first + count
 
 
 class ArmTimer:
@@ -731,8 +734,17 @@ def surrogate_error(P, torch, oracle, fr, med, opt, src, sg, desc, n_plain=1_000
     return res
 
 
+# FP32/INT32 lane operations per ray served by the surrogate's finish kernel:
+# exit line from the straight line and the residual (40), the lens in FP32
+# (two spheres 2 x 130, the stop 20), the sensor plane (125), the spot
+# deposit (450), list reads and bookkeeping (20)
+OPS_FINISH_RAY = 40 + 2 * 130 + 20 + 125 + 450 + 20
+TIGHT_BUDGET_PX = 0.001
+
+
 def run_c4(args, rank, world):
-    """The default line: C4, plain vs surrogate vs projection alone."""
+    """The default line: C4, plain tracer vs the surrogate path (the value),
+    the network forced on every served ray, and a tight-budget comparison."""
     import torch
     import oracle
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -757,6 +769,7 @@ def run_c4(args, rank, world):
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     timer = ArmTimer(P, torch, flush, world)
+    rays = fr.n_rays
     # A1 once per density field: the medium build, timed on its own
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
@@ -770,15 +783,6 @@ def run_c4(args, rank, world):
     desc_all = P.frame_desc(med.h, opt.h, src_all, n_src, fr.rays_per_source, fr.frame_index, fr.seed, fr.step,
                             img, stats)
     desc = P.frame_desc(med.h, opt.h, src, hi - lo, fr.rays_per_source, fr.frame_index, fr.seed, fr.step, img, stats)
-    # training, once per density field (every rank trains the same surrogate)
-    t0 = time.perf_counter()
-    sg, rep = P.pivbos_surrogate_train(desc_all, fr.integrator, P.pivbos_surrogate_default_cfg())
-    train_s = time.perf_counter() - t0
-    cfg_p = P.pivbos_surrogate_default_cfg()
-    cfg_p.use_network = 0
-    t0 = time.perf_counter()
-    sgp, repp = P.pivbos_surrogate_train(desc_all, fr.integrator, cfg_p)
-    train_p_s = time.perf_counter() - t0
 
     def reduce():
         if world > 1:
@@ -799,123 +803,181 @@ def run_c4(args, rank, world):
             P.pivbos_image_finalize(img, H * W, fimg)
         return f
 
-    sur_kernels = ("surrogate_prep", "surrogate_net", "surrogate_finish", "surrogate_fallback", "render", "sort")
-    try:
-        clocks = Clocks(local)
-        clocks.start()
-        time.sleep(0.3)
-        ms_plain, l_plain, k_plain = timer(plain_step, args.steps, args.warmup, ("render", "sort"))
-        img_plain = img.clone() if world > 1 and rank == 0 else None
-        ms_proj, l_proj, k_proj = timer(sur_step(sgp), args.steps, args.warmup, sur_kernels)
-        ms_sur, l_sur, k_sur = timer(sur_step(sg), args.steps, args.warmup, sur_kernels)
-        clk = clocks.stop()
-        n_fb = P.pivbos_surrogate_render(sg, desc_all, count_fallback=True)
-        n_fb_p = P.pivbos_surrogate_render(sgp, desc_all, count_fallback=True)
-        if world > 1 and rank == 0:
-            # the sharded image is the single-GPU image, bit for bit
-            ref = torch.zeros_like(img)
-            P.pivbos_render(med.h, opt.h, src_all, n_src, fr.rays_per_source, fr.seed, fr.frame_index,
-                            fr.integrator, fr.step, ref)
-            P.pivbos_sync()
-            assert torch.equal(ref, img_plain), "sharded image differs from the single-GPU image"
-        # e2e through the C ABI with host buffers: sources in, image out, every step
-        e2e_plain = e2e_sur = None
-        if not args.no_e2e:
-            src_h = torch.tensor(fr.sources[lo:hi], dtype=torch.float64).pin_memory()
-            img_h = torch.zeros((H, W), dtype=torch.int64).pin_memory()
-            fimg_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    def wall(fn):
+        fn()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            fn()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        return rays * max(1, args.steps) / dt
 
-            def e2e_plain_step():
-                # the C ABI copies host sources in and the host image out itself
-                img_h.zero_()
-                P.pivbos_render_range(med.h, opt.h, src_h, hi - lo, lo, fr.rays_per_source, fr.seed,
-                                      fr.frame_index, fr.integrator, fr.step, img_h)
-                if world > 1:
-                    img.copy_(img_h, non_blocking=True)
-                    reduce()
-                    P.pivbos_image_finalize(img, H * W, fimg)
+    sur_kernels = ("surrogate_prep", "surrogate_net", "surrogate_finish", "surrogate_fallback", "sort")
+
+    def surrogate_arm(label, with_e2e=False, **cfg_fields):
+        """Train a surrogate (outside the timed region; every rank trains the
+        same one), time its render, measure its error; returns the arm."""
+        cfg = P.pivbos_surrogate_default_cfg()
+        for k, v in cfg_fields.items():
+            setattr(cfg, k, v)
+        t0 = time.perf_counter()
+        g, rep = P.pivbos_surrogate_train(desc_all, fr.integrator, cfg)
+        train_s = time.perf_counter() - t0
+        try:
+            ms, launches, kt = timer(sur_step(g), args.steps, args.warmup, sur_kernels)
+            n_fb = P.pivbos_surrogate_render(g, desc_all, count_fallback=True)
+            e2e = None
+            if with_e2e and not args.no_e2e:
+                src_h = torch.tensor(fr.sources[lo:hi], dtype=torch.float64).pin_memory()
+                fimg_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+
+                def e2e_step():
+                    src.copy_(src_h, non_blocking=True)
+                    sur_step(g)()
                     fimg_h.copy_(fimg, non_blocking=True)
 
-            def e2e_sur_step():
-                src.copy_(src_h, non_blocking=True)
-                sur_step(sg)()
-                fimg_h.copy_(fimg, non_blocking=True)
-
-            def wall(fn):
-                fn()
-                torch.cuda.synchronize()
-                t1 = time.perf_counter()
-                for _ in range(max(1, args.steps)):
-                    fn()
-                torch.cuda.synchronize()
-                dt = time.perf_counter() - t1
-                if world > 1:
-                    t = torch.tensor([dt], dtype=torch.float64, device=dev)
-                    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                    dt = float(t.item())
-                return fr.n_rays * max(1, args.steps) / dt
-
-            e2e_plain = {"value": wall(e2e_plain_step), "unit": "rays/s",
-                         "h2d_bytes_per_step": int(src_h.numel() * 8 + H * W * 8),
-                         "d2h_bytes_per_step": int(H * W * 8 + (H * W * 4 if world > 1 else 0)),
-                         "path": "pivbos_render_range with host sources and a host image (the call copies)"}
-            e2e_sur = {"value": wall(e2e_sur_step), "unit": "rays/s", "h2d_bytes_per_step": int(src_h.numel() * 8),
+                e2e = {"value": wall(e2e_step), "unit": "rays/s", "h2d_bytes_per_step": int(src_h.numel() * 8),
                        "d2h_bytes_per_step": int(H * W * 4),
                        "path": "pinned host sources -> device, pivbos_surrogate_render_range, "
                                "pivbos_image_finalize, float image -> pinned host"}
-        err = err_p = None
-        if rank == 0:
-            err = surrogate_error(P, torch, oracle, fr, med, opt, src_all, sg, desc_all)
-            err_p = surrogate_error(P, torch, oracle, fr, med, opt, src_all, sgp, desc_all)
-    finally:
-        P.pivbos_surrogate_destroy(sg)
-        P.pivbos_surrogate_destroy(sgp)
-    rays = fr.n_rays
+            err = (surrogate_error(P, torch, oracle, fr, med, opt, src_all, g, desc_all)
+                   if rank == 0 and not args.only else None)
+        finally:
+            P.pivbos_surrogate_destroy(g)
+        r = rep.as_dict()
+        t = ms * 1e-3 / args.steps
+        return {"label": label, "config": {k: v for k, v in cfg_fields.items()},
+                "rays_per_s": rays * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                "gpu_launches": launches, "served_frac": (rays - n_fb) / rays,
+                "served_frac_network": r["val_served_frac_net"], "fallback_rays": int(n_fb),
+                "network_trained": bool(r["network_trained"]), "born_segments": r["born_segments"],
+                "train_seconds": round(train_s, 3), "kernels": kt, "error": err, "report": r, "e2e": e2e,
+                "_t": t}
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if args.only in ("surrogate", "network"):
+        # a profiling capture of one surrogate arm (no line is printed)
+        surrogate_arm(args.only, use_network=-1 if args.only == "surrogate" else 1)
+        clocks.stop()
+        return
+    ms_plain, l_plain, k_plain = timer(plain_step, args.steps, args.warmup, ("render", "sort"))
+    if args.only == "plain":
+        clocks.stop()
+        return
+    img_plain = img.clone() if world > 1 and rank == 0 else None
+    sur = surrogate_arm("surrogate (automatic predictor choice, the default)", with_e2e=True)
+    net = surrogate_arm("network's correction on every served ray", use_network=1)
+    tight = {"budget_px": TIGHT_BUDGET_PX}
+    if not args.no_tight:
+        tight["projection"] = surrogate_arm("projection alone", use_network=0, err_budget_px=TIGHT_BUDGET_PX)
+        tight["surrogate"] = surrogate_arm("automatic predictor choice", err_budget_px=TIGHT_BUDGET_PX)
+    clk = clocks.stop()
+    if world > 1 and rank == 0:
+        # the sharded image is the single-GPU image, bit for bit
+        ref = torch.zeros_like(img)
+        P.pivbos_render(med.h, opt.h, src_all, n_src, fr.rays_per_source, fr.seed, fr.frame_index, fr.integrator,
+                        fr.step, ref)
+        P.pivbos_sync()
+        assert torch.equal(ref, img_plain), "sharded image differs from the single-GPU image"
+    e2e_plain = None
+    if not args.no_e2e:
+        src_h = torch.tensor(fr.sources[lo:hi], dtype=torch.float64).pin_memory()
+        img_h = torch.zeros((H, W), dtype=torch.int64).pin_memory()
+        fimg_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+
+        def e2e_plain_step():
+            # the C ABI copies host sources in and the host image out itself
+            img_h.zero_()
+            P.pivbos_render_range(med.h, opt.h, src_h, hi - lo, lo, fr.rays_per_source, fr.seed, fr.frame_index,
+                                  fr.integrator, fr.step, img_h)
+            if world > 1:
+                img.copy_(img_h, non_blocking=True)
+                reduce()
+                P.pivbos_image_finalize(img, H * W, fimg)
+                fimg_h.copy_(fimg, non_blocking=True)
+
+        e2e_plain = {"value": wall(e2e_plain_step), "unit": "rays/s",
+                     "h2d_bytes_per_step": int(src_h.numel() * 8 + H * W * 8),
+                     "d2h_bytes_per_step": int(H * W * 8 + (H * W * 4 if world > 1 else 0)),
+                     "path": "pivbos_render_range with host sources and a host image (the call copies)"}
     v_plain = rays * args.steps / (ms_plain * 1e-3)
-    v_proj = rays * args.steps / (ms_proj * 1e-3)
-    v_sur = rays * args.steps / (ms_sur * 1e-3)
+    v_sur = sur["rays_per_s"]
     peaks, src_kind = _peaks()
     peak_tf = peaks.get("bf16_tflops", 1900.0)
-    # roofline of the surrogate step's dominant kernel, the network: the
-    # forward's FLOPs for the rays it served, per launch
-    net = k_sur["surrogate_net"]
-    served = rays - n_fb
-    rf = None
-    if net["ms_per_launch"]:
-        per_launch_rays = served / net["launches_per_step"]
-        achieved = per_launch_rays * MLP_FLOP_PER_RAY / (net["ms_per_launch"] * 1e-3) / 1e12
-        rf = {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak_tf, "unit": "TFLOP/s",
-              "frac": round(achieved / peak_tf, 4),
-              "traffic": (recorded_traffic("surrogate_c4_traffic", "surrogate", scale_to_rays=per_launch_rays)
-                          if args.scale == 1.0 and world == 1 else None),
-              "kernel": "surr_net_kernel", "op": "BF16 MLP forward on tcgen05, %d FLOP per served ray"
-                                                  % MLP_FLOP_PER_RAY,
-              "peak_source": "%s bf16_tflops (burst)" % src_kind, "launch_ms": round(net["ms_per_launch"], 3),
-              "rays_per_launch": int(per_launch_rays)}
+    clk_hz = (clk.get("sm_max_mhz") or 2070.0) * 1e6
+
+    def net_roofline(arm):
+        k = arm["kernels"]["surrogate_net"]
+        if not k["ms_per_launch"]:
+            return None
+        served_net = arm["served_frac_network"] * rays / world
+        per_launch = served_net / k["launches_per_step"]
+        achieved = per_launch * MLP_FLOP_PER_RAY / (k["ms_per_launch"] * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": round(achieved / peak_tf, 4),
+                "traffic": (recorded_traffic("surrogate_net_c4_traffic", "surrogate", scale_to_rays=per_launch)
+                            if args.scale == 1.0 and world == 1 else None),
+                "kernel": "surr_net_kernel", "op": "BF16 MLP forward on tcgen05, %d FLOP per ray it corrects"
+                                                   % MLP_FLOP_PER_RAY,
+                "peak_source": "%s bf16_tflops (burst)" % src_kind, "launch_ms": round(k["ms_per_launch"], 3),
+                "rays_per_launch": int(per_launch)}
+
+    def finish_roofline(arm):
+        k = arm["kernels"]["surrogate_finish"]
+        if not k["ms_per_launch"]:
+            return None
+        per_launch = arm["served_frac"] * rays / world / k["launches_per_step"]
+        achieved = per_launch * OPS_FINISH_RAY / (k["ms_per_launch"] * 1e-3) / 1e12
+        peak = N_SM * ISSUE_LANES_PER_SM * clk_hz / 1e12
+        return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": (recorded_traffic("surrogate_finish_c4_traffic", "surrogate", scale_to_rays=per_launch)
+                            if args.scale == 1.0 and world == 1 else None),
+                "kernel": "surr_finish_kernel", "op": "FP32/INT32 lane operation, %d per served ray" % OPS_FINISH_RAY,
+                "peak_source": "issue rate derived from 152 SMs x 128 lanes x max SM clock",
+                "launch_ms": round(k["ms_per_launch"], 3), "rays_per_launch": int(per_launch)}
+
+    for arm in [sur, net] + [tight[k] for k in ("projection", "surrogate") if k in tight]:
+        arm["rooflines"] = {"surr_net_kernel": net_roofline(arm), "surr_finish_kernel": finish_roofline(arm)}
+    # the headline's roofline: the surrogate step's dominant kernel
+    ks = sur["kernels"]
+    dom = max(("surrogate_net", "surrogate_finish", "surrogate_prep"), key=lambda k: ks[k]["ms_per_step"])
+    rf = sur["rooflines"]["surr_net_kernel" if dom == "surrogate_net" else "surr_finish_kernel"]
+    if rf is not None:
+        rf = dict(rf, dominant_kernel_share=round(ks[dom]["ms_per_step"] / sur["ms_per_step"], 4))
     # the plain arm's render kernel: the gather roofline (128 B per field
     # evaluation through L1) and the issue roofline
     msteps = mean_steps(P, fr, opt, med, src_all)
     rk = k_plain["render"]
     rf_plain = None
     if rk["ms_per_launch"]:
-        per_launch = rays / world
         rf_plain = roofline([fr], [msteps], rk["ms_per_launch"], 1, clk.get("sm_max_mhz"),
                             recorded_traffic("render_c4_traffic", "render", rays_per_cta=2048,
-                                             scale_to_rays=per_launch)
+                                             scale_to_rays=rays / world)
                             if args.scale == 1.0 and world == 1 else None,
                             l1_gbs=measured_l1_gbs(P), ray_frac=1.0 / world)
-    # once per density field: medium build + table + data + training
-    t_plain, t_sur = ms_plain * 1e-3 / args.steps, ms_sur * 1e-3 / args.steps
-    t_proj = ms_proj * 1e-3 / args.steps
-    amort = {"medium_build_ms": round(medium_ms, 2), "surrogate_train_seconds": round(train_s, 3),
-             "projection_build_seconds": round(train_p_s, 3),
-             "break_even_images_surrogate": (train_s / (t_plain - t_sur)) if t_plain > t_sur else None,
-             "break_even_images_projection": (train_p_s / (t_plain - t_proj)) if t_plain > t_proj else None,
-             "rays_per_s_one_image_incl_training": rays / (train_s + t_sur),
-             "rays_per_s_ten_images_incl_training": 10 * rays / (train_s + 10 * t_sur),
-             "plain_rays_per_s_one_image_incl_medium": rays / (medium_ms * 1e-3 + t_plain),
-             "note": "the medium build is needed by every arm; the surrogate (table, data, training) is built "
-                     "once per density field and serves every image rendered through that field"}
+    # once per density field: the medium build, and the surrogate's table,
+    # data and (when the network is trained) training
+    t_plain = ms_plain * 1e-3 / args.steps
+    amort = {"medium_build_ms": round(medium_ms, 2)}
+    for name, arm in (("surrogate", sur), ("network", net)):
+        amort[name] = {"build_seconds": arm["train_seconds"],
+                       "break_even_images": (arm["train_seconds"] / (t_plain - arm["_t"])) if t_plain > arm["_t"]
+                       else None,
+                       "rays_per_s_one_image_incl_build": rays / (arm["train_seconds"] + arm["_t"]),
+                       "rays_per_s_ten_images_incl_build": 10 * rays / (arm["train_seconds"] + 10 * arm["_t"])}
+    amort["plain_rays_per_s_one_image_incl_medium"] = rays / (medium_ms * 1e-3 + t_plain)
+    amort["note"] = ("every arm needs the medium; a surrogate is built once per density field and serves every "
+                     "image rendered through that field")
+    for arm in [sur, net] + [tight[k] for k in ("projection", "surrogate") if k in tight]:
+        arm.pop("_t", None)
     c1 = t1 = u16 = None
     if world == 1 and not args.no_table1:
         try:
@@ -936,21 +998,16 @@ def run_c4(args, rank, world):
     if rank == 0:
         out = {
             "metric": METRIC, "value": v_sur, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_sur / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": sur["ms_per_step"], "higher_is_better": True,
             "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
-            "dtype": "bf16 network (f32 accumulation) / f32 projection, optics and integration (double-float pairs "
-                     "for plain-path positions and directions) / int64 image",
+            "dtype": "f32 projection, optics and deposit weights; bf16 network with f32 accumulation where it "
+                     "runs; double-float pairs on the plain path; int64 image",
             "data": "synthetic", "config": config_for(args),
-            "gpu_launches": l_sur, "clocks": clk, "roofline": rf, "e2e": e2e_sur, "cpu_baseline": cpu,
-            "impl": "pivbos",
-            "plain_rays_per_s": v_plain, "surrogate_rays_per_s": v_sur, "projection_rays_per_s": v_proj,
-            "speedup_vs_plain": v_sur / v_plain,
-            "surrogate": {"rays_per_s": v_sur, "ms_per_step": ms_sur / args.steps, "gpu_launches": l_sur,
-                          "served_frac": served / rays, "fallback_rays": int(n_fb), "kernels": k_sur,
-                          "error": err, "report": rep.as_dict(), "e2e": e2e_sur},
-            "projection": {"rays_per_s": v_proj, "ms_per_step": ms_proj / args.steps, "gpu_launches": l_proj,
-                           "served_frac": (rays - n_fb_p) / rays, "fallback_rays": int(n_fb_p), "kernels": k_proj,
-                           "error": err_p, "report": repp.as_dict()},
+            "gpu_launches": sur["gpu_launches"], "clocks": clk, "roofline": rf, "e2e": sur["e2e"],
+            "cpu_baseline": cpu, "impl": "pivbos",
+            "plain_rays_per_s": v_plain, "surrogate_rays_per_s": v_sur, "speedup_vs_plain": v_sur / v_plain,
+            "rms_px_vs_oracle": (sur["error"] or {}).get("rms_px_vs_oracle"),
+            "surrogate": sur, "network": net, "tight_budget": tight,
             "plain": {"rays_per_s": v_plain, "ms_per_step": ms_plain / args.steps, "gpu_launches": l_plain,
                       "kernels": k_plain, "mean_steps_per_ray": msteps, "roofline": rf_plain, "e2e": e2e_plain},
             "per_density_field": amort,
@@ -1375,6 +1432,10 @@ def main():
     ap.add_argument("--workload", default="c4", choices=sorted(WORKLOAD_NAMES))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=("plain", "surrogate", "network"), default=None,
+                    help="C4: run one arm's timed steps and print nothing (profiling captures)")
+    ap.add_argument("--no-tight", action="store_true",
+                    help="skip the tight-budget comparison of the default line")
     ap.add_argument("--no-table1", action="store_true",
                     help="skip the C1, Sec. 4 BOS and 16-bit conversion sub-objects of the default line")
     ap.add_argument("--optics", default="plain", choices=OPTICS_VARIANTS,
