@@ -80,6 +80,9 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+_GRID = [None]   # --grid: a smaller C4 field for profiling captures only
+
+
 def _frames(workload, scale=1.0):
     """The workload's frames; scale < 1 shrinks source and ray counts (used
     only for profiling captures, never for a reported number)."""
@@ -90,7 +93,7 @@ def _frames(workload, scale=1.0):
     if workload == "c2":
         return scenes.c2(scale=scale)
     if workload == "c4":
-        return scenes.c4(scale=scale)
+        return scenes.c4(scale=scale, grid=_GRID[0])
     if workload == "c3":
         return scenes.c3(scale=scale)
     if workload == "table1":
@@ -425,7 +428,8 @@ def config_for(args):
     """The line's config object (both arms print the same one)."""
     wl = args.workload
     if wl == "c4" and not args.surrogate:
-        cfg = {"workload": WORKLOAD_NAMES["c4"] + ("" if args.scale == 1.0 else " (scaled by %g)" % args.scale),
+        cfg = {"workload": WORKLOAD_NAMES["c4"] + ("" if args.scale == 1.0 else " (scaled by %g)" % args.scale)
+               + ("" if not getattr(args, "grid", None) else " (grid %d^3)" % args.grid),
                "name": "c4", "arms": "plain tracer vs surrogate (projection + tcgen05 network, plain fallback) "
                                      "vs projection alone",
                "budget_px_rms": 0.01, "rays_per_step": 0, "l2": "flushed between steps (inputs also > L2)"}
@@ -992,6 +996,12 @@ def run_c4(args, rank, world):
             u16 = measure_image_u16(P, dev)
         except Exception as exc:
             u16 = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    c3 = None
+    if world == 1 and not args.no_batch:
+        try:
+            c3 = measure_batch(args, rank, world, steps=1, warmup=1)
+        except Exception as exc:
+            c3 = {"error": "%s: %s" % (type(exc).__name__, exc)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_subset_rate(fr)
@@ -1018,6 +1028,8 @@ def run_c4(args, rank, world):
             out["table1"] = t1
         if u16 is not None:
             out["image_u16"] = u16
+        if c3 is not None:
+            out["c3"] = c3
         print(json.dumps(out), flush=True)
 
 
@@ -1365,14 +1377,12 @@ def run_table1_line(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
-def run_batch(args, rank, world):
-    """C3: all frames in one persistent launch (CUDA graph replay per step)."""
+def measure_batch(args, rank, world, steps, warmup):
+    """C3: all frames in one persistent launch (CUDA graph replay per step);
+    returns the measurement."""
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1812_05902_gb300 import build as libbuild
-    libbuild.build()
     from paper_1812_05902_gb300 import pivbos as P
     frames = _frames("c3", args.scale)
     for fr in frames:
@@ -1387,40 +1397,37 @@ def run_batch(args, rank, world):
                                   fr.frame_index, fr.seed, fr.step, imgs[-1]))
     batch = P.pivbos_batch_create(descs, scenes.RK4, None)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        P.pivbos_batch_render(batch)
-    P.pivbos_sync()
-    clocks = Clocks(local)
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    launches0 = P.pivbos_kernel_launches()
-    times = []
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        P.pivbos_batch_render(batch)
-        e1.record(stream)
-        times.append((e0, e1))
-    torch.cuda.synchronize()
-    launches = P.pivbos_kernel_launches() - launches0
-    clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in times)
+    try:
+        clocks = Clocks(local)
+        clocks.start()
+        time.sleep(0.3)
+        timer = ArmTimer(P, torch, flush, world)
+        ms, launches, kt = timer(lambda: P.pivbos_batch_render(batch), steps, warmup, ("batch",))
+        clk = clocks.stop()
+    finally:
+        P.pivbos_batch_destroy(batch)
     rays = sum(fr.n_rays for fr in frames)
-    P.pivbos_batch_destroy(batch)
+    return {"workload": WORKLOAD_NAMES["c3"], "name": "c3", "frames": len(frames), "rays_per_step": rays,
+            "value": rays * steps * world / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms / steps,
+            "steps": steps, "warmup": warmup, "gpu_launches": launches, "clocks": clk}
+
+
+def run_batch(args, rank, world):
+    """C3: all frames in one persistent launch (CUDA graph replay per step)."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1812_05902_gb300 import build as libbuild
+    libbuild.build()
+    res = measure_batch(args, rank, world, args.steps, args.warmup)
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": rays * args.steps * world / (ms * 1e-3), "unit": "rays/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": res["value"], "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (double-float f32 pairs for positions/directions)",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAMES["c3"] + ("" if args.scale == 1.0 else " (scaled by %g)" % args.scale),
-                       "name": "c3", "frames": len(frames), "rays_per_step": rays, "l2": "flushed between steps"},
-            "gpu_launches": int(launches), "clocks": clk, "roofline": None, "e2e": None, "cpu_baseline": None,
-            "impl": "pivbos"}), flush=True)
+            "data": "synthetic", "config": dict(config_for(args), frames=res["frames"]),
+            "gpu_launches": res["gpu_launches"], "clocks": res["clocks"], "roofline": None, "e2e": None,
+            "cpu_baseline": None, "impl": "pivbos", "batch": res}), flush=True)
 
 
 def main():
@@ -1432,8 +1439,11 @@ def main():
     ap.add_argument("--workload", default="c4", choices=sorted(WORKLOAD_NAMES))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="C4 field nodes per axis (profiling captures only; default 256)")
     ap.add_argument("--only", choices=("plain", "surrogate", "network"), default=None,
                     help="C4: run one arm's timed steps and print nothing (profiling captures)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the C3 batch sub-object of the default line")
     ap.add_argument("--no-tight", action="store_true",
                     help="skip the tight-budget comparison of the default line")
     ap.add_argument("--no-table1", action="store_true",
@@ -1445,6 +1455,7 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (profiling captures only; the JSON line says so)")
     args = ap.parse_args()
+    _GRID[0] = args.grid
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
