@@ -1,6 +1,8 @@
-// MLP kernels of the surrogate (see mlp.cuh): tensor-core forward, backward
-// (dX and dW per layer) and Adam.  Warp-level BF16 mma.sync m16n8k16 with
-// ldmatrix operand loads from shared memory, FP32 accumulation.
+// MLP kernels of the surrogate (see mlp.cuh): inference and training on
+// tcgen05 (mlp_tc.cuh, mlp_train_tc.cuh), Adam, and the warp-level BF16
+// mma.sync m16n8k16 forward and backward (dX and dW per layer, ldmatrix
+// operand loads from shared memory, FP32 accumulation) that PIVBOS_MLP_TC=0
+// selects instead.
 #include <math.h>
 #include <stdlib.h>
 
@@ -8,6 +10,7 @@
 #include "mlp.cuh"
 #include "mlp_device.cuh"
 #include "mlp_tc.cuh"
+#include "mlp_train_tc.cuh"
 
 namespace pivbos {
 namespace {
@@ -222,9 +225,27 @@ __global__ void mlp_reduce_kernel(const float* __restrict__ partial, int splits,
     grad[e] = s;
 }
 
+// BF16 copies of parameter i = p: the weights [out][in] and, for layers 1-4,
+// transposed [in][out] (the backward's operands).
+__device__ __forceinline__ void store_bf16(int i, float p, __nv_bfloat16* __restrict__ wbf,
+                                           __nv_bfloat16* __restrict__ wbfT)
+{
+    int l = 0;
+    while (l + 1 < kMlpLayers && i >= mlp_w_offset(l + 1)) ++l;
+    const int local = i - mlp_w_offset(l);
+    if (local < mlp_in(l) * mlp_out(l)) {
+        const __nv_bfloat16 b = __float2bfloat16(p);
+        wbf[mlp_wbf_offset(l) + local] = b;
+        if (l > 0 && wbfT) {
+            const int o = local / mlp_in(l), j = local - o * mlp_in(l);
+            wbfT[mlp_wbf_offset(l) + j * mlp_out(l) + o] = b;
+        }
+    }
+}
+
 __global__ void mlp_adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                                const float* __restrict__ g, __nv_bfloat16* __restrict__ wbf, float lr, float bc1,
-                                float bc2)
+                                const float* __restrict__ g, __nv_bfloat16* __restrict__ wbf,
+                                __nv_bfloat16* __restrict__ wbfT, float lr, float bc1, float bc2)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kMlpParams) return;
@@ -235,20 +256,15 @@ __global__ void mlp_adam_kernel(float* __restrict__ p, float* __restrict__ m, fl
     v[i] = vi;
     const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
     p[i] = pi;
-    int l = 0;
-    while (l + 1 < kMlpLayers && i >= mlp_w_offset(l + 1)) ++l;
-    const int local = i - mlp_w_offset(l);
-    if (local < mlp_in(l) * mlp_out(l)) wbf[mlp_wbf_offset(l) + local] = __float2bfloat16(pi);
+    store_bf16(i, pi, wbf, wbfT);
 }
 
-__global__ void mlp_tobf16_kernel(const float* __restrict__ p, __nv_bfloat16* __restrict__ wbf)
+__global__ void mlp_tobf16_kernel(const float* __restrict__ p, __nv_bfloat16* __restrict__ wbf,
+                                  __nv_bfloat16* __restrict__ wbfT)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kMlpParams) return;
-    int l = 0;
-    while (l + 1 < kMlpLayers && i >= mlp_w_offset(l + 1)) ++l;
-    const int local = i - mlp_w_offset(l);
-    if (local < mlp_in(l) * mlp_out(l)) wbf[mlp_wbf_offset(l) + local] = __float2bfloat16(p[i]);
+    store_bf16(i, p[i], wbf, wbfT);
 }
 
 // Inference forward on tcgen05: persistent CTAs of one warpgroup, one
@@ -347,6 +363,7 @@ cudaError_t mlp_alloc(MlpDev& d, int splits)
     if (e == cudaSuccess) e = cudaMalloc(&d.v, sizeof(float) * kMlpParams);
     if (e == cudaSuccess) e = cudaMalloc(&d.grad, sizeof(float) * kMlpParams);
     if (e == cudaSuccess) e = cudaMalloc(&d.wbf, sizeof(__nv_bfloat16) * kMlpWeights);
+    if (e == cudaSuccess) e = cudaMalloc(&d.wbfT, sizeof(__nv_bfloat16) * kMlpWeights);
     if (e == cudaSuccess) e = cudaMalloc(&d.partial, sizeof(float) * (size_t)splits * (kMlpHidden * kMlpHidden + kMlpHidden));
     if (e == cudaSuccess) e = cudaMalloc(&d.status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
@@ -361,6 +378,12 @@ cudaError_t mlp_alloc(MlpDev& d, int splits)
             e = cudaFuncSetAttribute(mlp_dx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dx_smem());
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(mlp_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(mlptr::TrainSmem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mlp_dw_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(mlptr::DwSmem));
     }
     return e;
 }
@@ -374,6 +397,7 @@ void mlp_free(MlpDev& d)
     cudaFree(d.v);
     cudaFree(d.grad);
     cudaFree(d.wbf);
+    cudaFree(d.wbfT);
     cudaFree(d.partial);
     d = MlpDev();
 }
@@ -382,7 +406,10 @@ cudaError_t mlp_work_alloc(MlpWork& w, int max_rows)
 {
     w.max_rows = max_rows;
     cudaError_t e = cudaMalloc(&w.act, sizeof(__nv_bfloat16) * 4 * (size_t)max_rows * kMlpHidden);
-    if (e == cudaSuccess) e = cudaMalloc(&w.dz, sizeof(__nv_bfloat16) * 2 * (size_t)max_rows * kMlpHidden);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&w.dz, sizeof(__nv_bfloat16) * (4 * (size_t)max_rows * kMlpHidden +
+                                                       (size_t)max_rows * mlptr::kDz4));
+    if (e == cudaSuccess) e = cudaMalloc(&w.partial, sizeof(float) * (size_t)kMlpTcSplits * kMlpParams);
     if (e == cudaSuccess) e = cudaMalloc(&w.y, sizeof(float) * (size_t)max_rows * kMlpOut);
     if (e == cudaSuccess) e = cudaMalloc(&w.loss, sizeof(double));
     return e;
@@ -394,12 +421,13 @@ void mlp_work_free(MlpWork& w)
     cudaFree(w.dz);
     cudaFree(w.y);
     cudaFree(w.loss);
+    cudaFree(w.partial);
     w = MlpWork();
 }
 
 cudaError_t mlp_sync_bf16(const MlpDev& d, cudaStream_t s)
 {
-    mlp_tobf16_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(d.params, d.wbf);
+    mlp_tobf16_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(d.params, d.wbf, d.wbfT);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -438,6 +466,21 @@ cudaError_t mlp_forward(const MlpDev& d, const __nv_bfloat16* X, int n, float* Y
 {
     if (n <= 0) return cudaSuccess;
     if (!work && use_tc()) return mlp_forward_tc(d, X, n, Y, s);
+    if (work && use_tc()) {
+        // the tcgen05 training forward; with targets also the loss and the
+        // backward chain (mlp_backward then only forms the weight gradients)
+        if (T) {
+            cudaError_t e = cudaMemsetAsync(work->loss, 0, sizeof(double), s);
+            if (e != cudaSuccess) return e;
+        }
+        const int tiles = (n + mlptc::kRows - 1) / mlptc::kRows;
+        timing_begin("mlp_forward", s);
+        mlp_train_tc_kernel<<<min(sm_count(), tiles), 128, sizeof(mlptr::TrainSmem), s>>>(
+            d.wbf, d.wbfT, d.params, X, n, Y, T, work->act, work->dz, T ? work->loss : nullptr, d.status);
+        timing_end("mlp_forward", s);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const int tiles = (n + 15) / 16;
     const int grid = min(sm_count(), (tiles + 7) / 8);
     if (work && T) {
@@ -456,6 +499,19 @@ cudaError_t mlp_forward(const MlpDev& d, const __nv_bfloat16* X, int n, float* Y
 cudaError_t mlp_backward(MlpDev& d, const __nv_bfloat16* X, int n, MlpWork& w, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
+    if (use_tc()) {
+        // weight gradients of the five layers over row splits, then their sum
+        const int chunks = (n + mlptc::kRows - 1) / mlptc::kRows;
+        const int splits = min(kMlpTcSplits, chunks);
+        const int rows_per_split = (chunks + splits - 1) / splits * mlptc::kRows;
+        timing_begin("mlp_backward", s);
+        mlp_dw_tc_kernel<<<dim3((unsigned)splits, kMlpLayers), 128, sizeof(mlptr::DwSmem), s>>>(
+            X, w.act, w.dz, n, rows_per_split, w.partial, d.status);
+        mlp_reduce_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(w.partial, splits, kMlpParams, d.grad);
+        timing_end("mlp_backward", s);
+        count_launches(2);
+        return cudaGetLastError();
+    }
     const int tiles = (n + 15) / 16;
     const int gx = min(sm_count(), (tiles + 7) / 8);
     const int rows_per_split = ((n + d.splits - 1) / d.splits + 15) / 16 * 16;
@@ -488,7 +544,8 @@ cudaError_t mlp_adam(MlpDev& d, int t, float lr, cudaStream_t s)
     // of it at small t)
     const float bc1 = (float)(1.0 - pow(0.9, (double)t));
     const float bc2 = (float)(1.0 - pow(0.999, (double)t));
-    mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(d.params, d.m, d.v, d.grad, d.wbf, lr, bc1, bc2);
+    mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(d.params, d.m, d.v, d.grad, d.wbf, d.wbfT, lr, bc1,
+                                                             bc2);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1,6 +1,8 @@
 // The surrogate's MLP: 16 inputs -> 128 -> 128 -> 128 -> 128 -> 4, ReLU on the
 // hidden layers, BF16 operands with FP32 accumulation on the tensor cores
-// (warp-level mma.sync m16n8k16), FP32 master weights and Adam.
+// (tcgen05 for inference and training; the warp-level mma.sync kernels
+// remain as the alternative PIVBOS_MLP_TC=0 selects), FP32 master weights
+// and Adam.
 //
 // Parameter layout (FP32 master and gradients): layer by layer, W [out][in]
 // row-major then b [out].  BF16 copies of the weights keep [out][in].
@@ -41,6 +43,7 @@ struct MlpDev {
     float* v = nullptr;            // Adam second moment
     float* grad = nullptr;         // [kMlpParams]
     __nv_bfloat16* wbf = nullptr;  // BF16 weights [kMlpWeights]
+    __nv_bfloat16* wbfT = nullptr; // the same, each layer transposed ([in][out]): the backward's operands
     float* partial = nullptr;      // dW/db partial sums [splits][max layer params]
     int splits = 0;
     int* status = nullptr;         // device word: nonzero after a tensor-core wait gave up
@@ -49,11 +52,15 @@ struct MlpDev {
 // Training workspace for batches of up to max_rows rows.
 struct MlpWork {
     __nv_bfloat16* act = nullptr;  // hidden-layer outputs H1..H4 [4][rows][128]
-    __nv_bfloat16* dz = nullptr;   // two gradient buffers [2][rows][128]
+    __nv_bfloat16* dz = nullptr;   // gradients: dZ of the hidden layers [4][rows][128], then dZ of the
+                                   // output layer [rows][16] (the mma.sync path uses the first two planes)
     float* y = nullptr;            // outputs [rows][4]
     double* loss = nullptr;        // loss sum
+    float* partial = nullptr;      // tcgen05 weight gradients per split [kMlpTcSplits][kMlpParams]
     int max_rows = 0;
 };
+
+constexpr int kMlpTcSplits = 32;   // row splits of the tcgen05 weight-gradient kernel
 
 cudaError_t mlp_alloc(MlpDev& d, int splits);
 void mlp_free(MlpDev& d);

@@ -1,8 +1,9 @@
 """The surrogate network's GPU kernels against the FP64 reference
 (oracle/mlp.py), element by element, through the testing library's hooks
-(include/pivbos_testing.h): the tensor-core inference forward, the training
-forward, the backward's gradients, the Adam step, and the network kernel of
-the surrogate render itself (biases carried through the tensor core).
+(include/pivbos_testing.h): the tcgen05 inference forward, the tcgen05
+training step (forward, loss, backward chain and weight gradients), the Adam
+step, and the network kernel of the surrogate render itself (biases carried
+through the tensor core).
 
 Inputs and weights are BF16-representable.  The reference that stores the
 hidden activations and back-propagated gradients in BF16 at the same points
@@ -94,10 +95,12 @@ def test_forward_loss_and_gradients_per_element(n):
     y_inf = P.pivbos_mlp_forward(p, x)
     y_tr = P.pivbos_mlp_train_forward(p, x)
     loss, g = P.pivbos_mlp_loss_grad(p, x, t)
-    y_ref, _ = mlp.forward(p, x, bf16=True)
-    y_ref_split, _ = mlp.forward(_split_bias_params(p), x, bf16=True)
-    loss_ref, g_ref = mlp.loss_and_grad(p, x, t, bf16=True)
-    errs = {"y_inference": _per_element(y_inf, y_ref_split, OUT_RTOL, "inference forward", OUT_FLIP),
+    # both forwards carry each bias through the tensor core as a BF16
+    # leading part and remainder: the network they evaluate has those biases
+    ps = _split_bias_params(p)
+    y_ref, _ = mlp.forward(ps, x, bf16=True)
+    loss_ref, g_ref = mlp.loss_and_grad(ps, x, t, bf16=True)
+    errs = {"y_inference": _per_element(y_inf, y_ref, OUT_RTOL, "inference forward", OUT_FLIP),
             "y_training": _per_element(y_tr, y_ref, OUT_RTOL, "training forward", OUT_FLIP),
             "loss": abs(loss - loss_ref) / loss_ref}
     assert errs["loss"] <= 1e-4, errs
