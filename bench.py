@@ -209,7 +209,8 @@ def recorded_traffic(record, kind="render", rays_per_cta=None, scale_to_rays=Non
     A record taken on a smaller launch (its rays_per_launch) is scaled to
     scale_to_rays rays in proportion (the field and image parts of the
     traffic do not grow with the rays, so the scaled figure is an upper
-    bound)."""
+    bound), unless the record says its traffic is the launch's fixed part
+    (scales_with_rays false: used as it is)."""
     try:
         with open(os.path.join(ROOT, "profiles", record + ".json")) as f:
             rec = json.load(f)
@@ -220,7 +221,7 @@ def recorded_traffic(record, kind="render", rays_per_cta=None, scale_to_rays=Non
     if rays_per_cta is not None and rec.get("rays_per_cta", rays_per_cta) != rays_per_cta:
         return None
     b = float(rec["dram_bytes_read"] + rec["dram_bytes_write"])
-    if scale_to_rays and rec.get("rays_per_launch"):
+    if scale_to_rays and rec.get("rays_per_launch") and rec.get("scales_with_rays", True):
         b *= scale_to_rays / float(rec["rays_per_launch"])
     return int(b)
 

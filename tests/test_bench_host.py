@@ -124,3 +124,18 @@ def test_roofline_of_a_sharded_launch():
     half = bench.roofline([fr], [100.0], 5.0, 1, 2000.0, l1_gbs=30000.0, ray_frac=0.5)
     assert half["achieved"] == pytest.approx(whole["achieved"], rel=1e-3)
     assert half["rays_per_launch"] == whole["rays_per_launch"] // 2
+
+
+def test_traffic_record_of_a_fixed_part_is_not_scaled(tmp_path, monkeypatch):
+    rec = {"source_hash": bench.kernel_source_hash("render"), "dram_bytes_read": 300, "dram_bytes_write": 100,
+           "rays_per_launch": 1000, "scales_with_rays": False}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "t.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc = tmp_path / "paper_1812_05902_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in bench.KERNEL_SOURCES["render"]:
+        (csrc / name).write_bytes(open(os.path.join(os.path.dirname(bench.__file__), "paper_1812_05902_gb300",
+                                                    "csrc", name), "rb").read())
+    assert bench.recorded_traffic("t", scale_to_rays=5000) == 400
