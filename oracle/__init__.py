@@ -36,7 +36,7 @@ REACHED, KILLED_STOP, KILLED_MISS, KILLED_TIR, KILLED_OFF_SENSOR, KILLED_MAXSTEP
 RAY_STATE = np.dtype([
     ("vol_pos", "<f8", (3,)), ("vol_dir", "<f8", (3,)),
     ("sensor_xy", "<f8", (2,)), ("sensor_dir", "<f8", (3,)),
-    ("status", "<i4"), ("steps", "<i4"),
+    ("status", "<i4"), ("steps", "<i4"), ("opl", "<f8"),
 ])
 
 

@@ -276,6 +276,7 @@ typedef struct {
     double sensor_xy[2];
     double sensor_dir[3];
     int32_t status, steps;
+    double opl;   /* optical path inside the box, integral of n ds (0 if the ray never enters it) */
 } om_ray_state;
 
 /* Eq. 8 as printed (rule 0: 2.44 pi f# (M+1) lambda) or the textbook Airy
@@ -504,6 +505,7 @@ int om_trace_optics(const om_optics *o, const double P[3], const double d_in[3],
     double R[3] = { P[0], P[1], P[2] }, d[3] = { d_in[0], d_in[1], d_in[2] };
     for (int a = 0; a < 3; ++a) { out->vol_pos[a] = P[a]; out->vol_dir[a] = d_in[a]; }
     out->steps = 0;
+    out->opl = 0.0;
     return om_optics_to_sensor(o, R, d, OM_REACHED, out);
 }
 
@@ -513,6 +515,13 @@ int om_trace(const om_medium *m, const om_optics *o, const double src[3],
 {
     double R[3], d[3], p[3];
     int status = OM_REACHED, steps = 0;
+    /* Reading of the task's "path-length accumulation across the volume": the
+     * optical path inside the box, integral of n ds.  With Sharma's parameter
+     * (dt = ds / n, so ds = n dt) it is the integral of n^2 dt, taken along
+     * the integrated path: Simpson's rule on the Runge-Kutta stage points
+     * (t, t + h/2, t + h) for Eqs. 3-5, the left rule for the first-order
+     * scheme. */
+    double opl = 0.0;
 
     /* Sec. 3.1: origin = source, direction = unit vector to the lens point */
     om_lens_point(seed, source_id, ray_id, frame, o->aim_r, o->aim_z, p);
@@ -571,15 +580,20 @@ int om_trace(const om_medium *m, const om_optics *o, const double src[3],
                 if (step >= dexit) { h = dexit > 0.0 ? dexit : 0.0; done = 1; }
                 if (integrator == OM_RK4) {
                     /* Eqs. 3 and 5 (Sharma et al.'s Runge-Kutta-Nystrom step) */
-                    double A[3], B[3], C[3], X[3];
+                    double A[3], B[3], C[3], X[3], nA, nB, nC, gq[3];
                     om_D(m, R, A);
+                    om_sample(m, R, &nA, gq);
                     for (int a = 0; a < 3; ++a) A[a] *= h;
                     for (int a = 0; a < 3; ++a) X[a] = R[a] + (0.5 * T[a] + A[a] / 8.0) * h;
                     om_D(m, X, B);
+                    om_sample(m, X, &nB, gq);
                     for (int a = 0; a < 3; ++a) B[a] *= h;
                     for (int a = 0; a < 3; ++a) X[a] = R[a] + (T[a] + 0.5 * B[a]) * h;
                     om_D(m, X, C);
+                    om_sample(m, X, &nC, gq);
                     for (int a = 0; a < 3; ++a) C[a] *= h;
+                    nA += 1.0; nB += 1.0; nC += 1.0;
+                    opl += h / 6.0 * (nA * nA + 4.0 * nB * nB + nC * nC);
                     for (int a = 0; a < 3; ++a) {
                         R[a] = R[a] + (T[a] + (A[a] + 2.0 * B[a]) / 6.0) * h;
                         T[a] = T[a] + (A[a] + 4.0 * B[a] + C[a]) / 6.0;
@@ -587,8 +601,11 @@ int om_trace(const om_medium *m, const om_optics *o, const double src[3],
                 } else {
                     /* first-order (piecewise-linear) scheme: both updates from
                      * the state at the start of the step */
-                    double Dv[3];
+                    double Dv[3], nA, gq[3];
                     om_D(m, R, Dv);
+                    om_sample(m, R, &nA, gq);
+                    nA += 1.0;
+                    opl += h * nA * nA;
                     for (int a = 0; a < 3; ++a) {
                         R[a] = R[a] + T[a] * h;
                         T[a] = T[a] + Dv[a] * h;
@@ -604,6 +621,7 @@ int om_trace(const om_medium *m, const om_optics *o, const double src[3],
     if (out) {
         for (int a = 0; a < 3; ++a) { out->vol_pos[a] = R[a]; out->vol_dir[a] = d[a]; }
         out->steps = steps;
+        out->opl = opl;
     }
 
     return om_optics_to_sensor(o, R, d, status, out);

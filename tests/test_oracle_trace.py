@@ -191,3 +191,92 @@ def test_max_step_budget_kills():
     # a ray running almost parallel to the faces inside a long box would need
     # more than the budget only if the budget were wrong; check the formula
     assert med.max_steps(1e-3) == math.ceil(2 * math.sqrt(sum(x * x for x in L)) / 1e-3) + 4
+
+
+def _sinh_minus_x(x):
+    """sinh(x) - x without cancellation for small x."""
+    if abs(x) < 0.1:
+        x2 = x * x
+        return x * x2 / 6.0 * (1.0 + x2 / 20.0 * (1.0 + x2 / 42.0 * (1.0 + x2 / 72.0)))
+    return math.sinh(x) - x
+
+
+def _closed_form_opl(src, d0, n_nodes_y, o, h, L):
+    """Optical path of the exact slab ray inside the box: the integral of
+    n ds = n^2 dt (dt = ds/n) with n = g Y, Y(t) = a cosh(gt) + b sinh(gt),
+    a = n(y0)/g, b = T_y0/g:
+    n(y0)^2 (t/2 + sinh(2gt)/(4g)) + n(y0) T_y0 sinh(gt)^2/g + T_y0^2 (sinh(2gt) - 2gt)/(4g^2) * g."""
+    ny = len(n_nodes_y)
+    y_nodes = o[1] + h[1] * np.arange(ny)
+    g, c = np.polyfit(y_nodes, n_nodes_y, 1)
+    n_src = 1.0 + c + g * src[1]
+    T0 = n_src * d0
+    t = (o[2] + L[2] - src[2]) / T0[2]
+    x = 2.0 * g * t
+    return (n_src ** 2 * (0.5 * t + (x + _sinh_minus_x(x)) / (4.0 * g))
+            + n_src * T0[1] * math.sinh(g * t) ** 2 / g
+            + T0[1] ** 2 * _sinh_minus_x(x) / (4.0 * g))
+
+
+def test_optical_path_in_a_uniform_medium_is_n_times_the_length():
+    """n constant: the ray is straight and its optical path inside the box is
+    n times the distance from its entry to its exit (both schemes, any step)."""
+    rho = scenes.uniform_rho(8, 9, 10, 1.3)
+    K = 0.225e-3
+    n = 1.0 + K * float(np.float32(1.3))
+    med = oracle.Medium(rho, (-0.02, -0.02, 0.3), (0.04 / 7, 0.04 / 8, 0.05 / 9), K)
+    opt = _far_sensor_optics(1.0, 0.01)
+    src = np.array([0.001, -0.002, 0.0])
+    for integ in (oracle.EULER, oracle.RK4):
+        for k in range(10):
+            st = oracle.trace(med, opt, src, 3, 0, k, 0, integ, 0.37e-3)
+            p = oracle.lens_point(3, 0, k, 0, 0.01, 1.0)
+            d = (p - src) / np.linalg.norm(p - src)
+            entry = src + (0.3 - src[2]) / d[2] * d
+            length = np.linalg.norm(st["vol_pos"] - entry)
+            # the rounding of the position accumulated at z ~ 0.3 m, which the
+            # clipped last step turns into the summed parameter: ~2^-53 |z| a step
+            tol = 4.0 * st["steps"] * 2.0 ** -53 * abs(st["vol_pos"][2])
+            assert abs(st["opl"] - n * length) <= tol, (st["opl"], n * length, tol)
+    # a ray that never enters the box has no optical path inside it
+    st = oracle.trace(med, opt, np.array([0.5, 0.5, 0.0]), 3, 0, 0, 0, oracle.RK4, 0.37e-3)
+    assert st["steps"] == 0 and st["opl"] == 0.0
+
+
+def test_optical_path_in_a_linear_slab_closed_form_and_order():
+    """The optical path against the closed form of the exact arc: fourth order
+    for Eqs. 3-5 with Simpson's rule on their stage points, first order for
+    the first-order scheme; to rounding at the workload's weak gradient."""
+    g = 20.0
+    med, o, L, h, rr = _slab(g, 1.6, exact_nodes=True)
+    opt = _far_sensor_optics(0.3, 0.004)
+    src = np.array([0.002, -0.003, 1e-12])
+    errs = {}
+    for integ in (oracle.RK4, oracle.EULER):
+        for step in (L[2] / 8, L[2] / 16, L[2] / 32, L[2] / 64):
+            e = []
+            for k in range(6):
+                st = oracle.trace(med, opt, src, 11, 0, k, 0, integ, step)
+                p = oracle.lens_point(11, 0, k, 0, 0.004, 0.3)
+                d0 = (p - src) / np.linalg.norm(p - src)
+                e.append(abs(st["opl"] - _closed_form_opl(src, d0, rr, o, h, L)))
+            errs[(integ, step)] = max(e)
+    r4 = [errs[(oracle.RK4, L[2] / 2**k)] / errs[(oracle.RK4, L[2] / 2**(k + 1))] for k in (3, 4, 5)]
+    r1 = [errs[(oracle.EULER, L[2] / 2**k)] / errs[(oracle.EULER, L[2] / 2**(k + 1))] for k in (3, 4, 5)]
+    for r in r4:
+        assert 12.0 < r < 20.0, r4
+    for r in r1:
+        assert 1.7 < r < 2.3, r1
+    # the workload's gradient: RK4 with Simpson's rule matches to rounding
+    med, o, L, h, rr = _slab(2.7e-4, 1.00027, L=(0.05, 0.05, 0.01), N=(32, 32, 32), z0=0.495,
+                             exact_nodes=True)
+    opt = _far_sensor_optics(1.155, 0.0065)
+    src = np.array([0.004, 0.006, 0.0])
+    for k in range(10):
+        st = oracle.trace(med, opt, src, 0, 5, k, 0, oracle.RK4, 0.2e-3)
+        p = oracle.lens_point(0, 5, k, 0, 0.0065, 1.155)
+        d0 = (p - src) / np.linalg.norm(p - src)
+        entry = src + (o[2] - src[2]) / d0[2] * d0
+        ref = _closed_form_opl(entry, d0, rr, o, h, L)
+        tol = 4.0 * st["steps"] * 2.0 ** -53 * abs(st["vol_pos"][2])   # as in the uniform medium
+        assert abs(st["opl"] - ref) <= tol, (st["opl"], ref, tol)
