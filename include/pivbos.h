@@ -94,7 +94,7 @@ typedef struct {
     double clear_radius;   /* m, clear (or stop) radius */
 } pivbos_surface;
 
-/* Per-ray result of pivbos_trace_exit_states (96 bytes, naturally aligned). */
+/* Per-ray result of pivbos_trace_exit_states (104 bytes, naturally aligned). */
 typedef struct {
     double vol_pos[3];     /* where the ray left the density box (its source if it never entered) */
     double vol_dir[3];     /* unit direction there */
@@ -102,6 +102,10 @@ typedef struct {
     double sensor_dir[3];  /* unit direction at the sensor plane */
     int32_t status;        /* PIVBOS_RAY_* */
     int32_t steps;         /* integration steps taken inside the box */
+    double opl;            /* optical path inside the box, integral of n ds (m): the integral of n^2 dt in
+                              the parameter of Eqs. 3-5, by Simpson's rule on the RK4 stage points (the left
+                              rule for the first-order scheme), summed in double-float; 0 if the ray never
+                              enters the box */
 } pivbos_ray_state;
 
 typedef struct pivbos_medium pivbos_medium;

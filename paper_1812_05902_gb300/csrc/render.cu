@@ -33,6 +33,7 @@ trace_states_kernel(const TraceParams P, const int64_t* __restrict__ ray_ids, in
         st.sensor_xy[0] = st.sensor_xy[1] = 0.0;
         st.status = PIVBOS_RAY_MISS;
         st.steps = 0;
+        st.opl = 0.0;
         atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_INVALID_ARG);
     } else {
         const uint32_t sid = (uint32_t)(id / rps), k = (uint32_t)(id - (int64_t)sid * rps);

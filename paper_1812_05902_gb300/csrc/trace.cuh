@@ -136,9 +136,10 @@ struct CellCache<true> {
 
 // D = n grad n (Eq. 6) from the trilinear samples of n - 1 and grad n at the
 // grid point gh + gl (see cell_split), written as the weighted sum of the
-// eight corner values, w = (1-fx or fx)(1-fy or fy)(1-fz or fz).
+// eight corner values, w = (1-fx or fx)(1-fy or fy)(1-fz or fz).  The fourth
+// component is the sampled n - 1 (for the optical path; unused otherwise).
 template <bool CACHE>
-__device__ __forceinline__ float3 eval_D_split(const DevMedium& m, CellCache<CACHE>& cc, float hx, float lx, float hy,
+__device__ __forceinline__ float4 eval_D_split(const DevMedium& m, CellCache<CACHE>& cc, float hx, float lx, float hy,
                                                float ly, float hz, float lz)
 {
     int i, j, k;
@@ -182,7 +183,7 @@ __device__ __forceinline__ float3 eval_D_split(const DevMedium& m, CellCache<CAC
         v.w = fmaf(w[q], c[q].w, v.w);
     }
     const float n = 1.0f + v.x;
-    return make_float3(n * v.y, n * v.z, n * v.w);
+    return make_float4(n * v.y, n * v.z, n * v.w, v.x);
 }
 
 struct RayOut {
@@ -504,6 +505,7 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
     int status = PIVBOS_RAY_REACHED;
     int steps = 0;
     out.w = 1.0f;
+    if (st) st->opl = 0.0;
     if constexpr (EXT) {
         if (o.rad_mode) out.w = ray_radiance(o, dx.hi, dy.hi, dz.hi);
     }
@@ -522,9 +524,11 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
             df grx = df_mul(df_sub(R0x, dfk(m.origin[0])), ihx);
             df gry = df_mul(df_sub(R0y, dfk(m.origin[1])), ihy);
             df grz = df_mul(df_sub(R0z, dfk(m.origin[2])), ihz);
-            const float n0 = 1.0f + sample_field(m, grx.hi + grx.lo, gry.hi + gry.lo, grz.hi + grz.lo).x;
+            // n at the entry as double-float (1 + dn in FP32 would round the
+            // tangent's length, hence the ray's parameter, by ~6e-8)
+            const df n0 = df_add_f(dfv(1.0f), sample_field(m, grx.hi + grx.lo, gry.hi + gry.lo, grz.hi + grz.lo).x);
             // reading: no refraction at the faces; T = n d at the entry
-            const df T0x = df_mul_f(dx, n0), T0y = df_mul_f(dy, n0), T0z = df_mul_f(dz, n0);
+            const df T0x = df_mul(dx, n0), T0y = df_mul(dy, n0), T0z = df_mul(dz, n0);
             const df dGx = df_mul(df_mul(T0x, ihx), dfk(P.step_df));
             const df dGy = df_mul(df_mul(T0y, ihy), dfk(P.step_df));
             const df dGz = df_mul(df_mul(T0z, ihz), dfk(P.step_df));
@@ -535,6 +539,11 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
             const float hstep = P.step;
             const float ex = (float)(m.n[0] - 1), ey = (float)(m.n[1] - 1), ez = (float)(m.n[2] - 1);
             float h_last = 0.f;
+            // optical path inside the box (exit states only): the integral of
+            // n^2 dt = the parameter run plus the integral of n^2 - 1, the
+            // latter by the stage weights (Simpson on the RK4 stage points,
+            // the left rule for the first-order scheme), summed in double-float
+            df opl_rest = dfv(0.f);
             int k = 0;
             bool done = false;
             CellCache<CACHE> cache;
@@ -559,6 +568,7 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
                 // First-order scheme: one stage, rho += tau h, tau += A.
                 float sRx = 0.f, sRy = 0.f, sRz = 0.f;   // sum of wR * K
                 float sTx = 0.f, sTy = 0.f, sTz = 0.f;   // sum of wT * K
+                float sQ = 0.f;                           // sum of wT * (n^2 - 1)
                 float kx = 0.f, ky = 0.f, kz = 0.f;      // K of the previous stage
                 constexpr int kStages = INTEG == PIVBOS_RK4 ? 3 : 1;
 #pragma unroll
@@ -568,7 +578,7 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
                     const float px = (cT * Tx + cK * kx) * h;
                     const float py = (cT * Ty + cK * ky) * h;
                     const float pz = (cT * Tz + cK * kz) * h;
-                    const float3 Dv = eval_D_split<CACHE>(m, cache, grx.hi, fmaf(px, ix, ox), gry.hi,
+                    const float4 Dv = eval_D_split<CACHE>(m, cache, grx.hi, fmaf(px, ix, ox), gry.hi,
                                                           fmaf(py, iy, oy), grz.hi, fmaf(pz, iz, oz));
                     kx = Dv.x * h;
                     ky = Dv.y * h;
@@ -577,7 +587,9 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
                     const float wT = INTEG == PIVBOS_RK4 ? (sg == 1 ? 4.f / 6.f : 1.f / 6.f) : 1.f;
                     sRx = fmaf(wR, kx, sRx); sRy = fmaf(wR, ky, sRy); sRz = fmaf(wR, kz, sRz);
                     sTx = fmaf(wT, kx, sTx); sTy = fmaf(wT, ky, sTy); sTz = fmaf(wT, kz, sTz);
+                    if (st) sQ = fmaf(wT, Dv.w * (2.0f + Dv.w), sQ);   // n^2 - 1 = dn (2 + dn)
                 }
+                if (st) opl_rest = df_add_f(opl_rest, sQ * h);
                 rhx = fmaf(tax + sRx, h, rhx);
                 rhy = fmaf(tay + sRy, h, rhy);
                 rhz = fmaf(taz + sRz, h, rhz);
@@ -595,6 +607,7 @@ __device__ __forceinline__ void trace_ray(const TraceParams& P, df sx, df sy, df
             steps = done ? k + 1 : k;
             if (!done) status = PIVBOS_RAY_MAXSTEP;
             const df t_exit = df_add_f(df_mul_f(dfk(P.step_df), (float)k), h_last);
+            if (st) st->opl = df_to_double(df_add(t_exit, opl_rest));
             Rx = df_add_f(df_add(R0x, df_mul(T0x, t_exit)), rhx);
             Ry = df_add_f(df_add(R0y, df_mul(T0y, t_exit)), rhy);
             Rz = df_add_f(df_add(R0z, df_mul(T0z, t_exit)), rhz);

@@ -29,9 +29,9 @@ MAX_WINDOW = 12
 RAY_STATE = np.dtype([
     ("vol_pos", "<f8", (3,)), ("vol_dir", "<f8", (3,)),
     ("sensor_xy", "<f8", (2,)), ("sensor_dir", "<f8", (3,)),
-    ("status", "<i4"), ("steps", "<i4"),
+    ("status", "<i4"), ("steps", "<i4"), ("opl", "<f8"),
 ])
-assert RAY_STATE.itemsize == 96
+assert RAY_STATE.itemsize == 104
 
 
 class pivbos_surface(ctypes.Structure):

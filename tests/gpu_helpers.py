@@ -12,6 +12,9 @@ from paper_1812_05902_gb300 import scenes
 TOL_PX = 1e-5       # sensor position, pixels
 TOL_RAD = 1e-6      # direction, radians
 TOL_IMG = 1e-4      # image, relative L2
+# optical path inside the box (m): the GPU's last, clipped step is an FP32
+# parameter (~1e-11 m of path); the integral is summed in double-float
+TOL_OPL = 1e-10
 
 
 def torch_cuda():
@@ -102,6 +105,11 @@ def compare_states(g, o, pitch, vol_scale, max_status_mismatch_frac=2e-4, label=
     steps_same = same & (o["steps"] > 0)
     if np.any(steps_same):
         res["steps_diff"] = int(np.max(np.abs(g["steps"][steps_same] - o["steps"][steps_same])))
+    if "opl" in (g.dtype.names or ()) and "opl" in (o.dtype.names or ()):
+        # rays whose step counts agree (a clipped last step decided the other
+        # way changes the path by up to a step)
+        ok = same & (g["steps"] == o["steps"])
+        res["opl_m"] = float(np.max(np.abs(g["opl"][ok] - o["opl"][ok]))) if np.any(ok) else 0.0
     _log("states", res)
     if exact:
         assert res["status_mismatch"] == 0, res
@@ -114,6 +122,8 @@ def compare_states(g, o, pitch, vol_scale, max_status_mismatch_frac=2e-4, label=
         assert res["sensor_angle"] <= TOL_RAD, res
     if "steps_diff" in res:
         assert res["steps_diff"] <= 1, res
+    if "opl_m" in res:
+        assert res["opl_m"] <= TOL_OPL, res
     return res
 
 
