@@ -775,69 +775,98 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
                    int64_t* __restrict__ image, int64_t* __restrict__ stats, unsigned long long* __restrict__ counter)
 {
     __shared__ unsigned long long tile[kTileW * kTileH];
-    __shared__ unsigned long long s_item;
-    __shared__ int anchor_tid, sax, say;
-    const int tid = threadIdx.x;
+    __shared__ unsigned long long s_item[2];
+    __shared__ int w_ok[8], w_ax[8], w_ay[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const uint64_t n = min(*sv.count, (unsigned long long)sv.capacity);
     const uint64_t items = (n + 255) / 256;
     unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
-    for (;;) {
-        if (tid == 0) {
-            s_item = atomicAdd(counter, 1ull);
-            anchor_tid = 0x7fffffff;
-        }
-        for (int q = tid; q < kTileW * kTileH; q += blockDim.x) tile[q] = 0ull;
-        __syncthreads();
-        const uint64_t it = s_item;
-        if (it >= items) break;
+    // this thread's entry of an item: the straight line from the prep kernel
+    // and the residual (none for a ray that never enters the box)
+    struct Entry4 {
+        float4 l, r;
+        bool active;
+    };
+    auto fetch = [&](uint64_t it, Entry4& e) {
         const uint64_t pos = it * 256 + tid;
+        e.active = it < items && pos < n;
+        e.l = make_float4(0.f, 0.f, 0.f, 0.f);
+        e.r = e.l;
+        if (e.active) {
+            e.l = __ldcs(sv.L + pos);
+            if (!(__ldcs(sv.ids + pos) & kStraightBit)) e.r = __ldcs(resid + pos);
+        }
+    };
+    if (tid == 0) s_item[0] = atomicAdd(counter, 1ull);
+    for (int q = tid; q < kTileW * kTileH; q += blockDim.x) tile[q] = 0ull;
+    __syncthreads();
+    int buf = 0;
+    uint64_t it = s_item[0];
+    Entry4 cur;
+    fetch(it, cur);
+    // Three barriers per item: the anchors (and the next item) are known, the
+    // deposits are in the tile, the tile is flushed and clear again.  The
+    // next item's entries load while this one deposits.
+    while (it < items) {
+        if (tid == 0) s_item[buf ^ 1] = atomicAdd(counter, 1ull);
         RayOut r;
         r.status = PIVBOS_RAY_MISS;
-        const bool active = pos < n;
-        if (active) {
-            // the straight line from the prep kernel, plus the residual (none
-            // for a ray that never enters the box)
-            const float4 l = __ldcs(sv.L + pos);
-            float res[4] = {0.f, 0.f, 0.f, 0.f};
-            if (!(__ldcs(sv.ids + pos) & kStraightBit)) {
-                const float4 rv = __ldcs(resid + pos);
-                res[0] = rv.x; res[1] = rv.y; res[2] = rv.z; res[3] = rv.w;
-            }
+        int fx = 0, fy = 0;
+        if (cur.active) {
+            const float res[4] = {cur.r.x, cur.r.y, cur.r.z, cur.r.w};
             r.status = PIVBOS_RAY_REACHED;
-            surr_sensor<EXT>(P.o, S, l.x, l.y, l.z, l.w, res, r.status, r.px, r.py);
+            surr_sensor<EXT>(P.o, S, cur.l.x, cur.l.y, cur.l.z, cur.l.w, res, r.status, r.px, r.py);
             r.w = 1.0f;
             if constexpr (EXT) {
                 // the ray's radiance from its direction at the source: the
                 // straight line's slopes
                 if (P.o.rad_mode) {
-                    const float inn = rsqrtf(fmaf(l.z, l.z, fmaf(l.w, l.w, 1.0f)));
-                    r.w = ray_radiance(P.o, l.z * inn, l.w * inn, inn);
+                    const float inn = rsqrtf(fmaf(cur.l.z, cur.l.z, fmaf(cur.l.w, cur.l.w, 1.0f)));
+                    r.w = ray_radiance(P.o, cur.l.z * inn, cur.l.w * inn, inn);
                 }
             }
             cnt[r.status]++;
-            if (r.status == PIVBOS_RAY_REACHED) atomicMin(&anchor_tid, tid);
+            if (r.status == PIVBOS_RAY_REACHED) {
+                float f;
+                fx = df_floor(r.px, f) - kTileW / 2;
+                fy = df_floor(r.py, f) - kTileH / 2;
+            }
+        }
+        // the tile's anchor: the first ray that reaches the sensor, in thread order
+        const bool reached = cur.active && r.status == PIVBOS_RAY_REACHED;
+        const unsigned dep = __ballot_sync(0xffffffffu, reached);
+        const int leader = dep ? __ffs(dep) - 1 : 0;
+        const int lx = __shfl_sync(0xffffffffu, fx, leader), ly = __shfl_sync(0xffffffffu, fy, leader);
+        if (lane == 0) {
+            w_ok[warp] = dep != 0;
+            w_ax[warp] = lx;
+            w_ay[warp] = ly;
         }
         __syncthreads();
-        if (tid == anchor_tid) {
-            float f;
-            sax = df_floor(r.px, f) - kTileW / 2;
-            say = df_floor(r.py, f) - kTileH / 2;
-        }
-        __syncthreads();
-        const int ax = anchor_tid == 0x7fffffff ? -(1 << 28) : sax;
-        const int ay = anchor_tid == 0x7fffffff ? -(1 << 28) : say;
-        const unsigned dep = __ballot_sync(0xffffffffu, active && r.status == PIVBOS_RAY_REACHED);
-        if (active && r.status == PIVBOS_RAY_REACHED)
-            deposit_ray<EXT>(P.o, r.px, r.py, tile, ax, ay, image, r.w, dep);
+        int ax = -(1 << 28), ay = -(1 << 28);
+        for (int w = 0; w < nw; ++w)
+            if (w_ok[w]) {
+                ax = w_ax[w];
+                ay = w_ay[w];
+                break;
+            }
+        const uint64_t it_next = s_item[buf ^ 1];
+        Entry4 nxt;
+        fetch(it_next, nxt);
+        if (reached) deposit_ray<EXT>(P.o, r.px, r.py, tile, ax, ay, image, r.w, dep);
         __syncthreads();
         for (int q = tid; q < kTileW * kTileH; q += blockDim.x) {
             const unsigned long long v = tile[q];
             if (v) {
+                tile[q] = 0ull;
                 const int gx = ax + (q % kTileW), gy = ay + (q / kTileW);
                 atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * P.o.W + gx]), v);
             }
         }
         __syncthreads();
+        it = it_next;
+        cur = nxt;
+        buf ^= 1;
     }
     if (stats) {
 #pragma unroll
