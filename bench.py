@@ -744,6 +744,13 @@ def surrogate_error(P, torch, oracle, fr, med, opt, src, sg, desc, n_plain=1_000
 # (two spheres 2 x 130, the stop 20), the sensor plane (125), the spot
 # deposit (450), list reads and bookkeeping (20)
 OPS_FINISH_RAY = 40 + 2 * 130 + 20 + 125 + 450 + 20
+# ... and per ray of the direct pass (a surrogate without the network: the
+# prep and finish kernels' work in one kernel), besides the finish work of
+# each served ray: ray generation in FP32 from the Philox words (330), the
+# box test (40), entry point, features and bin (60), the one-segment
+# projection's two table lookups with their first moments (2 x 110), the
+# fallback-list ballot (10)
+OPS_DIRECT_RAY = 330 + 40 + 60 + 2 * 110 + 10
 TIGHT_BUDGET_PX = 0.001
 
 
@@ -822,7 +829,8 @@ def run_c4(args, rank, world):
             dt = float(t.item())
         return rays * max(1, args.steps) / dt
 
-    sur_kernels = ("surrogate_prep", "surrogate_net", "surrogate_finish", "surrogate_fallback", "sort")
+    sur_kernels = ("surrogate_direct", "surrogate_prep", "surrogate_net", "surrogate_finish", "surrogate_fallback",
+                   "sort")
 
     def surrogate_arm(label, with_e2e=False, **cfg_fields):
         """Train a surrogate (outside the timed region; every rank trains the
@@ -949,12 +957,33 @@ def run_c4(args, rank, world):
                 "peak_source": "issue rate derived from 152 SMs x 128 lanes x max SM clock",
                 "launch_ms": round(k["ms_per_launch"], 3), "rays_per_launch": int(per_launch)}
 
+    def direct_roofline(arm):
+        k = arm["kernels"]["surrogate_direct"]
+        if not k["ms_per_launch"]:
+            return None
+        per_launch = rays / world / k["launches_per_step"]
+        ops = OPS_DIRECT_RAY + arm["served_frac"] * OPS_FINISH_RAY
+        achieved = per_launch * ops / (k["ms_per_launch"] * 1e-3) / 1e12
+        peak = N_SM * ISSUE_LANES_PER_SM * clk_hz / 1e12
+        return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": (recorded_traffic("surrogate_direct_c4_traffic", "surrogate", scale_to_rays=per_launch)
+                            if args.scale == 1.0 and world == 1 else None),
+                "kernel": "surr_direct_kernel",
+                "op": "FP32/INT32 lane operation, %d per ray and %d more per served ray"
+                      % (OPS_DIRECT_RAY, OPS_FINISH_RAY),
+                "peak_source": "issue rate derived from 152 SMs x 128 lanes x max SM clock",
+                "launch_ms": round(k["ms_per_launch"], 3), "rays_per_launch": int(per_launch)}
+
     for arm in [sur, net] + [tight[k] for k in ("projection", "surrogate") if k in tight]:
-        arm["rooflines"] = {"surr_net_kernel": net_roofline(arm), "surr_finish_kernel": finish_roofline(arm)}
+        arm["rooflines"] = {"surr_net_kernel": net_roofline(arm), "surr_finish_kernel": finish_roofline(arm),
+                            "surr_direct_kernel": direct_roofline(arm)}
     # the headline's roofline: the surrogate step's dominant kernel
     ks = sur["kernels"]
-    dom = max(("surrogate_net", "surrogate_finish", "surrogate_prep"), key=lambda k: ks[k]["ms_per_step"])
-    rf = sur["rooflines"]["surr_net_kernel" if dom == "surrogate_net" else "surr_finish_kernel"]
+    dom = max(("surrogate_direct", "surrogate_net", "surrogate_finish", "surrogate_prep"),
+              key=lambda k: ks[k]["ms_per_step"])
+    rf = sur["rooflines"][{"surrogate_direct": "surr_direct_kernel", "surrogate_net": "surr_net_kernel"}
+                          .get(dom, "surr_finish_kernel")]
     if rf is not None:
         rf = dict(rf, dominant_kernel_share=round(ks[dom]["ms_per_step"] / sur["ms_per_step"], 4))
     # the plain arm's render kernel: the gather roofline (128 B per field
@@ -1101,6 +1130,7 @@ def run_surrogate(args, rank, world, steps, warmup, embedded, workload="c4"):
         k_ms, k_n = P.pivbos_timing_read("surrogate_net")
         p_ms, p_n = P.pivbos_timing_read("surrogate_prep")
         q_ms, q_n = P.pivbos_timing_read("surrogate_finish")
+        d_ms, d_n = P.pivbos_timing_read("surrogate_direct")
         f_ms, f_n = P.pivbos_timing_read("surrogate_fallback")
         n_fb = P.pivbos_surrogate_render(sg, desc, count_fallback=True)
         # error of the surrogate path: against the plain tracer on 10^6 rays,
@@ -1171,6 +1201,7 @@ def run_surrogate(args, rank, world, steps, warmup, embedded, workload="c4"):
         "sampled_rays": int(ok.sum()), "budget_px": 0.01,
         "served_frac": served / rays, "fallback_rays": int(n_fb),
         "kernel_ms_per_render": {"prep": p_ms / steps, "net": k_ms / steps, "finish": q_ms / steps,
+                                 "direct": d_ms / steps,
                                  "fallback": f_ms / max(f_n, 1)},
         "train_seconds": train_wall, "report": rep.as_dict(),
         "roofline": ({"bound": "tensor", "achieved": round(achieved, 2), "peak": peak_tf, "unit": "TFLOP/s",

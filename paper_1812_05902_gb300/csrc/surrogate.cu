@@ -810,7 +810,25 @@ static pivbos_status surrogate_render_impl(const pivbos_surrogate* sg, const piv
     P.src_df = sdf;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sg->device);
-    if (e == cudaSuccess) {
+    // no bin takes the network: one direct pass (no served list), unless
+    // PIVBOS_SURR_DIRECT=0 asks for the three-kernel path (read per call, so
+    // that a check can render both ways)
+    const char* dir_env = getenv("PIVBOS_SURR_DIRECT");
+    const bool direct = sg->S.use_net == 0 && !(dir_env && atoi(dir_env) == 0);
+    if (e == cudaSuccess && direct) {
+        const uint64_t items = (total + pivbos::kMaxOrderRays - 1) / pivbos::kMaxOrderRays;
+        const unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)sms * pivbos::kDirectCtasPerSm);
+        pivbos::timing_begin("surrogate_direct", s);
+        if (pivbos::optics_ext(P.o))
+            pivbos::surr_direct_kernel<true><<<grid, 256, 0, s>>>(P, sg->S, 0, total, fb, counters + 1, capacity,
+                                                                  frame->image, frame->stats);
+        else
+            pivbos::surr_direct_kernel<false><<<grid, 256, 0, s>>>(P, sg->S, 0, total, fb, counters + 1, capacity,
+                                                                   frame->image, frame->stats);
+        pivbos::timing_end("surrogate_direct", s);
+        pivbos::count_launches(1);
+        e = cudaGetLastError();
+    } else if (e == cudaSuccess) {
         // three kernels per chunk of up to 2^26 rays: prep -> network -> finish
         const uint64_t chunk = std::min<uint64_t>(total, 1ull << 26);
         const int use_net = sg->S.use_net;
@@ -851,10 +869,10 @@ static pivbos_status surrogate_render_impl(const pivbos_surrogate* sg, const piv
                 }
                 pivbos::timing_begin("surrogate_finish", s);
                 if (pivbos::optics_ext(P.o))
-                    pivbos::surr_finish_kernel<true><<<sms * 4, 256, 0, s>>>(
+                    pivbos::surr_finish_kernel<true><<<sms * pivbos::kFinishCtasPerSm, 256, 0, s>>>(
                         P, sg->S, sv, use_net ? sv.R : sv.B, frame->image, frame->stats, sv.count + 1);
                 else
-                    pivbos::surr_finish_kernel<false><<<sms * 4, 256, 0, s>>>(
+                    pivbos::surr_finish_kernel<false><<<sms * pivbos::kFinishCtasPerSm, 256, 0, s>>>(
                         P, sg->S, sv, use_net ? sv.R : sv.B, frame->image, frame->stats, sv.count + 1);
                 pivbos::timing_end("surrogate_finish", s);
                 pivbos::count_launches(1);

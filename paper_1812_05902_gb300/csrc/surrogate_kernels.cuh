@@ -769,12 +769,14 @@ surr_net_kernel(const SurrParams S, const __nv_bfloat16* __restrict__ wbf, const
 // Finish: the served list in chunks of 256 consecutive entries (one round of
 // the prep kernel's rays: a few neighbouring sources), each chunk deposited
 // into a shared tile anchored at its first hit.
+constexpr int kFinishCtasPerSm = 4;   // resident CTAs per SM (the grid is this many per SM)
+
 template <bool EXT>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, kFinishCtasPerSm)
 surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const float4* __restrict__ resid,
                    int64_t* __restrict__ image, int64_t* __restrict__ stats, unsigned long long* __restrict__ counter)
 {
-    __shared__ unsigned long long tile[kTileW * kTileH];
+    __shared__ uint32_t tile[2 * kTileW * kTileH];   // split: at most 256 quanta per pixel per item
     __shared__ unsigned long long s_item[2];
     __shared__ int w_ok[8], w_ax[8], w_ay[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -798,7 +800,7 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
         }
     };
     if (tid == 0) s_item[0] = atomicAdd(counter, 1ull);
-    for (int q = tid; q < kTileW * kTileH; q += blockDim.x) tile[q] = 0ull;
+    for (int q = tid; q < 2 * kTileW * kTileH; q += blockDim.x) tile[q] = 0u;
     __syncthreads();
     int buf = 0;
     uint64_t it = s_item[0];
@@ -856,9 +858,8 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
         if (reached) deposit_ray<EXT>(P.o, r.px, r.py, tile, ax, ay, image, r.w, dep);
         __syncthreads();
         for (int q = tid; q < kTileW * kTileH; q += blockDim.x) {
-            const unsigned long long v = tile[q];
+            const unsigned long long v = take_split(tile, q);
             if (v) {
-                tile[q] = 0ull;
                 const int gx = ax + (q % kTileW), gy = ay + (q / kTileW);
                 atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * P.o.W + gx]), v);
             }
@@ -872,6 +873,130 @@ surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const
 #pragma unroll
         for (int q = 0; q < PIVBOS_RAY_NSTATUS; ++q)
             if (cnt[q]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[q]), (unsigned long long)cnt[q]);
+    }
+}
+
+// Direct render, for a surrogate whose served bins all take the projection
+// alone: the prep and finish kernels' work in one pass, with no served list
+// in HBM.  Items of kMaxOrderRays consecutive rays of the Morton-ordered
+// (slot, ray) space (one source or a few neighbouring ones); each ray is
+// generated, served by the projection (or, never entering the box, by its
+// straight line) and deposited into the CTA's split tile, anchored at the
+// round's first hit (a round is 256 rays, one per thread) and flushed after
+// every round; rays of bins without a predictor go to the fallback list (a
+// warp-level append).  Two barriers per round: the anchors are known, the
+// deposits are in the tile (the flush then runs while the next round's rays
+// are prepared).
+// The deposits are the finish kernel's quanta for the same rays, so the
+// image and status counts are the three-kernel path's, bit for bit.
+constexpr int kDirectCtasPerSm = 4;
+
+template <bool EXT>
+__global__ void __launch_bounds__(256, kDirectCtasPerSm)
+surr_direct_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_t c1,
+                   uint32_t* __restrict__ fb_ids, unsigned long long* __restrict__ fb_count, uint32_t fb_capacity,
+                   int64_t* __restrict__ image, int64_t* __restrict__ stats)
+{
+    __shared__ uint32_t tile[2 * kTileW * kTileH];   // split: at most 256 quanta per pixel per round
+    __shared__ uint32_t order[kMaxOrderRays];
+    __shared__ int w_ok[8], w_ax[8], w_ay[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const uint32_t rps = P.rays_per_source;
+    unsigned cnt[PIVBOS_RAY_NSTATUS] = {0, 0, 0, 0, 0, 0};
+    for (int q = tid; q < 2 * kTileW * kTileH; q += blockDim.x) tile[q] = 0u;
+    const uint64_t items = (c1 - c0 + kMaxOrderRays - 1) / kMaxOrderRays;
+    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const uint64_t first = c0 + it * kMaxOrderRays;
+        const uint32_t n_here = (uint32_t)(min(first + kMaxOrderRays, c1) - first);
+        const bool reorder = P.reorder && S.born_k >= 8;
+        if (reorder) order_chunk(P, order, first, n_here);
+        for (uint32_t r0 = 0; r0 < n_here; r0 += 256) {
+            const uint32_t pos = r0 + tid;
+            const bool active = pos < n_here;
+            const uint64_t idx = first + (reorder && active ? (order[pos] & 0x7ffu) : pos);
+            int mode = 3;   // 0 projection, 1 fallback, 2 straight, 3 none
+            RayOut r;
+            r.status = PIVBOS_RAY_MISS;
+            r.w = 1.0f;
+            if (active) {
+                const uint32_t flat = (uint32_t)idx;
+                const uint32_t slot = flat / rps, k = flat - slot * rps;
+                const uint32_t sid = __ldg(P.perm + slot) + P.source_offset;
+                const float2* sp = P.src_df + 3 * (size_t)slot;
+                const float2 a = __ldg(sp), b = __ldg(sp + 1), c = __ldg(sp + 2);
+                Entry e;
+                surr_entry_f(P, S, a.x + a.y, b.x + b.y, c.x + c.y, sid, k, e);
+                if (!e.enters) mode = 2;
+                else mode = ((__ldg(S.bin_ok + (e.bin >> 5)) >> (e.bin & 31)) & 1u) ? 0 : 1;
+                if (mode != 1) {
+                    float res[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (mode == 0) born_residual(S, e, res);
+                    r.status = PIVBOS_RAY_REACHED;
+                    surr_sensor<EXT>(P.o, S, e.xs, e.ys, e.ux, e.uy, res, r.status, r.px, r.py);
+                    if constexpr (EXT) {
+                        // the ray's radiance from its direction at the source
+                        if (P.o.rad_mode) {
+                            const float inn = rsqrtf(fmaf(e.ux, e.ux, fmaf(e.uy, e.uy, 1.0f)));
+                            r.w = ray_radiance(P.o, e.ux * inn, e.uy * inn, inn);
+                        }
+                    }
+                    cnt[r.status]++;
+                }
+            }
+            // the fallback list: one atomic per warp
+            const unsigned fbm = __ballot_sync(0xffffffffu, mode == 1);
+            if (fbm) {
+                unsigned long long fb0 = 0ull;
+                if (lane == __ffs(fbm) - 1) fb0 = atomicAdd(fb_count, (unsigned long long)__popc(fbm));
+                fb0 = __shfl_sync(0xffffffffu, fb0, __ffs(fbm) - 1);
+                if (mode == 1) {
+                    const unsigned long long q = fb0 + __popc(fbm & ((1u << lane) - 1u));
+                    if (q < fb_capacity) fb_ids[q] = (uint32_t)idx;
+                    else atomicCAS(P.status_word, 0, (int)PIVBOS_ERR_OVERFLOW);   // cannot happen: capacity = rays
+                }
+            }
+            // the tile's anchor: the round's first hit in thread order
+            const bool reached = mode != 1 && r.status == PIVBOS_RAY_REACHED;
+            int fx = 0, fy = 0;
+            if (reached) {
+                float f;
+                fx = df_floor(r.px, f) - kTileW / 2;
+                fy = df_floor(r.py, f) - kTileH / 2;
+            }
+            const unsigned dep = __ballot_sync(0xffffffffu, reached);
+            const int leader = dep ? __ffs(dep) - 1 : 0;
+            const int lx = __shfl_sync(0xffffffffu, fx, leader), ly = __shfl_sync(0xffffffffu, fy, leader);
+            if (lane == 0) {
+                w_ok[warp] = dep != 0;
+                w_ax[warp] = lx;
+                w_ay[warp] = ly;
+            }
+            __syncthreads();
+            int ax = -(1 << 28), ay = -(1 << 28);
+            for (int w = 0; w < nw; ++w)
+                if (w_ok[w]) {
+                    ax = w_ax[w];
+                    ay = w_ay[w];
+                    break;
+                }
+            if (reached) deposit_ray<EXT>(P.o, r.px, r.py, tile, ax, ay, image, r.w, dep);
+            __syncthreads();
+            for (int q = tid; q < kTileW * kTileH; q += blockDim.x) {
+                const unsigned long long v = take_split(tile, q);
+                if (v) {
+                    const int gx = ax + (q % kTileW), gy = ay + (q / kTileW);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * P.o.W + gx]), v);
+                }
+            }
+        }
+    }
+    if (stats) {
+#pragma unroll
+        for (int q = 0; q < PIVBOS_RAY_NSTATUS; ++q) {
+            unsigned v = cnt[q];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[q]), (unsigned long long)v);
+        }
     }
 }
 

@@ -699,6 +699,35 @@ __device__ __forceinline__ void add_q(unsigned long long* tile, int ax, int ay, 
     }
 }
 
+// The split tile: two planes of 32-bit cells, kTileW * kTileH each, holding
+// the low 16 bits of the quanta added to a pixel and the rest (a quantum is
+// below 2^33).  Both sums stay exact for up to 2^15 quanta per pixel between
+// flushes; a pixel's value is (rest << 16) + low.  Many rays of a few sources
+// land on the same pixels, and 32-bit shared-memory additions serialise on
+// a shared address more cheaply than 64-bit ones.
+__device__ __forceinline__ void add_q(uint32_t* tile, int ax, int ay, int64_t* image, int W, int gx, int gy,
+                                      unsigned long long q)
+{
+    const int tx = gx - ax, ty = gy - ay;
+    if ((unsigned)tx < (unsigned)kTileW && (unsigned)ty < (unsigned)kTileH) {
+        const int c = ty * kTileW + tx;
+        atomicAdd(&tile[c], (uint32_t)(q & 0xffffull));
+        atomicAdd(&tile[kTileW * kTileH + c], (uint32_t)(q >> 16));
+    } else {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&image[(size_t)gy * W + gx]), q);
+    }
+}
+
+// Value of cell c of a split tile, and the cell cleared.
+__device__ __forceinline__ unsigned long long take_split(uint32_t* tile, int c)
+{
+    const uint32_t lo = tile[c], hi = tile[kTileW * kTileH + c];
+    if ((lo | hi) == 0u) return 0ull;
+    tile[c] = 0u;
+    tile[kTileW * kTileH + c] = 0u;
+    return ((unsigned long long)hi << 16) + lo;
+}
+
 // Round-to-nearest-even of a non-negative float below 2^33 to an integer
 // with FP32/INT32 instructions only (the 64-bit float-to-integer conversion
 // runs on GB300's narrow FP64 pipe).  Below 2^23 adding 2^23 rounds to an
@@ -729,9 +758,9 @@ __device__ __forceinline__ long long round_pos_to_ll(float x)
 // WEIGHTED: the ray carries the radiance weight w in [0, 1] and adds
 // round(w 2^32) in all; otherwise exactly 2^32.  lanes: the warp's lanes
 // that deposit together (the caller's ballot), for the aggregated adds.
-template <bool WEIGHTED = false>
+template <bool WEIGHTED = false, class TileT = unsigned long long>
 __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
-                                            unsigned long long* tile, int ax, int ay, int64_t* image,
+                                            TileT* tile, int ax, int ay, int64_t* image,
                                             float w = 1.0f, unsigned lanes = 0u)
 {
     SpotWindow sw;

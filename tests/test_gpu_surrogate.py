@@ -387,6 +387,53 @@ def test_render_path_matches_per_ray_positions(mode):
     assert rel < 1e-5
 
 
+def test_direct_pass_equals_the_three_kernel_path():
+    """A surrogate whose bins all take the projection alone renders in one
+    direct pass (no served list); PIVBOS_SURR_DIRECT=0 selects the
+    prep -> finish path.  Both deposit the same quanta for the same rays
+    (and send the same rays to the fallback list), so images, status counts
+    and fallback counts must be equal bit for bit -- with plain optics and
+    with a Mie radiance weighting each ray (the extended-optics variant)."""
+    import os
+    import torch
+    from paper_1812_05902_gb300 import pivbos as P
+    frame = scenes.c4(scale=0.002, grid=64)[0]
+    med, opt = gpu_handles(frame)
+    src = torch.tensor(frame.sources, dtype=torch.float64, device="cuda")
+    img = torch.zeros((frame.optics.height, frame.optics.width), dtype=torch.int64, device="cuda")
+    st = torch.zeros(P.RAY_NSTATUS, dtype=torch.int64, device="cuda")
+    s12, _ = P.pivbos_mie(1e-6, frame.optics.wavelength, frame.optics.n_object, 1.59)
+    mie = P.pivbos_optics_radiance(opt.h, (1.0, 0.0, 0.0), None, s12)
+    cfg = _cfg(P, n_train=1_000_000, n_val=400_000, min_bin_count=2, err_budget_px=0.002, use_network=0)
+    try:
+        for label, oh in (("plain optics", opt.h), ("Mie radiance", mie)):
+            desc = P.frame_desc(med.h, oh, src, len(frame.sources), frame.rays_per_source, frame.frame_index,
+                                frame.seed, frame.step, img, st)
+            sg, _ = P.pivbos_surrogate_train(desc, frame.integrator, cfg)
+            out = []
+            try:
+                for direct in (True, False):
+                    os.environ["PIVBOS_SURR_DIRECT"] = "1" if direct else "0"
+                    try:
+                        img.zero_()
+                        st.zero_()
+                        n_fb = P.pivbos_surrogate_render(sg, desc, count_fallback=True)
+                        P.pivbos_sync()
+                        out.append((img.clone(), st.clone(), n_fb))
+                    finally:
+                        del os.environ["PIVBOS_SURR_DIRECT"]
+            finally:
+                P.pivbos_surrogate_destroy(sg)
+            (d_img, d_st, d_fb), (t_img, t_st, t_fb) = out
+            print("%s: direct vs three kernels, %d rays reached, %d fallback" % (label, int(d_st[0]), d_fb))
+            assert 0 < d_fb < frame.n_rays
+            assert d_fb == t_fb
+            assert torch.equal(d_st, t_st) and torch.equal(d_img, t_img)
+            assert int(d_img.sum()) > 0
+    finally:
+        P.pivbos_optics_destroy(mie)
+
+
 def test_bos_slab_with_first_order_integrator():
     """The surrogate on the BOS linear-gradient slab (dots in front of the box,
     the first-order integrator, an ideal lens): every ray served, the error
