@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(256, kFinishCtasPerSm)
 surr_finish_kernel(const TraceParams P, const SurrParams S, ServedList sv, const float4* __restrict__ resid,
                    int64_t* __restrict__ image, int64_t* __restrict__ stats, unsigned long long* __restrict__ counter)
 {
-    __shared__ uint32_t tile[2 * kTileW * kTileH];   // split: at most 256 quanta per pixel per item
+    __shared__ uint32_t tile[2 * kTileW * kTileH];   // split: 256 rays per flush, two additions per pixel each
     __shared__ unsigned long long s_item[2];
     __shared__ int w_ok[8], w_ax[8], w_ay[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -897,7 +897,7 @@ surr_direct_kernel(const TraceParams P, const SurrParams S, uint64_t c0, uint64_
                    uint32_t* __restrict__ fb_ids, unsigned long long* __restrict__ fb_count, uint32_t fb_capacity,
                    int64_t* __restrict__ image, int64_t* __restrict__ stats)
 {
-    __shared__ uint32_t tile[2 * kTileW * kTileH];   // split: at most 256 quanta per pixel per round
+    __shared__ uint32_t tile[2 * kTileW * kTileH];   // split: 256 rays per flush, two additions per pixel each
     __shared__ uint32_t order[kMaxOrderRays];
     __shared__ int w_ok[8], w_ax[8], w_ay[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;

@@ -700,9 +700,11 @@ __device__ __forceinline__ void add_q(unsigned long long* tile, int ax, int ay, 
 }
 
 // The split tile: two planes of 32-bit cells, kTileW * kTileH each, holding
-// the low 16 bits of the quanta added to a pixel and the rest (a quantum is
-// below 2^33).  Both sums stay exact for up to 2^15 quanta per pixel between
-// flushes; a pixel's value is (rest << 16) + low.  Many rays of a few sources
+// for the values added to a pixel the sum of their low 16 bits and the sum
+// of the rest (floor(v / 2^16), modulo 2^32: a remainder can be negative).
+// The low sum is exact for up to 2^16 additions per pixel between flushes;
+// the rest, read as a signed 32-bit number, is exact while the pixel's value
+// stays below 2^47 (2^15 rays' worth), and the value is rest * 2^16 + low.  Many rays of a few sources
 // land on the same pixels, and 32-bit shared-memory additions serialise on
 // a shared address more cheaply than 64-bit ones.
 __device__ __forceinline__ void add_q(uint32_t* tile, int ax, int ay, int64_t* image, int W, int gx, int gy,
@@ -725,7 +727,7 @@ __device__ __forceinline__ unsigned long long take_split(uint32_t* tile, int c)
     if ((lo | hi) == 0u) return 0ull;
     tile[c] = 0u;
     tile[kTileW * kTileH + c] = 0u;
-    return ((unsigned long long)hi << 16) + lo;
+    return (unsigned long long)((long long)(int32_t)hi * 65536ll + (long long)lo);
 }
 
 // Round-to-nearest-even of a non-negative float below 2^33 to an integer
@@ -772,6 +774,26 @@ __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
     }
     long long sum = 0, qmax = -1;
     int imax = 0, jmax = 0;
+#if !PIVBOS_DEPOSIT_AGG
+    // One pass: every quantum is added as it is computed, then the rounding
+    // remainder (of either sign) onto the first largest quantum's pixel --
+    // the same pixel totals as adding it with that quantum (integer sums
+    // commute; a negative remainder wraps in the 64-bit cells and, in the
+    // split tile, in the 32-bit plane of the upper bits).
+#pragma unroll 1
+    for (int j = 0; j < sw.ny; ++j) {
+        const float wyj = sw.wy[j] * sw.scale;
+#pragma unroll 1
+        for (int i = 0; i < sw.nx; ++i) {
+            const long long q = round_pos_to_ll(sw.wx[i] * wyj);
+            sum += q;
+            if (q > qmax) { qmax = q; imax = i; jmax = j; }
+            if (q != 0) add_q(tile, ax, ay, image, o.W, sw.x0 + i, sw.y0 + j, (unsigned long long)q);
+        }
+    }
+    const long long rem = total - sum;
+    if (rem != 0) add_q(tile, ax, ay, image, o.W, sw.x0 + imax, sw.y0 + jmax, (unsigned long long)rem);
+#else
 #pragma unroll 1
     for (int j = 0; j < sw.ny; ++j) {
         const float wyj = sw.wy[j] * sw.scale;
@@ -783,7 +805,6 @@ __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
         }
     }
     const long long rem = total - sum;
-#if PIVBOS_DEPOSIT_AGG
     if (lanes) {
         const int n = sw.nx * sw.ny;
         const int steps = (int)__reduce_max_sync(lanes, (unsigned)n);
@@ -812,7 +833,6 @@ __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
         }
         return;
     }
-#endif
 #pragma unroll 1
     for (int j = 0; j < sw.ny; ++j) {
         const float wyj = sw.wy[j] * sw.scale;
@@ -823,6 +843,7 @@ __device__ __forceinline__ void deposit_ray(const DevOptics& o, df px, df py,
             if (q != 0) add_q(tile, ax, ay, image, o.W, sw.x0 + i, sw.y0 + j, (unsigned long long)q);
         }
     }
+#endif
 }
 
 
