@@ -193,16 +193,19 @@ __device__ __forceinline__ void born_residual(const SurrParams& S, const Entry& 
         const float dxm = q * ((zm - S.zhi_f) * gx - hx), dym = q * ((zm - S.zhi_f) * gy - hy);
         const float c = S.persp / (S.aim_z - zm);
         const float xi = (e.xe + ux * (zm - e.ze) + dxm) * c, eta = (e.ye + uy * (zm - e.ze) + dym) * c;
-        float3 Ga, Ha, Gb, Hb;
+        // the last segment ends on the box's far face, the table's top level,
+        // where the integrals start: zero there, not read
+        const bool last = k == S.born_k - 1;
+        float3 Ga, Ha, Gb = make_float3(0.f, 0.f, 0.f), Hb = Gb;
         float Hx, Hy, Hz;
         if (S.born_k >= 8) {
             table_lookup<false>(S, xi, eta, za, Ga, Ha);
-            table_lookup<false>(S, xi, eta, zb, Gb, Hb);
+            if (!last) table_lookup<false>(S, xi, eta, zb, Gb, Hb);
             const float zo = zm - S.zhi_f;
             Hx = zo * (Ga.x - Gb.x); Hy = zo * (Ga.y - Gb.y); Hz = zo * (Ga.z - Gb.z);
         } else {
             table_lookup<true>(S, xi, eta, za, Ga, Ha);
-            table_lookup<true>(S, xi, eta, zb, Gb, Hb);
+            if (!last) table_lookup<true>(S, xi, eta, zb, Gb, Hb);
             Hx = Ha.x - Hb.x; Hy = Ha.y - Hb.y; Hz = Ha.z - Hb.z;
         }
         const float Gx = Ga.x - Gb.x, Gy = Ga.y - Gb.y, Gz = Ga.z - Gb.z;
