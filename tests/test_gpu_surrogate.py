@@ -118,7 +118,7 @@ def test_surrogate_error_against_plain_tracer_and_oracle(trained):
     # fallback rays are the plain tracer's own result
     fb = flags[both] == 1
     assert np.max(np.abs(d[fb])) < 1e-9
-    # against the oracle on 1e5 of the rays (the metric's judge)
+    # against the oracle on 1e5 of the rays (the metric's reference)
     n_or = 100_000
     o = oracle_states(frame, ids[:n_or])
     ok = (status[:n_or] == 0) & (o["status"] == 0)
