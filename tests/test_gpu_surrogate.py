@@ -387,17 +387,21 @@ def test_render_path_matches_per_ray_positions(mode):
     assert rel < 1e-5
 
 
-def test_direct_pass_equals_the_three_kernel_path():
+@pytest.mark.parametrize("workload", ["c4", "c2"])
+def test_direct_pass_equals_the_three_kernel_path(workload):
     """A surrogate whose bins all take the projection alone renders in one
     direct pass (no served list); PIVBOS_SURR_DIRECT=0 selects the
     prep -> finish path.  Both deposit the same quanta for the same rays
     (and send the same rays to the fallback list), so images, status counts
     and fallback counts must be equal bit for bit -- with plain optics and
-    with a Mie radiance weighting each ray (the extended-optics variant)."""
+    with a Mie radiance weighting each ray (the extended-optics variant).
+    C4: particles inside the box; C2: dots in front of a box narrower than
+    the field of view, so that rays beside the box are served by their
+    straight line."""
     import os
     import torch
     from paper_1812_05902_gb300 import pivbos as P
-    frame = scenes.c4(scale=0.002, grid=64)[0]
+    frame = scenes.c4(scale=0.002, grid=64)[0] if workload == "c4" else scenes.c2(scale=0.002, grid=64)[0]
     med, opt = gpu_handles(frame)
     src = torch.tensor(frame.sources, dtype=torch.float64, device="cuda")
     img = torch.zeros((frame.optics.height, frame.optics.width), dtype=torch.int64, device="cuda")
@@ -426,7 +430,9 @@ def test_direct_pass_equals_the_three_kernel_path():
                 P.pivbos_surrogate_destroy(sg)
             (d_img, d_st, d_fb), (t_img, t_st, t_fb) = out
             print("%s: direct vs three kernels, %d rays reached, %d fallback" % (label, int(d_st[0]), d_fb))
-            assert 0 < d_fb < frame.n_rays
+            assert d_fb < frame.n_rays
+            if workload == "c4":
+                assert d_fb > 0                       # the fallback list is exercised
             assert d_fb == t_fb
             assert torch.equal(d_st, t_st) and torch.equal(d_img, t_img)
             assert int(d_img.sum()) > 0
