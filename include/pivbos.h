@@ -442,11 +442,15 @@ pivbos_status pivbos_surrogate_default_cfg(pivbos_surrogate_cfg* cfg);
 pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integrator,
                                      const pivbos_surrogate_cfg* cfg /* NULL = defaults */,
                                      pivbos_surrogate** out, pivbos_surrogate_report* report, void* stream);
-/* Render `frame` (same medium and optics, any sources): the network for
- * rays in served bins, the plain path for the rest; accumulates into the
- * frame's image and stats as pivbos_render does.  n_fallback (may be NULL;
- * if given, the call synchronises) receives the number of plain-traced
- * rays. */
+/* Render `frame` (same medium and optics, any sources): each ray of a
+ * served bin takes its bin's predictor (the projection, or the projection
+ * with the network's correction), the rest the plain path; accumulates into
+ * the frame's image and stats as pivbos_render does.  When no bin takes the
+ * network the served rays are rendered in one pass with no intermediate
+ * list; PIVBOS_SURR_DIRECT=0 in the environment (read per call) selects the
+ * list-based kernels instead, with the same image bit for bit.  n_fallback
+ * (may be NULL; if given, the call synchronises) receives the number of
+ * plain-traced rays. */
 pivbos_status pivbos_surrogate_render(const pivbos_surrogate* sg, const pivbos_frame_desc* frame,
                                       int64_t* n_fallback, void* stream);
 /* The surrogate render of sources [first_source, first_source + n_sources)
