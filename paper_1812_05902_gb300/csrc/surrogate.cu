@@ -192,13 +192,18 @@ constexpr double kAutoTrainBelow = 0.99;
 
 // Render cost of a held-out ray by how it is served, in units of one plain
 // integration step of one ray, measured on GB300 (C4: a plain step 18 ps; a
-// ray served by the projection alone 120 ps with 1 segment, 219 ps with 8,
-// 530 ps with 32 -- prep and finish; the network's forward 95 ps more; a
-// plain fallback ray its steps plus ~120 ps of generation, optics and
-// deposit).
-inline double cost_projection(int segments) { return 6.0 + 0.72 * segments; }
+// ray served by the projection alone in the direct pass 83.5 ps with 1
+// segment, 465 ps with 32; the network's forward 95 ps more; a plain
+// fallback ray its steps plus ~120 ps of generation, optics and deposit).
+inline double cost_projection(int segments) { return 3.9 + 0.68 * segments; }
 constexpr double kCostNetworkExtra = 5.3;
 constexpr double kCostFallbackRay = 7.0;
+// A plan whose bins take no network renders its served rays in one direct
+// pass, without the served list and the separate finish kernel a plan with
+// the network needs: about 1.5 plain steps cheaper per served ray (C4 with
+// one projection segment: 83.5 ms against prep + finish 110.0 ms per 1e9
+// rays, at ~18 ps per plain RK4 step).
+constexpr double kCostListRay = 1.5;
 
 struct Mixed {
     double err2 = 0.0, steps = 0.0, rays = 0.0, net_rays = 0.0, cost = 0.0;
@@ -209,10 +214,11 @@ struct Mixed {
 // multiplier lam, every bin takes the option of least cost + lam * err2;
 // lam is the smallest (bisected) whose summed error meets budget2, which
 // minimises the render cost under the budget up to the bins' granularity.
-// Bins with fewer than min_count held-out rays fall back.
+// Bins with fewer than min_count held-out rays fall back.  with_net false
+// leaves the network out (the projection alone or the fallback per bin).
 Mixed choose_mixed(const std::vector<double>& err2n, const std::vector<double>& err2p,
                    const std::vector<double>& steps, const std::vector<unsigned>& cnt, int min_count, double budget2,
-                   int segments, std::vector<uint32_t>* ok, std::vector<uint32_t>* net)
+                   int segments, bool with_net, std::vector<uint32_t>* ok, std::vector<uint32_t>* net)
 {
     const int nb = (int)cnt.size();
     const double kCostProjection = cost_projection(segments), kCostNetwork = kCostProjection + kCostNetworkExtra;
@@ -228,7 +234,7 @@ Mixed choose_mixed(const std::vector<double>& err2n, const std::vector<double>& 
                 const double cp = kCostProjection * n + lam * err2p[b];
                 const double cn = kCostNetwork * n + lam * err2n[b];
                 if (cp < best) { best = cp; choice = 1; }
-                if (cn < best) { best = cn; choice = 2; }
+                if (with_net && cn < best) { best = cn; choice = 2; }
             }
             if (choice == 0) {
                 m.cost += fb;
@@ -269,7 +275,7 @@ Mixed choose_mixed(const std::vector<double>& err2n, const std::vector<double>& 
         const double n = cnt[b], fb = steps[b] + kCostFallbackRay * n;
         const double sp = fb - kCostProjection * n, sn = fb - kCostNetwork * n;
         if (sp > 0.0) ups.push_back({sp / fmax(err2p[b], 1e-300), sp, err2p[b], b, 1});
-        if (sn > 0.0) ups.push_back({sn / fmax(err2n[b], 1e-300), sn, err2n[b], b, 2});
+        if (with_net && sn > 0.0) ups.push_back({sn / fmax(err2n[b], 1e-300), sn, err2n[b], b, 2});
     }
     std::sort(ups.begin(), ups.end(), [](const Up& x, const Up& y) {
         return x.ratio != y.ratio ? x.ratio > y.ratio : (x.b != y.b ? x.b < y.b : x.choice < y.choice);
@@ -685,7 +691,19 @@ pivbos_status pivbos_surrogate_train(const pivbos_frame_desc* frame, int integra
         // per bin: the projection alone, the projection with the network's
         // correction, or the plain fallback, whichever costs least under the
         // error budget
-        const Mixed mx = choose_mixed(err2[0], err2[1], stp, hc, c.min_bin_count, budget2, S.born_k, &ok, &netb);
+        Mixed mx = choose_mixed(err2[0], err2[1], stp, hc, c.min_bin_count, budget2, S.born_k, true, &ok, &netb);
+        // the plan without the network, rendered by the direct pass, when
+        // it costs less than the plan with it on the list-based kernels
+        if (mx.net_rays > 0) {
+            std::vector<uint32_t> ok_p(nbins / 32, 0u), net_p(nbins / 32, 0u);
+            const Mixed mp =
+                choose_mixed(err2[0], err2[1], stp, hc, c.min_bin_count, budget2, S.born_k, false, &ok_p, &net_p);
+            if (mp.cost - kCostListRay * mp.rays <= mx.cost) {
+                mx = mp;
+                ok = ok_p;
+                netb = net_p;
+            }
+        }
         sv[0] = choose_bins(err2[0], stp, hc, c.min_bin_count, budget2, nullptr);
         sv[1] = choose_bins(err2[1], stp, hc, c.min_bin_count, budget2, nullptr);
         sv[2] = choose_bins(err2[2], stp, hc, c.min_bin_count, budget2, nullptr);
