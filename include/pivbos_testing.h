@@ -6,8 +6,8 @@
  * an FP64 reference, and so that benchmarks can measure a roofline
  * denominator.  None has a counterpart in the paper.  The library links
  * libpivbos.so and runs its kernels; it shares pivbos_last_error() with it.
- * Every call runs on the current device, synchronously, and allocates its
- * own device memory.  Errors: INVALID_ARG (NULL pointers, n < 1), OOM, CUDA,
+ * Every call but pivbos_plan_bins (host only) runs on the current device,
+ * synchronously, and allocates its own device memory.  Errors: INVALID_ARG (NULL pointers, n < 1), OOM, CUDA,
  * DEVICE_TIMEOUT (a bounded tensor-core wait gave up).
  */
 #ifndef PIVBOS_TESTING_H
@@ -61,6 +61,23 @@ pivbos_status pivbos_surrogate_net_apply(const float* params, const float* x, co
  * loads from an L1-resident buffer (every SM streams 48 KB), in bytes per
  * second -- the denominator of the field-gather rooflines. */
 pivbos_status pivbos_probe_l1_bandwidth(double* bytes_per_second);
+
+/* The surrogate's per-bin plan, as pivbos_surrogate_train makes it (host
+ * code, no device): for each of n_bins entry bins (a multiple of 32) with
+ * counts[b] held-out rays, their summed squared sensor errors err2p[b]
+ * (projection alone) and err2n[b] (with the network's correction) and their
+ * plain-path steps steps[b], serve the bin by the projection alone, the
+ * projection with the correction (only if with_net) or the plain fallback,
+ * at the least render cost (in plain steps; segments projection segments)
+ * whose served squared error stays within budget2; bins with fewer than
+ * min_count rays fall back.  served, network: n_bins / 32 words of bits
+ * (host, written).  out (host double [5]): served squared error, served
+ * steps, served rays, network rays, cost.  The paper has no counterpart: the
+ * learned surrogate is an addition to the method. */
+pivbos_status pivbos_plan_bins(const double* err2n, const double* err2p, const double* steps,
+                               const uint32_t* counts, int32_t n_bins, int32_t min_count, double budget2,
+                               int32_t segments, int32_t with_net, uint32_t* served, uint32_t* network,
+                               double* out);
 
 #ifdef __cplusplus
 }

@@ -299,6 +299,29 @@ Mixed choose_mixed(const std::vector<double>& err2n, const std::vector<double>& 
 
 }  // namespace
 
+namespace pivbos {
+
+// The per-bin plan of choose_mixed for the testing library (host code; its
+// declaration is in testing.cu): ok and net are n_bins / 32 words of bits;
+// returns the plan's cost in plain steps.
+double plan_bins(const double* err2n, const double* err2p, const double* steps, const unsigned* cnt, int n_bins,
+                 int min_count, double budget2, int segments, bool with_net, uint32_t* ok, uint32_t* net,
+                 double* err2_out, double* rays_out, double* net_rays_out)
+{
+    const std::vector<double> en(err2n, err2n + n_bins), ep(err2p, err2p + n_bins), st(steps, steps + n_bins);
+    const std::vector<unsigned> c(cnt, cnt + n_bins);
+    std::vector<uint32_t> okv((size_t)n_bins / 32, 0u), netv((size_t)n_bins / 32, 0u);
+    const Mixed m = choose_mixed(en, ep, st, c, min_count, budget2, segments, with_net, &okv, &netv);
+    std::copy(okv.begin(), okv.end(), ok);
+    std::copy(netv.begin(), netv.end(), net);
+    *err2_out = m.err2;
+    *rays_out = m.rays;
+    *net_rays_out = m.net_rays;
+    return m.cost;
+}
+
+}  // namespace pivbos
+
 extern "C" {
 
 pivbos_status pivbos_surrogate_default_cfg(pivbos_surrogate_cfg* c)

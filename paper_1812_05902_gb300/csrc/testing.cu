@@ -250,3 +250,35 @@ extern "C" pivbos_status pivbos_probe_l1_bandwidth(double* bytes_per_second)
     *bytes_per_second = 5.0 * (double)blocks * 256.0 * (double)iters * 16.0 / (ms * 1e-3);
     return PIVBOS_OK;
 }
+
+namespace pivbos {
+// The surrogate's per-bin plan (surrogate.cu, exported by libpivbos.so; host
+// code): for each entry bin the projection alone, with the network's
+// correction, or the plain fallback, the least render cost under the
+// squared-error budget budget2.  ok and net: n_bins / 32 words of bits.
+// Returns the plan's cost in plain steps.
+double plan_bins(const double* err2n, const double* err2p, const double* steps, const unsigned* cnt, int n_bins,
+                 int min_count, double budget2, int segments, bool with_net, uint32_t* ok, uint32_t* net,
+                 double* err2_out, double* rays_out, double* net_rays_out);
+}  // namespace pivbos
+
+extern "C" pivbos_status pivbos_plan_bins(const double* err2n, const double* err2p, const double* steps,
+                                          const uint32_t* counts, int32_t n_bins, int32_t min_count, double budget2,
+                                          int32_t segments, int32_t with_net, uint32_t* served, uint32_t* network,
+                                          double* out)
+{
+    pivbos::set_last_error("");
+    if (!err2n || !err2p || !steps || !counts || !served || !network || !out)
+        return terr(PIVBOS_ERR_INVALID_ARG, "NULL argument");
+    if (n_bins < 32 || n_bins % 32 != 0) return terr(PIVBOS_ERR_INVALID_ARG, "n_bins must be a positive multiple of 32");
+    if (segments < 1 || !(budget2 >= 0.0)) return terr(PIVBOS_ERR_INVALID_ARG, "segments < 1 or budget2 < 0");
+    out[4] = pivbos::plan_bins(err2n, err2p, steps, counts, n_bins, min_count, budget2, segments, with_net != 0, served,
+                               network, &out[0], &out[2], &out[3]);
+    // the plan's plain steps saved: the served bins' steps
+    double saved = 0.0;
+    for (int b = 0; b < n_bins; ++b)
+        if ((served[b >> 5] >> (b & 31)) & 1u) saved += steps[b];
+    out[1] = saved;
+    return PIVBOS_OK;
+}
+

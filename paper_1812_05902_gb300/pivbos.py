@@ -159,7 +159,8 @@ EXPORTED = ("pivbos_medium_create", "pivbos_medium_refill", "pivbos_medium_destr
             "pivbos_mie", "pivbos_optics_radiance", "pivbos_advect_sources", "pivbos_image_u16",
             "pivbos_selftest_wait_timeout")
 TESTING_EXPORTED = ("pivbos_mlp_forward", "pivbos_mlp_train_forward", "pivbos_mlp_loss_grad",
-                    "pivbos_mlp_adam_steps", "pivbos_surrogate_net_apply", "pivbos_probe_l1_bandwidth")
+                    "pivbos_mlp_adam_steps", "pivbos_surrogate_net_apply", "pivbos_probe_l1_bandwidth",
+                    "pivbos_plan_bins")
 MLP_PARAMS = 52228
 NOALLOC_MAX_SOURCES = 1 << 17
 
@@ -187,6 +188,7 @@ def testing_lib():
             "pivbos_mlp_adam_steps": ([P, P, P, P, I32, I32, P, P], I),
             "pivbos_surrogate_net_apply": ([P, P, P, P, I32, P], I),
             "pivbos_probe_l1_bandwidth": ([ctypes.POINTER(D)], I),
+            "pivbos_plan_bins": ([P, P, P, P, I32, I32, D, I32, I32, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(T, name)
@@ -519,6 +521,24 @@ def pivbos_probe_l1_bandwidth():
     v = ctypes.c_double()
     _check(testing_lib().pivbos_probe_l1_bandwidth(ctypes.byref(v)))
     return v.value
+
+
+def pivbos_plan_bins(err2n, err2p, steps, counts, min_count, budget2, segments, with_net=True):
+    """The surrogate's per-bin plan (testing library, host only): returns
+    (served bool [n], network bool [n], {err2, steps, rays, net_rays, cost})."""
+    err2n = np.ascontiguousarray(err2n, dtype=np.float64)
+    err2p = np.ascontiguousarray(err2p, dtype=np.float64)
+    steps = np.ascontiguousarray(steps, dtype=np.float64)
+    counts = np.ascontiguousarray(counts, dtype=np.uint32)
+    n = counts.size
+    served = np.zeros(max(n // 32, 1), dtype=np.uint32)
+    network = np.zeros_like(served)
+    out = np.zeros(5)
+    _check(testing_lib().pivbos_plan_bins(err2n.ctypes.data, err2p.ctypes.data, steps.ctypes.data, counts.ctypes.data,
+                                          n, min_count, float(budget2), segments, 1 if with_net else 0,
+                                          served.ctypes.data, network.ctypes.data, out.ctypes.data))
+    bits = lambda w: ((w[np.arange(n) >> 5] >> (np.arange(n) & 31).astype(np.uint32)) & 1).astype(bool)
+    return bits(served), bits(network), dict(zip(("err2", "steps", "rays", "net_rays", "cost"), out))
 
 
 def pivbos_selftest_wait_timeout(polls, stream=None):
